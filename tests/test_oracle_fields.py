@@ -1,0 +1,306 @@
+"""Pins for the oracle's primitive fields, sphere tracing and pruned fields."""
+import numpy as np
+import pytest
+
+from paper_2304_09673_b300 import scenegen as sg
+
+
+def _rot(seed):
+    q = np.random.default_rng(seed).normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+def test_sphere_field_points(orc):
+    c, r = np.array([0.1, -0.2, 0.05]), 0.3
+    s = sg.single_primitive(sg.SPHERE, list(c) + [r])
+    rng = np.random.default_rng(0)
+    u = rng.normal(size=(100, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    dist = rng.uniform(-0.29, 1.0, size=100)
+    pts = c + (r + dist)[:, None] * u
+    assert np.allclose(orc.field(s, pts), dist, atol=2e-7)
+
+
+def test_rounded_box_field_points(orc):
+    R = _rot(3)
+    c, b, rr = np.array([0.0, 0.1, -0.1]), np.array([0.2, 0.1, 0.15]), 0.02
+    rec = list(c) + list(R.T.reshape(-1)) + list(b) + [rr]
+    s = sg.single_primitive(sg.RBOX, rec)
+    M = s.params[0, 3:12].astype(np.float64).reshape(3, 3)
+    Rw = M.T  # local -> world of the stored (float) matrix
+    b32 = s.params[0, 12:15].astype(np.float64)
+    rr32 = float(s.params[0, 15])
+    c32 = s.params[0, 0:3].astype(np.float64)
+    pts, want = [], []
+    for ax in range(3):
+        for sgn in (-1, 1):
+            for dist in (0.05, 0.3):
+                loc = np.zeros(3)
+                loc[ax] = sgn * (b32[ax] + rr32 + dist)
+                pts.append(c32 + Rw @ loc)
+                want.append(dist)
+    # Near a corner the rounded box is a sphere of radius rr around the corner.
+    for dist in (0.01, 0.2):
+        loc = b32 + (rr32 + dist) * np.ones(3) / np.sqrt(3)
+        pts.append(c32 + Rw @ loc)
+        want.append(dist)
+    # Inside: distance to the nearest face (negative).
+    loc = np.array([b32[0] - 0.03, 0, 0])
+    pts.append(c32 + Rw @ loc)
+    want.append(-0.03 - rr32)
+    got = orc.field(s, np.array(pts))
+    assert np.allclose(got, want, atol=1e-6)
+
+
+def test_capsule_field_points(orc):
+    a, b, r = np.array([-0.2, 0.0, 0.1]), np.array([0.2, 0.1, -0.1]), 0.07
+    s = sg.single_primitive(sg.CAPSULE, list(a) + list(b) + [r])
+    rng = np.random.default_rng(5)
+    ab = b - a
+    n1 = np.cross(ab, [0, 0, 1.0])
+    n1 /= np.linalg.norm(n1)
+    pts, want = [], []
+    for _ in range(50):
+        h = rng.uniform(0, 1)
+        dist = rng.uniform(-0.06, 0.5)
+        pts.append(a + h * ab + (r + dist) * n1)
+        want.append(dist)
+    # beyond the end caps: distance to the end point
+    e = ab / np.linalg.norm(ab)
+    pts.append(b + (r + 0.1) * e)
+    want.append(0.1)
+    assert np.allclose(orc.field(s, np.array(pts)), want, atol=1e-6)
+
+
+def _ray_sphere(o, d, c, r):
+    w = o - c
+    A = d @ d
+    B = 2 * (w @ d)
+    Cc = w @ w - r * r
+    disc = B * B - 4 * A * Cc
+    if disc < 0:
+        return None
+    t = (-B - np.sqrt(disc)) / (2 * A)
+    return t if t > 0 else None
+
+
+def _angle(a, b):
+    a = a / np.linalg.norm(a)
+    b = b / np.linalg.norm(b)
+    return np.arccos(np.clip(a @ b, -1, 1))
+
+
+def test_trace_single_sphere_analytic(orc):
+    c, r = np.array([0.1, -0.05, 0.2]), 0.3
+    s = sg.single_primitive(sg.SPHERE, list(c) + [r])
+    cam = sg.default_camera(48, 40)
+    res = orc.trace(s, cam)
+    d64, _ = orc.camera_rays(cam, res["pi"], res["pj"])
+    o = np.array(cam.eye, np.float64)
+    c32 = s.params[0, :3].astype(np.float64)
+    r32 = float(s.params[0, 3])
+    nchk = 0
+    for k in range(len(res["pi"])):
+        d = d64[k]
+        t = _ray_sphere(o, d, c32, r32)
+        hit = bool(res["flags"][k] & 1)
+        if t is None:
+            # a miss may only be reported hit if the ray grazes within eps
+            if hit:
+                w = c32 - o
+                dist = np.linalg.norm(np.cross(w, d / np.linalg.norm(d)))
+                assert dist - r32 <= 1.5e-4
+            continue
+        p = o + t * d
+        n = (p - c32) / r32
+        cos = abs(n @ d) / np.linalg.norm(d)
+        if cos < 0.05:
+            continue
+        assert hit
+        assert res["depth"][k] == pytest.approx(t * np.linalg.norm(d), abs=1e-9)
+        assert _angle(res["normal"][k], n) < 1e-5
+        nchk += 1
+    assert nchk > 100
+
+
+def test_trace_single_box_analytic(orc):
+    R = _rot(11)
+    c, b = np.array([0.05, 0.0, -0.05]), np.array([0.25, 0.15, 0.2])
+    s = sg.single_primitive(sg.RBOX, list(c) + list(R.T.reshape(-1)) + list(b) + [0.0])
+    cam = sg.default_camera(72, 72)
+    res = orc.trace(s, cam)
+    d64, _ = orc.camera_rays(cam, res["pi"], res["pj"])
+    o = np.array(cam.eye, np.float64)
+    M = s.params[0, 3:12].astype(np.float64).reshape(3, 3)
+    c32 = s.params[0, :3].astype(np.float64)
+    b32 = s.params[0, 12:15].astype(np.float64)
+    nchk = 0
+    for k in range(len(res["pi"])):
+        d = d64[k]
+        lo, ld = M @ (o - c32), M @ d
+        with np.errstate(divide="ignore"):
+            ta, tb = (-b32 - lo) / ld, (b32 - lo) / ld
+        t0 = np.max(np.minimum(ta, tb))
+        t1 = np.min(np.maximum(ta, tb))
+        if t0 > t1:
+            continue
+        axis = int(np.argmax(np.minimum(ta, tb)))
+        nloc = np.zeros(3)
+        nloc[axis] = -np.sign(ld[axis])
+        nw = M.T @ nloc
+        loc = lo + t0 * ld
+        # skip edges: distance of the entry point to the face's border
+        others = [i for i in range(3) if i != axis]
+        if min(b32[i] - abs(loc[i]) for i in others) < 2e-3:
+            continue
+        if abs(nw @ d) / np.linalg.norm(d) < 0.05:
+            continue
+        assert res["flags"][k] & 1
+        assert res["depth"][k] == pytest.approx(t0 * np.linalg.norm(d), abs=1e-8)
+        assert _angle(res["normal"][k], nw) < 1e-5
+        nchk += 1
+    assert nchk > 100
+
+
+def test_trace_single_capsule_analytic(orc):
+    a, b, r = np.array([-0.25, -0.1, 0.0]), np.array([0.2, 0.2, -0.1]), 0.15
+    s = sg.single_primitive(sg.CAPSULE, list(a) + list(b) + [r])
+    cam = sg.default_camera(72, 72)
+    res = orc.trace(s, cam)
+    d64, _ = orc.camera_rays(cam, res["pi"], res["pj"])
+    o = np.array(cam.eye, np.float64)
+    a32, b32, r32 = (s.params[0, 0:3].astype(np.float64), s.params[0, 3:6].astype(np.float64),
+                     float(s.params[0, 6]))
+    nchk = 0
+    for k in range(len(res["pi"])):
+        d = d64[k]
+        # analytic: smallest positive root over the two spheres and the finite cylinder
+        cands = []
+        for cc in (a32, b32):
+            t = _ray_sphere(o, d, cc, r32)
+            if t is not None:
+                cands.append(t)
+        ab = b32 - a32
+        e = ab / np.linalg.norm(ab)
+        w = o - a32
+        dp = d - (d @ e) * e
+        wp = w - (w @ e) * e
+        A, B, Cc = dp @ dp, 2 * (wp @ dp), wp @ wp - r32 * r32
+        disc = B * B - 4 * A * Cc
+        if disc >= 0:
+            t = (-B - np.sqrt(disc)) / (2 * A)
+            h = (w + t * d) @ e
+            if 0 <= h <= np.linalg.norm(ab) and t > 0:
+                cands.append(t)
+        if not cands:
+            continue
+        t = min(cands)
+        p = o + t * d
+        hh = np.clip((p - a32) @ ab / (ab @ ab), 0, 1)
+        n = (p - (a32 + hh * ab)) / r32
+        if abs(n @ d) / np.linalg.norm(d) < 0.05:
+            continue
+        assert res["flags"][k] & 1
+        assert res["depth"][k] == pytest.approx(t * np.linalg.norm(d), abs=1e-8)
+        assert _angle(res["normal"][k], n) < 1e-5
+        nchk += 1
+    assert nchk > 100
+
+
+def _random_points(scene, n, seed, orc):
+    lo, hi, _ = orc.scene_bounds(scene)
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo - 0.1, hi + 0.1, size=(n, 3))
+
+
+def test_lipschitz_bound_sampled(orc):
+    # Sec. 10: the sphere tracer's Lipschitz bound L = 1.45 covers the field
+    # compression of the compact operators.  Sampled on exterior pairs.
+    worst = 0.0
+    for seed in range(4):
+        s = sg.make_scene(64, 8, 500 + seed)
+        rng = np.random.default_rng(seed)
+        a = _random_points(s, 4000, seed, orc)
+        b = a + rng.normal(scale=0.01, size=a.shape)
+        fa, fb = orc.field(s, a), orc.field(s, b)
+        m = (fa >= 0) & (fb >= 0)
+        ratio = np.abs(fa - fb)[m] / np.linalg.norm(a - b, axis=1)[m]
+        worst = max(worst, ratio.max())
+    assert worst <= orc.LIPSCHITZ
+    assert worst > 0.5
+
+
+def test_all_active_equals_dense(orc):
+    s = sg.workload_small(3)
+    pts = _random_points(s, 500, 0, orc)
+    act = np.ones(s.n_nodes, bool)
+    assert np.array_equal(orc.field(s, pts, act), orc.field(s, pts))
+
+
+def _voi_contains(orc, scene, st, p):
+    """Independent point-in-VOI test (sphere / oriented box / capsule)."""
+    out = np.zeros(scene.n_nodes, bool)
+    for i in np.flatnonzero(scene.kind < 16):
+        q = scene.params[i].astype(np.float64)
+        d = st["roi"][st["po_of"][i]]
+        k = scene.kind[i]
+        if k == sg.SPHERE:
+            out[i] = np.linalg.norm(p - q[:3]) <= q[3] + d
+        elif k == sg.RBOX:
+            loc = q[3:12].reshape(3, 3) @ (p - q[:3])
+            out[i] = np.all(np.abs(loc) <= q[12:15] + q[15] + d)
+        else:
+            a, b = q[0:3], q[3:6]
+            ab = b - a
+            h = np.clip((p - a) @ ab / (ab @ ab), 0, 1)
+            out[i] = np.linalg.norm(p - a - h * ab) <= q[6] + d
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_local_equivalence_sign(orc, seed):
+    # Sec. 3 / Sec. 5: with A = primitives whose volume of interest contains p,
+    # sign(f_A(p)) = sign(f(p)).
+    s = sg.make_scene(48, 7, 900 + seed)
+    st = orc.structure(s)
+    pts = _random_points(s, 400, seed, orc)
+    f = orc.field(s, pts)
+    for p, fp in zip(pts, f):
+        act = _voi_contains(orc, s, st, p)
+        fa = orc.field(s, p[None], act)[0]
+        assert (fa > 0) == (fp > 0), (fa, fp)
+        if fp > 0:
+            assert fa >= fp - 1e-12
+
+
+def test_union_only_exact_inside(orc):
+    # Sec. 5: for union trees f_A(p) = f(p) wherever f(p) <= 0.
+    s = sg.make_scene(48, 7, 77, op_mix=(1, 0, 0))
+    st = orc.structure(s)
+    pts = _random_points(s, 600, 3, orc)
+    f = orc.field(s, pts)
+    n_in = 0
+    for p, fp in zip(pts, f):
+        if fp > 0:
+            continue
+        act = _voi_contains(orc, s, st, p)
+        assert orc.field(s, p[None], act)[0] == pytest.approx(fp, abs=1e-12)
+        n_in += 1
+    assert n_in > 10
+
+
+def test_first_hit_no_earlier_crossing(orc):
+    # Sphere tracing reports the first crossing: fine FP64 marching finds no
+    # f <= 0 sample before the reported hit (sampled rays).
+    s = sg.workload_small(1)
+    cam = sg.default_camera(64, 64)
+    res = orc.trace(s, cam)
+    hit = np.flatnonzero(res["flags"] & 1)[::7][:40]
+    d64, _ = orc.camera_rays(cam, res["pi"][hit], res["pj"][hit])
+    t_hit = res["depth"][hit] / np.linalg.norm(d64, axis=1)
+    z_first = orc.march(s, cam, res["pi"][hit], res["pj"][hit], t_hit - 2e-4, h=2e-4)
+    assert np.all(np.isinf(z_first))
