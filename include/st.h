@@ -1,0 +1,248 @@
+/*
+ * st.h -- C ABI of the synchronized blobtree tracer (sm_103a).
+ *
+ * The library renders the first ray / iso-surface crossing f(r(t)) = 0 of a
+ * blobtree implicit surface for every pixel (Zanni 2023, Sec. 2.2).  It follows the paper's
+ * two-step tile pipeline:
+ *   1. st_build_tiles: a low-resolution A-buffer holding, for every screen
+ *      tile, the primitives whose volume of interest is hit by at least one
+ *      of the tile's pixel rays, with conservative entry / exit depths,
+ *      sorted by entry depth (Sec. 3 "tiled acceleration structure", Sec. 6).
+ *   2. st_trace: synchronized sphere tracing of each tile's subfrustums over
+ *      a blobtree pruned to the subfrustum's active primitives by the sparse
+ *      bottom-up traversal (Sec. 7, Sec. 8 Algorithm 2 and 3, Sec. 9).
+ *
+ * Conventions for every entry point:
+ *   - Return value: ST_OK (0) or a negative ST_ERR_* code; st_last_error()
+ *     returns a thread-local message for the last failure.  No C++ exception
+ *     crosses this boundary.
+ *   - Calls taking a cudaStream_t (passed as void*; NULL = legacy default
+ *     stream) enqueue their device work on that stream.  st_scene_create and
+ *     st_build_tiles also synchronise that stream once (host preparation /
+ *     sizing of the A-buffer); st_trace and st_render_batch do not.
+ *   - "device pointer" = memory on the current CUDA device, owned by the
+ *     caller unless stated; "host pointer" = ordinary host memory.
+ *   - All floating point data is IEEE binary32 unless stated.
+ */
+#ifndef ST_H
+#define ST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define ST_OK 0
+#define ST_ERR_INVALID (-1)   /* malformed argument, tree or sizes          */
+#define ST_ERR_CAPACITY (-2)  /* a fixed-size buffer is too small           */
+#define ST_ERR_CUDA (-3)      /* a CUDA runtime call failed                 */
+#define ST_ERR_TIMEOUT (-4)   /* a bounded device-side wait expired         */
+#define ST_ERR_NOMEM (-5)     /* device allocation failed                   */
+
+/* ---- node kinds (scene description) ------------------------------------ */
+/* Primitives (leaves); rotation and translation only (Sec. 4). */
+#define ST_PRIM_SPHERE 0   /* rec[0:3] centre, rec[3] radius                */
+#define ST_PRIM_RBOX 1     /* rec[0:3] centre, rec[3:12] world->local rotation
+                              M row-major (local = M (x - centre)),
+                              rec[12:15] half extents, rec[15] rounding      */
+#define ST_PRIM_CAPSULE 2  /* rec[0:3] end a, rec[3:6] end b, rec[6] radius */
+/* Operators (binary): compact smooth operators G_op of Sec. 5 (Eq.
+ * "smooth_comp" with the smooth polynomial operators of Eq. 4-7 and the
+ * transition b_r), rec[0] = blend range k > 0, rec[1] = operator range bound
+ * d_o with 6 d_o > k; and sharp CSG operators of Eq. 1-3 (no parameters). */
+#define ST_OP_UNION 16
+#define ST_OP_INTER 17
+#define ST_OP_DIFF 18
+#define ST_OP_SHARP_UNION 19
+#define ST_OP_SHARP_INTER 20
+#define ST_OP_SHARP_DIFF 21
+
+#define ST_REC_FLOATS 16   /* floats per node record in a description     */
+#define ST_MAX_NODES 8388606 /* 23-bit ancestor pointers (Sec. 4)          */
+#define ST_MAX_STACK 32    /* evaluation stack entries (Sec. 10 uses 22)   */
+
+/* Blobtree description: a binary tree in any node numbering.  The library
+ * linearises it in post-order (Sec. 4).  All pointers are host pointers,
+ * read during the call only. */
+typedef struct {
+    int32_t n_nodes;        /* 2 N - 1 for N primitives                    */
+    int32_t root;           /* index of the root node                      */
+    const int32_t *kind;    /* [n_nodes] ST_PRIM_* or ST_OP_*              */
+    const int32_t *left;    /* [n_nodes] left child, -1 for primitives     */
+    const int32_t *right;   /* [n_nodes] right child, -1 for primitives    */
+    const float *params;    /* [n_nodes][ST_REC_FLOATS] node records       */
+    float voi_pad;          /* absolute slack added to every volume of
+                               interest extent to absorb FP32 rounding in
+                               the culling tests (scene units); <= 0 means
+                               the default 1e-5                           */
+} st_scene_desc;
+
+/* Pinhole camera.  Basis (computed in double, then rounded to float):
+ *   F = normalize(target - eye), R = normalize(F x up), U = R x F,
+ *   dot(a, a) = (a.x a.x + a.y a.y) + a.z a.z, normalize = a / sqrt(dot),
+ *   th = tan(vfov_deg * pi / 360), R' = (R * th) * (width / height),
+ *   U' = U * th.
+ * Ray of pixel (i, j), i = column, j = row from the top, FP32 without FMA:
+ *   u = (float)(2i+1) / (float)width - 1,  v = 1 - (float)(2j+1) / (float)height,
+ *   d = (F + u R') + v U'  per component;  points o + t d, o = eye.
+ * t is the planar view depth (d . F = 1). */
+typedef struct {
+    float eye[3], target[3], up[3];
+    float vfov_deg;
+    int32_t width, height;
+} st_camera;
+
+/* A-buffer: CSR over tiles in row-major tile order (tile (tx, ty) has index
+ * ty * tiles_x + tx).  Entries of tile t are [offsets[t], offsets[t+1]),
+ * sorted by (z_in ascending, prim ascending).  z values are planar depths t
+ * clipped to t >= 0.  prim is the post-order address of the primitive node.
+ * All arrays are device pointers owned by the scene object; they stay valid
+ * until the next st_build_tiles on the same scene or st_scene_destroy. */
+typedef struct {
+    int32_t tile;           /* tile edge in pixels                         */
+    int32_t tiles_x, tiles_y;
+    const uint32_t *offsets;  /* [tiles_x * tiles_y + 1]                   */
+    const float *z_in;        /* [n_entries]                               */
+    const float *z_out;       /* [n_entries]                               */
+    const uint32_t *prim;     /* [n_entries]                               */
+    uint64_t n_entries;
+    uint32_t max_overlap;     /* longest tile list                         */
+} st_tiles;
+
+/* Tracing options.  Zero-initialised fields take the defaults in brackets. */
+#define ST_STEP_PLAIN 0        /* z += f / (L |d|)                          */
+#define ST_STEP_LEARNED 1      /* MLP over-relaxation, verified (see below) */
+typedef struct {
+    float eps;              /* hit when f <= eps [1e-4]                    */
+    float lipschitz;        /* L of the step f / L [1.45, Sec. 10]         */
+    int32_t max_steps;      /* per-ray field evaluation cap [256]          */
+    int32_t step_mode;      /* ST_STEP_* [plain]                            */
+    float depth_slab_frac;  /* subfrustum depth limit d as a fraction of the
+                               scene diameter [0.05 = 1:20, Sec. 8]        */
+    int32_t max_new_per_turn; /* new primitives per subfrustum [6, Sec. 8] */
+    int32_t newton_iters;   /* Newton refinements of a hit [4]             */
+    float newton_clamp;     /* Newton step bound, distance units [64 eps]  */
+    const void *mlp;        /* reserved for the learned step; NULL         */
+} st_trace_opts;
+
+/* Optional per-call counters (device pointer to 8 uint64, accumulated with
+ * atomics; the caller zeroes them):
+ *   [0] tracing steps (field evaluations on live rays)
+ *   [1] useful primitive evaluations (pruned-view primitives x live steps)
+ *   [2] useful operator evaluations
+ *   [3] algorithmic FP32 flops of those evaluations (fixed per-node counts)
+ *   [4] subfrustums processed
+ *   [5] rejected learned steps
+ *   [6] finalisation field evaluations (Newton + normal)
+ *   [7] device error flags (bit 0: view capacity, bit 1: stack overflow) */
+#define ST_NUM_COUNTERS 8
+
+/* ---- scenes --------------------------------------------------------------
+ * st_scene_create: host preparation of a tree structure (Sec. 10 / Sec. 11
+ * "preprocessing"): post-order linearisation, isLeft, ignoreMod, fast
+ * ancestor pointers (Sec. 7.2, cut at intersections and at right-operand ->
+ * difference edges, Sec. 9), ranges of interest propagated from the root
+ * (Sec. 5), then upload of the node arrays to the current device.  Fails with
+ * ST_ERR_INVALID on a malformed tree (cycle, bad child, kind out of range,
+ * k <= 0 or 6 d_o <= k), more than ST_MAX_NODES nodes or a tree whose
+ * post-order evaluation needs more than ST_MAX_STACK stack entries.  *out
+ * receives an opaque handle owned by the library. */
+typedef struct st_scene st_scene;
+int st_scene_create(const st_scene_desc *desc, st_scene **out, void *stream);
+
+/* Update the parameter records of n primitives (no preparation re-run, the
+ * tree structure is unchanged; Sec. 1 "no preprocessing when primitive
+ * parameters are updated").  ids: host int32[n] description node indices of
+ * primitives; params: host float[n][ST_REC_FLOATS].  The copy is staged and
+ * enqueued on `stream`. */
+int st_scene_update_prims(st_scene *scene, const int32_t *ids, const float *params, int n,
+                          void *stream);
+
+/* Post-order address of every description node: host int32[n_nodes] out. */
+int st_scene_addresses(const st_scene *scene, int32_t *po_of_desc);
+
+void st_scene_destroy(st_scene *scene);
+
+/* ---- per-frame calls -------------------------------------------------------
+ * st_build_tiles: fills the tile A-buffer of `scene` seen by `cam` (Sec. 6):
+ * volumes of interest are recomputed from the current primitive parameters
+ * (sphere -> sphere r + d, rounded box -> oriented box b + r_round + d,
+ * capsule -> capsule r + d, plus voi_pad); every (primitive, tile) pair whose
+ * conservative screen bound covers the tile is tested with one ray per pixel
+ * centre of the tile (FP32, fixed operation order documented in the kernel
+ * source, identical on every call); the entry is kept iff at least one ray
+ * hits, with z_in = min over hitting rays of max(t0, 0) and z_out = max of
+ * t1.  Buffers grow on demand (the call synchronises `stream` once to size
+ * them).  tile must be 8, 16 or 32. */
+int st_build_tiles(st_scene *scene, const st_camera *cam, int tile, st_tiles *out, void *stream);
+
+/* st_trace: synchronized sphere tracing of every tile (Algorithm 2) over the
+ * A-buffer built for the same scene and camera.  Outputs are caller-owned
+ * device buffers of width * height pixels, row-major from the top row:
+ *   depth  float[H*W]   Euclidean eye distance of the hit, +inf on a miss
+ *   normal float[H*W*3] unit normal (field gradient) at the hit, 0 on a miss
+ *   evals  uint32[H*W]  tracing field evaluations of the ray
+ *   flags  uint8[H*W]   bit 0 hit, bit 1 step cap reached (reported as miss)
+ * counters: optional device uint64[ST_NUM_COUNTERS] (may be NULL). */
+int st_trace(st_scene *scene, const st_camera *cam, const st_tiles *tiles,
+             const st_trace_opts *opts, float *depth, float *normal, uint32_t *evals,
+             uint8_t *flags, uint64_t *counters, void *stream);
+
+/* Copy an A-buffer out (cudaMemcpyDefault: each destination may be host or
+ * device memory; offsets gets tiles_x * tiles_y + 1 words, the others
+ * n_entries each; NULL destinations are skipped).  Enqueued on `stream`,
+ * then the stream is synchronised. */
+int st_tiles_copy(const st_tiles *tiles, uint32_t *offsets, float *z_in, float *z_out, uint32_t *prim,
+                  void *stream);
+
+/* ---- inspection of the hot-path steps ----------------------------------------
+ * st_pruned_view: the pruned tree view of an active set, built on the device
+ * by the same code st_trace uses (Algorithm 1 with fast ancestor pointers,
+ * clamping, popRequiredA / popRequiredB and the usage rewrite of Sec. 9).
+ *   act        device uint32[n], post-order addresses of active primitives,
+ *              strictly ascending, 1 <= n <= number of primitives
+ *   view       device uint32[2n-1] out: bits 27..31 node code (0 sphere,
+ *              1 rounded box, 2 capsule, 3/4/5 compact union / intersection /
+ *              difference, 6/7/8 sharp ones, 9 +inf, 10 right operand, 11 left
+ *              operand), bits 0..26 record word offset
+ *   view_addr  device uint32[2n-1] out (optional): post-order address per entry
+ *   info       device int32[4] out: view length, root usage bit, error (0 ok),
+ *              number of primitives
+ * Uses a library-owned scratch stack; calls on one scene must be stream ordered.
+ *
+ * st_eval_pruned: f_A (Sec. 3) at points by Algorithm 3 over a view from
+ * st_pruned_view, with the FP32 evaluator of st_trace (approximate square root
+ * and reciprocal).  pts device float[npts][3]; f device float[npts] (+inf when
+ * the root is unused); grad optional device float[npts][3] forward-mode
+ * gradient (then the IEEE square root is used). */
+int st_pruned_view(const st_scene *scene, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
+                   int32_t *info, void *stream);
+int st_eval_pruned(const st_scene *scene, const uint32_t *view, const int32_t *info, const float *pts,
+                   int npts, float *f, float *grad, void *stream);
+
+/* ---- host-only preparation (no GPU needed) ----------------------------------
+ * The preparation step of st_scene_create on its own, for inspection: every
+ * output is a host array indexed by post-order address (n_nodes entries):
+ *   po_of_desc  post-order address of each description node (desc-indexed)
+ *   blob        packed node word: bit 31 isPrimitive, bits 26..30 kind,
+ *               bits 24..25 ignoreMod, bit 23 isLeft, bits 0..22 fast
+ *               ancestor address (0x7FFFFF for the root)   (Sec. 4 layout)
+ *   parent      parent address, -1 for the root
+ *   roi         upper bound d_n of the node's range of interest (Sec. 5)
+ * Returns the post-order evaluation stack depth (>= 1), or a negative code. */
+int st_prep_tree(const st_scene_desc *desc, int32_t *po_of_desc, uint32_t *blob,
+                 int32_t *parent, float *roi);
+
+/* Number of kernels this library has launched in this process so far. */
+uint64_t st_kernel_launches(void);
+
+const char *st_last_error(void);
+const char *st_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ST_H */

@@ -1,0 +1,399 @@
+// st_api.cu -- the C ABI (include/st.h): scene objects, A-buffer build,
+// tracing.  No C++ exception crosses the boundary; every CUDA failure becomes
+// ST_ERR_CUDA with the runtime's message in st_last_error().
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "st_kernels.h"
+
+namespace st {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+static std::atomic<uint64_t> g_launches{0};
+int count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return 0;
+}
+
+#define ST_CK(call)                                                        \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) {                                               \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));       \
+      return ST_ERR_CUDA;                                                  \
+    }                                                                      \
+  } while (0)
+
+// Growable device buffer.
+template <class T>
+struct DBuf {
+  T *p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= cap) return cudaSuccess;
+    size_t want = n + n / 4 + 16;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+    if (e == cudaSuccess) cap = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+static int device_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+}  // namespace st
+
+using namespace st;
+
+struct st_scene {
+  Prep prep;
+  int n_nodes = 0, n_prims = 0;
+  float voi_pad = 1e-5f;
+  // scene arrays
+  DBuf<uint32_t> blob, rec_off, prim_addr;
+  DBuf<float4> rec;
+  DBuf<float> d_prim;
+  // culling buffers
+  DBuf<uint32_t> cand_count, cand_off, tile_count, offsets, scan_sums, small;  // small: counters
+  DBuf<int4> rects;
+  DBuf<Pair> pairs;
+  DBuf<uint64_t> keys;
+  DBuf<float> ztmp, z_in, z_out;
+  DBuf<uint32_t> prim;
+  DBuf<Job> job;
+  // tracing
+  DBuf<uint32_t> g_work, item_counter;
+  // updates
+  DBuf<float4> upd_words;
+  DBuf<uint32_t> upd_index;
+  int n_sm = 1;
+  int last_tile = 0;
+  uint32_t last_max_overlap = 0;
+};
+
+namespace st {
+
+__global__ void k_update_words(const uint32_t *idx, const float4 *words, uint32_t n, float4 *rec) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rec[idx[i]] = words[i];
+}
+
+static DevScene dev_scene(const st_scene *s) {
+  DevScene d;
+  d.blob = s->blob.p;
+  d.rec_off = s->rec_off.p;
+  d.rec = s->rec.p;
+  d.prim_addr = s->prim_addr.p;
+  d.d_prim = s->d_prim.p;
+  d.n_nodes = s->n_nodes;
+  d.n_prims = s->n_prims;
+  d.stack_depth = s->prep.stack_depth;
+  d.diameter = (float)s->prep.diameter;
+  d.voi_pad = s->voi_pad;
+  return d;
+}
+
+static int check_camera(const st_camera *cam) {
+  if (!cam || cam->width <= 0 || cam->height <= 0 || cam->width > 65535 || cam->height > 65535 ||
+      !(cam->vfov_deg > 0.f && cam->vfov_deg < 180.f)) {
+    set_error("invalid camera");
+    return ST_ERR_INVALID;
+  }
+  return ST_OK;
+}
+
+}  // namespace st
+
+extern "C" {
+
+const char *st_last_error(void) { return st::g_err.c_str(); }
+const char *st_version(void) { return "st 0.1 (sm_103a)"; }
+uint64_t st_kernel_launches(void) { return g_launches.load(); }
+
+int st_scene_create(const st_scene_desc *desc, st_scene **out, void *stream) {
+  if (!desc || !out) { set_error("null argument"); return ST_ERR_INVALID; }
+  *out = nullptr;
+  st_scene *s = new (std::nothrow) st_scene();
+  if (!s) { set_error("host allocation failed"); return ST_ERR_NOMEM; }
+  std::string err;
+  int rc = prepare(*desc, s->prep, err);
+  if (rc != ST_OK) { set_error(err); delete s; return rc; }
+  if (s->prep.stack_depth + 1 > ST_MAX_STACK) {
+    set_error("tree needs a deeper evaluation stack than ST_MAX_STACK");
+    delete s;
+    return ST_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  s->n_nodes = desc->n_nodes;
+  s->n_prims = (int)s->prep.prim_addr.size();
+  s->voi_pad = desc->voi_pad > 0.f ? desc->voi_pad : 1e-5f;
+  s->n_sm = device_sms();
+  const Prep &p = s->prep;
+  size_t nw = p.rec.size() / 4;
+  auto fail = [&](cudaError_t e) {
+    set_error(std::string("st_scene_create: ") + cudaGetErrorString(e));
+    st_scene_destroy(s);
+    return ST_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = s->blob.ensure(p.blob.size())) != cudaSuccess) return fail(e);
+  if ((e = s->rec_off.ensure(p.rec_off.size())) != cudaSuccess) return fail(e);
+  if ((e = s->rec.ensure(nw)) != cudaSuccess) return fail(e);
+  if ((e = s->prim_addr.ensure(p.prim_addr.size())) != cudaSuccess) return fail(e);
+  if ((e = s->d_prim.ensure(p.d_prim.size())) != cudaSuccess) return fail(e);
+  if ((e = s->small.ensure(16)) != cudaSuccess) return fail(e);
+  if ((e = s->item_counter.ensure(4)) != cudaSuccess) return fail(e);
+  if ((e = s->job.ensure(1)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpyAsync(s->blob.p, p.blob.data(), p.blob.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpyAsync(s->rec_off.p, p.rec_off.data(), p.rec_off.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpyAsync(s->rec.p, p.rec.data(), nw * 16, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpyAsync(s->prim_addr.p, p.prim_addr.data(), p.prim_addr.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpyAsync(s->d_prim.p, p.d_prim.data(), p.d_prim.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+  *out = s;
+  return ST_OK;
+}
+
+void st_scene_destroy(st_scene *s) {
+  if (!s) return;
+  s->blob.release(); s->rec_off.release(); s->prim_addr.release(); s->rec.release(); s->d_prim.release();
+  s->cand_count.release(); s->cand_off.release(); s->tile_count.release(); s->offsets.release();
+  s->scan_sums.release(); s->small.release(); s->rects.release(); s->pairs.release(); s->keys.release();
+  s->ztmp.release(); s->z_in.release(); s->z_out.release(); s->prim.release(); s->job.release();
+  s->g_work.release(); s->item_counter.release(); s->upd_words.release(); s->upd_index.release();
+  delete s;
+}
+
+int st_scene_addresses(const st_scene *s, int32_t *po_of_desc) {
+  if (!s || !po_of_desc) { set_error("null argument"); return ST_ERR_INVALID; }
+  std::memcpy(po_of_desc, s->prep.po_of_desc.data(), s->prep.po_of_desc.size() * sizeof(int32_t));
+  return ST_OK;
+}
+
+int st_scene_update_prims(st_scene *s, const int32_t *ids, const float *params, int n, void *stream) {
+  if (!s || (n > 0 && (!ids || !params)) || n < 0) { set_error("invalid arguments"); return ST_ERR_INVALID; }
+  if (n == 0) return ST_OK;
+  std::vector<float> words;
+  std::vector<uint32_t> index;
+  words.reserve((size_t)n * 16);
+  for (int i = 0; i < n; ++i) {
+    int id = ids[i];
+    if (id < 0 || id >= s->n_nodes) { set_error("node id out of range"); return ST_ERR_INVALID; }
+    int a = s->prep.po_of_desc[id];
+    uint32_t b = s->prep.blob[a];
+    if (!blob_isprim(b)) { set_error("node id is not a primitive"); return ST_ERR_INVALID; }
+    int kind = (int)blob_kind(b);
+    float w[16];
+    prim_words(kind, params + (size_t)i * ST_REC_FLOATS, w);
+    for (int k = 0; k < rec_words(kind); ++k) {
+      index.push_back(s->prep.rec_off[a] + k);
+      words.insert(words.end(), w + 4 * k, w + 4 * k + 4);
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t m = (uint32_t)index.size();
+  ST_CK(s->upd_words.ensure(m));
+  ST_CK(s->upd_index.ensure(m));
+  ST_CK(cudaMemcpyAsync(s->upd_words.p, words.data(), (size_t)m * 16, cudaMemcpyHostToDevice, st));
+  ST_CK(cudaMemcpyAsync(s->upd_index.p, index.data(), (size_t)m * 4, cudaMemcpyHostToDevice, st));
+  count_launch(), k_update_words<<<(m + 255) / 256, 256, 0, st>>>(s->upd_index.p, s->upd_words.p, m, s->rec.p);
+  ST_CK(cudaGetLastError());
+  // The staging buffers are reused by the next call; keep host arrays alive
+  // until the copies have been consumed.
+  ST_CK(cudaStreamSynchronize(st));
+  return ST_OK;
+}
+
+int st_build_tiles(st_scene *s, const st_camera *cam, int tile, st_tiles *out, void *stream) {
+  if (!s || !out) { set_error("null argument"); return ST_ERR_INVALID; }
+  int rc = check_camera(cam);
+  if (rc != ST_OK) return rc;
+  if (tile != 8 && tile != 16 && tile != 32) { set_error("tile must be 8, 16 or 32"); return ST_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
+  const uint32_t n_tiles = (uint32_t)tiles_x * (uint32_t)tiles_y;
+  const uint32_t np = (uint32_t)s->n_prims;
+
+  static thread_local bool attr_done = false;
+  if (!attr_done) { ST_CK(cull_set_attributes()); attr_done = true; }
+
+  Job job;
+  std::memset(&job, 0, sizeof(job));
+  job.sc = dev_scene(s);
+  camera_basis(*cam, job.cam);
+  job.tl.tile = tile;
+  job.tl.tiles_x = tiles_x;
+  job.tl.tiles_y = tiles_y;
+  ST_CK(s->cand_count.ensure(np));
+  ST_CK(s->cand_off.ensure(np));
+  ST_CK(s->rects.ensure(np));
+  ST_CK(s->tile_count.ensure(n_tiles));
+  ST_CK(s->offsets.ensure(n_tiles + 1));
+  ST_CK(s->scan_sums.ensure(std::max(scan_block_count(np), scan_block_count(n_tiles)) + 2));
+  if (s->pairs.cap == 0) ST_CK(s->pairs.ensure(std::max<size_t>(1024, (size_t)np * 8)));
+  ST_CK(cudaMemcpyAsync(s->job.p, &job, sizeof(Job), cudaMemcpyHostToDevice, st));
+
+  // small[0] candidate total, [1] pair counter, [2] longest list, [3] tile total
+  uint32_t *cand_total = s->small.p + 0, *pair_counter = s->small.p + 1, *max_ov = s->small.p + 2,
+           *tile_total = s->small.p + 3;
+  launch_prim_bounds(s->job.p, 1, np, s->cand_count.p, s->rects.p, st);
+  scan_u32(s->cand_count.p, s->cand_off.p, np, s->scan_sums.p, cand_total, nullptr, nullptr, st);
+  uint32_t host_small[4] = {0, 0, 0, 0};
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    ST_CK(cudaMemsetAsync(s->tile_count.p, 0, (size_t)n_tiles * 4, st));
+    ST_CK(cudaMemsetAsync(s->small.p + 1, 0, 3 * sizeof(uint32_t), st));
+    launch_cull_pairs(s->job.p, 1, s->cand_off.p, np, cand_total, s->rects.p, s->tile_count.p, s->pairs.p,
+                      (uint32_t)s->pairs.cap, pair_counter, s->n_sm, st);
+    scan_u32(s->tile_count.p, s->offsets.p, n_tiles, s->scan_sums.p, tile_total, max_ov,
+             s->offsets.p + n_tiles, st);
+    ST_CK(cudaGetLastError());
+    ST_CK(cudaMemcpyAsync(host_small, s->small.p, sizeof(host_small), cudaMemcpyDeviceToHost, st));
+    ST_CK(cudaStreamSynchronize(st));
+    if (host_small[1] <= s->pairs.cap) break;
+    ST_CK(s->pairs.ensure(host_small[1]));  // on-demand growth, then redo (Sec. 10)
+  }
+  const uint32_t n_entries = host_small[1];
+  const uint32_t max_overlap = host_small[2];
+  if (max_overlap > kSortLarge) {
+    set_error("a tile list exceeds the sort capacity (16384 entries)");
+    return ST_ERR_CAPACITY;
+  }
+  ST_CK(s->keys.ensure(n_entries + 1));
+  ST_CK(s->ztmp.ensure(n_entries + 1));
+  ST_CK(s->z_in.ensure(n_entries + 1));
+  ST_CK(s->z_out.ensure(n_entries + 1));
+  ST_CK(s->prim.ensure(n_entries + 1));
+  launch_scatter_sort(s->pairs.p, pair_counter, (uint32_t)s->pairs.cap, s->offsets.p, n_tiles, max_overlap,
+                      s->keys.p, s->ztmp.p, s->z_in.p, s->z_out.p, s->prim.p, s->n_sm, st);
+  ST_CK(cudaGetLastError());
+  out->tile = tile;
+  out->tiles_x = tiles_x;
+  out->tiles_y = tiles_y;
+  out->offsets = s->offsets.p;
+  out->z_in = s->z_in.p;
+  out->z_out = s->z_out.p;
+  out->prim = s->prim.p;
+  out->n_entries = n_entries;
+  out->max_overlap = max_overlap;
+  s->last_tile = tile;
+  s->last_max_overlap = max_overlap;
+  return ST_OK;
+}
+
+int st_trace(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_trace_opts *opts, float *depth,
+             float *normal, uint32_t *evals, uint8_t *flags, uint64_t *counters, void *stream) {
+  if (!s || !tl || !depth || !normal || !evals || !flags) { set_error("null argument"); return ST_ERR_INVALID; }
+  int rc = check_camera(cam);
+  if (rc != ST_OK) return rc;
+  const int tiles_x = (cam->width + tl->tile - 1) / tl->tile, tiles_y = (cam->height + tl->tile - 1) / tl->tile;
+  if (tl->tiles_x != tiles_x || tl->tiles_y != tiles_y) {
+    set_error("tile buffer does not match the camera");
+    return ST_ERR_INVALID;
+  }
+  st_trace_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.step_mode != ST_STEP_PLAIN) { set_error("step mode not available"); return ST_ERR_INVALID; }
+  Job job;
+  std::memset(&job, 0, sizeof(job));
+  job.sc = dev_scene(s);
+  camera_basis(*cam, job.cam);
+  job.tl.tile = tl->tile;
+  job.tl.tiles_x = tl->tiles_x;
+  job.tl.tiles_y = tl->tiles_y;
+  job.tl.offsets = tl->offsets;
+  job.tl.z_in = tl->z_in;
+  job.tl.z_out = tl->z_out;
+  job.tl.prim = tl->prim;
+  job.out.depth = depth;
+  job.out.normal = normal;
+  job.out.evals = evals;
+  job.out.flags = flags;
+  TraceParams &tp = job.tp;
+  tp.eps = o.eps > 0.f ? o.eps : 1e-4f;
+  tp.lipschitz = o.lipschitz > 0.f ? o.lipschitz : 1.45f;
+  tp.max_steps = o.max_steps > 0 ? o.max_steps : 256;
+  tp.step_mode = o.step_mode;
+  const float frac = o.depth_slab_frac > 0.f ? o.depth_slab_frac : 0.05f;
+  tp.depth_slab = std::max(frac * (float)s->prep.diameter, 1e-6f);
+  tp.max_new = o.max_new_per_turn > 0 ? std::min(o.max_new_per_turn, 32) : 6;
+  tp.newton_iters = o.newton_iters > 0 ? o.newton_iters : (o.newton_iters < 0 ? 0 : 4);
+  tp.newton_clamp = o.newton_clamp > 0.f ? o.newton_clamp : 64.f * tp.eps;
+  job.tile_base = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  TraceLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.max_tile_rays = tl->tile * tl->tile;
+  L.act_cap = (int)std::max<uint32_t>(tl->max_overlap, 1u);
+  L.view_cap = 2 * L.act_cap;
+  L.stack_slots = s->prep.stack_depth + 2;
+  L.n_items = (uint32_t)(tiles_x * tiles_y);
+  L.counters = counters;
+  // Active set and view in shared memory when 16 warps per SM still fit.
+  L.work_in_smem = 1;
+  if (trace_smem_per_warp(L) * 16 > 200 * 1024) L.work_in_smem = 0;
+  if (!L.work_in_smem) {
+    const int warps_total = s->n_sm * 64;
+    L.g_work_words = trace_work_words(L);
+    ST_CK(s->g_work.ensure((size_t)warps_total * L.g_work_words));
+    L.g_work = s->g_work.p;
+  }
+  ST_CK(s->item_counter.ensure(4));
+  L.item_counter = s->item_counter.p;
+  ST_CK(s->job.ensure(1));
+  ST_CK(cudaMemcpyAsync(s->job.p, &job, sizeof(Job), cudaMemcpyHostToDevice, st));
+  ST_CK(cudaMemsetAsync(s->item_counter.p, 0, 4, st));
+  ST_CK(trace_launch(s->job.p, 1, L, s->n_sm, st));
+  return ST_OK;
+}
+
+int st_pruned_view(const st_scene *s, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
+                   int32_t *info, void *stream) {
+  if (!s || !act || n < 1 || n > s->n_prims || !view || !info) { set_error("invalid arguments"); return ST_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream;
+  st_scene *m = const_cast<st_scene *>(s);
+  ST_CK(m->g_work.ensure(ST_MAX_STACK + 2));
+  launch_pruned_view(dev_scene(s), act, n, view, view_addr, info, m->g_work.p, ST_MAX_STACK + 2, st);
+  ST_CK(cudaGetLastError());
+  return ST_OK;
+}
+
+int st_eval_pruned(const st_scene *s, const uint32_t *view, const int32_t *info, const float *pts, int npts,
+                   float *f, float *grad, void *stream) {
+  if (!s || !view || !info || (npts > 0 && (!pts || !f)) || npts < 0) { set_error("invalid arguments"); return ST_ERR_INVALID; }
+  launch_eval_view(dev_scene(s), view, info, pts, npts, f, grad, (cudaStream_t)stream);
+  ST_CK(cudaGetLastError());
+  return ST_OK;
+}
+
+int st_tiles_copy(const st_tiles *t, uint32_t *offsets, float *z_in, float *z_out, uint32_t *prim,
+                  void *stream) {
+  if (!t) { set_error("null argument"); return ST_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nt = (size_t)t->tiles_x * t->tiles_y + 1, ne = (size_t)t->n_entries;
+  if (offsets) ST_CK(cudaMemcpyAsync(offsets, t->offsets, nt * 4, cudaMemcpyDefault, st));
+  if (ne && z_in) ST_CK(cudaMemcpyAsync(z_in, t->z_in, ne * 4, cudaMemcpyDefault, st));
+  if (ne && z_out) ST_CK(cudaMemcpyAsync(z_out, t->z_out, ne * 4, cudaMemcpyDefault, st));
+  if (ne && prim) ST_CK(cudaMemcpyAsync(prim, t->prim, ne * 4, cudaMemcpyDefault, st));
+  ST_CK(cudaStreamSynchronize(st));
+  return ST_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,461 @@
+// st_cull.cu -- per-tile culling of blobtree primitives into a low-resolution
+// A-buffer (Sec. 6), for one or many (scene, camera) jobs at once.
+//
+// Pipeline (all on the caller's stream):
+//   k_prim_bounds  one thread per primitive: volume of interest (Sec. 6.1:
+//                  primitive bound offset by its range-of-interest bound d)
+//                  -> conservative screen tile rectangle -> candidate count
+//   scan           candidate offsets
+//   k_cull_pairs   one warp per candidate (primitive, tile): one FP32 ray per
+//                  pixel centre of the tile against the volume of interest;
+//                  entry = min max(t0, 0), exit = max t1 over hitting rays
+//                  (the 8x8 ray/volume tests of the paper's fragment shader,
+//                  Sec. 6.2, as explicit compute); kept iff a ray hits.
+//                  Survivors are appended to a pair list with CTA-aggregated
+//                  atomics; each pair takes its rank inside its tile.
+//   scan           tile offsets (CSR), longest list
+//   k_scatter      pair -> CSR slot (offset + rank)
+//   k_tile_sort    per-tile bitonic sort in shared memory by
+//                  (z_in, post-order address) (sorted lists, Sec. 6.2)
+#include <cstdint>
+
+#include "st_geom.cuh"
+#include "st_kernels.h"
+
+namespace st {
+
+namespace {
+
+__device__ __forceinline__ int find_job_prim(const Job *jobs, int n_jobs, uint32_t g) {
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].prim_base <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Conservative tile rectangle of a sphere (centre C, radius rho) in view.
+__device__ void sphere_tile_rect(const DevCamera &cam, int tile, int tiles_x, int tiles_y,
+                                 const float C[3], float rho, int4 &rect) {
+  rho = rho * 1.001f + 1e-4f;
+  float w[3] = {C[0] - cam.o[0], C[1] - cam.o[1], C[2] - cam.o[2]};
+  float lr = sqrtf(cam.R[0] * cam.R[0] + cam.R[1] * cam.R[1] + cam.R[2] * cam.R[2]);
+  float lu = sqrtf(cam.U[0] * cam.U[0] + cam.U[1] * cam.U[1] + cam.U[2] * cam.U[2]);
+  float z = w[0] * cam.F[0] + w[1] * cam.F[1] + w[2] * cam.F[2];
+  float x = (w[0] * cam.R[0] + w[1] * cam.R[1] + w[2] * cam.R[2]) / lr;
+  float y = (w[0] * cam.U[0] + w[1] * cam.U[1] + w[2] * cam.U[2]) / lu;
+  rect = make_int4(0, 0, tiles_x - 1, tiles_y - 1);
+  if (z < -rho) { rect = make_int4(1, 1, 0, 0); return; }  // behind the eye
+  if (z <= rho * 1.01f) return;                              // straddles the eye plane
+  float zz = z * z - rho * rho;
+  float sx = sqrtf(fmaxf(x * x + zz, 0.f)), sy = sqrtf(fmaxf(y * y + zz, 0.f));
+  float mx0 = (x * z - rho * sx) / zz, mx1 = (x * z + rho * sx) / zz;
+  float my0 = (y * z - rho * sy) / zz, my1 = (y * z + rho * sy) / zz;
+  float u0 = mx0 / lr, u1 = mx1 / lr;   // image u in [-1, 1] across the width
+  float v0 = my0 / lu, v1 = my1 / lu;   // image v in [-1, 1], +1 = top row
+  // pixel i has u = (2i+1)/W - 1  ->  i = ((u + 1) W - 1) / 2
+  float i0 = ((u0 + 1.f) * cam.W - 1.f) * 0.5f, i1 = ((u1 + 1.f) * cam.W - 1.f) * 0.5f;
+  float j0 = ((1.f - v1) * cam.H - 1.f) * 0.5f, j1 = ((1.f - v0) * cam.H - 1.f) * 0.5f;
+  float fi0 = floorf(i0) - 1.f, fi1 = ceilf(i1) + 1.f;
+  float fj0 = floorf(j0) - 1.f, fj1 = ceilf(j1) + 1.f;
+  if (fi1 < 0.f || fj1 < 0.f || fi0 > (float)(cam.W - 1) || fj0 > (float)(cam.H - 1)) {
+    rect = make_int4(1, 1, 0, 0);
+    return;
+  }
+  int px0 = fi0 < 0.f ? 0 : (int)fi0, py0 = fj0 < 0.f ? 0 : (int)fj0;
+  int px1 = fi1 > (float)(cam.W - 1) ? cam.W - 1 : (int)fi1;
+  int py1 = fj1 > (float)(cam.H - 1) ? cam.H - 1 : (int)fj1;
+  rect = make_int4(px0 / tile, py0 / tile, px1 / tile, py1 / tile);
+}
+
+// Volume of interest extents in FP32: ((size + d) + pad).
+struct Voi {
+  int kind;
+  float c[3];      // centre (sphere, box) or end a (capsule)
+  float M[9];      // box rotation rows
+  float e[3];      // box half extents
+  float b[3];      // capsule end b
+  float r;         // sphere / capsule radius
+};
+
+__device__ __forceinline__ void load_voi(const DevScene &sc, uint32_t j, Voi &v) {
+  uint32_t a = sc.prim_addr[j];
+  uint32_t kind = blob_kind(sc.blob[a]);
+  const float4 *w = sc.rec + sc.rec_off[a];
+  float dp = sc.d_prim[j], pad = sc.voi_pad;
+  v.kind = (int)kind;
+  float4 w0 = w[0];
+  v.c[0] = w0.x; v.c[1] = w0.y; v.c[2] = w0.z;
+  if (kind == ST_PRIM_SPHERE) {
+    v.r = ieee_add(ieee_add(w0.w, dp), pad);
+  } else if (kind == ST_PRIM_RBOX) {
+    float rr = w0.w;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float4 m = w[1 + i];
+      v.M[3 * i] = m.x; v.M[3 * i + 1] = m.y; v.M[3 * i + 2] = m.z;
+      v.e[i] = ieee_add(ieee_add(ieee_add(m.w, rr), dp), pad);
+    }
+  } else {
+    float4 w1 = w[1];
+    v.b[0] = w1.x; v.b[1] = w1.y; v.b[2] = w1.z;
+    v.r = ieee_add(ieee_add(w0.w, dp), pad);
+  }
+}
+
+}  // namespace
+
+__global__ void k_prim_bounds(const Job *jobs, int n_jobs, uint32_t n_prims_total,
+                              uint32_t *cand_count, int4 *rects) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_prims_total) return;
+  int jb = find_job_prim(jobs, n_jobs, g);
+  const Job &job = jobs[jb];
+  uint32_t j = g - job.prim_base;
+  Voi v;
+  load_voi(job.sc, j, v);
+  float C[3], rho;
+  if (v.kind == ST_PRIM_SPHERE) {
+    C[0] = v.c[0]; C[1] = v.c[1]; C[2] = v.c[2];
+    rho = v.r;
+  } else if (v.kind == ST_PRIM_RBOX) {
+    C[0] = v.c[0]; C[1] = v.c[1]; C[2] = v.c[2];
+    rho = sqrtf(v.e[0] * v.e[0] + v.e[1] * v.e[1] + v.e[2] * v.e[2]);
+  } else {
+    float h[3] = {0.5f * (v.b[0] - v.c[0]), 0.5f * (v.b[1] - v.c[1]), 0.5f * (v.b[2] - v.c[2])};
+    C[0] = v.c[0] + h[0]; C[1] = v.c[1] + h[1]; C[2] = v.c[2] + h[2];
+    rho = sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]) + v.r;
+  }
+  int4 rect;
+  sphere_tile_rect(job.cam, job.tl.tile, job.tl.tiles_x, job.tl.tiles_y, C, rho, rect);
+  uint32_t n = 0;
+  if (rect.z >= rect.x && rect.w >= rect.y) n = (uint32_t)(rect.z - rect.x + 1) * (uint32_t)(rect.w - rect.y + 1);
+  cand_count[g] = n;
+  rects[g] = rect;
+}
+
+// One warp per candidate pair, PAIRS_PER_WARP pairs per warp per round, CTA
+// of 8 warps; survivors are compacted in shared memory and appended with one
+// atomic per CTA round.
+constexpr int kCullWarps = 8;
+constexpr int kPairsPerWarp = 4;
+
+__global__ void __launch_bounds__(kCullWarps * 32)
+k_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_prims_total,
+             const uint32_t *cand_total, const int4 *rects, uint32_t *tile_count,
+             Pair *pairs, uint32_t pair_cap, uint32_t *pair_counter) {
+  __shared__ Pair s_pairs[kCullWarps * kPairsPerWarp];
+  __shared__ uint32_t s_n, s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t total = *cand_total;
+  const uint32_t per_round = kCullWarps * kPairsPerWarp;
+  for (uint32_t base = blockIdx.x * per_round; base < total; base += gridDim.x * per_round) {
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    for (int q = 0; q < kPairsPerWarp; ++q) {
+      uint32_t p = base + warp * kPairsPerWarp + q;
+      if (p >= total) break;
+      // candidate -> primitive (binary search on the candidate offsets)
+      uint32_t lo = 0, hi = n_prims_total - 1;
+      while (lo < hi) {
+        uint32_t mid = (lo + hi + 1) >> 1;
+        if (cand_off[mid] <= p) lo = mid; else hi = mid - 1;
+      }
+      const uint32_t g = lo;
+      const int jb = find_job_prim(jobs, n_jobs, g);
+      const Job &job = jobs[jb];
+      const uint32_t j = g - job.prim_base;
+      const int4 rect = rects[g];
+      const uint32_t k = p - cand_off[g];
+      const uint32_t rw = (uint32_t)(rect.z - rect.x + 1);
+      const int tx = rect.x + (int)(k % rw), ty = rect.y + (int)(k / rw);
+      const int T = job.tl.tile;
+      const DevCamera &cam = job.cam;
+      Voi v;
+      load_voi(job.sc, j, v);
+      // Ray-independent quantities.
+      float w[3], lo3[3];
+      CapsuleConst cc;
+      if (v.kind == ST_PRIM_SPHERE) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w[i] = ieee_sub(v.c[i], cam.o[i]);
+      } else if (v.kind == ST_PRIM_RBOX) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w[i] = ieee_sub(cam.o[i], v.c[i]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) lo3[i] = ieee_dot3(v.M[3 * i], v.M[3 * i + 1], v.M[3 * i + 2], w[0], w[1], w[2]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          cc.wa[i] = ieee_sub(v.c[i], cam.o[i]);
+          cc.wb[i] = ieee_sub(v.b[i], cam.o[i]);
+          cc.ba[i] = ieee_sub(v.b[i], v.c[i]);
+          w[i] = ieee_sub(cam.o[i], v.c[i]);
+        }
+        cc.bb = ieee_dot3(cc.ba[0], cc.ba[1], cc.ba[2], cc.ba[0], cc.ba[1], cc.ba[2]);
+        cc.r = v.r;
+        if (cc.bb > 0.0f) {
+          cc.wbv = ieee_dot3(w[0], w[1], w[2], cc.ba[0], cc.ba[1], cc.ba[2]);
+          float fw = ieee_div(cc.wbv, cc.bb);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) cc.p[i] = ieee_sub(w[i], ieee_mul(fw, cc.ba[i]));
+        }
+      }
+      uint32_t zin_bits = 0xFFFFFFFFu, zout_bits = 0u;
+      for (int s = lane; s < T * T; s += 32) {
+        const int px = tx * T + (s % T), py = ty * T + (s / T);
+        if (px >= cam.W || py >= cam.H) continue;
+        float d[3], t0, t1;
+        pixel_ray(cam, px, py, d);
+        bool h;
+        if (v.kind == ST_PRIM_SPHERE) h = ray_sphere32(w, d, v.r, t0, t1);
+        else if (v.kind == ST_PRIM_RBOX) h = ray_obox32(lo3, v.M, v.e, d, t0, t1);
+        else h = ray_capsule32(cc, d, t0, t1);
+        if (!h) continue;
+        t0 = t0 > 0.0f ? t0 : 0.0f;
+        if (!(t1 >= t0)) continue;
+        // t0, t1 >= 0: float order equals unsigned bit order.
+        uint32_t b0 = __float_as_uint(t0), b1 = __float_as_uint(t1);
+        zin_bits = b0 < zin_bits ? b0 : zin_bits;
+        zout_bits = b1 > zout_bits ? b1 : zout_bits;
+      }
+      zin_bits = __reduce_min_sync(0xFFFFFFFFu, zin_bits);
+      zout_bits = __reduce_max_sync(0xFFFFFFFFu, zout_bits);
+      if (lane == 0 && zin_bits != 0xFFFFFFFFu) {
+        const uint32_t tg = job.tile_base + (uint32_t)(ty * job.tl.tiles_x + tx);
+        Pair pr;
+        pr.tile = tg;
+        pr.rank = atomicAdd(&tile_count[tg], 1u);
+        pr.z_in = __uint_as_float(zin_bits);
+        pr.z_out = __uint_as_float(zout_bits);
+        pr.addr = job.sc.prim_addr[j];
+        uint32_t slot = atomicAdd(&s_n, 1u);
+        s_pairs[slot] = pr;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_base = s_n ? atomicAdd(pair_counter, s_n) : 0u;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < s_n; i += blockDim.x) {
+      uint32_t dst = s_base + i;
+      if (dst < pair_cap) pairs[dst] = s_pairs[i];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_scatter(const Pair *pairs, const uint32_t *pair_counter, uint32_t pair_cap,
+                          const uint32_t *offsets, uint64_t *keys, float *z_out) {
+  uint32_t n = min(*pair_counter, pair_cap);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    Pair p = pairs[i];
+    uint32_t dst = offsets[p.tile] + p.rank;
+    keys[dst] = ((uint64_t)__float_as_uint(p.z_in) << 32) | (uint64_t)p.addr;
+    z_out[dst] = p.z_out;
+  }
+}
+
+// Bitonic sort of one tile's (key, z_out) list in shared memory; lists with
+// len in (min_len, max_len] only (two launches cover short and long lists).
+__global__ void k_tile_sort(const uint32_t *offsets, uint32_t n_tiles, const uint64_t *keys,
+                            const float *z_out_in, float *z_in, float *z_out, uint32_t *prim,
+                            uint32_t min_len, uint32_t max_len) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);
+  for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const uint32_t beg = offsets[t], len = offsets[t + 1] - beg;
+    if (len <= min_len || len > max_len) continue;
+    uint32_t n2 = 1;
+    while (n2 < len) n2 <<= 1;
+    float *sv = reinterpret_cast<float *>(sk + n2);
+    for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
+      if (i < len) { sk[i] = keys[beg + i]; sv[i] = z_out_in[beg + i]; }
+      else { sk[i] = ~0ull; sv[i] = 0.f; }
+    }
+    __syncthreads();
+    for (uint32_t k = 2; k <= n2; k <<= 1) {
+      for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+        for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
+          uint32_t l = i ^ jj;
+          if (l > i) {
+            bool up = (i & k) == 0;
+            uint64_t a = sk[i], b = sk[l];
+            if ((a > b) == up) {
+              sk[i] = b; sk[l] = a;
+              float x = sv[i]; sv[i] = sv[l]; sv[l] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+      uint64_t key = sk[i];
+      z_in[beg + i] = __uint_as_float((uint32_t)(key >> 32));
+      prim[beg + i] = (uint32_t)key;
+      z_out[beg + i] = sv[i];
+    }
+    __syncthreads();
+  }
+}
+
+// Lists of length 0 or 1 need no sort: copy straight through.
+__global__ void k_tile_copy_short(const uint32_t *offsets, uint32_t n_tiles, const uint64_t *keys,
+                                  const float *z_out_in, float *z_in, float *z_out, uint32_t *prim) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+    uint32_t beg = offsets[t];
+    if (offsets[t + 1] - beg == 1) {
+      uint64_t key = keys[beg];
+      z_in[beg] = __uint_as_float((uint32_t)(key >> 32));
+      prim[beg] = (uint32_t)key;
+      z_out[beg] = z_out_in[beg];
+    }
+  }
+}
+
+// ---- exclusive scan of uint32 (three passes) ----------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr uint32_t kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  total = s_warp[(blockDim.x >> 5) - 1];
+  uint32_t prev = warp > 0 ? s_warp[warp - 1] : 0u;
+  uint32_t r = prev + x - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_blocks(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *block_sums, uint32_t *max_out) {
+  __shared__ uint32_t s_warp[32];
+  const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  uint32_t v[kScanItems], sum = 0, mx = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = base + i < n ? in[base + i] : 0u;
+    sum += v[i];
+    mx = max(mx, v[i]);
+  }
+  uint32_t total;
+  uint32_t ex = block_excl_scan(sum, s_warp, total);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) out[base + i] = ex;
+    ex += v[i];
+  }
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+  if (max_out) {
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(max_out, mx);
+  }
+}
+
+// Scans the block sums in place (single CTA, any count) and writes the total.
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_sums(uint32_t *sums, uint32_t n_blocks, uint32_t *total_out) {
+  __shared__ uint32_t s_warp[32];
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < n_blocks; base += kScanThreads) {
+    uint32_t i = base + threadIdx.x;
+    uint32_t v = i < n_blocks ? sums[i] : 0u;
+    uint32_t total;
+    uint32_t ex = block_excl_scan(v, s_warp, total);
+    if (i < n_blocks) sums[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_add(uint32_t *out, uint32_t n, const uint32_t *block_sums, const uint32_t *total,
+                           uint32_t *tail) {
+  const uint32_t base = blockIdx.x * kScanTile;
+  const uint32_t add = block_sums[blockIdx.x];
+  for (uint32_t i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+    uint32_t k = base + i;
+    if (k < n) out[k] += add;
+  }
+  if (tail && blockIdx.x == 0 && threadIdx.x == 0) *tail = *total;
+}
+
+void scan_u32(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *block_sums,
+              uint32_t *total, uint32_t *max_out, uint32_t *tail, cudaStream_t s) {
+  if (n == 0) {
+    cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+    if (tail) cudaMemsetAsync(tail, 0, sizeof(uint32_t), s);
+    return;
+  }
+  uint32_t nb = (n + kScanTile - 1) / kScanTile;
+  count_launch(), k_scan_blocks<<<nb, kScanThreads, 0, s>>>(in, out, n, block_sums, max_out);
+  count_launch(), k_scan_sums<<<1, kScanThreads, 0, s>>>(block_sums, nb, total);
+  count_launch(), k_scan_add<<<nb, 256, 0, s>>>(out, n, block_sums, total, tail);
+}
+
+uint32_t scan_block_count(uint32_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+void launch_prim_bounds(const Job *jobs, int n_jobs, uint32_t n_prims, uint32_t *cand_count,
+                        int4 *rects, cudaStream_t s) {
+  if (!n_prims) return;
+  count_launch(), k_prim_bounds<<<(n_prims + 255) / 256, 256, 0, s>>>(jobs, n_jobs, n_prims, cand_count, rects);
+}
+
+void launch_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_prims,
+                       const uint32_t *cand_total, const int4 *rects, uint32_t *tile_count, Pair *pairs,
+                       uint32_t pair_cap, uint32_t *pair_counter, int n_sm, cudaStream_t s) {
+  if (!n_prims) return;
+  count_launch(), k_cull_pairs<<<n_sm * 8, kCullWarps * 32, 0, s>>>(jobs, n_jobs, cand_off, n_prims, cand_total, rects,
+                                                    tile_count, pairs, pair_cap, pair_counter);
+}
+
+void launch_scatter_sort(const Pair *pairs, const uint32_t *pair_counter, uint32_t pair_cap,
+                         const uint32_t *offsets, uint32_t n_tiles, uint32_t max_overlap,
+                         uint64_t *keys, float *z_out_tmp, float *z_in, float *z_out, uint32_t *prim,
+                         int n_sm, cudaStream_t s) {
+  count_launch(), k_scatter<<<n_sm * 8, 256, 0, s>>>(pairs, pair_counter, pair_cap, offsets, keys, z_out_tmp);
+  if (!n_tiles) return;
+  count_launch(), k_tile_copy_short<<<(n_tiles + 255) / 256, 256, 0, s>>>(offsets, n_tiles, keys, z_out_tmp, z_in, z_out, prim);
+  // Short lists: up to kSortSmall entries (48 KB of shared memory).
+  const uint32_t small = kSortSmall;
+  if (max_overlap > 1) {
+    uint32_t cap = max_overlap < small ? max_overlap : small;
+    uint32_t n2 = 1;
+    while (n2 < cap) n2 <<= 1;
+    size_t sm = (size_t)n2 * 12;
+    count_launch(), k_tile_sort<<<n_tiles < 65535u ? n_tiles : 65535u, 256, sm, s>>>(offsets, n_tiles, keys, z_out_tmp, z_in,
+                                                                     z_out, prim, 1, small);
+  }
+  if (max_overlap > small) {
+    uint32_t n2 = 1;
+    while (n2 < max_overlap) n2 <<= 1;
+    size_t sm = (size_t)n2 * 12;
+    count_launch(), k_tile_sort<<<n_sm, 1024, sm, s>>>(offsets, n_tiles, keys, z_out_tmp, z_in, z_out, prim, small,
+                                       kSortLarge);
+  }
+}
+
+cudaError_t cull_set_attributes() {
+  return cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)((size_t)kSortLarge * 12));
+}
+
+}  // namespace st

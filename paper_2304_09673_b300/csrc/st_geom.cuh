@@ -1,0 +1,139 @@
+// st_geom.cuh -- FP32 ray generation and ray / volume-of-interest interval
+// tests with a fixed operation order: every arithmetic step is one IEEE
+// round-to-nearest operation (explicit __f*_rn intrinsics, no contraction),
+// so the culling decisions are reproducible bit for bit on any host that
+// follows the same order.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "st_internal.h"
+
+namespace st {
+
+__device__ __forceinline__ float ieee_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float ieee_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ieee_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float ieee_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float ieee_sqrt(float a) { return __fsqrt_rn(a); }
+// (a0 b0 + a1 b1) + a2 b2
+__device__ __forceinline__ float ieee_dot3(float a0, float a1, float a2, float b0, float b1, float b2) {
+  return ieee_add(ieee_add(ieee_mul(a0, b0), ieee_mul(a1, b1)), ieee_mul(a2, b2));
+}
+
+// Pixel-centre ray direction of pixel (i, j) (see st_camera in st.h).
+__device__ __forceinline__ void pixel_ray(const DevCamera &c, int i, int j, float d[3]) {
+  float u = ieee_sub(ieee_div((float)(2 * i + 1), (float)c.W), 1.0f);
+  float v = ieee_sub(1.0f, ieee_div((float)(2 * j + 1), (float)c.H));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = ieee_add(ieee_add(c.F[k], ieee_mul(u, c.R[k])), ieee_mul(v, c.U[k]));
+}
+
+// Sphere (centre c, radius r) against ray o + t d: closest-approach form.
+// w = c - o, tc = (w.d)/(d.d), q = w - tc d, h2 = q.q; miss if h2 > r^2;
+// s = sqrt((r^2 - h2)/(d.d)); [tc - s, tc + s].  `w` is ray independent.
+__device__ __forceinline__ bool ray_sphere32(const float w[3], const float d[3], float r,
+                                             float &t0, float &t1) {
+  float dd = ieee_dot3(d[0], d[1], d[2], d[0], d[1], d[2]);
+  float wd = ieee_dot3(w[0], w[1], w[2], d[0], d[1], d[2]);
+  float tc = ieee_div(wd, dd);
+  float qx = ieee_sub(w[0], ieee_mul(tc, d[0]));
+  float qy = ieee_sub(w[1], ieee_mul(tc, d[1]));
+  float qz = ieee_sub(w[2], ieee_mul(tc, d[2]));
+  float h2 = ieee_dot3(qx, qy, qz, qx, qy, qz);
+  float r2 = ieee_mul(r, r);
+  if (h2 > r2) return false;
+  float s = ieee_sqrt(ieee_div(ieee_sub(r2, h2), dd));
+  t0 = ieee_sub(tc, s);
+  t1 = ieee_add(tc, s);
+  return true;
+}
+
+// Oriented box: slabs in the local frame.  lo[i] = M_i . (o - c) (ray
+// independent), ld_i = M_i . d, e = half extents.
+__device__ __forceinline__ bool ray_obox32(const float lo[3], const float M[9], const float e[3],
+                                           const float d[3], float &t0, float &t1) {
+  float a_lo = -INFINITY, a_hi = INFINITY;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float ld = ieee_dot3(M[3 * i], M[3 * i + 1], M[3 * i + 2], d[0], d[1], d[2]);
+    if (ld == 0.0f) {
+      if (lo[i] < -e[i] || lo[i] > e[i]) return false;
+      continue;
+    }
+    float ta = ieee_div(ieee_sub(-e[i], lo[i]), ld);
+    float tb = ieee_div(ieee_sub(e[i], lo[i]), ld);
+    float a = ta < tb ? ta : tb;
+    float b = ta < tb ? tb : ta;
+    if (a > a_lo) a_lo = a;
+    if (b < a_hi) a_hi = b;
+  }
+  if (a_lo > a_hi) return false;
+  t0 = a_lo;
+  t1 = a_hi;
+  return true;
+}
+
+// Capsule (a, b, r): hull of the intervals of the two end spheres and of the
+// cylinder between the end planes.  Ray-independent inputs: wa = a - o,
+// wb = b - o (sphere form), w = o - a, ba = b - a, bb = ba.ba, wbv = w.ba,
+// fw = wbv / bb, p = w - fw ba.
+struct CapsuleConst {
+  float wa[3], wb[3], ba[3], p[3];
+  float bb, wbv, r;
+};
+
+__device__ __forceinline__ bool ray_capsule32(const CapsuleConst &k, const float d[3], float &t0,
+                                              float &t1) {
+  float lo = INFINITY, hi = -INFINITY, s0, s1;
+  if (ray_sphere32(k.wa, d, k.r, s0, s1)) { if (s0 < lo) lo = s0; if (s1 > hi) hi = s1; }
+  if (ray_sphere32(k.wb, d, k.r, s0, s1)) { if (s0 < lo) lo = s0; if (s1 > hi) hi = s1; }
+  if (k.bb > 0.0f) {
+    float db = ieee_dot3(d[0], d[1], d[2], k.ba[0], k.ba[1], k.ba[2]);
+    float fd = ieee_div(db, k.bb);
+    float ux = ieee_sub(d[0], ieee_mul(fd, k.ba[0]));
+    float uy = ieee_sub(d[1], ieee_mul(fd, k.ba[1]));
+    float uz = ieee_sub(d[2], ieee_mul(fd, k.ba[2]));
+    float A = ieee_dot3(ux, uy, uz, ux, uy, uz);
+    float r2 = ieee_mul(k.r, k.r);
+    bool ok = true;
+    float c0 = -INFINITY, c1 = INFINITY;
+    if (A > 0.0f) {
+      float pu = ieee_dot3(k.p[0], k.p[1], k.p[2], ux, uy, uz);
+      float tc = -ieee_div(pu, A);
+      float hx = ieee_add(k.p[0], ieee_mul(tc, ux));
+      float hy = ieee_add(k.p[1], ieee_mul(tc, uy));
+      float hz = ieee_add(k.p[2], ieee_mul(tc, uz));
+      float h2 = ieee_dot3(hx, hy, hz, hx, hy, hz);
+      if (h2 > r2) {
+        ok = false;
+      } else {
+        float s = ieee_sqrt(ieee_div(ieee_sub(r2, h2), A));
+        c0 = ieee_sub(tc, s);
+        c1 = ieee_add(tc, s);
+      }
+    } else {
+      float p2 = ieee_dot3(k.p[0], k.p[1], k.p[2], k.p[0], k.p[1], k.p[2]);
+      if (p2 > r2) ok = false;
+    }
+    if (ok) {
+      if (db == 0.0f) {
+        if (k.wbv < 0.0f || k.wbv > k.bb) ok = false;
+      } else {
+        float ta = -ieee_div(k.wbv, db);
+        float tb = ieee_div(ieee_sub(k.bb, k.wbv), db);
+        float sa = ta < tb ? ta : tb;
+        float sb = ta < tb ? tb : ta;
+        if (sa > c0) c0 = sa;
+        if (sb < c1) c1 = sb;
+        if (c0 > c1) ok = false;
+      }
+    }
+    if (ok) { if (c0 < lo) lo = c0; if (c1 > hi) hi = c1; }
+  }
+  if (lo > hi) return false;
+  t0 = lo;
+  t1 = hi;
+  return true;
+}
+
+}  // namespace st

@@ -1,0 +1,127 @@
+// st_internal.h -- device-side data layout shared by the library's sources.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "st.h"
+
+namespace st {
+
+// ---- packed node word (Sec. 4 "blob" bitfield, own field order) -----------
+constexpr uint32_t kAncBits = 23;
+constexpr uint32_t kAncMask = (1u << kAncBits) - 1u;  // 0x7FFFFF = no ancestor
+constexpr uint32_t kNoAnc = kAncMask;
+__host__ __device__ inline uint32_t blob_anc(uint32_t b) { return b & kAncMask; }
+__host__ __device__ inline uint32_t blob_isleft(uint32_t b) { return (b >> 23) & 1u; }
+__host__ __device__ inline uint32_t blob_igm(uint32_t b) { return (b >> 24) & 3u; }
+__host__ __device__ inline uint32_t blob_kind(uint32_t b) { return (b >> 26) & 31u; }
+__host__ __device__ inline uint32_t blob_isprim(uint32_t b) { return b >> 31; }
+__host__ __device__ inline uint32_t make_blob(uint32_t isprim, uint32_t kind, uint32_t igm,
+                                              uint32_t isleft, uint32_t anc) {
+  return (isprim << 31) | (kind << 26) | (igm << 24) | (isleft << 23) | (anc & kAncMask);
+}
+
+// ---- pruned-view node codes --------------------------------------------------
+// A view entry is uint32: bits 27..31 code, bits 0..26 record word offset.
+enum ViewCode : uint32_t {
+  V_SPHERE = 0, V_RBOX = 1, V_CAPSULE = 2,            // primitives (< V_FIRST_OP)
+  V_UNION = 3, V_INTER = 4, V_DIFF = 5,               // compact smooth G_op
+  V_SUNION = 6, V_SINTER = 7, V_SDIFF = 8,            // sharp CSG
+  V_INF = 9, V_RIGHT = 10, V_LEFT = 11,               // usage rewrites (Sec. 9)
+};
+constexpr uint32_t V_FIRST_OP = 3;
+constexpr uint32_t kViewOffBits = 27;
+constexpr uint32_t kViewOffMask = (1u << kViewOffBits) - 1u;
+
+// Record words (float4) per node kind.
+//   sphere : [c, r]
+//   rbox   : [c, r_round] [M row0, b.x] [M row1, b.y] [M row2, b.z]
+//   capsule: [a, r] [b, 0] [b - a, 1/|b - a|^2]
+//   compact operator: [k, d_o, 6 / (6 d_o - k), 1 / k]
+//   sharp operator  : [0, 0, 0, 0]
+__host__ __device__ inline int rec_words(int kind) {
+  return kind == ST_PRIM_RBOX ? 4 : kind == ST_PRIM_CAPSULE ? 3 : 1;
+}
+
+// Algorithmic FP32 flop counts per node evaluation (FMA = 2), counted from
+// the formulas: sphere |p-c|-r; rounded box; capsule; compact operator (two
+// smooth-operator evaluations, b_r and the range tests); sharp operator.
+constexpr uint32_t kFlopsSphere = 11;
+constexpr uint32_t kFlopsRbox = 40;
+constexpr uint32_t kFlopsCapsule = 25;
+constexpr uint32_t kFlopsCompactOp = 30;
+constexpr uint32_t kFlopsSharpOp = 2;
+constexpr uint32_t kFlopsStep = 6;
+
+// ---- device views of a scene, camera, A-buffer and outputs ---------------------
+struct DevScene {
+  const uint32_t *blob;      // [n_nodes] packed node words, post-order
+  const uint32_t *rec_off;   // [n_nodes] first record word of each node
+  const float4 *rec;         // record words
+  const uint32_t *prim_addr; // [n_prims] post-order address of primitive j
+  const float *d_prim;       // [n_prims] range-of-interest bound (Sec. 5)
+  int32_t n_nodes, n_prims, stack_depth;
+  float diameter, voi_pad;
+};
+
+struct DevCamera {
+  float o[3], F[3], R[3], U[3];  // R and U pre-scaled (see st.h)
+  int32_t W, H;
+};
+
+struct DevTiles {
+  int32_t tile, tiles_x, tiles_y;
+  const uint32_t *offsets;  // [n_tiles + 1]
+  const float *z_in, *z_out;
+  const uint32_t *prim;
+};
+
+struct DevOut {
+  float *depth, *normal;
+  uint32_t *evals;
+  uint8_t *flags;
+};
+
+struct TraceParams {
+  float eps, lipschitz, depth_slab, newton_clamp;
+  int32_t max_steps, max_new, newton_iters, step_mode;
+};
+
+// One culling or tracing job (a scene seen by a camera).
+struct Job {
+  DevScene sc;
+  DevCamera cam;
+  DevTiles tl;
+  DevOut out;
+  TraceParams tp;
+  uint32_t tile_base;   // first global tile index of this job
+  uint32_t prim_base;   // first global primitive index of this job
+  uint32_t cand_base;   // unused slot (alignment)
+  uint32_t pad;
+};
+
+// ---- host preparation ----------------------------------------------------------
+struct Prep {
+  std::vector<int32_t> po_of_desc, desc_of_po, parent;
+  std::vector<uint32_t> blob, rec_off, prim_addr;
+  std::vector<float> roi, d_prim, rec;  // rec: 4 floats per word
+  std::vector<int32_t> prim_desc;       // description index of primitive j
+  int stack_depth = 0;
+  double diameter = 0;
+};
+
+// Returns ST_OK or ST_ERR_INVALID with `err` set.
+int prepare(const st_scene_desc &d, Prep &p, std::string &err);
+// Record words of one primitive description record (host-side conversion).
+void prim_words(int kind, const float *q, float *words /* 4 * rec_words */);
+
+void camera_basis(const st_camera &c, DevCamera &out);
+
+void set_error(const std::string &msg);
+// Host-side count of kernel launches issued by the library.
+int count_launch();
+
+}  // namespace st

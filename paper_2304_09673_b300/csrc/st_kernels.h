@@ -1,0 +1,55 @@
+// st_kernels.h -- launch wrappers shared between the C ABI and the kernels.
+#pragma once
+#include <cstdint>
+
+#include "st_internal.h"
+
+namespace st {
+
+struct Pair {          // a surviving (primitive, tile) pair of the culling pass
+  uint32_t tile, rank;
+  float z_in, z_out;
+  uint32_t addr;
+};
+
+constexpr uint32_t kSortSmall = 4096;    // shared-memory sort, 48 KB
+constexpr uint32_t kSortLarge = 16384;   // shared-memory sort, 192 KB
+
+void scan_u32(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *block_sums, uint32_t *total,
+              uint32_t *max_out, uint32_t *tail, cudaStream_t s);
+uint32_t scan_block_count(uint32_t n);
+
+void launch_prim_bounds(const Job *jobs, int n_jobs, uint32_t n_prims, uint32_t *cand_count, int4 *rects,
+                        cudaStream_t s);
+void launch_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_prims,
+                       const uint32_t *cand_total, const int4 *rects, uint32_t *tile_count, Pair *pairs,
+                       uint32_t pair_cap, uint32_t *pair_counter, int n_sm, cudaStream_t s);
+void launch_scatter_sort(const Pair *pairs, const uint32_t *pair_counter, uint32_t pair_cap,
+                         const uint32_t *offsets, uint32_t n_tiles, uint32_t max_overlap, uint64_t *keys,
+                         float *z_out_tmp, float *z_in, float *z_out, uint32_t *prim, int n_sm, cudaStream_t s);
+cudaError_t cull_set_attributes();
+
+// Tracing: per-warp working set layout is computed by trace_layout().
+struct TraceLaunch {
+  int32_t max_tile_rays;   // tile * tile of the largest tile in the launch
+  int32_t act_cap;         // active-set capacity (>= longest tile list)
+  int32_t view_cap;        // 2 * act_cap - 1
+  int32_t stack_slots;     // evaluation stack slots per lane
+  int32_t work_in_smem;    // 1: active set + view in shared memory
+  uint32_t *g_work;        // global per-warp working sets (when not in smem)
+  uint32_t g_work_words;   // words per warp in g_work
+  uint32_t n_items;        // total (job, tile) work items
+  uint32_t *item_counter;  // zeroed before launch
+  uint64_t *counters;      // optional ST_NUM_COUNTERS
+};
+
+size_t trace_smem_per_warp(const TraceLaunch &L);
+uint32_t trace_work_words(const TraceLaunch &L);
+cudaError_t trace_launch(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s);
+int trace_warps_per_cta();
+void launch_pruned_view(const DevScene &sc, const uint32_t *act, int n, uint32_t *view, uint32_t *vaddr,
+                        int32_t *info, uint32_t *bstk, int stack_cap, cudaStream_t s);
+void launch_eval_view(const DevScene &sc, const uint32_t *view, const int32_t *info, const float *pts, int npts,
+                      float *f, float *grad, cudaStream_t s);
+
+}  // namespace st

@@ -1,0 +1,266 @@
+"""Thin ctypes binding of ``libst.so`` (include/st.h): argument marshalling only.
+
+Every function keeps the C name.  Device buffers are torch CUDA tensors
+passed by pointer; streams are torch streams (default: the current one).
+Importing this module loads ``libst.so`` and raises if it is missing: there is
+no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+LIB_PATH = Path(__file__).resolve().parent / "libst.so"
+if not LIB_PATH.exists():
+    raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_2304_09673_b300.build "
+                      "(or __graft_entry__.build())")
+_lib = C.CDLL(str(LIB_PATH))
+
+ST_OK, ST_ERR_INVALID, ST_ERR_CAPACITY, ST_ERR_CUDA, ST_ERR_TIMEOUT, ST_ERR_NOMEM = 0, -1, -2, -3, -4, -5
+ST_STEP_PLAIN, ST_STEP_LEARNED = 0, 1
+ST_NUM_COUNTERS = 8
+ST_REC_FLOATS = 16
+
+
+class StError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.st_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed ({code}): {msg}")
+        self.code = code
+
+
+class st_scene_desc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("root", C.c_int32), ("kind", C.c_void_p),
+                ("left", C.c_void_p), ("right", C.c_void_p), ("params", C.c_void_p),
+                ("voi_pad", C.c_float)]
+
+
+class st_camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class st_tiles(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
+                ("offsets", C.c_void_p), ("z_in", C.c_void_p), ("z_out", C.c_void_p),
+                ("prim", C.c_void_p), ("n_entries", C.c_uint64), ("max_overlap", C.c_uint32)]
+
+
+class st_trace_opts(C.Structure):
+    _fields_ = [("eps", C.c_float), ("lipschitz", C.c_float), ("max_steps", C.c_int32),
+                ("step_mode", C.c_int32), ("depth_slab_frac", C.c_float),
+                ("max_new_per_turn", C.c_int32), ("newton_iters", C.c_int32),
+                ("newton_clamp", C.c_float), ("mlp", C.c_void_p)]
+
+
+_P = C.c_void_p
+_lib.st_last_error.restype = C.c_char_p
+_lib.st_version.restype = C.c_char_p
+_lib.st_scene_create.argtypes = [C.POINTER(st_scene_desc), C.POINTER(C.c_void_p), _P]
+_lib.st_scene_update_prims.argtypes = [_P, _P, _P, C.c_int, _P]
+_lib.st_scene_addresses.argtypes = [_P, _P]
+_lib.st_scene_destroy.argtypes = [_P]
+_lib.st_scene_destroy.restype = None
+_lib.st_build_tiles.argtypes = [_P, C.POINTER(st_camera), C.c_int, C.POINTER(st_tiles), _P]
+_lib.st_trace.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINTER(st_trace_opts),
+                          _P, _P, _P, _P, _P, _P]
+_lib.st_tiles_copy.argtypes = [C.POINTER(st_tiles), _P, _P, _P, _P, _P]
+_lib.st_pruned_view.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
+_lib.st_eval_pruned.argtypes = [_P, _P, _P, _P, C.c_int, _P, _P, _P]
+_lib.st_kernel_launches.restype = C.c_uint64
+_lib.st_prep_tree.argtypes = [C.POINTER(st_scene_desc), _P, _P, _P, _P]
+
+EXPORTED = ("st_scene_create", "st_scene_update_prims", "st_scene_addresses", "st_scene_destroy",
+            "st_build_tiles", "st_trace", "st_tiles_copy", "st_pruned_view", "st_eval_pruned", "st_prep_tree", "st_last_error",
+            "st_version", "st_kernel_launches")
+
+
+def lib():
+    return _lib
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise StError(rc, where)
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def make_desc(scene, voi_pad: float = 0.0):
+    """st_scene_desc over a scenegen.Scene (the numpy arrays are kept alive
+    on the returned object)."""
+    kind = np.ascontiguousarray(scene.kind, np.int32)
+    left = np.ascontiguousarray(scene.left, np.int32)
+    right = np.ascontiguousarray(scene.right, np.int32)
+    params = np.ascontiguousarray(scene.params, np.float32)
+    d = st_scene_desc(scene.n_nodes, scene.root, kind.ctypes.data, left.ctypes.data,
+                      right.ctypes.data, params.ctypes.data, voi_pad)
+    d._keep = (kind, left, right, params)
+    return d
+
+
+def make_camera(cam) -> st_camera:
+    c = st_camera()
+    c.eye[:] = [float(x) for x in cam.eye]
+    c.target[:] = [float(x) for x in cam.target]
+    c.up[:] = [float(x) for x in cam.up]
+    c.vfov_deg = float(cam.vfov_deg)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def make_opts(eps=1e-4, lipschitz=1.45, max_steps=256, step_mode=ST_STEP_PLAIN, depth_slab_frac=0.05,
+              max_new_per_turn=6, newton_iters=4, newton_clamp=0.0, mlp=None) -> st_trace_opts:
+    return st_trace_opts(eps, lipschitz, max_steps, step_mode, depth_slab_frac, max_new_per_turn,
+                         newton_iters, newton_clamp, mlp)
+
+
+# ---- entry points (same names as the C ABI) ----------------------------------------
+def st_scene_create(scene, voi_pad: float = 0.0, stream=None) -> C.c_void_p:
+    desc = make_desc(scene, voi_pad)
+    h = C.c_void_p()
+    _check(_lib.st_scene_create(C.byref(desc), C.byref(h), _stream(stream)), "st_scene_create")
+    return h
+
+
+def st_scene_update_prims(h, ids, params, stream=None) -> None:
+    ids = np.ascontiguousarray(ids, np.int32)
+    params = np.ascontiguousarray(params, np.float32).reshape(len(ids), ST_REC_FLOATS)
+    _check(_lib.st_scene_update_prims(h, ids.ctypes.data, params.ctypes.data, len(ids), _stream(stream)),
+           "st_scene_update_prims")
+
+
+def st_scene_addresses(h, n_nodes: int) -> np.ndarray:
+    out = np.empty(n_nodes, np.int32)
+    _check(_lib.st_scene_addresses(h, out.ctypes.data), "st_scene_addresses")
+    return out
+
+
+def st_scene_destroy(h) -> None:
+    _lib.st_scene_destroy(h)
+
+
+def st_build_tiles(h, cam, tile: int = 16, stream=None) -> st_tiles:
+    t = st_tiles()
+    c = make_camera(cam)
+    _check(_lib.st_build_tiles(h, C.byref(c), tile, C.byref(t), _stream(stream)), "st_build_tiles")
+    return t
+
+
+def st_trace(h, cam, tiles: st_tiles, opts: st_trace_opts | None, depth, normal, evals, flags,
+             counters=None, stream=None) -> None:
+    c = make_camera(cam)
+    o = opts if opts is not None else make_opts()
+    _check(_lib.st_trace(h, C.byref(c), C.byref(tiles), C.byref(o), _ptr(depth), _ptr(normal), _ptr(evals),
+                         _ptr(flags), _ptr(counters), _stream(stream)), "st_trace")
+
+
+def st_pruned_view(h, act, view, view_addr, info, stream=None) -> None:
+    _check(_lib.st_pruned_view(h, _ptr(act), int(act.numel()), _ptr(view), _ptr(view_addr), _ptr(info),
+                               _stream(stream)), "st_pruned_view")
+
+
+def st_eval_pruned(h, view, info, pts, f, grad=None, stream=None) -> None:
+    _check(_lib.st_eval_pruned(h, _ptr(view), _ptr(info), _ptr(pts), int(pts.numel() // 3), _ptr(f), _ptr(grad),
+                               _stream(stream)), "st_eval_pruned")
+
+
+def st_tiles_copy(tiles: st_tiles, stream=None):
+    """A-buffer to host numpy arrays: (offsets, z_in, z_out, prim)."""
+    nt = tiles.tiles_x * tiles.tiles_y + 1
+    ne = int(tiles.n_entries)
+    off = np.empty(nt, np.uint32)
+    zi = np.empty(max(ne, 1), np.float32)
+    zo = np.empty(max(ne, 1), np.float32)
+    pr = np.empty(max(ne, 1), np.uint32)
+    _check(_lib.st_tiles_copy(C.byref(tiles), off.ctypes.data, zi.ctypes.data, zo.ctypes.data,
+                              pr.ctypes.data, _stream(stream)), "st_tiles_copy")
+    return off, zi[:ne], zo[:ne], pr[:ne]
+
+
+def st_prep_tree(scene) -> dict:
+    """Host-only preparation (no GPU): post-order, packed blobs, parents, ROI."""
+    desc = make_desc(scene)
+    n = scene.n_nodes
+    po = np.empty(n, np.int32)
+    blob = np.empty(n, np.uint32)
+    parent = np.empty(n, np.int32)
+    roi = np.empty(n, np.float32)
+    depth = _check(_lib.st_prep_tree(C.byref(desc), po.ctypes.data, blob.ctypes.data, parent.ctypes.data,
+                                     roi.ctypes.data), "st_prep_tree")
+    return dict(po_of_desc=po, blob=blob, parent=parent, roi=roi, stack_depth=int(depth))
+
+
+def st_kernel_launches() -> int:
+    return int(_lib.st_kernel_launches())
+
+
+def st_version() -> str:
+    return _lib.st_version().decode()
+
+
+# ---- convenience ----------------------------------------------------------------
+class Renderer:
+    """One scene on the current CUDA device: owns the st_scene handle and the
+    output tensors of one resolution."""
+
+    def __init__(self, scene, cam, tile: int = 16, voi_pad: float = 0.0, stream=None):
+        import torch
+        self.scene = scene
+        self.cam = cam
+        self.tile = tile
+        self.stream = stream
+        self.h = st_scene_create(scene, voi_pad, stream)
+        W, H = cam.width, cam.height
+        dev = torch.device("cuda")
+        self.depth = torch.empty(H * W, dtype=torch.float32, device=dev)
+        self.normal = torch.empty(H * W * 3, dtype=torch.float32, device=dev)
+        self.evals = torch.empty(H * W, dtype=torch.int32, device=dev)
+        self.flags = torch.empty(H * W, dtype=torch.uint8, device=dev)
+        self.counters = torch.zeros(ST_NUM_COUNTERS, dtype=torch.int64, device=dev)
+        self.tiles = None
+
+    def build_tiles(self):
+        self.tiles = st_build_tiles(self.h, self.cam, self.tile, self.stream)
+        return self.tiles
+
+    def trace(self, opts=None, counters: bool = True):
+        if counters:
+            self.counters.zero_()
+        st_trace(self.h, self.cam, self.tiles, opts, self.depth, self.normal, self.evals, self.flags,
+                 self.counters if counters else None, self.stream)
+
+    def render(self, opts=None, counters: bool = True):
+        self.build_tiles()
+        self.trace(opts, counters)
+
+    def update_prims(self, ids, params):
+        st_scene_update_prims(self.h, ids, params, self.stream)
+
+    def addresses(self):
+        return st_scene_addresses(self.h, self.scene.n_nodes)
+
+    def close(self):
+        if self.h:
+            st_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

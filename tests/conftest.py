@@ -27,3 +27,21 @@ def gpu_available() -> bool:
         return torch.cuda.is_available()
     except Exception:
         return False
+
+
+@pytest.fixture(scope="session")
+def stlib():
+    """The C-ABI library, built in-tree if missing or stale."""
+    from paper_2304_09673_b300 import build
+    build.build()
+    from paper_2304_09673_b300 import st
+    return st
+
+
+@pytest.fixture(scope="session")
+def cuda(stlib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    return torch.device("cuda")

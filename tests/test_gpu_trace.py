@@ -1,0 +1,119 @@
+"""Synchronized tracing on the GPU (st_build_tiles + st_trace) against the
+oracle's dense FP64 sphere tracing: masks identical away from the silhouette
+band, depth within 1e-4 x scene diameter, normals within 1e-3 rad."""
+import numpy as np
+import pytest
+
+from paper_2304_09673_b300 import scenegen as sg
+from gpu_util import angle, band_mask, render
+
+pytestmark = pytest.mark.gpu
+
+
+def _parity(orc, s, cam, g, ref, pix=None, normal_tol=1e-3):
+    H, W = cam.height, cam.width
+    _, _, diam = orc.scene_bounds(s)
+    if pix is None:
+        band = band_mask(orc, s, cam, ref)
+        pi, pj = ref["pi"], ref["pj"]
+    else:
+        pi, pj = pix
+        band = np.zeros(len(pi), bool)
+    gf = g["flags"][pj, pi]
+    unconv = (gf & 2) != 0
+    assert unconv.mean() <= 1e-3, unconv.mean()
+    ghit = (gf & 1) != 0
+    ohit = (ref["flags"] & 1) != 0
+    band = band.reshape(-1) if pix is None else band
+    keep = ~band & ~unconv
+    mism = (ghit != ohit) & keep
+    assert mism.sum() == 0, f"{mism.sum()} mask mismatches of {keep.sum()}"
+    both = ghit & ohit & keep
+    dd = np.abs(g["depth"][pj, pi][both].astype(np.float64) - ref["depth"][both])
+    assert dd.max(initial=0) <= 1e-4 * diam, dd.max()
+    # normals: GPU normal vs FP64 central differences at the GPU's hit point
+    d64, _ = orc.camera_rays(cam, pi[both], pj[both])
+    o = np.array(cam.eye, np.float64)
+    t = g["depth"][pj, pi][both].astype(np.float64) / np.linalg.norm(d64, axis=1)
+    P = o + t[:, None] * d64
+    hh = 1e-6
+    c = np.zeros_like(P)
+    for k in range(3):
+        e = np.zeros(3); e[k] = hh
+        c[:, k] = (orc.field(s, P + e) - orc.field(s, P - e)) / (2 * hh)
+    a = angle(g["normal"][pj, pi][both].astype(np.float64), c)
+    # exclude creases (normal not defined): central differences disagree across h
+    c2 = np.zeros_like(P)
+    for k in range(3):
+        e = np.zeros(3); e[k] = 1e-5
+        c2[:, k] = (orc.field(s, P + e) - orc.field(s, P - e)) / 2e-5
+    smooth = angle(c, c2) < 1e-4
+    assert np.all(a[smooth] < normal_tol), np.sort(a[smooth])[-5:]
+    return dict(n_hit=int(both.sum()), band=int(band.sum()), max_depth_err=float(dd.max(initial=0)))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_trace_small_full_frame(stlib, orc, cuda, seed):
+    s = sg.workload_small(seed)
+    cam = sg.default_camera(256, 256)
+    g = render(stlib, s, cam)
+    ref = orc.trace(s, cam)
+    info = _parity(orc, s, cam, g, ref)
+    assert info["n_hit"] > 1000
+    c = g["counters"]
+    assert c[7] == 0                      # no device error flag
+    assert c[0] == g["evals"].sum()       # tracing steps == sum of per-ray evals
+    assert c[1] > 0 and c[3] > c[1]
+
+
+@pytest.mark.parametrize("kind,rec", [
+    (sg.SPHERE, [0.1, -0.05, 0.2, 0.3]),
+    (sg.CAPSULE, [-0.25, -0.1, 0.0, 0.2, 0.2, -0.1, 0.15]),
+])
+def test_trace_single_primitive(stlib, orc, cuda, kind, rec):
+    s = sg.single_primitive(kind, rec)
+    cam = sg.default_camera(96, 80)
+    g = render(stlib, s, cam)
+    ref = orc.trace(s, cam)
+    _parity(orc, s, cam, g, ref)
+
+
+def test_trace_ragged_and_tile_sizes(stlib, orc, cuda):
+    s = sg.workload_small(5)
+    cam = sg.default_camera(250, 170)
+    ref = orc.trace(s, cam)
+    for tile in (8, 16, 32):
+        g = render(stlib, s, cam, tile=tile)
+        _parity(orc, s, cam, g, ref)
+
+
+def test_trace_independent_of_segmentation_heuristics(stlib, orc, cuda):
+    # The result must not depend on the subfrustum heuristic constants (the
+    # number of new primitives per turn and the depth slab d).
+    s = sg.workload_small(6)
+    cam = sg.default_camera(128, 128)
+    ref = orc.trace(s, cam)
+    for mn, slab in ((1, 0.001), (32, 10.0), (6, 0.05)):
+        g = render(stlib, s, cam, max_new_per_turn=mn, depth_slab_frac=slab)
+        _parity(orc, s, cam, g, ref)
+
+
+def test_trace_1080p_sampled(stlib, orc, cuda):
+    s = sg.workload_1080p(100)
+    cam = sg.default_camera(1920, 1080)
+    g = render(stlib, s, cam)
+    rng = np.random.default_rng(1)
+    pi = rng.integers(0, 1920, 800).astype(np.int32)
+    pj = rng.integers(0, 1080, 800).astype(np.int32)
+    ref = orc.trace(s, cam, pi, pj)
+    # sampled pixels: band test per pixel from the oracle's own hit / min f
+    _, _, diam = orc.scene_bounds(s)
+    d64, _ = orc.camera_rays(cam, pi, pj)
+    cosn = np.abs(np.sum(ref["normal"] * d64 / np.linalg.norm(d64, axis=1, keepdims=True), axis=1))
+    ohit = (ref["flags"] & 1) != 0
+    band = (ohit & (cosn < 0.05)) | (~ohit & (ref["min_f"] < 1e-4 * diam))
+    keep = ~band
+    sub = dict(flags=ref["flags"][keep], depth=ref["depth"][keep], normal=ref["normal"][keep],
+               min_f=ref["min_f"][keep], pi=pi[keep], pj=pj[keep])
+    _parity(orc, s, cam, g, sub, pix=(pi[keep], pj[keep]))
+    assert (g["flags"] & 2).mean() <= 1e-3
