@@ -793,13 +793,15 @@ static void grad_at(const Tree *t, const double p[3], double h, double g[3]) {
  * Newton steps along the ray (step clamped to +-newton_clamp in distance),
  * then depth = z |d| (Euclidean distance to the eye) and the normal is the
  * normalised central-difference gradient (h = 1e-6).  min_f receives the
- * smallest field value met along the ray (silhouette-band test).
+ * smallest field value met along the ray and resid the field value at the
+ * refined hit (both for the silhouette-band test: a hit whose refined point
+ * is not a root is a near miss, the ray grazes within eps of the surface).
  * flags: bit0 hit, bit1 step cap reached. */
 void or_trace(int n, int root, const int32_t *kind, const int32_t *left, const int32_t *right,
               const float *params, const float *cam, double eps, double lipschitz,
               int max_steps, int newton, double newton_clamp, int npx, const int32_t *pi,
               const int32_t *pj, double *depth, double *normal, int32_t *steps,
-              uint8_t *flags, double *min_f) {
+              uint8_t *flags, double *min_f, double *resid) {
     Tree t;
     tree_init(&t, n, root, kind, left, right, params);
     Cam c;
@@ -846,10 +848,12 @@ void or_trace(int n, int root, const int32_t *kind, const int32_t *left, const i
             double p[3] = {c.o[0] + z * d[0], c.o[1] + z * d[1], c.o[2] + z * d[2]}, g[3];
             grad_at(&t, p, 1e-6, g);
             double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            resid[px] = field_rec(&t, root, p, NULL);
             depth[px] = z * dn;
             for (int k = 0; k < 3; ++k) normal[3 * (size_t)px + k] = gn > 0 ? g[k] / gn : 0.0;
         } else {
             depth[px] = INFINITY;
+            resid[px] = INFINITY;
             for (int k = 0; k < 3; ++k) normal[3 * (size_t)px + k] = 0.0;
         }
         steps[px] = st;

@@ -67,7 +67,7 @@ def _declare(L):
     L.or_camera_rays.restype = None
     L.or_cull.argtypes = [I, I, P, P, P, P, P, I, I, F, I, P, I, P, P, P, P]
     L.or_cull.restype = I
-    L.or_trace.argtypes = [I, I, P, P, P, P, P, D, D, I, I, D, I, P, P, P, P, P, P, P]
+    L.or_trace.argtypes = [I, I, P, P, P, P, P, D, D, I, I, D, I, P, P, P, P, P, P, P, P]
     L.or_trace.restype = None
     L.or_march.argtypes = [I, I, P, P, P, P, P, D, I, P, P, P, P]
     L.or_march.restype = None
@@ -203,7 +203,7 @@ def cull(scene, cam, tile: int, mode: int, tiles=None, pad: float = VOI_PAD, cap
 def trace(scene, cam, pi=None, pj=None, eps: float = EPS, lipschitz: float = LIPSCHITZ,
           max_steps: int = 100000, newton: int = 4, newton_clamp: float | None = None):
     """Naive dense FP64 sphere tracing of the pixels (pi, pj) (all pixels if
-    None).  Returns dict(depth, normal, steps, flags, min_f)."""
+    None).  Returns dict(depth, normal, steps, flags, min_f, resid)."""
     if pi is None:
         jj, ii = np.mgrid[0:cam.height, 0:cam.width]
         pi, pj = ii.reshape(-1), jj.reshape(-1)
@@ -217,11 +217,13 @@ def trace(scene, cam, pi=None, pj=None, eps: float = EPS, lipschitz: float = LIP
     steps = np.empty(n, np.int32)
     flags = np.empty(n, np.uint8)
     min_f = np.empty(n, np.float64)
+    resid = np.empty(n, np.float64)
     keep, sa = _scene_args(scene)
     ca = cam_array(cam)
     lib().or_trace(*sa, _p(ca), eps, lipschitz, max_steps, newton, newton_clamp, n, _p(pi),
-                   _p(pj), _p(depth), _p(normal), _p(steps), _p(flags), _p(min_f))
-    return dict(depth=depth, normal=normal, steps=steps, flags=flags, min_f=min_f, pi=pi, pj=pj)
+                   _p(pj), _p(depth), _p(normal), _p(steps), _p(flags), _p(min_f), _p(resid))
+    return dict(depth=depth, normal=normal, steps=steps, flags=flags, min_f=min_f, resid=resid,
+                pi=pi, pj=pj)
 
 
 def march(scene, cam, pi, pj, z_stop, h: float = 1e-5):

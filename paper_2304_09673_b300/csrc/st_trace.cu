@@ -416,15 +416,18 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         pixel_ray(cam, x0 + r % tw, y0 + r / tw, d);
         const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         const float lim = tp.newton_clamp / dn;
+        bool beyond = false;  // the crossing lies past z_end: not this subfrustum's
         for (int it = 0; it < tp.newton_iters; ++it) {
           Dual<1> pd[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k) { pd[k].v = cam.o[k] + zz * d[k]; pd[k].g[0] = d[k]; }
           LocalStack<Dual<1>> ls;
           const Dual<1> fd = eval_view<Dual<1>>(W.view, vi.n_view, sc.rec, pd, ls);
+          beyond = false;
           if (fd.g[0] != 0.f && isfinite(fd.v)) {
             float step = -fd.v / fd.g[0];
             step = fminf(fmaxf(step, -lim), lim);
+            beyond = zz + step > z_end && fd.v > 0.f;
             zz = fminf(fmaxf(zz + step, z_begin), z_end);
           }
         }
@@ -438,7 +441,12 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         }
         LocalStack<Dual<3>> ls3;
         const Dual<3> fg = eval_view<Dual<3>>(W.view, vi.n_view, sc.rec, pg, ls3);
-        if (v) {
+        if (v && beyond) {
+          // Hand the ray back: the next subfrustum starts at z_end and owns
+          // the crossing.
+          W.ray_z[r] = z_end;
+          W.ray_st[r] = W.ray_st[r] & 0xFFFFFFu;
+        } else if (v) {
           const float gn = sqrtf(fg.g[0] * fg.g[0] + fg.g[1] * fg.g[1] + fg.g[2] * fg.g[2]);
           const float ig = gn > 0.f ? 1.f / gn : 0.f;
           const int px = x0 + r % tw, py = y0 + r / tw;

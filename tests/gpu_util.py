@@ -30,10 +30,19 @@ def render(st, scene, cam, tile=16, **opts):
         r.close()
 
 
+NEAR_MISS_RESID = 1e-8   # |f| at a refined true crossing is ~1e-12
+
+
+def near_miss(ref):
+    return ((ref["flags"] & 1) != 0) & (np.abs(ref["resid"]) > NEAR_MISS_RESID)
+
+
 def band_mask(orc, scene, cam, ref):
     """Silhouette band (excluded from mask / depth parity): oracle mask differs
-    from a 4-neighbour, grazing oracle hit (|n.d| < 0.05), or an oracle miss
-    that came within 1e-4 * diameter of the surface."""
+    from a 4-neighbour, grazing oracle hit (|n.d| < 0.05), an oracle "hit"
+    whose refined point is not a root (the ray passes within eps of the surface
+    without crossing it), or an oracle miss that came within 1e-4 * diameter
+    of the surface."""
     H, W = cam.height, cam.width
     hit = (ref["flags"] & 1).reshape(H, W).astype(bool)
     band = np.zeros((H, W), bool)
@@ -45,6 +54,7 @@ def band_mask(orc, scene, cam, ref):
     dn = d64 / np.linalg.norm(d64, axis=1, keepdims=True)
     cosn = np.abs(np.sum(ref["normal"] * dn, axis=1)).reshape(H, W)
     band |= hit & (cosn < 0.05)
+    band |= hit & (np.abs(ref["resid"]).reshape(H, W) > NEAR_MISS_RESID)
     _, _, diam = orc.scene_bounds(scene)
     band |= (~hit) & (ref["min_f"].reshape(H, W) < 1e-4 * diam)
     return band
