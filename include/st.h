@@ -126,6 +126,17 @@ typedef struct {
     int32_t newton_iters;   /* Newton refinements of a hit [4]             */
     float newton_clamp;     /* Newton step bound, distance units [64 eps]  */
     const void *mlp;        /* reserved for the learned step; NULL         */
+    uint32_t *tile_stats;   /* optional device uint32[n_tiles][16] per-tile
+                               diagnostics: [0] total, [1] segmentation +
+                               view build, [2] marching, [3] hit refinement
+                               SM clock cycles / 16 (first warp); [4]
+                               subfrustums; [5] tracing steps; [6] longest
+                               view; [7] A-buffer list length; summed over
+                               warps: [8] lockstep passes, [9] warp-wide
+                               single-point passes, [10] / [11] their cycles
+                               / 16, [12] refinement cycles / 16; [13] sum of
+                               view lengths, [14] sum of operator levels
+                               (NULL = off)                                */
 } st_trace_opts;
 
 /* Optional per-call counters (device pointer to 8 uint64, accumulated with
@@ -204,10 +215,11 @@ int st_tiles_copy(const st_tiles *tiles, uint32_t *offsets, float *z_in, float *
  * clamping, popRequiredA / popRequiredB and the usage rewrite of Sec. 9).
  *   act        device uint32[n], post-order addresses of active primitives,
  *              strictly ascending, 1 <= n <= number of primitives
- *   view       device uint32[2n-1] out: bits 27..31 node code (0 sphere,
+ *   view       device uint32[2n-1] out: bits 28..31 node code (0 sphere,
  *              1 rounded box, 2 capsule, 3/4/5 compact union / intersection /
  *              difference, 6/7/8 sharp ones, 9 +inf, 10 right operand, 11 left
- *              operand), bits 0..26 record word offset
+ *              operand), bit 27 set (record in the scene's global array),
+ *              bits 0..26 record word offset
  *   view_addr  device uint32[2n-1] out (optional): post-order address per entry
  *   info       device int32[4] out: view length, root usage bit, error (0 ok),
  *              number of primitives

@@ -344,8 +344,10 @@ int st_trace(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_tra
   L.act_cap = (int)std::max<uint32_t>(tl->max_overlap, 1u);
   L.view_cap = 2 * L.act_cap;
   L.stack_slots = s->prep.stack_depth + 2;
+  L.dc_words = 768;
   L.n_items = (uint32_t)(tiles_x * tiles_y);
   L.counters = counters;
+  L.tile_stats = o.tile_stats;
   // Active set and view in shared memory when 16 warps per SM still fit.
   L.work_in_smem = 1;
   if (trace_smem_per_warp(L) * 16 > 200 * 1024) L.work_in_smem = 0;

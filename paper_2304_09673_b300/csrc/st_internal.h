@@ -25,7 +25,9 @@ __host__ __device__ inline uint32_t make_blob(uint32_t isprim, uint32_t kind, ui
 }
 
 // ---- pruned-view node codes --------------------------------------------------
-// A view entry is uint32: bits 27..31 code, bits 0..26 record word offset.
+// A view entry is uint32: bits 28..31 code, bit 27 set when the record is
+// read from the scene's global record array (else from the view's shared
+// parameter cache), bits 0..26 record word offset.
 enum ViewCode : uint32_t {
   V_SPHERE = 0, V_RBOX = 1, V_CAPSULE = 2,            // primitives (< V_FIRST_OP)
   V_UNION = 3, V_INTER = 4, V_DIFF = 5,               // compact smooth G_op
@@ -33,8 +35,9 @@ enum ViewCode : uint32_t {
   V_INF = 9, V_RIGHT = 10, V_LEFT = 11,               // usage rewrites (Sec. 9)
 };
 constexpr uint32_t V_FIRST_OP = 3;
-constexpr uint32_t kViewOffBits = 27;
-constexpr uint32_t kViewOffMask = (1u << kViewOffBits) - 1u;
+constexpr uint32_t kViewCodeShift = 28;
+constexpr uint32_t kViewGlobal = 1u << 27;
+constexpr uint32_t kViewOffMask = (1u << 27) - 1u;
 
 // Record words (float4) per node kind.
 //   sphere : [c, r]

@@ -36,11 +36,13 @@ struct TraceLaunch {
   int32_t view_cap;        // 2 * act_cap - 1
   int32_t stack_slots;     // evaluation stack slots per lane
   int32_t work_in_smem;    // 1: active set + view in shared memory
+  int32_t dc_words;        // shared parameter cache per view buffer (float4 words)
   uint32_t *g_work;        // global per-warp working sets (when not in smem)
   uint32_t g_work_words;   // words per warp in g_work
   uint32_t n_items;        // total (job, tile) work items
   uint32_t *item_counter;  // zeroed before launch
   uint64_t *counters;      // optional ST_NUM_COUNTERS
+  uint32_t *tile_stats;    // optional [n_items][8] diagnostics
 };
 
 size_t trace_smem_per_warp(const TraceLaunch &L);

@@ -27,62 +27,82 @@
 
 namespace st {
 
-constexpr int kWarps = 4;
+constexpr int kWarps = 4;   // warps per CTA; a CTA traces one tile at a time
+constexpr int kR = 2;       // rays per lane (shared node decode, two evaluation chains)
 
 int trace_warps_per_cta() { return kWarps; }
 
 enum RayStatus : uint32_t { R_ALIVE = 0, R_HIT = 1, R_UNCONV = 2 };
 
-// Per-warp working set.  Shared memory always holds the ray state, queues and
-// the evaluation stack; the active set and the view live either in shared
-// memory or in a global per-warp region (long tile lists).
-struct WarpWork {
-  float *ray_z;          // [max_tile_rays] current depth of each ray
-  uint32_t *ray_st;      // [max_tile_rays] steps | status << 24
-  uint16_t *alive;       // [max_tile_rays] tile-local ids of pending rays
-  uint16_t *hits;        // [max_tile_rays] rays that hit in this subfrustum
-  float *stk;            // [stack_slots][32]
-  uint32_t *bstk;        // [stack_slots + 2] Algorithm 1 stack (anc | usage << 31)
-  uint32_t *act[2];      // [act_cap] active primitive addresses (sorted)
-  float *act_ze[2];      // [act_cap] their exit depths
-  uint32_t *view;        // [view_cap]
-};
-
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Shared memory of a CTA: ray state, two pending-ray lists, per-warp hit
+// lists, per-warp evaluation stacks (float2 slots), the Algorithm 1 stack,
+// and (when they fit) the active set and two pruned views.
 __host__ __device__ inline size_t smem_fixed_bytes(const TraceLaunch &L) {
-  size_t r = (size_t)L.max_tile_rays;
-  return align16(r * 4) + align16(r * 4) + align16(r * 2) + align16(r * 2) +
-         align16((size_t)L.stack_slots * 32 * 4) + align16((size_t)(L.stack_slots + 2) * 4);
+  const size_t r = (size_t)L.max_tile_rays;
+  return align16(r * 4) + align16(r * 4) + 2 * align16(r * 2) + (size_t)kWarps * align16(r * 2) +
+         (size_t)kWarps * align16((size_t)L.stack_slots * 32 * 8) + align16((size_t)(L.stack_slots + 2) * 4) +
+         2 * (size_t)L.dc_words * 16;
 }
-__host__ __device__ inline size_t work_bytes(const TraceLaunch &L) {
-  return align16((size_t)L.act_cap * 4) * 4 + align16((size_t)L.view_cap * 4);
-}
+constexpr int kMaxLevels = 64;   // operator levels of a view usable by the tail mode
 
-__host__ __device__ inline size_t smem_per_warp(const TraceLaunch &L) {
+__host__ __device__ inline size_t work_bytes(const TraceLaunch &L) {
+  return align16((size_t)L.act_cap * 4) * 4 + 2 * align16((size_t)L.view_cap * 4) +
+         2 * align16((size_t)L.view_cap * 8) + 2 * align16((size_t)(kMaxLevels + 1) * 4);
+}
+__host__ __device__ inline size_t smem_per_cta(const TraceLaunch &L) {
   return smem_fixed_bytes(L) + (L.work_in_smem ? work_bytes(L) : 0);
 }
-size_t trace_smem_per_warp(const TraceLaunch &L) { return smem_per_warp(L); }
+size_t trace_smem_per_warp(const TraceLaunch &L) { return smem_per_cta(L) / kWarps; }
 uint32_t trace_work_words(const TraceLaunch &L) { return (uint32_t)(work_bytes(L) / 4); }
 
-__device__ WarpWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork) {
-  WarpWork w;
-  size_t r = (size_t)L.max_tile_rays;
+struct CtaWork {
+  float *ray_z;       // [rays] depth reached by each ray
+  uint32_t *ray_st;   // [rays] steps | status << 24
+  uint16_t *alive[2]; // pending rays, read list / append list (alternating)
+  uint16_t *hits;     // [kWarps][rays] rays that hit in the current subfrustum
+  float2 *stk;        // [kWarps][stack_slots][32]
+  uint32_t *bstk;     // Algorithm 1 stack
+  uint32_t *act[2];
+  float *act_ze[2];
+  uint32_t *view[2];
+  float4 *dc[2];       // shared parameter cache of each view (the paper's D_cache)
+  uint2 *ops[2];       // operators of each view sorted by level: (self | left << 16, right)
+  int *lvl_off[2];     // [kMaxLevels + 1] level offsets into ops
+};
+
+__device__ CtaWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork) {
+  CtaWork w;
+  const size_t r = (size_t)L.max_tile_rays;
   w.ray_z = (float *)p; p += align16(r * 4);
   w.ray_st = (uint32_t *)p; p += align16(r * 4);
-  w.alive = (uint16_t *)p; p += align16(r * 2);
-  w.hits = (uint16_t *)p; p += align16(r * 2);
-  w.stk = (float *)p; p += align16((size_t)L.stack_slots * 32 * 4);
+  w.alive[0] = (uint16_t *)p; p += align16(r * 2);
+  w.alive[1] = (uint16_t *)p; p += align16(r * 2);
+  w.hits = (uint16_t *)p; p += (size_t)kWarps * align16(r * 2);
+  w.stk = (float2 *)p; p += (size_t)kWarps * align16((size_t)L.stack_slots * 32 * 8);
   w.bstk = (uint32_t *)p; p += align16((size_t)(L.stack_slots + 2) * 4);
+  w.dc[0] = (float4 *)p; p += (size_t)L.dc_words * 16;
+  w.dc[1] = (float4 *)p; p += (size_t)L.dc_words * 16;
   unsigned char *q = L.work_in_smem ? p : (unsigned char *)gwork;
-  size_t a = align16((size_t)L.act_cap * 4);
+  const size_t a = align16((size_t)L.act_cap * 4);
   w.act[0] = (uint32_t *)q; q += a;
   w.act[1] = (uint32_t *)q; q += a;
   w.act_ze[0] = (float *)q; q += a;
   w.act_ze[1] = (float *)q; q += a;
-  w.view = (uint32_t *)q;
+  w.view[0] = (uint32_t *)q; q += align16((size_t)L.view_cap * 4);
+  w.view[1] = (uint32_t *)q; q += align16((size_t)L.view_cap * 4);
+  w.ops[0] = (uint2 *)q; q += align16((size_t)L.view_cap * 8);
+  w.ops[1] = (uint2 *)q; q += align16((size_t)L.view_cap * 8);
+  w.lvl_off[0] = (int *)q; q += align16((size_t)(kMaxLevels + 1) * 4);
+  w.lvl_off[1] = (int *)q;
   return w;
 }
+
+// Select one of a pair of buffers by a run-time bit without indexing an
+// array (keeps the work-area pointers in registers).
+template <class P>
+__device__ __forceinline__ P pick(P const (&a)[2], int i) { return (i & 1) ? a[1] : a[0]; }
 
 __device__ __forceinline__ int find_job_tile(const Job *jobs, int n_jobs, uint32_t item) {
   int lo = 0, hi = n_jobs - 1;
@@ -115,7 +135,7 @@ struct ViewInfo {
   int err;
 };
 
-__device__ ViewInfo build_view(const DevScene &sc, const uint32_t *act, int n, uint32_t *view,
+__device__ __forceinline__ ViewInfo build_view(const DevScene &sc, const uint32_t *act, int n, uint32_t *view,
                                uint32_t *bstk, int stack_cap, uint32_t *vaddr = nullptr) {
   ViewInfo vi = {0, 0, 0, 0, 0u, 0};
   int sp = 0;
@@ -131,7 +151,7 @@ __device__ ViewInfo build_view(const DevScene &sc, const uint32_t *act, int n, u
     {
       const uint32_t code = blob_kind(nb);  // primitive kinds equal their view codes
       if (vaddr) vaddr[nv] = P;
-      view[nv++] = (code << kViewOffBits) | __ldg(sc.rec_off + P);
+      view[nv++] = (code << kViewCodeShift) | kViewGlobal | __ldg(sc.rec_off + P);
       vi.flops += node_flops(code);
       vi.n_prim++;
     }
@@ -163,7 +183,7 @@ __device__ ViewInfo build_view(const DevScene &sc, const uint32_t *act, int n, u
           else if (!ok || b == 0u) code = V_INF;
           else code = b == 1u ? V_RIGHT : V_LEFT;
           if (vaddr) vaddr[nv] = pop;
-          view[nv++] = (code << kViewOffBits) | __ldg(sc.rec_off + pop);
+          view[nv++] = (code << kViewCodeShift) | kViewGlobal | __ldg(sc.rec_off + pop);
           vi.flops += node_flops(code);
           vi.n_op++;
           u = (ok && b != 0u) ? 1u : 0u;
@@ -190,305 +210,667 @@ __device__ ViewInfo build_view(const DevScene &sc, const uint32_t *act, int n, u
   return vi;
 }
 
+// Parameter cache fill (Sec. 8 "local pruned tree view"): the records of the
+// view's nodes are copied into the view's shared cache, warp-cooperatively,
+// in view order until the cache is full; the remaining nodes keep reading
+// the scene's global records.  Record words needed per node code.
+__device__ __forceinline__ int code_words(uint32_t code) {
+  switch (code) {
+    case V_SPHERE: return 1;
+    case V_RBOX: return 4;
+    case V_CAPSULE: return 3;
+    case V_UNION: case V_INTER: case V_DIFF: return 1;
+    default: return 0;
+  }
+}
+
+__device__ __forceinline__ void fill_dcache(uint32_t *view, int n_view, const float4 *rec, float4 *dc, int cap) {
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  for (int b = 0; b < n_view; b += 32) {
+    const int i = b + lane;
+    const uint32_t w = i < n_view ? view[i] : 0u;
+    const int nw = i < n_view ? code_words(w >> kViewCodeShift) : 0;
+    int x = nw;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    const int off = base + x - nw;
+    if (nw > 0 && off + nw <= cap) {
+      const float4 *sp = rec + (w & kViewOffMask);
+      for (int k = 0; k < nw; ++k) dc[off + k] = __ldg(sp + k);
+      view[i] = (w & ~(kViewGlobal | kViewOffMask)) | (uint32_t)off;
+    }
+    base += __shfl_sync(0xFFFFFFFFu, x, 31);
+    if (base >= cap) break;
+  }
+  __syncwarp();
+}
+
+// ---- subfrustum preparation (warp 0) -------------------------------------------
+struct SegState {   // registers of warp 0, kept across the subfrustums of a tile
+  uint32_t next;
+  int n_act, cur;
+  float z_end, maxze;
+};
+
+struct SubInfo {    // one prepared subfrustum, published in shared memory
+  float z_begin, z_end;
+  int n_view, root_used, n_prim, n_op, err, done;
+  int n_lvl;          // operator levels of the schedule (0: tail mode unavailable)
+  uint32_t flops;
+};
+
+// Level schedule of a view for the warp-wide evaluation of a single point:
+// operators grouped by their height in the pruned tree, each with the view
+// indices of its operands.  One lane; uses the Algorithm 1 stack memory.
+// Returns the number of levels, or 0 when there are more than kMaxLevels or
+// the view does not fit 16-bit indices.
+__device__ __forceinline__ int build_schedule(const uint32_t *view, int n_view, uint2 *ops, int *lvl_off, uint32_t *bstk,
+                              int stack_cap) {
+  if (n_view <= 0 || n_view > 65535) return 0;
+  // lvl_off doubles as the per-level counter array during the build.
+  for (int h = 0; h <= kMaxLevels; ++h) lvl_off[h] = 0;
+  int sp = 0, max_lvl = 0;
+  // pass 1: heights and level counts (stack entry: index | level << 16)
+  for (int i = 0; i < n_view; ++i) {
+    const uint32_t code = view[i] >> kViewCodeShift;
+    if (code < V_FIRST_OP) {
+      if (sp >= stack_cap) return 0;
+      bstk[sp++] = (uint32_t)i;
+    } else {
+      const uint32_t r = bstk[--sp], l = bstk[--sp];
+      const int lev = (int)max(l >> 16, r >> 16) + 1;
+      if (lev > kMaxLevels) return 0;
+      lvl_off[lev]++;
+      max_lvl = max(max_lvl, lev);
+      bstk[sp++] = (uint32_t)i | ((uint32_t)lev << 16);
+    }
+  }
+  // exclusive offsets: lvl_off[h] = start of level h+1 (levels are 1-based)
+  int acc = 0;
+  for (int h = 1; h <= max_lvl; ++h) {
+    const int c = lvl_off[h];
+    lvl_off[h - 1] = acc;
+    acc += c;
+  }
+  lvl_off[max_lvl] = acc;
+  // pass 2: place operators (cursor per level kept in lvl_off, restored after)
+  sp = 0;
+  for (int i = 0; i < n_view; ++i) {
+    const uint32_t code = view[i] >> kViewCodeShift;
+    if (code < V_FIRST_OP) {
+      bstk[sp++] = (uint32_t)i;
+    } else {
+      const uint32_t r = bstk[--sp], l = bstk[--sp];
+      const int lev = (int)max(l >> 16, r >> 16) + 1;
+      ops[lvl_off[lev - 1]++] = make_uint2((uint32_t)i | ((l & 0xFFFFu) << 16), r & 0xFFFFu);
+      bstk[sp++] = (uint32_t)i | ((uint32_t)lev << 16);
+    }
+  }
+  // the cursors now hold the level ends; shift back to level starts
+  for (int h = max_lvl; h >= 1; --h) lvl_off[h] = lvl_off[h - 1];
+  lvl_off[0] = 0;
+  return max_lvl;
+}
+
+
+// Tracking active primitives (Sec. 8): discard those with z_e <= z_end,
+// fetch new ones from the depth-sorted list while the four conditions hold,
+// keep the set sorted by node address; then Algorithm 1 (one lane) builds the
+// pruned view into `view`.  Warp-collective; lane 0 writes *out.
+__device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, const DevScene &sc, const TraceParams &tp,
+                            const float *zin_l, const float *zout_l, const uint32_t *prim_l, uint32_t len,
+                            int vb, int stack_slots, int dc_words, SubInfo *out) {
+  uint32_t *view = pick(C.view, vb);
+  const int lane = threadIdx.x & 31;
+  // ---- discard ----
+  {
+    int kept = 0;
+    float mz = -INFINITY;
+    for (int b = 0; b < sg.n_act; b += 32) {
+      const int i = b + lane;
+      const bool v = i < sg.n_act;
+      const float ze = v ? pick(C.act_ze, sg.cur)[i] : -INFINITY;
+      const uint32_t ad = v ? pick(C.act, sg.cur)[i] : 0u;
+      const bool keep = v && ze > sg.z_end;
+      const uint32_t km = __ballot_sync(0xFFFFFFFFu, keep);
+      if (keep) {
+        const int dst = kept + __popc(km & lanemask_lt());
+        pick(C.act, sg.cur ^ 1)[dst] = ad;
+        pick(C.act_ze, sg.cur ^ 1)[dst] = ze;
+        mz = fmaxf(mz, ze);
+      }
+      kept += __popc(km);
+    }
+    sg.n_act = kept;
+    sg.cur ^= 1;
+    sg.maxze = warp_max(mz);
+    __syncwarp();
+  }
+  SubInfo info;
+  info.done = (sg.n_act == 0 && sg.next >= len) ? 1 : 0;
+  info.err = 0;
+  info.n_view = info.root_used = info.n_prim = info.n_op = info.n_lvl = 0;
+  info.flops = 0u;
+  info.z_begin = info.z_end = sg.z_end;
+  if (!info.done) {
+    // ---- fetch (no empty space, depth slab d, max new per turn; no overlap cap) ----
+    float z_begin = sg.z_end;
+    if (sg.next < len) {
+      z_begin = fmaxf(sg.z_end, __ldg(zin_l + sg.next));
+      const uint32_t c = sg.next + (uint32_t)lane;
+      const bool valid = lane < tp.max_new && c < len;
+      const float zb = valid ? __ldg(zin_l + c) : INFINITY;
+      const float ze = valid ? __ldg(zout_l + c) : -INFINITY;
+      const uint32_t pa = valid ? __ldg(prim_l + c) : 0xFFFFFFFFu;
+      float run = ze;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xFFFFFFFFu, run, o);
+        if (lane >= o) run = fmaxf(run, y);
+      }
+      float excl = __shfl_up_sync(0xFFFFFFFFu, run, 1);
+      excl = lane == 0 ? sg.maxze : fmaxf(excl, sg.maxze);
+      const bool ok = valid && ((lane == 0 && sg.n_act == 0) ||
+                                (zb <= excl && zb - z_begin < tp.depth_slab));
+      const uint32_t fail = __ballot_sync(0xFFFFFFFFu, !ok);
+      const int take = fail ? __ffs(fail) - 1 : 32;
+      const bool taken = lane < take;
+      sg.maxze = warp_max(taken ? fmaxf(ze, sg.maxze) : sg.maxze);
+      // sorted merge by node address
+      int rank_new = 0;
+      for (int j = 0; j < take; ++j) rank_new += (__shfl_sync(0xFFFFFFFFu, pa, j) < pa) ? 1 : 0;
+      const uint32_t *A = pick(C.act, sg.cur);
+      const float *AZ = pick(C.act_ze, sg.cur);
+      uint32_t *B = pick(C.act, sg.cur ^ 1);
+      float *BZ = pick(C.act_ze, sg.cur ^ 1);
+      if (taken) {
+        int lo = 0, hi = sg.n_act;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (A[mid] < pa) lo = mid + 1; else hi = mid;
+        }
+        B[rank_new + lo] = pa;
+        BZ[rank_new + lo] = ze;
+      }
+      for (int b = 0; b < sg.n_act; b += 32) {
+        const int i = b + lane;
+        const uint32_t ad = i < sg.n_act ? A[i] : 0xFFFFFFFFu;
+        int before = 0;
+        for (int j = 0; j < take; ++j) before += (__shfl_sync(0xFFFFFFFFu, pa, j) < ad) ? 1 : 0;
+        if (i < sg.n_act) {
+          B[i + before] = ad;
+          BZ[i + before] = AZ[i];
+        }
+      }
+      sg.n_act += take;
+      sg.cur ^= 1;
+      sg.next += (uint32_t)take;
+    }
+    sg.z_end = sg.next < len ? fminf(__ldg(zin_l + sg.next), sg.maxze) : sg.maxze;
+    info.z_begin = z_begin;
+    info.z_end = sg.z_end;
+    __syncwarp();
+    // ---- pruned view (Algorithm 1), one lane ----
+    ViewInfo vi;
+    if (lane == 0) {
+      vi = build_view(sc, pick(C.act, sg.cur), sg.n_act, view, C.bstk, stack_slots);
+      info.n_view = vi.n_view;
+      info.root_used = vi.root_used;
+      info.n_prim = vi.n_prim;
+      info.n_op = vi.n_op;
+      info.flops = vi.flops;
+      info.err = vi.err;
+      if (!vi.err && vi.root_used) info.n_lvl = build_schedule(view, vi.n_view, pick(C.ops, vb), pick(C.lvl_off, vb), C.bstk, stack_slots);
+    }
+    __syncwarp();
+    const int nv = __shfl_sync(0xFFFFFFFFu, info.n_view, 0);
+    const int used = __shfl_sync(0xFFFFFFFFu, info.root_used, 0);
+    if (used) fill_dcache(view, nv, sc.rec, pick(C.dc, vb), dc_words);
+  }
+  if (lane == 0) *out = info;
+  __syncwarp();
+}
+
+// ---- warp-wide evaluation of one point (tail mode) ------------------------------------
+// All lanes hold the same point p.  Primitives are evaluated in parallel,
+// then operators level by level (operands always sit on lower levels).
+// `vals` is per-warp shared memory of at least n_view floats.
+__device__ __forceinline__ float tail_eval(const uint32_t *view, int n_view, const uint2 *ops, const int *lvl_off, int n_lvl,
+                           const RecSrc &src, const float p[3], float *vals) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < n_view; i += 32) {
+    const uint32_t w = view[i];
+    const uint32_t code = w >> kViewCodeShift;
+    if (code >= V_FIRST_OP) continue;
+    const float4 *q = rec_ptr(src, w);
+    float v;
+    if (code == V_SPHERE) v = sd_sphere<float>(ldrec(q), p);
+    else if (code == V_RBOX) v = sd_rbox<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p);
+    else v = sd_capsule<float>(ldrec(q), ldrec(q + 2), p);
+    vals[i] = v;
+  }
+  __syncwarp();
+  for (int h = 0; h < n_lvl; ++h) {
+    const int e = lvl_off[h + 1];
+    for (int j = lvl_off[h] + lane; j < e; j += 32) {
+      const uint2 o = ops[j];
+      const int self = (int)(o.x & 0xFFFFu), li = (int)(o.x >> 16), ri = (int)o.y;
+      const uint32_t w = view[self];
+      const float f0 = vals[li], f1 = vals[ri];
+      const float4 *q = rec_ptr(src, w);
+      float v;
+      switch (w >> kViewCodeShift) {
+        case V_UNION: v = op_compact<V_UNION, float>(ldrec(q), f0, f1); break;
+        case V_INTER: v = op_compact<V_INTER, float>(ldrec(q), f0, f1); break;
+        case V_DIFF: v = op_compact<V_DIFF, float>(ldrec(q), f0, f1); break;
+        case V_SUNION: v = op_sharp<V_SUNION, float>(f0, f1); break;
+        case V_SINTER: v = op_sharp<V_SINTER, float>(f0, f1); break;
+        case V_SDIFF: v = op_sharp<V_SDIFF, float>(f0, f1); break;
+        case V_INF: v = INFINITY; break;
+        case V_RIGHT: v = f1; break;
+        default: v = f0; break;
+      }
+      vals[self] = v;
+    }
+    __syncwarp();
+  }
+  const float r = vals[n_view - 1];
+  __syncwarp();
+  return r;
+}
+
+// ---- marching one subfrustum: lockstep evaluation with ray refill -----------------
+struct MarchCtx {
+  const DevCamera *cam;
+  const TraceParams *tp;
+  const DevOut *out;
+  int x0, y0, tw;
+};
+
+__device__ __forceinline__ void load_ray(const MarchCtx &M, const CtaWork &C, int r, float z_begin, float &z,
+                                         uint32_t &steps, float d[3], float &inv_ld) {
+  z = fmaxf(C.ray_z[r], z_begin);
+  steps = C.ray_st[r] & 0xFFFFFFu;
+  pixel_ray(*M.cam, M.x0 + r % M.tw, M.y0 + r / M.tw, d);
+  inv_ld = 1.0f / (M.tp->lipschitz * sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+}
+
+__device__ __forceinline__ void write_miss(const MarchCtx &M, int r, uint32_t steps, uint8_t flag) {
+  const size_t o = (size_t)(M.y0 + r / M.tw) * M.cam->W + (M.x0 + r % M.tw);
+  M.out->depth[o] = INFINITY;
+  M.out->normal[3 * o] = 0.f;
+  M.out->normal[3 * o + 1] = 0.f;
+  M.out->normal[3 * o + 2] = 0.f;
+  M.out->evals[o] = steps;
+  M.out->flags[o] = flag;
+}
+
+// Appends the rays of the set lanes to a shared list (warp-aggregated).
+__device__ __forceinline__ void append_rays(bool want, int r, uint16_t *list, int *counter) {
+  const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
+  if (!m) return;
+  int base = 0;
+  const int lane = threadIdx.x & 31;
+  if (lane == __ffs(m) - 1) base = atomicAdd(counter, __popc(m));
+  base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
+  if (want) list[base + __popc(m & lanemask_lt())] = (uint16_t)r;
+}
+
+// Returns the number of live ray-steps taken by this lane.  `wvals` is the
+// warp's evaluation-stack memory viewed as floats (tail mode scratch).
+__device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &C, const RecSrc &src, const SubInfo &inf,
+                              const uint32_t *view, const uint2 *ops, const int *lvl_off, const uint16_t *alive_in,
+                              int n_in, int *q_head, uint16_t *alive_out, int *n_out, uint16_t *hits, int &n_hits,
+                              float2 *stk_lane, float *wvals, int vals_cap, unsigned long long *dbg) {
+  long long d_ncyc = 0, d_tcyc = 0;
+  int d_nit = 0, d_tev = 0;
+  const int lane = threadIdx.x & 31;
+  const float eps = M.tp->eps;
+  const float z_begin = inf.z_begin, z_end = inf.z_end;
+  int ray[kR];
+  float z[kR], d[kR][3], inv_ld[kR];
+  uint32_t steps[kR];
+#pragma unroll
+  for (int s = 0; s < kR; ++s) { ray[s] = -1; z[s] = 0.f; inv_ld[s] = 0.f; steps[s] = 0; d[s][0] = d[s][1] = d[s][2] = 0.f; }
+  bool drained = false;
+  uint32_t live_steps = 0;
+  SmemStack2 stk{stk_lane};
+  // Tail mode pays one parallel pass per remaining ray instead of one
+  // lockstep pass over the whole view for all rays.
+  const bool tail_ok = inf.n_lvl > 0 && inf.n_view <= vals_cap;
+  const int tail_cost = (inf.n_prim + 31) / 32 + 2 * inf.n_lvl + 2;
+
+  // One step of slot s with field value fs: hit / leave the subfrustum /
+  // step cap / advance.  Records hits and hand-overs in shared memory.
+  auto step_slot = [&](int s, float fs, bool &hit, bool &exit) {
+    hit = exit = false;
+    if (ray[s] < 0) return;
+    ++steps[s];
+    ++live_steps;
+    if (fs <= eps) {
+      hit = true;
+      C.ray_z[ray[s]] = z[s];
+      C.ray_st[ray[s]] = steps[s] | (R_HIT << 24);
+      return;
+    }
+    z[s] += fs * inv_ld[s];   // sphere-tracing step f / (L |d|)
+    if (z[s] >= z_end) {
+      exit = true;
+      C.ray_z[ray[s]] = z_end;
+      C.ray_st[ray[s]] = steps[s];
+    } else if ((int)steps[s] >= M.tp->max_steps) {
+      C.ray_st[ray[s]] = steps[s] | (R_UNCONV << 24);
+      write_miss(M, ray[s], steps[s], 2);
+      ray[s] = -1;
+    }
+  };
+  auto retire = [&](int s, bool hit, bool exit) {   // warp-collective
+    const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit);
+    if (hit) hits[n_hits + __popc(hm & lanemask_lt())] = (uint16_t)ray[s];
+    n_hits += __popc(hm);
+    append_rays(exit, ray[s], alive_out, n_out);
+    if (hit || exit) ray[s] = -1;
+  };
+
+  for (;;) {
+    // ---- refill empty slots from the tile's pending-ray list ----
+    uint32_t need_m[kR];
+    int n_need = 0;
+#pragma unroll
+    for (int s = 0; s < kR; ++s) {
+      need_m[s] = __ballot_sync(0xFFFFFFFFu, ray[s] < 0);
+      n_need += __popc(need_m[s]);
+    }
+    if (n_need && !drained) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(q_head, n_need);
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      if (base + n_need >= n_in) drained = true;
+      int off = 0;
+#pragma unroll
+      for (int s = 0; s < kR; ++s) {
+        const int rk = base + off + __popc(need_m[s] & lanemask_lt());
+        if (ray[s] < 0 && rk < n_in) {
+          ray[s] = alive_in[rk];
+          load_ray(M, C, ray[s], z_begin, z[s], steps[s], d[s], inv_ld[s]);
+        }
+        off += __popc(need_m[s]);
+      }
+    }
+    int n_live = 0;
+#pragma unroll
+    for (int s = 0; s < kR; ++s) n_live += __popc(__ballot_sync(0xFFFFFFFFu, ray[s] >= 0));
+    if (n_live == 0) break;
+
+    if (drained && tail_ok && n_live * tail_cost < inf.n_view) {
+      // ---- tail: evaluate each remaining ray with the whole warp ----
+#pragma unroll
+      for (int s = 0; s < kR; ++s) {
+        uint32_t m = __ballot_sync(0xFFFFFFFFu, ray[s] >= 0);
+        while (m) {
+          const int owner = __ffs(m) - 1;
+          m &= m - 1;
+          const float zz = __shfl_sync(0xFFFFFFFFu, z[s], owner);
+          const float p[3] = {M.cam->o[0] + zz * __shfl_sync(0xFFFFFFFFu, d[s][0], owner),
+                              M.cam->o[1] + zz * __shfl_sync(0xFFFFFFFFu, d[s][1], owner),
+                              M.cam->o[2] + zz * __shfl_sync(0xFFFFFFFFu, d[s][2], owner)};
+          const long long tt0 = clock64();
+          const float f = tail_eval(view, inf.n_view, ops, lvl_off, inf.n_lvl, src, p, wvals);
+          d_tcyc += clock64() - tt0;
+          ++d_tev;
+          bool hit = false, exit = false;
+          if (lane == owner) step_slot(s, f, hit, exit);
+          retire(s, hit, exit);
+        }
+      }
+      continue;
+    }
+
+    // ---- one lockstep field evaluation per slot (Algorithm 3 over the view) ----
+    float p[kR][3], f[kR];
+#pragma unroll
+    for (int s = 0; s < kR; ++s) {
+      p[s][0] = M.cam->o[0] + z[s] * d[s][0];
+      p[s][1] = M.cam->o[1] + z[s] * d[s][1];
+      p[s][2] = M.cam->o[2] + z[s] * d[s][2];
+    }
+    const long long nt0 = clock64();
+    eval_view_r<kR, float>(view, inf.n_view, src, p, f, stk);
+    d_ncyc += clock64() - nt0;
+    ++d_nit;
+#pragma unroll
+    for (int s = 0; s < kR; ++s) {
+      bool hit, exit;
+      step_slot(s, f[s], hit, exit);
+      retire(s, hit, exit);
+    }
+  }
+  if (dbg && lane == 0) {
+    atomicAdd(&dbg[0], (unsigned long long)d_nit);
+    atomicAdd(&dbg[1], (unsigned long long)d_tev);
+    atomicAdd(&dbg[2], (unsigned long long)d_ncyc);
+    atomicAdd(&dbg[3], (unsigned long long)d_tcyc);
+  }
+  return live_steps;
+}
+
+// Hit refinement: Newton steps along the ray on f_A (value + derivative along
+// d), then the gradient of f_A from three directional derivatives; a
+// crossing that lies past z_end is handed to the next subfrustum.
+__device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &C, const RecSrc &src, const SubInfo &inf,
+                              const uint32_t *view, const uint16_t *hits, int n_hits, uint16_t *alive_out,
+                              int *n_out, float2 *stk_lane, uint64_t &c_fin) {
+  const int lane = threadIdx.x & 31;
+  SmemStackD1 stk{stk_lane};
+  const DevCamera &cam = *M.cam;
+  for (int b = 0; b < n_hits; b += 32) {
+    const int idx = b + lane;
+    const bool v = idx < n_hits;
+    const int r = v ? hits[idx] : 0;
+    float zz = v ? C.ray_z[r] : inf.z_begin;
+    float d[3];
+    pixel_ray(cam, M.x0 + r % M.tw, M.y0 + r / M.tw, d);
+    const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const float lim = M.tp->newton_clamp / dn;
+    bool beyond = false;
+    for (int it = 0; it < M.tp->newton_iters; ++it) {
+      Dual<1> pd[1][3], fd[1];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { pd[0][k].v = cam.o[k] + zz * d[k]; pd[0][k].g[0] = d[k]; }
+      eval_view_r<1, Dual<1>>(view, inf.n_view, src, pd, fd, stk);
+      beyond = false;
+      if (fd[0].g[0] != 0.f && isfinite(fd[0].v)) {
+        float step = -fd[0].v / fd[0].g[0];
+        step = fminf(fmaxf(step, -lim), lim);
+        beyond = zz + step > inf.z_end && fd[0].v > 0.f;
+        zz = fminf(fmaxf(zz + step, inf.z_begin), inf.z_end);
+      }
+    }
+    float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+      Dual<1> pd[1][3], fd[1];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) { pd[0][j].v = cam.o[j] + zz * d[j]; pd[0][j].g[0] = j == k ? 1.f : 0.f; }
+      eval_view_r<1, Dual<1>>(view, inf.n_view, src, pd, fd, stk);
+      g[0] = k == 0 ? fd[0].g[0] : g[0];
+      g[1] = k == 1 ? fd[0].g[0] : g[1];
+      g[2] = k == 2 ? fd[0].g[0] : g[2];
+    }
+    const bool back = v && beyond;
+    if (back) {
+      C.ray_z[r] = inf.z_end;
+      C.ray_st[r] = C.ray_st[r] & 0xFFFFFFu;
+    }
+    append_rays(back, r, alive_out, n_out);
+    if (v && !beyond) {
+      const float gn = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+      const float ig = gn > 0.f ? 1.f / gn : 0.f;
+      const size_t o = (size_t)(M.y0 + r / M.tw) * cam.W + (M.x0 + r % M.tw);
+      M.out->depth[o] = zz * dn;
+      M.out->normal[3 * o] = g[0] * ig;
+      M.out->normal[3 * o + 1] = g[1] * ig;
+      M.out->normal[3 * o + 2] = g[2] * ig;
+      M.out->evals[o] = C.ray_st[r] & 0xFFFFFFu;
+      M.out->flags[o] = 1;
+      c_fin += (uint64_t)M.tp->newton_iters + 3;
+    }
+  }
+}
+
 // ---- the tracing kernel ----------------------------------------------------------
 __global__ void __launch_bounds__(kWarps * 32)
 k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_item;
+  __shared__ SubInfo s_info[2];
+  __shared__ int s_qhead[3], s_nctr[3];
+  __shared__ uint32_t s_steps;
+  __shared__ unsigned long long s_dbg[8];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const size_t per_warp = smem_per_warp(L);
-  const uint32_t gwarp = blockIdx.x * kWarps + warp;
-  WarpWork W = carve(smem + per_warp * warp, L, L.g_work ? L.g_work + (size_t)gwarp * L.g_work_words : nullptr);
-  SmemStack vstk{W.stk + lane};
+  const CtaWork C = carve(smem, L, L.g_work ? L.g_work + (size_t)blockIdx.x * L.g_work_words : nullptr);
+  float2 *stk_lane = C.stk + (size_t)warp * L.stack_slots * 32 + lane;
+  float *wvals = reinterpret_cast<float *>(C.stk + (size_t)warp * L.stack_slots * 32);
+  uint16_t *my_hits = C.hits + (size_t)warp * L.max_tile_rays;
 
   uint64_t c_steps = 0, c_prim = 0, c_op = 0, c_flops = 0, c_sub = 0, c_fin = 0;
   uint32_t c_err = 0;
 
   for (;;) {
-    uint32_t item = 0;
-    if (lane == 0) item = atomicAdd(L.item_counter, 1u);
-    item = __shfl_sync(0xFFFFFFFFu, item, 0);
+    if (threadIdx.x == 0) s_item = atomicAdd(L.item_counter, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
     if (item >= L.n_items) break;
     const int jb = find_job_tile(jobs, n_jobs, item);
     const Job &job = jobs[jb];
     const DevScene &sc = job.sc;
-    const DevCamera &cam = job.cam;
-    const TraceParams &tp = job.tp;
     const uint32_t tile = item - job.tile_base;
     const int T = job.tl.tile;
     const int tx = (int)(tile % (uint32_t)job.tl.tiles_x), ty = (int)(tile / (uint32_t)job.tl.tiles_x);
-    const int x0 = tx * T, y0 = ty * T;
-    const int tw = min(T, cam.W - x0), th = min(T, cam.H - y0);
-    const int nr = tw * th;
+    MarchCtx M;
+    M.cam = &job.cam;
+    M.tp = &job.tp;
+    M.out = &job.out;
+    M.x0 = tx * T;
+    M.y0 = ty * T;
+    M.tw = min(T, job.cam.W - M.x0);
+    const int th = min(T, job.cam.H - M.y0);
+    const int nr = M.tw * th;
     const uint32_t lbeg = job.tl.offsets[tile], len = job.tl.offsets[tile + 1] - lbeg;
     const float *zin_l = job.tl.z_in + lbeg;
     const float *zout_l = job.tl.z_out + lbeg;
     const uint32_t *prim_l = job.tl.prim + lbeg;
+    const long long t_tile0 = clock64();
+    long long t_prep = 0, t_march = 0, t_fin = 0;
+    uint32_t s_sub = 0, s_maxview = 0;
 
-    for (int r = lane; r < nr; r += 32) {
-      W.ray_z[r] = 0.f;
-      W.ray_st[r] = 0u;
-      W.alive[r] = (uint16_t)r;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      C.ray_z[r] = 0.f;
+      C.ray_st[r] = 0u;
+      pick(C.alive, 0)[r] = (uint16_t)r;
     }
-    int n_alive = nr;
-    uint32_t next = 0;
-    int n_act = 0, cur = 0;
-    float z_end = 0.f, maxze = -INFINITY;
-    __syncwarp();
-
-    while (n_alive > 0) {
-      // ---- discard active primitives with z_e <= z_end (Sec. 8) ----
-      {
-        int kept = 0;
-        float mz = -INFINITY;
-        for (int b = 0; b < n_act; b += 32) {
-          const int i = b + lane;
-          const bool v = i < n_act;
-          const float ze = v ? W.act_ze[cur][i] : -INFINITY;
-          const uint32_t ad = v ? W.act[cur][i] : 0u;
-          const bool keep = v && ze > z_end;
-          const uint32_t km = __ballot_sync(0xFFFFFFFFu, keep);
-          if (keep) {
-            const int dst = kept + __popc(km & lanemask_lt());
-            W.act[cur ^ 1][dst] = ad;
-            W.act_ze[cur ^ 1][dst] = ze;
-            mz = fmaxf(mz, ze);
-          }
-          kept += __popc(km);
-        }
-        n_act = kept;
-        cur ^= 1;
-        maxze = warp_max(mz);
-        __syncwarp();
+    if (threadIdx.x == 0) {
+      s_nctr[0] = nr; s_nctr[1] = 0; s_nctr[2] = 0;
+      s_qhead[0] = 0; s_qhead[1] = 0; s_qhead[2] = 0;
+      s_steps = 0u;
+      for (int i = 0; i < 8; ++i) s_dbg[i] = 0ull;
+    }
+    SegState sg;
+    sg.next = 0; sg.n_act = 0; sg.cur = 0; sg.z_end = 0.f; sg.maxze = -INFINITY;
+    if (warp == 0) {
+      const long long t0 = clock64();
+      prepare_sub(sg, C, sc, job.tp, zin_l, zout_l, prim_l, len, 0, L.stack_slots, L.dc_words, &s_info[0]);
+      t_prep += clock64() - t0;
+    }
+    __syncthreads();
+    int n_pending = nr;
+    int k = 0;
+    for (;; ++k) {
+      const SubInfo inf = s_info[k & 1];
+      if (inf.done || inf.err || n_pending == 0) {
+        if (inf.err) c_err |= (uint32_t)inf.err;
+        break;
       }
-      if (n_act == 0 && next >= len) break;  // no primitive left: remaining rays miss
-      // ---- fetch new primitives of interest (four conditions of Sec. 8) ----
-      float z_begin = z_end;
-      int take = 0;
-      if (next < len) {
-        z_begin = fmaxf(z_end, __ldg(zin_l + next));
-        const uint32_t c = next + (uint32_t)lane;
-        const bool valid = lane < tp.max_new && c < len;
-        const float zb = valid ? __ldg(zin_l + c) : INFINITY;
-        const float ze = valid ? __ldg(zout_l + c) : -INFINITY;
-        const uint32_t pa = valid ? __ldg(prim_l + c) : 0xFFFFFFFFu;
-        // exclusive running max of exit depths (including the active set)
-        float run = ze;
+      const int rd = k % 3, wr = (k + 1) % 3, rs = (k + 2) % 3;
+      const uint16_t *alive_in = pick(C.alive, k & 1);
+      uint16_t *alive_out = pick(C.alive, (k + 1) & 1);
+      if (threadIdx.x == 0) { s_nctr[rs] = 0; s_qhead[rs] = 0; }
+      if (warp == 0) {
+        // The next subfrustum's view is built while the other warps march.
+        const long long t0 = clock64();
+        prepare_sub(sg, C, sc, job.tp, zin_l, zout_l, prim_l, len, (k + 1) & 1, L.stack_slots, L.dc_words,
+                    &s_info[(k + 1) & 1]);
+        t_prep += clock64() - t0;
+        c_sub += 1;
+        s_sub += 1;
+        s_maxview = max(s_maxview, (uint32_t)inf.n_view);
+      }
+      if (inf.root_used) {
+        const long long t0 = clock64();
+        int n_hits = 0;
+        const RecSrc src{sc.rec, pick(C.dc, k & 1)};
+        const uint32_t ls = march_sub(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
+                                      n_pending, &s_qhead[rd], alive_out, &s_nctr[wr], my_hits, n_hits, stk_lane,
+                                      wvals, 2 * L.stack_slots * 32, L.tile_stats ? s_dbg : nullptr);
+        const long long t1 = clock64();
+        c_steps += ls;
+        c_prim += (uint64_t)ls * inf.n_prim;
+        c_op += (uint64_t)ls * inf.n_op;
+        c_flops += (uint64_t)ls * (inf.flops + kFlopsStep);
+        finalize_hits(M, C, src, inf, pick(C.view, k & 1), my_hits, n_hits, alive_out, &s_nctr[wr], stk_lane, c_fin);
+        if (L.tile_stats && lane == 0) {
+          atomicAdd(&s_dbg[4], (unsigned long long)(clock64() - t1));
+          if (warp == 0) { atomicAdd(&s_dbg[5], (unsigned long long)inf.n_view); atomicAdd(&s_dbg[6], (unsigned long long)inf.n_lvl); }
+        }
+        if (warp == 0) {
+          t_march += t1 - t0;
+          t_fin += clock64() - t1;
+        }
+        if (L.tile_stats) {
+          uint32_t w = ls;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          float y = __shfl_up_sync(0xFFFFFFFFu, run, o);
-          if (lane >= o) run = fmaxf(run, y);
+          for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xFFFFFFFFu, w, o);
+          if (lane == 0 && w) atomicAdd(&s_steps, w);
         }
-        float excl = __shfl_up_sync(0xFFFFFFFFu, run, 1);
-        excl = lane == 0 ? maxze : fmaxf(excl, maxze);
-        const bool ok = valid && ((lane == 0 && n_act == 0) ||
-                                  (zb <= excl && zb - z_begin < tp.depth_slab));
-        const uint32_t fail = __ballot_sync(0xFFFFFFFFu, !ok);
-        take = fail ? __ffs(fail) - 1 : 32;
-        const bool taken = lane < take;
-        maxze = warp_max(taken ? fmaxf(ze, maxze) : maxze);
-        // ---- sorted merge by node address (Algorithm 1 needs address order) ----
-        int rank_new = 0;
-        for (int j = 0; j < take; ++j) {
-          const uint32_t o = __shfl_sync(0xFFFFFFFFu, pa, j);
-          rank_new += (o < pa) ? 1 : 0;
-        }
-        const uint32_t *A = W.act[cur];
-        const float *AZ = W.act_ze[cur];
-        uint32_t *B = W.act[cur ^ 1];
-        float *BZ = W.act_ze[cur ^ 1];
-        if (taken) {
-          int lo = 0, hi = n_act;  // number of active addresses < pa
-          while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (A[mid] < pa) lo = mid + 1; else hi = mid;
-          }
-          B[rank_new + lo] = pa;
-          BZ[rank_new + lo] = ze;
-        }
-        for (int b = 0; b < n_act; b += 32) {
-          const int i = b + lane;
-          uint32_t ad = i < n_act ? A[i] : 0xFFFFFFFFu;
-          int before = 0;
-          for (int j = 0; j < take; ++j) {
-            const uint32_t o = __shfl_sync(0xFFFFFFFFu, pa, j);
-            before += (o < ad) ? 1 : 0;
-          }
-          if (i < n_act) {
-            B[i + before] = ad;
-            BZ[i + before] = AZ[i];
-          }
-        }
-        n_act += take;
-        cur ^= 1;
-        next += (uint32_t)take;
+      } else {
+        // f_A = +inf in this subfrustum: no crossing, every pending ray moves on.
+        for (int i = threadIdx.x; i < n_pending; i += blockDim.x) alive_out[i] = alive_in[i];
+        if (threadIdx.x == 0) s_nctr[wr] = n_pending;
       }
-      z_end = next < len ? fminf(__ldg(zin_l + next), maxze) : maxze;
-      __syncwarp();
-
-      // ---- pruned view (Algorithm 1), one lane ----
-      ViewInfo vi;
-      if (lane == 0) vi = build_view(sc, W.act[cur], n_act, W.view, W.bstk, L.stack_slots);
-      vi.n_view = __shfl_sync(0xFFFFFFFFu, vi.n_view, 0);
-      vi.root_used = __shfl_sync(0xFFFFFFFFu, vi.root_used, 0);
-      vi.n_prim = __shfl_sync(0xFFFFFFFFu, vi.n_prim, 0);
-      vi.n_op = __shfl_sync(0xFFFFFFFFu, vi.n_op, 0);
-      vi.flops = __shfl_sync(0xFFFFFFFFu, vi.flops, 0);
-      vi.err = __shfl_sync(0xFFFFFFFFu, vi.err, 0);
-      __syncwarp();
-      c_sub += 1;
-      if (vi.err) { c_err |= (uint32_t)vi.err; break; }
-      if (!vi.root_used) continue;  // f_A = +inf: no crossing in this subfrustum
-
-      // ---- synchronized sphere tracing of [z_begin, z_end] with ray refill ----
-      int head = 0;
-      int ray = -1;
-      float z = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, inv_ld = 0.f;
-      uint32_t steps = 0;
-      uint32_t live_steps = 0;
-      int n_hits = 0;
-      const float eps = tp.eps;
-      for (;;) {
-        const uint32_t need = __ballot_sync(0xFFFFFFFFu, ray < 0);
-        if (need && head < n_alive) {
-          const int rk = __popc(need & lanemask_lt());
-          if (ray < 0 && head + rk < n_alive) {
-            ray = W.alive[head + rk];
-            z = fmaxf(W.ray_z[ray], z_begin);
-            steps = W.ray_st[ray] & 0xFFFFFFu;
-            float d[3];
-            pixel_ray(cam, x0 + ray % tw, y0 + ray / tw, d);
-            dx = d[0]; dy = d[1]; dz = d[2];
-            inv_ld = 1.0f / (tp.lipschitz * sqrtf(dx * dx + dy * dy + dz * dz));
-          }
-          head = min(n_alive, head + __popc(need));
-        }
-        const bool live = ray >= 0;
-        if (!__any_sync(0xFFFFFFFFu, live)) break;
-        const float p[3] = {cam.o[0] + z * dx, cam.o[1] + z * dy, cam.o[2] + z * dz};
-        const float f = eval_view<float>(W.view, vi.n_view, sc.rec, p, vstk);
-        bool hit = false;
-        if (live) {
-          ++steps;
-          ++live_steps;
-          if (f <= eps) {
-            hit = true;
-          } else {
-            z += f * inv_ld;
-            if (z >= z_end) {
-              W.ray_z[ray] = z_end;
-              W.ray_st[ray] = steps;
-              ray = -1;
-            } else if ((int)steps >= tp.max_steps) {
-              W.ray_st[ray] = steps | (R_UNCONV << 24);
-              const int px = x0 + ray % tw, py = y0 + ray / tw;
-              const size_t o = (size_t)py * cam.W + px;
-              job.out.depth[o] = INFINITY;
-              job.out.normal[3 * o] = 0.f; job.out.normal[3 * o + 1] = 0.f; job.out.normal[3 * o + 2] = 0.f;
-              job.out.evals[o] = steps;
-              job.out.flags[o] = 2;
-              ray = -1;
-            }
-          }
-        }
-        const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit);
-        if (hit) {
-          W.hits[n_hits + __popc(hm & lanemask_lt())] = (uint16_t)ray;
-          W.ray_z[ray] = z;
-          W.ray_st[ray] = steps | (R_HIT << 24);
-          ray = -1;
-        }
-        n_hits += __popc(hm);
-      }
-      c_steps += live_steps;
-      c_prim += (uint64_t)live_steps * vi.n_prim;
-      c_op += (uint64_t)live_steps * vi.n_op;
-      c_flops += (uint64_t)live_steps * (vi.flops + kFlopsStep);
-      __syncwarp();
-
-      // ---- hit refinement: Newton on the ray, normal = grad f_A ----
-      for (int b = 0; b < n_hits; b += 32) {
-        const int idx = b + lane;
-        const bool v = idx < n_hits;
-        const int r = v ? W.hits[idx] : 0;
-        float zz = v ? W.ray_z[r] : z_begin;
-        float d[3];
-        pixel_ray(cam, x0 + r % tw, y0 + r / tw, d);
-        const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const float lim = tp.newton_clamp / dn;
-        bool beyond = false;  // the crossing lies past z_end: not this subfrustum's
-        for (int it = 0; it < tp.newton_iters; ++it) {
-          Dual<1> pd[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) { pd[k].v = cam.o[k] + zz * d[k]; pd[k].g[0] = d[k]; }
-          LocalStack<Dual<1>> ls;
-          const Dual<1> fd = eval_view<Dual<1>>(W.view, vi.n_view, sc.rec, pd, ls);
-          beyond = false;
-          if (fd.g[0] != 0.f && isfinite(fd.v)) {
-            float step = -fd.v / fd.g[0];
-            step = fminf(fmaxf(step, -lim), lim);
-            beyond = zz + step > z_end && fd.v > 0.f;
-            zz = fminf(fmaxf(zz + step, z_begin), z_end);
-          }
-        }
-        Dual<3> pg[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          pg[k].v = cam.o[k] + zz * d[k];
-          pg[k].g[0] = k == 0 ? 1.f : 0.f;
-          pg[k].g[1] = k == 1 ? 1.f : 0.f;
-          pg[k].g[2] = k == 2 ? 1.f : 0.f;
-        }
-        LocalStack<Dual<3>> ls3;
-        const Dual<3> fg = eval_view<Dual<3>>(W.view, vi.n_view, sc.rec, pg, ls3);
-        if (v && beyond) {
-          // Hand the ray back: the next subfrustum starts at z_end and owns
-          // the crossing.
-          W.ray_z[r] = z_end;
-          W.ray_st[r] = W.ray_st[r] & 0xFFFFFFu;
-        } else if (v) {
-          const float gn = sqrtf(fg.g[0] * fg.g[0] + fg.g[1] * fg.g[1] + fg.g[2] * fg.g[2]);
-          const float ig = gn > 0.f ? 1.f / gn : 0.f;
-          const int px = x0 + r % tw, py = y0 + r / tw;
-          const size_t o = (size_t)py * cam.W + px;
-          job.out.depth[o] = zz * dn;
-          job.out.normal[3 * o] = fg.g[0] * ig;
-          job.out.normal[3 * o + 1] = fg.g[1] * ig;
-          job.out.normal[3 * o + 2] = fg.g[2] * ig;
-          job.out.evals[o] = W.ray_st[r] & 0xFFFFFFu;
-          job.out.flags[o] = 1;
-          c_fin += (uint64_t)tp.newton_iters + 1;
-        }
-      }
-      __syncwarp();
-
-      // ---- drop finished rays from the pending list ----
-      {
-        int kept = 0;
-        for (int b = 0; b < n_alive; b += 32) {
-          const int i = b + lane;
-          const int r = i < n_alive ? W.alive[i] : 0;
-          const bool keep = i < n_alive && (W.ray_st[r] >> 24) == R_ALIVE;
-          const uint32_t km = __ballot_sync(0xFFFFFFFFu, keep);
-          __syncwarp();
-          if (keep) W.alive[kept + __popc(km & lanemask_lt())] = (uint16_t)r;
-          kept += __popc(km);
-          __syncwarp();
-        }
-        n_alive = kept;
-      }
+      __syncthreads();
+      n_pending = s_nctr[wr];
     }
     // ---- rays still pending when the list is exhausted: misses ----
-    for (int i = lane; i < n_alive; i += 32) {
-      const int r = W.alive[i];
-      const int px = x0 + r % tw, py = y0 + r / tw;
-      const size_t o = (size_t)py * cam.W + px;
-      job.out.depth[o] = INFINITY;
-      job.out.normal[3 * o] = 0.f; job.out.normal[3 * o + 1] = 0.f; job.out.normal[3 * o + 2] = 0.f;
-      job.out.evals[o] = W.ray_st[r] & 0xFFFFFFu;
-      job.out.flags[o] = 0;
+    for (int i = threadIdx.x; i < n_pending; i += blockDim.x) {
+      const int r = pick(C.alive, k & 1)[i];
+      write_miss(M, r, C.ray_st[r] & 0xFFFFFFu, 0);
     }
-    __syncwarp();
+    __syncthreads();
+    if (L.tile_stats && threadIdx.x == 0) {
+      uint32_t *ts = L.tile_stats + (size_t)item * 16;
+      ts[8] = (uint32_t)s_dbg[0];
+      ts[9] = (uint32_t)s_dbg[1];
+      ts[10] = (uint32_t)(s_dbg[2] >> 4);
+      ts[11] = (uint32_t)(s_dbg[3] >> 4);
+      ts[12] = (uint32_t)(s_dbg[4] >> 4);
+      ts[13] = (uint32_t)s_dbg[5];
+      ts[14] = (uint32_t)s_dbg[6];
+      ts[15] = 0;
+      ts[0] = (uint32_t)((clock64() - t_tile0) >> 4);
+      ts[1] = (uint32_t)(t_prep >> 4);
+      ts[2] = (uint32_t)(t_march >> 4);
+      ts[3] = (uint32_t)(t_fin >> 4);
+      ts[4] = s_sub;
+      ts[5] = s_steps;
+      ts[6] = s_maxview;
+      ts[7] = len;
+    }
+    __syncthreads();
   }
 
   if (L.counters) {
@@ -505,7 +887,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       atomicAdd((unsigned long long *)&L.counters[1], (unsigned long long)c_prim);
       atomicAdd((unsigned long long *)&L.counters[2], (unsigned long long)c_op);
       atomicAdd((unsigned long long *)&L.counters[3], (unsigned long long)c_flops);
-      atomicAdd((unsigned long long *)&L.counters[4], (unsigned long long)c_sub);
+      if (warp == 0) atomicAdd((unsigned long long *)&L.counters[4], (unsigned long long)c_sub);
       atomicAdd((unsigned long long *)&L.counters[6], (unsigned long long)c_fin);
       if (c_err) atomicOr((unsigned long long *)&L.counters[7], (unsigned long long)c_err);
     }
@@ -538,7 +920,7 @@ __global__ void k_eval_view(DevScene sc, const uint32_t *view, const int32_t *in
   if (!grad) {
     const float p[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
     LocalStack<float> ls;
-    f[i] = eval_view<float>(view, n_view, sc.rec, p, ls);
+    f[i] = eval_view<float>(view, n_view, RecSrc{sc.rec, nullptr}, p, ls);
   } else {
     Dual<3> p[3];
     for (int k = 0; k < 3; ++k) {
@@ -546,7 +928,7 @@ __global__ void k_eval_view(DevScene sc, const uint32_t *view, const int32_t *in
       p[k].g[0] = k == 0; p[k].g[1] = k == 1; p[k].g[2] = k == 2;
     }
     LocalStack<Dual<3>> ls;
-    Dual<3> r = eval_view<Dual<3>>(view, n_view, sc.rec, p, ls);
+    Dual<3> r = eval_view<Dual<3>>(view, n_view, RecSrc{sc.rec, nullptr}, p, ls);
     f[i] = r.v;
     grad[3 * i] = r.g[0]; grad[3 * i + 1] = r.g[1]; grad[3 * i + 2] = r.g[2];
   }
@@ -563,7 +945,7 @@ void launch_eval_view(const DevScene &sc, const uint32_t *view, const int32_t *i
 }
 
 cudaError_t trace_launch(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s) {
-  const size_t smem = trace_smem_per_warp(L) * kWarps;
+  const size_t smem = smem_per_cta(L);
   cudaError_t e = cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -575,7 +957,7 @@ cudaError_t trace_launch(const Job *jobs, int n_jobs, const TraceLaunch &L, int 
 }
 
 int trace_ctas_per_sm(const TraceLaunch &L) {
-  const size_t smem = trace_smem_per_warp(L) * kWarps;
+  const size_t smem = smem_per_cta(L);
   if (cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   int per_sm = 0;

@@ -52,7 +52,7 @@ class st_trace_opts(C.Structure):
     _fields_ = [("eps", C.c_float), ("lipschitz", C.c_float), ("max_steps", C.c_int32),
                 ("step_mode", C.c_int32), ("depth_slab_frac", C.c_float),
                 ("max_new_per_turn", C.c_int32), ("newton_iters", C.c_int32),
-                ("newton_clamp", C.c_float), ("mlp", C.c_void_p)]
+                ("newton_clamp", C.c_float), ("mlp", C.c_void_p), ("tile_stats", C.c_void_p)]
 
 
 _P = C.c_void_p
@@ -124,9 +124,13 @@ def make_camera(cam) -> st_camera:
 
 
 def make_opts(eps=1e-4, lipschitz=1.45, max_steps=256, step_mode=ST_STEP_PLAIN, depth_slab_frac=0.05,
-              max_new_per_turn=6, newton_iters=4, newton_clamp=0.0, mlp=None) -> st_trace_opts:
-    return st_trace_opts(eps, lipschitz, max_steps, step_mode, depth_slab_frac, max_new_per_turn,
-                         newton_iters, newton_clamp, mlp)
+              max_new_per_turn=6, newton_iters=4, newton_clamp=0.0, mlp=None, tile_stats=None) -> st_trace_opts:
+    o = st_trace_opts(eps, lipschitz, max_steps, step_mode, depth_slab_frac, max_new_per_turn,
+                      newton_iters, newton_clamp, mlp, None)
+    if tile_stats is not None:
+        o.tile_stats = tile_stats.data_ptr()
+        o._keep = tile_stats
+    return o
 
 
 # ---- entry points (same names as the C ABI) ----------------------------------------

@@ -42,7 +42,7 @@ def test_view_matches_definition(stlib, orc, cuda, seed):
             assert info[0] == len(addr) and info[3] == m
             assert info[1] == ru
             v = view.cpu().numpy().view(np.uint32)
-            codes = v >> 27
+            codes = v >> 28
             assert np.array_equal(vaddr.cpu().numpy()[:len(addr)], addr)
             assert [CODE_TO_OP[int(c)] for c in codes] == opc.tolist()
             # kept operators keep their own kind
