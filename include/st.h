@@ -209,6 +209,33 @@ int st_trace(st_scene *scene, const st_camera *cam, const st_tiles *tiles,
 int st_tiles_copy(const st_tiles *tiles, uint32_t *offsets, float *z_in, float *z_out, uint32_t *prim,
                   void *stream);
 
+/* ---- tracing without device allocation ----------------------------------------
+ * st_trace_noalloc: same arguments, outputs and results as st_trace, but the
+ * call itself allocates no device memory (no cudaMalloc or cudaFree and no
+ * allocating library routine).  It is meant for callers that cannot allocate
+ * at draw time: render loops that run under a fixed memory budget or must
+ * not stall on an allocation (cudaMalloc can synchronise the device), and
+ * hosts whose device memory is owned by another allocator.  The paper has no
+ * counterpart to this call.
+ *
+ * Its scratch memory (the work-queue counter, the job record and, for long
+ * tile lists, the per-CTA work areas) is one fixed 32 MiB device array
+ * defined in the library; every device that loads the library holds it until
+ * the process exits (st_trace_noalloc_scratch_bytes() returns the size).  A
+ * launch whose work areas would not fit returns ST_ERR_CAPACITY with the
+ * needed size in st_last_error(); st_trace has no such limit.
+ *
+ * The first call on a device resolves the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call reuses the same array, which keeps the previous call's contents: the
+ * call clears what must start at zero, but two calls whose work overlaps on
+ * the GPU (different streams, or without ordering between them) race on the
+ * array and give undefined results. */
+int st_trace_noalloc(st_scene *scene, const st_camera *cam, const st_tiles *tiles,
+                     const st_trace_opts *opts, float *depth, float *normal, uint32_t *evals,
+                     uint8_t *flags, uint64_t *counters, void *stream);
+size_t st_trace_noalloc_scratch_bytes(void);
+
 /* ---- inspection of the hot-path steps ----------------------------------------
  * st_pruned_view: the pruned tree view of an active set, built on the device
  * by the same code st_trace uses (Algorithm 1 with fast ancestor pointers,

@@ -109,6 +109,14 @@ static DevScene dev_scene(const st_scene *s) {
   return d;
 }
 
+// Read-only facts of a scene for entry points defined in other files.
+void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, int *n_sm) {
+  *sc = dev_scene(s);
+  *stack_depth = s->prep.stack_depth;
+  *diameter = s->prep.diameter;
+  *n_sm = s->n_sm;
+}
+
 static int check_camera(const st_camera *cam) {
   if (!cam || cam->width <= 0 || cam->height <= 0 || cam->width > 65535 || cam->height > 65535 ||
       !(cam->vfov_deg > 0.f && cam->vfov_deg < 180.f)) {

@@ -49,6 +49,7 @@ size_t trace_smem_per_warp(const TraceLaunch &L);
 uint32_t trace_work_words(const TraceLaunch &L);
 cudaError_t trace_launch(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s);
 int trace_warps_per_cta();
+int trace_ctas_per_sm(const TraceLaunch &L);
 void launch_pruned_view(const DevScene &sc, const uint32_t *act, int n, uint32_t *view, uint32_t *vaddr,
                         int32_t *info, uint32_t *bstk, int stack_cap, cudaStream_t s);
 void launch_eval_view(const DevScene &sc, const uint32_t *view, const int32_t *info, const float *pts, int npts,

@@ -1,0 +1,177 @@
+// st_noalloc.cu -- st_trace_noalloc: the tracing call without any device
+// allocation.  Its scratch memory (work-queue counter, the job record and,
+// for long tile lists, the per-CTA work areas) lives in one file-scope
+// device array of fixed size that every device loading the library keeps
+// until the process exits.
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "st_kernels.h"
+
+namespace st {
+void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, int *n_sm);
+}
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(32) << 20;   // 32 MiB
+constexpr size_t kCounterOff = 0;                     // uint32 work-queue counter
+constexpr size_t kJobOff = 256;                       // st::Job record
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_trace_scratch[kScratchBytes];
+
+std::mutex g_scratch_mu;
+unsigned char *g_scratch_addr[kMaxDevices] = {};
+
+// The host-side name of g_trace_scratch is not a device address: resolve it
+// once per device, with that device current.
+int scratch_for_current_device(unsigned char **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    st::set_error(std::string("st_trace_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+    return ST_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    st::set_error("st_trace_noalloc: device ordinal out of range");
+    return ST_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_trace_scratch);
+    if (e != cudaSuccess || !ptr) {
+      st::set_error(std::string("st_trace_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      return ST_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = static_cast<unsigned char *>(ptr);
+  }
+  *out = g_scratch_addr[dev];
+  return ST_OK;
+}
+
+// Writes the job record into the scratch array from the launch parameters
+// (no host staging buffer).
+__global__ void k_put_job(st::Job job, st::Job *dst) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dst = job;
+}
+
+}  // namespace
+
+#define NA_CK(call)                                                         \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) {                                                \
+      st::set_error(std::string("st_trace_noalloc: " #call ": ") + cudaGetErrorString(e_)); \
+      return ST_ERR_CUDA;                                                   \
+    }                                                                       \
+  } while (0)
+
+extern "C" size_t st_trace_noalloc_scratch_bytes(void) { return kScratchBytes; }
+
+extern "C" int st_trace_noalloc(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_trace_opts *opts,
+                                float *depth, float *normal, uint32_t *evals, uint8_t *flags, uint64_t *counters,
+                                void *stream) {
+  using namespace st;
+  if (!s || !cam || !tl || !depth || !normal || !evals || !flags) {
+    set_error("st_trace_noalloc: null argument");
+    return ST_ERR_INVALID;
+  }
+  if (cam->width <= 0 || cam->height <= 0 || cam->width > 65535 || cam->height > 65535 ||
+      !(cam->vfov_deg > 0.f && cam->vfov_deg < 180.f)) {
+    set_error("st_trace_noalloc: invalid camera");
+    return ST_ERR_INVALID;
+  }
+  if (tl->tile != 8 && tl->tile != 16 && tl->tile != 32) {
+    set_error("st_trace_noalloc: tile must be 8, 16 or 32");
+    return ST_ERR_INVALID;
+  }
+  const int tiles_x = (cam->width + tl->tile - 1) / tl->tile, tiles_y = (cam->height + tl->tile - 1) / tl->tile;
+  if (tl->tiles_x != tiles_x || tl->tiles_y != tiles_y) {
+    set_error("st_trace_noalloc: tile buffer does not match the camera");
+    return ST_ERR_INVALID;
+  }
+  st_trace_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.step_mode != ST_STEP_PLAIN) {
+    set_error("st_trace_noalloc: step mode not available");
+    return ST_ERR_INVALID;
+  }
+  unsigned char *scratch = nullptr;
+  int rc = scratch_for_current_device(&scratch);
+  if (rc != ST_OK) return rc;
+
+  Job job;
+  std::memset(&job, 0, sizeof(job));
+  int stack_depth = 0, n_sm = 1;
+  double diameter = 0;
+  scene_facts(s, &job.sc, &stack_depth, &diameter, &n_sm);
+  camera_basis(*cam, job.cam);
+  job.tl.tile = tl->tile;
+  job.tl.tiles_x = tl->tiles_x;
+  job.tl.tiles_y = tl->tiles_y;
+  job.tl.offsets = tl->offsets;
+  job.tl.z_in = tl->z_in;
+  job.tl.z_out = tl->z_out;
+  job.tl.prim = tl->prim;
+  job.out.depth = depth;
+  job.out.normal = normal;
+  job.out.evals = evals;
+  job.out.flags = flags;
+  TraceParams &tp = job.tp;
+  tp.eps = o.eps > 0.f ? o.eps : 1e-4f;
+  tp.lipschitz = o.lipschitz > 0.f ? o.lipschitz : 1.45f;
+  tp.max_steps = o.max_steps > 0 ? o.max_steps : 256;
+  tp.step_mode = o.step_mode;
+  const float frac = o.depth_slab_frac > 0.f ? o.depth_slab_frac : 0.05f;
+  tp.depth_slab = std::max(frac * (float)diameter, 1e-6f);
+  tp.max_new = o.max_new_per_turn > 0 ? std::min(o.max_new_per_turn, 32) : 6;
+  tp.newton_iters = o.newton_iters > 0 ? o.newton_iters : (o.newton_iters < 0 ? 0 : 4);
+  tp.newton_clamp = o.newton_clamp > 0.f ? o.newton_clamp : 64.f * tp.eps;
+  job.tile_base = 0;
+
+  TraceLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.max_tile_rays = tl->tile * tl->tile;
+  L.act_cap = (int)std::max<uint32_t>(tl->max_overlap, 1u);
+  L.view_cap = 2 * L.act_cap;
+  L.stack_slots = stack_depth + 2;
+  L.dc_words = 768;
+  L.n_items = (uint32_t)(tiles_x * tiles_y);
+  L.counters = counters;
+  L.tile_stats = o.tile_stats;
+  L.work_in_smem = 1;
+  if (trace_smem_per_warp(L) * 16 > 200 * 1024) L.work_in_smem = 0;
+
+  const size_t work_off = (kJobOff + sizeof(Job) + 255) & ~size_t(255);
+  if (!L.work_in_smem) {
+    const int per_sm = trace_ctas_per_sm(L);
+    if (per_sm < 1) {
+      set_error("st_trace_noalloc: no valid launch configuration");
+      return ST_ERR_INVALID;
+    }
+    L.g_work_words = trace_work_words(L);
+    const size_t need = (size_t)n_sm * per_sm * L.g_work_words * 4;
+    if (work_off + need > kScratchBytes) {
+      set_error("st_trace_noalloc: the per-CTA work areas for tile lists of " + std::to_string(tl->max_overlap) +
+                " entries need " + std::to_string(work_off + need) + " bytes, more than the 32 MiB static scratch; "
+                "use st_trace");
+      return ST_ERR_CAPACITY;
+    }
+    L.g_work = reinterpret_cast<uint32_t *>(scratch + work_off);
+  }
+  L.item_counter = reinterpret_cast<uint32_t *>(scratch + kCounterOff);
+  Job *job_dev = reinterpret_cast<Job *>(scratch + kJobOff);
+
+  cudaStream_t st = (cudaStream_t)stream;
+  // The scratch keeps the previous call's contents: the queue counter must
+  // start at zero; the job record and work areas are fully rewritten.
+  NA_CK(cudaMemsetAsync(L.item_counter, 0, sizeof(uint32_t), st));
+  count_launch(), k_put_job<<<1, 32, 0, st>>>(job, job_dev);
+  NA_CK(cudaGetLastError());
+  NA_CK(trace_launch(job_dev, 1, L, n_sm, st));
+  return ST_OK;
+}

@@ -70,11 +70,14 @@ _lib.st_tiles_copy.argtypes = [C.POINTER(st_tiles), _P, _P, _P, _P, _P]
 _lib.st_pruned_view.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
 _lib.st_eval_pruned.argtypes = [_P, _P, _P, _P, C.c_int, _P, _P, _P]
 _lib.st_kernel_launches.restype = C.c_uint64
+_lib.st_trace_noalloc.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINTER(st_trace_opts),
+                                  _P, _P, _P, _P, _P, _P]
+_lib.st_trace_noalloc_scratch_bytes.restype = C.c_size_t
 _lib.st_prep_tree.argtypes = [C.POINTER(st_scene_desc), _P, _P, _P, _P]
 
 EXPORTED = ("st_scene_create", "st_scene_update_prims", "st_scene_addresses", "st_scene_destroy",
             "st_build_tiles", "st_trace", "st_tiles_copy", "st_pruned_view", "st_eval_pruned", "st_prep_tree", "st_last_error",
-            "st_version", "st_kernel_launches")
+            "st_version", "st_kernel_launches", "st_trace_noalloc", "st_trace_noalloc_scratch_bytes")
 
 
 def lib():
@@ -171,6 +174,19 @@ def st_trace(h, cam, tiles: st_tiles, opts: st_trace_opts | None, depth, normal,
     o = opts if opts is not None else make_opts()
     _check(_lib.st_trace(h, C.byref(c), C.byref(tiles), C.byref(o), _ptr(depth), _ptr(normal), _ptr(evals),
                          _ptr(flags), _ptr(counters), _stream(stream)), "st_trace")
+
+
+def st_trace_noalloc(h, cam, tiles: st_tiles, opts: st_trace_opts | None, depth, normal, evals, flags,
+                     counters=None, stream=None) -> None:
+    """st_trace without device allocation (fixed scratch array in the library)."""
+    c = make_camera(cam)
+    o = opts if opts is not None else make_opts()
+    _check(_lib.st_trace_noalloc(h, C.byref(c), C.byref(tiles), C.byref(o), _ptr(depth), _ptr(normal),
+                                 _ptr(evals), _ptr(flags), _ptr(counters), _stream(stream)), "st_trace_noalloc")
+
+
+def st_trace_noalloc_scratch_bytes() -> int:
+    return int(_lib.st_trace_noalloc_scratch_bytes())
 
 
 def st_pruned_view(h, act, view, view_addr, info, stream=None) -> None:
