@@ -115,6 +115,12 @@ typedef struct {
 /* Tracing options.  Zero-initialised fields take the defaults in brackets. */
 #define ST_STEP_PLAIN 0        /* z += f / (L |d|)                          */
 #define ST_STEP_LEARNED 1      /* MLP over-relaxation, verified (see below) */
+#define ST_STEP_OVERRELAX 2    /* z += omega f / (L |d|), verified: a step whose
+                                  landing sphere does not overlap the previous
+                                  one is rejected, the ray returns to the
+                                  previous point, takes the plain step and
+                                  relaxes again once it has crossed the stored
+                                  landing sphere (Sec. 10)                 */
 typedef struct {
     float eps;              /* hit when f <= eps [1e-4]                    */
     float lipschitz;        /* L of the step f / L [1.45, Sec. 10]         */
@@ -131,12 +137,13 @@ typedef struct {
                                view build, [2] marching, [3] hit refinement
                                SM clock cycles / 16 (first warp); [4]
                                subfrustums; [5] tracing steps; [6] longest
-                               view; [7] A-buffer list length; summed over
-                               warps: [8] lockstep passes, [9] warp-wide
-                               single-point passes, [10] / [11] their cycles
-                               / 16, [12] refinement cycles / 16; [13] sum of
-                               view lengths, [14] sum of operator levels
+                               view; [7] A-buffer list length; [12]
+                               refinement cycles / 16 summed over warps;
+                               [13] sum of view lengths, [14] sum of
+                               operator levels; [8-11], [15] zero
                                (NULL = off)                                */
+    float omega;            /* relaxation factor of ST_STEP_OVERRELAX [1.7,
+                               Sec. 10]                                    */
 } st_trace_opts;
 
 /* Optional per-call counters (device pointer to 8 uint64, accumulated with

@@ -317,7 +317,10 @@ int st_trace(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_tra
   st_trace_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.step_mode != ST_STEP_PLAIN) { set_error("step mode not available"); return ST_ERR_INVALID; }
+  if (o.step_mode != ST_STEP_PLAIN && o.step_mode != ST_STEP_OVERRELAX) {
+    set_error("step mode not available");
+    return ST_ERR_INVALID;
+  }
   Job job;
   std::memset(&job, 0, sizeof(job));
   job.sc = dev_scene(s);
@@ -343,6 +346,7 @@ int st_trace(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_tra
   tp.max_new = o.max_new_per_turn > 0 ? std::min(o.max_new_per_turn, 32) : 6;
   tp.newton_iters = o.newton_iters > 0 ? o.newton_iters : (o.newton_iters < 0 ? 0 : 4);
   tp.newton_clamp = o.newton_clamp > 0.f ? o.newton_clamp : 64.f * tp.eps;
+  tp.omega = o.omega > 1.f ? std::min(o.omega, 2.f) : 1.7f;
   job.tile_base = 0;
   cudaStream_t st = (cudaStream_t)stream;
 
@@ -356,6 +360,7 @@ int st_trace(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_tra
   L.n_items = (uint32_t)(tiles_x * tiles_y);
   L.counters = counters;
   L.tile_stats = o.tile_stats;
+  L.step_mode = tp.step_mode;
   // Active set and view in shared memory when 16 warps per SM still fit.
   L.work_in_smem = 1;
   if (trace_smem_per_warp(L) * 16 > 200 * 1024) L.work_in_smem = 0;

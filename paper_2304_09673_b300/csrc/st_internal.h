@@ -91,6 +91,7 @@ struct DevOut {
 struct TraceParams {
   float eps, lipschitz, depth_slab, newton_clamp;
   int32_t max_steps, max_new, newton_iters, step_mode;
+  float omega;   // relaxation factor of ST_STEP_OVERRELAX
 };
 
 // One culling or tracing job (a scene seen by a camera).

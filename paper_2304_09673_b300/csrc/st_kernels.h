@@ -42,7 +42,8 @@ struct TraceLaunch {
   uint32_t n_items;        // total (job, tile) work items
   uint32_t *item_counter;  // zeroed before launch
   uint64_t *counters;      // optional ST_NUM_COUNTERS
-  uint32_t *tile_stats;    // optional [n_items][8] diagnostics
+  uint32_t *tile_stats;    // optional [n_items][16] diagnostics
+  int32_t step_mode;       // selects the kernel instantiation
 };
 
 size_t trace_smem_per_warp(const TraceLaunch &L);

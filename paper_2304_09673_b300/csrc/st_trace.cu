@@ -522,20 +522,32 @@ __device__ __forceinline__ void append_rays(bool want, int r, uint16_t *list, in
 
 // Returns the number of live ray-steps taken by this lane.  `wvals` is the
 // warp's evaluation-stack memory viewed as floats (tail mode scratch).
+template <int MODE>
 __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &C, const RecSrc &src, const SubInfo &inf,
                               const uint32_t *view, const uint2 *ops, const int *lvl_off, const uint16_t *alive_in,
                               int n_in, int *q_head, uint16_t *alive_out, int *n_out, uint16_t *hits, int &n_hits,
-                              float2 *stk_lane, float *wvals, int vals_cap, unsigned long long *dbg) {
-  long long d_ncyc = 0, d_tcyc = 0;
-  int d_nit = 0, d_tev = 0;
+                              float2 *stk_lane, float *wvals, int vals_cap, uint64_t &c_rej) {
+  uint32_t rejected = 0;
   const int lane = threadIdx.x & 31;
   const float eps = M.tp->eps;
   const float z_begin = inf.z_begin, z_end = inf.z_end;
   int ray[kR];
   float z[kR], d[kR][3], inv_ld[kR];
   uint32_t steps[kR];
+  // Relaxed stepping state (Sec. 10 "overrelaxed sphere tracing"): the
+  // surface-free radius rp of the previous point, the last step length dzp
+  // (0: no previous point in this subfrustum; a plain step has dzp = rp and
+  // can never be rejected), the plain-step position zf = previous point + rp
+  // to fall back to, and a stored surface-free sphere (zs, rs; rs < 0:
+  // none); relaxation is off from a rejected step until that sphere is crossed.
+  float rp[kR], dzp[kR], zf[kR], zs[kR], rs[kR];
+  uint32_t relax_off = 0u;
 #pragma unroll
-  for (int s = 0; s < kR; ++s) { ray[s] = -1; z[s] = 0.f; inv_ld[s] = 0.f; steps[s] = 0; d[s][0] = d[s][1] = d[s][2] = 0.f; }
+  for (int s = 0; s < kR; ++s) {
+    ray[s] = -1; z[s] = 0.f; inv_ld[s] = 0.f; steps[s] = 0; d[s][0] = d[s][1] = d[s][2] = 0.f;
+    rp[s] = dzp[s] = zf[s] = 0.f; zs[s] = 0.f; rs[s] = -1.f;
+  }
+  const float omega_c = MODE == ST_STEP_OVERRELAX ? M.tp->omega : 1.f;
   bool drained = false;
   uint32_t live_steps = 0;
   SmemStack2 stk{stk_lane};
@@ -546,18 +558,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
 
   // One step of slot s with field value fs: hit / leave the subfrustum /
   // step cap / advance.  Records hits and hand-overs in shared memory.
-  auto step_slot = [&](int s, float fs, bool &hit, bool &exit) {
-    hit = exit = false;
-    if (ray[s] < 0) return;
-    ++steps[s];
-    ++live_steps;
-    if (fs <= eps) {
-      hit = true;
-      C.ray_z[ray[s]] = z[s];
-      C.ray_st[ray[s]] = steps[s] | (R_HIT << 24);
-      return;
-    }
-    z[s] += fs * inv_ld[s];   // sphere-tracing step f / (L |d|)
+  auto leave_or_cap = [&](int s, bool &exit) {
     if (z[s] >= z_end) {
       exit = true;
       C.ray_z[ray[s]] = z_end;
@@ -567,6 +568,61 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       write_miss(M, ray[s], steps[s], 2);
       ray[s] = -1;
     }
+  };
+  // One step of slot s with field value fs and proposed relaxation factor
+  // om_prop: rejection test of the previous relaxed step, hit, reuse of a
+  // stored sphere, then the (possibly relaxed) step f / (L |d|) x omega.
+  auto step_slot = [&](int s, float fs, float om_prop, bool &hit, bool &exit) {
+    hit = exit = false;
+    if (ray[s] < 0) return;
+    ++steps[s];
+    ++live_steps;
+    const uint32_t bit = 1u << s;
+    const float r = fabsf(fs) * inv_ld[s];   // surface-free radius along the ray
+    if (MODE != ST_STEP_PLAIN && r + rp[s] < dzp[s]) {
+      // The unbounding spheres of the last two points do not overlap: the
+      // relaxed step may have skipped a crossing.  Keep the landing sphere,
+      // return to the previous point and take the plain step from there.
+      zs[s] = z[s];
+      rs[s] = r;
+      z[s] = zf[s];
+      dzp[s] = 0.f;
+      relax_off |= bit;
+      ++rejected;
+      if (z[s] >= zs[s] - rs[s]) {
+        z[s] = zs[s] + rs[s];
+        rs[s] = -1.f;
+        relax_off &= ~bit;
+      }
+      leave_or_cap(s, exit);
+      return;
+    }
+    if (fs <= eps) {
+      hit = true;
+      C.ray_z[ray[s]] = z[s];
+      C.ray_st[ray[s]] = steps[s] | (R_HIT << 24);
+      return;
+    }
+    if (MODE == ST_STEP_PLAIN) {
+      z[s] += r;
+      leave_or_cap(s, exit);
+      return;
+    }
+    float om = (relax_off & bit) ? 1.f : om_prop;
+    float dz = om * r;
+    if (om > 1.f && z[s] + dz >= z_end) { om = 1.f; dz = r; }   // relaxed steps never cross z_end
+    zf[s] = z[s] + r;
+    rp[s] = r;
+    dzp[s] = dz;
+    z[s] += dz;
+    if ((relax_off & bit) && rs[s] >= 0.f && z[s] >= zs[s] - rs[s]) {
+      // Plain stepping reached the stored surface-free sphere: cross it.
+      z[s] = fmaxf(z[s], zs[s] + rs[s]);
+      rs[s] = -1.f;
+      relax_off &= ~bit;
+      dzp[s] = 0.f;
+    }
+    leave_or_cap(s, exit);
   };
   auto retire = [&](int s, bool hit, bool exit) {   // warp-collective
     const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit);
@@ -597,6 +653,10 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         if (ray[s] < 0 && rk < n_in) {
           ray[s] = alive_in[rk];
           load_ray(M, C, ray[s], z_begin, z[s], steps[s], d[s], inv_ld[s]);
+          dzp[s] = 0.f;
+          rp[s] = 0.f;
+          rs[s] = -1.f;
+          relax_off &= ~(1u << s);
         }
         off += __popc(need_m[s]);
       }
@@ -618,12 +678,9 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
           const float p[3] = {M.cam->o[0] + zz * __shfl_sync(0xFFFFFFFFu, d[s][0], owner),
                               M.cam->o[1] + zz * __shfl_sync(0xFFFFFFFFu, d[s][1], owner),
                               M.cam->o[2] + zz * __shfl_sync(0xFFFFFFFFu, d[s][2], owner)};
-          const long long tt0 = clock64();
           const float f = tail_eval(view, inf.n_view, ops, lvl_off, inf.n_lvl, src, p, wvals);
-          d_tcyc += clock64() - tt0;
-          ++d_tev;
           bool hit = false, exit = false;
-          if (lane == owner) step_slot(s, f, hit, exit);
+          if (lane == owner) step_slot(s, f, omega_c, hit, exit);
           retire(s, hit, exit);
         }
       }
@@ -638,23 +695,15 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       p[s][1] = M.cam->o[1] + z[s] * d[s][1];
       p[s][2] = M.cam->o[2] + z[s] * d[s][2];
     }
-    const long long nt0 = clock64();
     eval_view_r<kR, float>(view, inf.n_view, src, p, f, stk);
-    d_ncyc += clock64() - nt0;
-    ++d_nit;
 #pragma unroll
     for (int s = 0; s < kR; ++s) {
       bool hit, exit;
-      step_slot(s, f[s], hit, exit);
+      step_slot(s, f[s], omega_c, hit, exit);
       retire(s, hit, exit);
     }
   }
-  if (dbg && lane == 0) {
-    atomicAdd(&dbg[0], (unsigned long long)d_nit);
-    atomicAdd(&dbg[1], (unsigned long long)d_tev);
-    atomicAdd(&dbg[2], (unsigned long long)d_ncyc);
-    atomicAdd(&dbg[3], (unsigned long long)d_tcyc);
-  }
+  c_rej += rejected;
   return live_steps;
 }
 
@@ -723,7 +772,8 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
 }
 
 // ---- the tracing kernel ----------------------------------------------------------
-__global__ void __launch_bounds__(kWarps * 32)
+template <int MODE>
+__global__ void __launch_bounds__(kWarps * 32, 4)
 k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_item;
@@ -738,7 +788,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   float *wvals = reinterpret_cast<float *>(C.stk + (size_t)warp * L.stack_slots * 32);
   uint16_t *my_hits = C.hits + (size_t)warp * L.max_tile_rays;
 
-  uint64_t c_steps = 0, c_prim = 0, c_op = 0, c_flops = 0, c_sub = 0, c_fin = 0;
+  uint64_t c_steps = 0, c_prim = 0, c_op = 0, c_flops = 0, c_sub = 0, c_fin = 0, c_rej = 0;
   uint32_t c_err = 0;
 
   for (;;) {
@@ -814,9 +864,9 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         const long long t0 = clock64();
         int n_hits = 0;
         const RecSrc src{sc.rec, pick(C.dc, k & 1)};
-        const uint32_t ls = march_sub(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
+        const uint32_t ls = march_sub<MODE>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
                                       n_pending, &s_qhead[rd], alive_out, &s_nctr[wr], my_hits, n_hits, stk_lane,
-                                      wvals, 2 * L.stack_slots * 32, L.tile_stats ? s_dbg : nullptr);
+                                      wvals, 2 * L.stack_slots * 32, c_rej);
         const long long t1 = clock64();
         c_steps += ls;
         c_prim += (uint64_t)ls * inf.n_prim;
@@ -825,7 +875,10 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         finalize_hits(M, C, src, inf, pick(C.view, k & 1), my_hits, n_hits, alive_out, &s_nctr[wr], stk_lane, c_fin);
         if (L.tile_stats && lane == 0) {
           atomicAdd(&s_dbg[4], (unsigned long long)(clock64() - t1));
-          if (warp == 0) { atomicAdd(&s_dbg[5], (unsigned long long)inf.n_view); atomicAdd(&s_dbg[6], (unsigned long long)inf.n_lvl); }
+          if (warp == 0) {
+            atomicAdd(&s_dbg[5], (unsigned long long)inf.n_view);
+            atomicAdd(&s_dbg[6], (unsigned long long)inf.n_lvl);
+          }
         }
         if (warp == 0) {
           t_march += t1 - t0;
@@ -881,8 +934,10 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       c_op += __shfl_xor_sync(0xFFFFFFFFu, c_op, o);
       c_flops += __shfl_xor_sync(0xFFFFFFFFu, c_flops, o);
       c_fin += __shfl_xor_sync(0xFFFFFFFFu, c_fin, o);
+      c_rej += __shfl_xor_sync(0xFFFFFFFFu, c_rej, o);
     }
     if (lane == 0) {
+      atomicAdd((unsigned long long *)&L.counters[5], (unsigned long long)c_rej);
       atomicAdd((unsigned long long *)&L.counters[0], (unsigned long long)c_steps);
       atomicAdd((unsigned long long *)&L.counters[1], (unsigned long long)c_prim);
       atomicAdd((unsigned long long *)&L.counters[2], (unsigned long long)c_op);
@@ -944,24 +999,40 @@ void launch_eval_view(const DevScene &sc, const uint32_t *view, const int32_t *i
   if (npts > 0) count_launch(), k_eval_view<<<(npts + 127) / 128, 128, 0, s>>>(sc, view, info, pts, npts, f, grad);
 }
 
-cudaError_t trace_launch(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s) {
+template <int MODE>
+static cudaError_t trace_launch_mode(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s) {
   const size_t smem = smem_per_cta(L);
-  cudaError_t e = cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_trace<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace, kWarps * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<MODE>, kWarps * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  count_launch(), k_trace<<<n_sm * per_sm, kWarps * 32, smem, s>>>(jobs, n_jobs, L);
+  count_launch(), k_trace<MODE><<<n_sm * per_sm, kWarps * 32, smem, s>>>(jobs, n_jobs, L);
   return cudaGetLastError();
+}
+
+cudaError_t trace_launch(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s) {
+  switch (L.step_mode) {
+    case ST_STEP_OVERRELAX: return trace_launch_mode<ST_STEP_OVERRELAX>(jobs, n_jobs, L, n_sm, s);
+    default: return trace_launch_mode<ST_STEP_PLAIN>(jobs, n_jobs, L, n_sm, s);
+  }
 }
 
 int trace_ctas_per_sm(const TraceLaunch &L) {
   const size_t smem = smem_per_cta(L);
-  if (cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace, kWarps * 32, smem);
+  if (L.step_mode == ST_STEP_OVERRELAX) {
+    if (cudaFuncSetAttribute(k_trace<ST_STEP_OVERRELAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<ST_STEP_OVERRELAX>, kWarps * 32, smem);
+  } else {
+    if (cudaFuncSetAttribute(k_trace<ST_STEP_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<ST_STEP_PLAIN>, kWarps * 32, smem);
+  }
   return per_sm;
 }
 
