@@ -114,7 +114,9 @@ typedef struct {
 
 /* Tracing options.  Zero-initialised fields take the defaults in brackets. */
 #define ST_STEP_PLAIN 0        /* z += f / (L |d|)                          */
-#define ST_STEP_LEARNED 1      /* MLP over-relaxation, verified (see below) */
+#define ST_STEP_LEARNED 1      /* relaxed step with omega proposed per step by
+                                  the MLP of st_mlp_* (BF16 tensor cores),
+                                  verified like ST_STEP_OVERRELAX        */
 #define ST_STEP_OVERRELAX 2    /* z += omega f / (L |d|), verified: a step whose
                                   landing sphere does not overlap the previous
                                   one is rejected, the ray returns to the
@@ -131,7 +133,8 @@ typedef struct {
     int32_t max_new_per_turn; /* new primitives per subfrustum [6, Sec. 8] */
     int32_t newton_iters;   /* Newton refinements of a hit [4]             */
     float newton_clamp;     /* Newton step bound, distance units [64 eps]  */
-    const void *mlp;        /* reserved for the learned step; NULL         */
+    const void *mlp;        /* ST_STEP_LEARNED: device pointer (16-byte
+                               aligned) to MLP weights packed by st_mlp_pack */
     uint32_t *tile_stats;   /* optional device uint32[n_tiles][16] per-tile
                                diagnostics: [0] total, [1] segmentation +
                                view build, [2] marching, [3] hit refinement
@@ -215,6 +218,50 @@ int st_trace(st_scene *scene, const st_camera *cam, const st_tiles *tiles,
  * then the stream is synchronised. */
 int st_tiles_copy(const st_tiles *tiles, uint32_t *offsets, float *z_in, float *z_out, uint32_t *prim,
                   void *stream);
+
+/* ---- learned relaxation factor (MLP 6 -> 32 -> 32 -> 1) ---------------------------
+ * Not part of the paper: a small network proposes the relaxation factor
+ * omega in (1, 2) of each sphere-tracing step (ST_STEP_LEARNED) from the
+ * local ray state; every proposal goes through the rejection test of
+ * ST_STEP_OVERRELAX, so the plain step stays the fallback.
+ * Features of a step (fixed scaling): 8 f / L; 8 f_prev / L (f when none);
+ * 8 x previous step length (0 when none); steps / 64;
+ * log2(1 + primitives in the pruned view) / 8; log2(1 + tile list length) / 8.
+ * Network: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), o = w3 . h2 + b3,
+ * omega = 1 + sigmoid(o).  FP32 parameter vector (st_mlp_param_count() =
+ * 1313 floats): W1[32][6], b1[32], W2[32][32], b2[32], w3[32], b3.
+ *
+ * st_trace_record: plain synchronized tracing (as st_trace) that also writes
+ * one training record per plain step of the rays whose pixel index is a
+ * multiple of ray_stride: 8 floats = the 6 features of the step, the label
+ * 0.97 x 2 / (1 + k) clamped to [1, 2] with k = 1 - f_next / f (the largest
+ * factor whose relaxed step passes the overlap test when the field drops
+ * linearly), and 0.  records: device float[rec_cap][8]; rec_count: device
+ * uint32 zeroed by the caller, returns the number of records produced (it
+ * may exceed rec_cap; only rec_cap are stored).
+ *
+ * st_mlp_grad: adds to grad (device float[1313]) the gradient, and to
+ * loss_sum (device float[1]) the value, of sum_i w_i (omega_i - y_i)^2 over
+ * records i (x: device float[n][6], y: device float[n]), w_i = 4 when
+ * omega_i > y_i else 1.  FP32.
+ * st_mlp_adam: one Adam step on params with grad x grad_scale (bias
+ * corrected for step >= 1); m, v: device float[1313] moments.
+ * st_mlp_pack: host float[1313] -> host buffer of st_mlp_pack_size() bytes
+ * (BF16 weights, FP32 biases) for opts.mlp / st_mlp_infer.
+ * st_mlp_infer: omega for n feature rows with the tracer's BF16 tensor-core
+ * inference (packed: device, 16-byte aligned). */
+int st_trace_record(st_scene *scene, const st_camera *cam, const st_tiles *tiles,
+                    const st_trace_opts *opts, float *depth, float *normal, uint32_t *evals,
+                    uint8_t *flags, float *records, uint32_t rec_cap, uint32_t *rec_count,
+                    int ray_stride, void *stream);
+size_t st_mlp_pack_size(void);
+int st_mlp_param_count(void);
+int st_mlp_pack(const float *params, void *packed);
+int st_mlp_grad(const float *params, const float *x, const float *y, int n, float *grad,
+                float *loss_sum, void *stream);
+int st_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr,
+                float beta1, float beta2, float eps, float grad_scale, void *stream);
+int st_mlp_infer(const void *packed, const float *x, int n, float *omega, void *stream);
 
 /* ---- tracing without device allocation ----------------------------------------
  * st_trace_noalloc: same arguments, outputs and results as st_trace, but the

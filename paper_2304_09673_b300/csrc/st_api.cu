@@ -11,6 +11,10 @@
 
 namespace st {
 
+int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_trace_opts &o, float *depth,
+                 float *normal, uint32_t *evals, uint8_t *flags, uint64_t *counters, void *stream, float *records,
+                 uint32_t rec_cap, uint32_t *rec_count, int rec_stride);
+
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
 static std::atomic<uint64_t> g_launches{0};
@@ -317,8 +321,44 @@ int st_trace(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_tra
   st_trace_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.step_mode != ST_STEP_PLAIN && o.step_mode != ST_STEP_OVERRELAX) {
-    set_error("step mode not available");
+  if (o.step_mode != ST_STEP_PLAIN && o.step_mode != ST_STEP_OVERRELAX && o.step_mode != ST_STEP_LEARNED) {
+    set_error("unknown step mode");
+    return ST_ERR_INVALID;
+  }
+  if (o.step_mode == ST_STEP_LEARNED && (!o.mlp || ((uintptr_t)o.mlp & 15u))) {
+    set_error("ST_STEP_LEARNED needs opts.mlp: 16-byte aligned device pointer to packed MLP weights");
+    return ST_ERR_INVALID;
+  }
+  return trace_common(s, cam, tl, o, depth, normal, evals, flags, counters, stream, nullptr, 0, nullptr, 0);
+}
+
+int st_trace_record(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_trace_opts *opts,
+                    float *depth, float *normal, uint32_t *evals, uint8_t *flags, float *records,
+                    uint32_t rec_cap, uint32_t *rec_count, int ray_stride, void *stream) {
+  if (!s || !tl || !depth || !normal || !evals || !flags || !records || !rec_count || ray_stride < 1) {
+    set_error("st_trace_record: invalid arguments");
+    return ST_ERR_INVALID;
+  }
+  int rc = check_camera(cam);
+  if (rc != ST_OK) return rc;
+  st_trace_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  o.step_mode = ST_STEP_RECORD;
+  return trace_common(s, cam, tl, o, depth, normal, evals, flags, nullptr, stream, records, rec_cap, rec_count,
+                      ray_stride);
+}
+
+}  // extern "C"
+
+namespace st {
+
+int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_trace_opts &o, float *depth,
+                 float *normal, uint32_t *evals, uint8_t *flags, uint64_t *counters, void *stream, float *records,
+                 uint32_t rec_cap, uint32_t *rec_count, int rec_stride) {
+  const int tiles_x = (cam->width + tl->tile - 1) / tl->tile, tiles_y = (cam->height + tl->tile - 1) / tl->tile;
+  if (tl->tiles_x != tiles_x || tl->tiles_y != tiles_y) {
+    set_error("tile buffer does not match the camera");
     return ST_ERR_INVALID;
   }
   Job job;
@@ -361,6 +401,12 @@ int st_trace(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_tra
   L.counters = counters;
   L.tile_stats = o.tile_stats;
   L.step_mode = tp.step_mode;
+  L.mlp = tp.step_mode == ST_STEP_LEARNED ? o.mlp : nullptr;
+  L.records = records;
+  L.rec_cap = rec_cap;
+  L.rec_count = rec_count;
+  L.rec_stride = rec_stride > 0 ? rec_stride : 1;
+  if (tp.step_mode == ST_STEP_LEARNED && L.stack_slots < 10) L.stack_slots = 10;
   // Active set and view in shared memory when 16 warps per SM still fit.
   L.work_in_smem = 1;
   if (trace_smem_per_warp(L) * 16 > 200 * 1024) L.work_in_smem = 0;
@@ -378,6 +424,10 @@ int st_trace(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_tra
   ST_CK(trace_launch(s->job.p, 1, L, s->n_sm, st));
   return ST_OK;
 }
+
+}  // namespace st
+
+extern "C" {
 
 int st_pruned_view(const st_scene *s, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
                    int32_t *info, void *stream) {

@@ -44,7 +44,14 @@ struct TraceLaunch {
   uint64_t *counters;      // optional ST_NUM_COUNTERS
   uint32_t *tile_stats;    // optional [n_items][16] diagnostics
   int32_t step_mode;       // selects the kernel instantiation
+  const void *mlp;         // packed MLP weights (learned step)
+  float *records;          // recording mode: [rec_cap][8] step records
+  uint32_t rec_cap;
+  uint32_t *rec_count;     // device counter (zeroed by the caller)
+  int32_t rec_stride;      // record rays whose pixel index % stride == 0
 };
+
+constexpr int ST_STEP_RECORD = 3;   // plain stepping that records training data
 
 size_t trace_smem_per_warp(const TraceLaunch &L);
 uint32_t trace_work_words(const TraceLaunch &L);

@@ -1,0 +1,167 @@
+// st_mlp.cuh -- the learned relaxation factor: step features and the warp-level
+// BF16 tensor-core inference of the MLP 6 -> 32 -> 32 -> 1 (ReLU, output
+// omega = 1 + sigmoid(o)) used inside the tracer.
+//
+// Parameter vector (FP32, ST_MLP_PARAMS floats, training layout):
+//   W1[32][6] (out, in), b1[32], W2[32][32], b2[32], w3[32], b3
+// Packed inference layout (st_mlp_pack, kMlpPackBytes):
+//   W1 as bf16 [32][16] (out, in zero-padded), W2 bf16 [32][32],
+//   w3 bf16 [8][32] (row 0 = w3, rows 1..7 zero), b1 f32[32], b2 f32[32], b3 f32.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace st {
+
+constexpr int kMlpIn = 6, kMlpH = 32;
+constexpr int kMlpParams = kMlpH * kMlpIn + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;  // 1313
+constexpr size_t kMlpPackBytes = 4096;
+constexpr size_t kMlpW1Off = 0, kMlpW2Off = 1024, kMlpW3Off = 3072, kMlpB1Off = 3584, kMlpB2Off = 3712,
+                 kMlpB3Off = 3840;
+
+// Step features (fixed scaling, identical in recording and inference):
+//   x0 = 8 f / L, x1 = 8 f_prev / L (f when there is no previous point),
+//   x2 = 8 x previous step length in distance units (0 when none),
+//   x3 = steps / 64, x4 = log2(1 + primitives in the view) / 8,
+//   x5 = log2(1 + A-buffer list length) / 8.
+__host__ __device__ inline void step_features(float f, float f_prev, float dz_prev_dist, bool have_prev,
+                                              uint32_t steps, int n_prim, uint32_t list_len, float inv_l,
+                                              float x[6]) {
+  x[0] = 8.f * f * inv_l;
+  x[1] = 8.f * (have_prev ? f_prev : f) * inv_l;
+  x[2] = have_prev ? 8.f * dz_prev_dist : 0.f;
+  x[3] = (float)steps * (1.f / 64.f);
+  x[4] = log2f(1.f + (float)n_prim) * 0.125f;
+  x[5] = log2f(1.f + (float)list_len) * 0.125f;
+}
+
+// Training label of one recorded plain step (learned-step reading of the
+// paper's over-relaxation, Sec. 10): with consecutive plain-step values
+// f_i, f_{i+1}, the field drops at rate k = 1 - f_{i+1} / f_i per plain step
+// and a relaxed step omega passes the sphere-overlap test while
+// omega <= 2 / (1 + k).  Label = 0.97 x that bound, clamped to [1, 2].
+__host__ __device__ inline float step_label(float f_i, float f_next) {
+  float k = 1.f - f_next / f_i;
+  k = fminf(fmaxf(k, 0.f), 1.f);
+  const float w = 0.97f * 2.f / (1.f + k);
+  return fminf(fmaxf(w, 1.f), 2.f);
+}
+
+struct MlpSmem {   // packed weights staged in shared memory (16-byte aligned)
+  const uint32_t *w1;   // bf16 pairs, [32][8]
+  const uint32_t *w2;   // [32][16]
+  const uint32_t *w3;   // [8][16]
+  const float *b1, *b2;
+  float b3;
+};
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Warp-collective: evaluates the MLP on 64 rows (row s * 32 + lane holds
+// feature vector x[s] of this lane, s = 0, 1) and returns omega per row.
+// xs: per-warp shared scratch of 64 x 16 bf16 (2 KB), os: 64 floats.
+__device__ __forceinline__ void mlp_omega_warp(const MlpSmem &W, const float (&x)[2][6], float (&omega)[2],
+                                               __nv_bfloat16 *xs, float *os) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    uint32_t *row = reinterpret_cast<uint32_t *>(xs + (s * 32 + lane) * 16);
+    row[0] = pack_bf16(x[s][0], x[s][1]);
+    row[1] = pack_bf16(x[s][2], x[s][3]);
+    row[2] = pack_bf16(x[s][4], x[s][5]);
+#pragma unroll
+    for (int k = 3; k < 8; ++k) row[k] = 0u;
+  }
+  __syncwarp();
+  const uint32_t *xu = reinterpret_cast<const uint32_t *>(xs);
+#pragma unroll 1
+  for (int mt = 0; mt < 4; ++mt) {
+    uint32_t a[4];
+    a[0] = xu[(mt * 16 + g) * 8 + t];
+    a[1] = xu[(mt * 16 + g + 8) * 8 + t];
+    a[2] = xu[(mt * 16 + g) * 8 + t + 4];
+    a[3] = xu[(mt * 16 + g + 8) * 8 + t + 4];
+    // layer 1: 16 inputs (6 used) -> 32
+    float h1[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float bl = W.b1[8 * q + 2 * t], bh = W.b1[8 * q + 2 * t + 1];
+      h1[q][0] = bl; h1[q][1] = bh; h1[q][2] = bl; h1[q][3] = bh;
+      mma_bf16(h1[q], a, W.w1[(8 * q + g) * 8 + t], W.w1[(8 * q + g) * 8 + t + 4]);
+    }
+    uint32_t a2[2][4];
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt) {
+      a2[kt][0] = pack_bf16(fmaxf(h1[2 * kt][0], 0.f), fmaxf(h1[2 * kt][1], 0.f));
+      a2[kt][1] = pack_bf16(fmaxf(h1[2 * kt][2], 0.f), fmaxf(h1[2 * kt][3], 0.f));
+      a2[kt][2] = pack_bf16(fmaxf(h1[2 * kt + 1][0], 0.f), fmaxf(h1[2 * kt + 1][1], 0.f));
+      a2[kt][3] = pack_bf16(fmaxf(h1[2 * kt + 1][2], 0.f), fmaxf(h1[2 * kt + 1][3], 0.f));
+    }
+    // layer 2: 32 -> 32
+    float h2[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float bl = W.b2[8 * q + 2 * t], bh = W.b2[8 * q + 2 * t + 1];
+      h2[q][0] = bl; h2[q][1] = bh; h2[q][2] = bl; h2[q][3] = bh;
+#pragma unroll
+      for (int kt = 0; kt < 2; ++kt)
+        mma_bf16(h2[q], a2[kt], W.w2[(8 * q + g) * 16 + 8 * kt + t], W.w2[(8 * q + g) * 16 + 8 * kt + t + 4]);
+    }
+    uint32_t a3[2][4];
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt) {
+      a3[kt][0] = pack_bf16(fmaxf(h2[2 * kt][0], 0.f), fmaxf(h2[2 * kt][1], 0.f));
+      a3[kt][1] = pack_bf16(fmaxf(h2[2 * kt][2], 0.f), fmaxf(h2[2 * kt][3], 0.f));
+      a3[kt][2] = pack_bf16(fmaxf(h2[2 * kt + 1][0], 0.f), fmaxf(h2[2 * kt + 1][1], 0.f));
+      a3[kt][3] = pack_bf16(fmaxf(h2[2 * kt + 1][2], 0.f), fmaxf(h2[2 * kt + 1][3], 0.f));
+    }
+    // layer 3: 32 -> 1 (column 0 of an 8-wide tile)
+    float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt)
+      mma_bf16(o, a3[kt], W.w3[g * 16 + 8 * kt + t], W.w3[g * 16 + 8 * kt + t + 4]);
+    if (t == 0) {
+      os[mt * 16 + g] = o[0] + W.b3;
+      os[mt * 16 + g + 8] = o[2] + W.b3;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const float v = os[s * 32 + lane];
+    omega[s] = 1.f + 1.f / (1.f + __expf(-v));
+  }
+  __syncwarp();
+}
+
+// Stages the packed weights into shared memory (CTA-collective).
+__device__ __forceinline__ MlpSmem load_mlp(const void *packed, unsigned char *sm) {
+  const uint4 *src = reinterpret_cast<const uint4 *>(packed);
+  uint4 *dst = reinterpret_cast<uint4 *>(sm);
+  for (int i = threadIdx.x; i < (int)(kMlpPackBytes / 16); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  MlpSmem w;
+  w.w1 = reinterpret_cast<const uint32_t *>(sm + kMlpW1Off);
+  w.w2 = reinterpret_cast<const uint32_t *>(sm + kMlpW2Off);
+  w.w3 = reinterpret_cast<const uint32_t *>(sm + kMlpW3Off);
+  w.b1 = reinterpret_cast<const float *>(sm + kMlpB1Off);
+  w.b2 = reinterpret_cast<const float *>(sm + kMlpB2Off);
+  w.b3 = *reinterpret_cast<const float *>(sm + kMlpB3Off);
+  return w;
+}
+
+}  // namespace st

@@ -24,6 +24,7 @@
 #include "st_field.cuh"
 #include "st_geom.cuh"
 #include "st_kernels.h"
+#include "st_mlp.cuh"
 
 namespace st {
 
@@ -43,7 +44,7 @@ __host__ __device__ inline size_t smem_fixed_bytes(const TraceLaunch &L) {
   const size_t r = (size_t)L.max_tile_rays;
   return align16(r * 4) + align16(r * 4) + 2 * align16(r * 2) + (size_t)kWarps * align16(r * 2) +
          (size_t)kWarps * align16((size_t)L.stack_slots * 32 * 8) + align16((size_t)(L.stack_slots + 2) * 4) +
-         2 * (size_t)L.dc_words * 16;
+         2 * (size_t)L.dc_words * 16 + (L.mlp ? kMlpPackBytes : 0);
 }
 constexpr int kMaxLevels = 64;   // operator levels of a view usable by the tail mode
 
@@ -68,6 +69,7 @@ struct CtaWork {
   float *act_ze[2];
   uint32_t *view[2];
   float4 *dc[2];       // shared parameter cache of each view (the paper's D_cache)
+  unsigned char *mlp;  // packed MLP weights (learned step) or null
   uint2 *ops[2];       // operators of each view sorted by level: (self | left << 16, right)
   int *lvl_off[2];     // [kMaxLevels + 1] level offsets into ops
 };
@@ -84,6 +86,8 @@ __device__ CtaWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork
   w.bstk = (uint32_t *)p; p += align16((size_t)(L.stack_slots + 2) * 4);
   w.dc[0] = (float4 *)p; p += (size_t)L.dc_words * 16;
   w.dc[1] = (float4 *)p; p += (size_t)L.dc_words * 16;
+  w.mlp = nullptr;
+  if (L.mlp) { w.mlp = p; p += kMlpPackBytes; }
   unsigned char *q = L.work_in_smem ? p : (unsigned char *)gwork;
   const size_t a = align16((size_t)L.act_cap * 4);
   w.act[0] = (uint32_t *)q; q += a;
@@ -522,11 +526,18 @@ __device__ __forceinline__ void append_rays(bool want, int r, uint16_t *list, in
 
 // Returns the number of live ray-steps taken by this lane.  `wvals` is the
 // warp's evaluation-stack memory viewed as floats (tail mode scratch).
+struct LearnCtx {      // learned step / recording context of a subfrustum
+  MlpSmem W;
+  uint32_t list_len;
+  const TraceLaunch *L;
+};
+
 template <int MODE>
 __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &C, const RecSrc &src, const SubInfo &inf,
                               const uint32_t *view, const uint2 *ops, const int *lvl_off, const uint16_t *alive_in,
                               int n_in, int *q_head, uint16_t *alive_out, int *n_out, uint16_t *hits, int &n_hits,
-                              float2 *stk_lane, float *wvals, int vals_cap, uint64_t &c_rej) {
+                              float2 *stk_lane, float *wvals, int vals_cap, uint64_t &c_rej,
+                              const LearnCtx &LC) {
   uint32_t rejected = 0;
   const int lane = threadIdx.x & 31;
   const float eps = M.tp->eps;
@@ -542,11 +553,18 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
   // none); relaxation is off from a rejected step until that sphere is crossed.
   float rp[kR], dzp[kR], zf[kR], zs[kR], rs[kR];
   uint32_t relax_off = 0u;
+  // Field value at the previous point (learned features); recording mode
+  // also keeps the value two points back, the step between them and how
+  // many consecutive plain steps this subfrustum has seen (0..2).
+  float fpv[kR], fpp[kR], dpp[kR];
+  int hv[kR];
 #pragma unroll
   for (int s = 0; s < kR; ++s) {
     ray[s] = -1; z[s] = 0.f; inv_ld[s] = 0.f; steps[s] = 0; d[s][0] = d[s][1] = d[s][2] = 0.f;
     rp[s] = dzp[s] = zf[s] = 0.f; zs[s] = 0.f; rs[s] = -1.f;
+    fpv[s] = fpp[s] = dpp[s] = 0.f; hv[s] = 0;
   }
+  const float inv_l = 1.f / M.tp->lipschitz;
   const float omega_c = MODE == ST_STEP_OVERRELAX ? M.tp->omega : 1.f;
   bool drained = false;
   uint32_t live_steps = 0;
@@ -578,8 +596,28 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
     ++steps[s];
     ++live_steps;
     const uint32_t bit = 1u << s;
+    if (MODE == ST_STEP_RECORD) {
+      // Record the previous plain step (its features and the label that
+      // the value reached now gives it), then remember this point.
+      const int r = ray[s];
+      const uint32_t pix = (uint32_t)(M.y0 + r / M.tw) * (uint32_t)M.cam->W + (uint32_t)(M.x0 + r % M.tw);
+      if (hv[s] >= 1 && (pix % (uint32_t)LC.L->rec_stride) == 0u) {
+        float x[6];
+        step_features(fpv[s], fpp[s], dpp[s], hv[s] >= 2, steps[s] - 1, inf.n_prim, LC.list_len, inv_l, x);
+        const uint32_t slot = atomicAdd(LC.L->rec_count, 1u);
+        if (slot < LC.L->rec_cap) {
+          float4 *dst = reinterpret_cast<float4 *>(LC.L->records + (size_t)slot * 8);
+          dst[0] = make_float4(x[0], x[1], x[2], x[3]);
+          dst[1] = make_float4(x[4], x[5], step_label(fpv[s], fs), 0.f);
+        }
+      }
+      fpp[s] = fpv[s];
+      dpp[s] = fs * inv_l;   // the plain step taken from this point, in distance units
+      fpv[s] = fs;
+      hv[s] = hv[s] < 2 ? hv[s] + 1 : 2;
+    }
     const float r = fabsf(fs) * inv_ld[s];   // surface-free radius along the ray
-    if (MODE != ST_STEP_PLAIN && r + rp[s] < dzp[s]) {
+    if (MODE != ST_STEP_PLAIN && MODE != ST_STEP_RECORD && r + rp[s] < dzp[s]) {
       // The unbounding spheres of the last two points do not overlap: the
       // relaxed step may have skipped a crossing.  Keep the landing sphere,
       // return to the previous point and take the plain step from there.
@@ -603,11 +641,12 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       C.ray_st[ray[s]] = steps[s] | (R_HIT << 24);
       return;
     }
-    if (MODE == ST_STEP_PLAIN) {
+    if (MODE == ST_STEP_PLAIN || MODE == ST_STEP_RECORD) {
       z[s] += r;
       leave_or_cap(s, exit);
       return;
     }
+    fpv[s] = fs;   // value at the point the (possibly relaxed) step starts from
     float om = (relax_off & bit) ? 1.f : om_prop;
     float dz = om * r;
     if (om > 1.f && z[s] + dz >= z_end) { om = 1.f; dz = r; }   // relaxed steps never cross z_end
@@ -657,6 +696,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
           rp[s] = 0.f;
           rs[s] = -1.f;
           relax_off &= ~(1u << s);
+          hv[s] = 0;
         }
         off += __popc(need_m[s]);
       }
@@ -679,8 +719,23 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
                               M.cam->o[1] + zz * __shfl_sync(0xFFFFFFFFu, d[s][1], owner),
                               M.cam->o[2] + zz * __shfl_sync(0xFFFFFFFFu, d[s][2], owner)};
           const float f = tail_eval(view, inf.n_view, ops, lvl_off, inf.n_lvl, src, p, wvals);
+          float om_t = omega_c;
+          if (MODE == ST_STEP_LEARNED) {
+            const float dzo = __shfl_sync(0xFFFFFFFFu, dzp[s], owner);
+            const float ilo = __shfl_sync(0xFFFFFFFFu, inv_ld[s], owner);
+            const float fpo = __shfl_sync(0xFFFFFFFFu, fpv[s], owner);
+            const uint32_t sto = __shfl_sync(0xFFFFFFFFu, steps[s], owner);
+            float x[2][6], omt[2];
+            const float dist = dzo > 0.f ? dzo / (M.tp->lipschitz * ilo) : 0.f;
+            step_features(f, fpo, dist, dzo > 0.f, sto + 1, inf.n_prim, LC.list_len, inv_l, x[0]);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) x[1][k] = x[0][k];
+            __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(wvals);
+            mlp_omega_warp(LC.W, x, omt, xs, wvals + 64 * 16 / 2);
+            om_t = omt[0];
+          }
           bool hit = false, exit = false;
-          if (lane == owner) step_slot(s, f, omega_c, hit, exit);
+          if (lane == owner) step_slot(s, f, om_t, hit, exit);
           retire(s, hit, exit);
         }
       }
@@ -696,10 +751,25 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       p[s][2] = M.cam->o[2] + z[s] * d[s][2];
     }
     eval_view_r<kR, float>(view, inf.n_view, src, p, f, stk);
+    float om[kR];
+#pragma unroll
+    for (int s = 0; s < kR; ++s) om[s] = omega_c;
+    if (MODE == ST_STEP_LEARNED) {
+      // One BF16 tensor-core MLP pass for the warp's 64 slots (the
+      // evaluation stack memory is free again and holds the fragments).
+      float x[2][6];
+#pragma unroll
+      for (int s = 0; s < kR; ++s) {
+        const float dist = dzp[s] > 0.f ? dzp[s] / (M.tp->lipschitz * inv_ld[s]) : 0.f;
+        step_features(f[s], fpv[s], dist, dzp[s] > 0.f, steps[s] + 1, inf.n_prim, LC.list_len, inv_l, x[s]);
+      }
+      __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(wvals);
+      mlp_omega_warp(LC.W, x, om, xs, wvals + 64 * 16 / 2);
+    }
 #pragma unroll
     for (int s = 0; s < kR; ++s) {
       bool hit, exit;
-      step_slot(s, f[s], omega_c, hit, exit);
+      step_slot(s, f[s], om[s], hit, exit);
       retire(s, hit, exit);
     }
   }
@@ -786,6 +856,10 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   const CtaWork C = carve(smem, L, L.g_work ? L.g_work + (size_t)blockIdx.x * L.g_work_words : nullptr);
   float2 *stk_lane = C.stk + (size_t)warp * L.stack_slots * 32 + lane;
   float *wvals = reinterpret_cast<float *>(C.stk + (size_t)warp * L.stack_slots * 32);
+  LearnCtx LC;
+  LC.L = &L;
+  LC.list_len = 0;
+  if (MODE == ST_STEP_LEARNED) LC.W = load_mlp(L.mlp, C.mlp);
   uint16_t *my_hits = C.hits + (size_t)warp * L.max_tile_rays;
 
   uint64_t c_steps = 0, c_prim = 0, c_op = 0, c_flops = 0, c_sub = 0, c_fin = 0, c_rej = 0;
@@ -812,6 +886,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     const int th = min(T, job.cam.H - M.y0);
     const int nr = M.tw * th;
     const uint32_t lbeg = job.tl.offsets[tile], len = job.tl.offsets[tile + 1] - lbeg;
+    LC.list_len = len;
     const float *zin_l = job.tl.z_in + lbeg;
     const float *zout_l = job.tl.z_out + lbeg;
     const uint32_t *prim_l = job.tl.prim + lbeg;
@@ -866,7 +941,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         const RecSrc src{sc.rec, pick(C.dc, k & 1)};
         const uint32_t ls = march_sub<MODE>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
                                       n_pending, &s_qhead[rd], alive_out, &s_nctr[wr], my_hits, n_hits, stk_lane,
-                                      wvals, 2 * L.stack_slots * 32, c_rej);
+                                      wvals, 2 * L.stack_slots * 32, c_rej, LC);
         const long long t1 = clock64();
         c_steps += ls;
         c_prim += (uint64_t)ls * inf.n_prim;
@@ -1015,25 +1090,29 @@ static cudaError_t trace_launch_mode(const Job *jobs, int n_jobs, const TraceLau
 cudaError_t trace_launch(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s) {
   switch (L.step_mode) {
     case ST_STEP_OVERRELAX: return trace_launch_mode<ST_STEP_OVERRELAX>(jobs, n_jobs, L, n_sm, s);
+    case ST_STEP_LEARNED: return trace_launch_mode<ST_STEP_LEARNED>(jobs, n_jobs, L, n_sm, s);
+    case ST_STEP_RECORD: return trace_launch_mode<ST_STEP_RECORD>(jobs, n_jobs, L, n_sm, s);
     default: return trace_launch_mode<ST_STEP_PLAIN>(jobs, n_jobs, L, n_sm, s);
   }
 }
 
-int trace_ctas_per_sm(const TraceLaunch &L) {
+template <int MODE>
+static int ctas_per_sm_mode(const TraceLaunch &L) {
   const size_t smem = smem_per_cta(L);
+  if (cudaFuncSetAttribute(k_trace<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
   int per_sm = 0;
-  if (L.step_mode == ST_STEP_OVERRELAX) {
-    if (cudaFuncSetAttribute(k_trace<ST_STEP_OVERRELAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<ST_STEP_OVERRELAX>, kWarps * 32, smem);
-  } else {
-    if (cudaFuncSetAttribute(k_trace<ST_STEP_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<ST_STEP_PLAIN>, kWarps * 32, smem);
-  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<MODE>, kWarps * 32, smem);
   return per_sm;
+}
+
+int trace_ctas_per_sm(const TraceLaunch &L) {
+  switch (L.step_mode) {
+    case ST_STEP_OVERRELAX: return ctas_per_sm_mode<ST_STEP_OVERRELAX>(L);
+    case ST_STEP_LEARNED: return ctas_per_sm_mode<ST_STEP_LEARNED>(L);
+    case ST_STEP_RECORD: return ctas_per_sm_mode<ST_STEP_RECORD>(L);
+    default: return ctas_per_sm_mode<ST_STEP_PLAIN>(L);
+  }
 }
 
 }  // namespace st

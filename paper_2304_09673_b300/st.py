@@ -74,11 +74,20 @@ _lib.st_kernel_launches.restype = C.c_uint64
 _lib.st_trace_noalloc.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINTER(st_trace_opts),
                                   _P, _P, _P, _P, _P, _P]
 _lib.st_trace_noalloc_scratch_bytes.restype = C.c_size_t
+_lib.st_trace_record.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINTER(st_trace_opts),
+                                 _P, _P, _P, _P, _P, C.c_uint32, _P, C.c_int, _P]
+_lib.st_mlp_pack_size.restype = C.c_size_t
+_lib.st_mlp_pack.argtypes = [_P, _P]
+_lib.st_mlp_grad.argtypes = [_P, _P, _P, C.c_int, _P, _P, _P]
+_lib.st_mlp_adam.argtypes = [_P, _P, _P, _P, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, _P]
+_lib.st_mlp_infer.argtypes = [_P, _P, C.c_int, _P, _P]
 _lib.st_prep_tree.argtypes = [C.POINTER(st_scene_desc), _P, _P, _P, _P]
 
 EXPORTED = ("st_scene_create", "st_scene_update_prims", "st_scene_addresses", "st_scene_destroy",
             "st_build_tiles", "st_trace", "st_tiles_copy", "st_pruned_view", "st_eval_pruned", "st_prep_tree", "st_last_error",
-            "st_version", "st_kernel_launches", "st_trace_noalloc", "st_trace_noalloc_scratch_bytes")
+            "st_version", "st_kernel_launches", "st_trace_noalloc", "st_trace_noalloc_scratch_bytes",
+            "st_trace_record", "st_mlp_pack_size", "st_mlp_param_count", "st_mlp_pack", "st_mlp_grad",
+            "st_mlp_adam", "st_mlp_infer")
 
 
 def lib():
@@ -189,6 +198,53 @@ def st_trace_noalloc(h, cam, tiles: st_tiles, opts: st_trace_opts | None, depth,
 
 def st_trace_noalloc_scratch_bytes() -> int:
     return int(_lib.st_trace_noalloc_scratch_bytes())
+
+
+def st_trace_record(h, cam, tiles: st_tiles, opts, depth, normal, evals, flags, records, rec_count,
+                    ray_stride: int = 1, stream=None) -> None:
+    """Plain tracing that also writes training records (device float[cap][8])."""
+    c = make_camera(cam)
+    o = opts if opts is not None else make_opts()
+    _check(_lib.st_trace_record(h, C.byref(c), C.byref(tiles), C.byref(o), _ptr(depth), _ptr(normal), _ptr(evals),
+                                _ptr(flags), _ptr(records), int(records.numel() // 8), _ptr(rec_count), ray_stride,
+                                _stream(stream)), "st_trace_record")
+
+
+MLP_PARAMS = 1313
+
+
+def st_mlp_pack_size() -> int:
+    return int(_lib.st_mlp_pack_size())
+
+
+def st_mlp_param_count() -> int:
+    return int(_lib.st_mlp_param_count())
+
+
+def st_mlp_pack(params) -> np.ndarray:
+    """FP32 parameter vector -> packed bytes (host numpy uint8)."""
+    p = np.ascontiguousarray(params, np.float32).reshape(-1)
+    if p.size != MLP_PARAMS:
+        raise ValueError("expected %d parameters" % MLP_PARAMS)
+    out = np.zeros(st_mlp_pack_size(), np.uint8)
+    _check(_lib.st_mlp_pack(p.ctypes.data, out.ctypes.data), "st_mlp_pack")
+    return out
+
+
+def st_mlp_grad(params, x, y, grad, loss_sum, stream=None) -> None:
+    _check(_lib.st_mlp_grad(_ptr(params), _ptr(x), _ptr(y), int(y.numel()), _ptr(grad), _ptr(loss_sum),
+                            _stream(stream)), "st_mlp_grad")
+
+
+def st_mlp_adam(params, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0,
+                stream=None) -> None:
+    _check(_lib.st_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), step, lr, beta1, beta2, eps, grad_scale,
+                            _stream(stream)), "st_mlp_adam")
+
+
+def st_mlp_infer(packed, x, omega, stream=None) -> None:
+    _check(_lib.st_mlp_infer(_ptr(packed), _ptr(x), int(omega.numel()), _ptr(omega), _stream(stream)),
+           "st_mlp_infer")
 
 
 def st_pruned_view(h, act, view, view_addr, info, stream=None) -> None:

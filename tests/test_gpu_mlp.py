@@ -1,0 +1,127 @@
+"""Learned relaxation factor on the GPU: training gradients and tensor-core
+inference against the FP64 reference, recording, and the learned tracer's
+parity with the oracle (every learned step is verified, so the frame must
+match whatever the weights are)."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2304_09673_b300 import scenegen as sg
+from gpu_util import render
+from test_gpu_trace import _parity
+
+pytestmark = pytest.mark.gpu
+
+
+def _records(rng, n):
+    X = np.stack([rng.uniform(0, 3, n), rng.uniform(0, 3, n), rng.uniform(0, 2, n), rng.uniform(0, 2, n),
+                  rng.uniform(0, 1, n), rng.uniform(0, 1.2, n)], 1).astype(np.float32)
+    y = rng.uniform(1, 2, n).astype(np.float32)
+    return X, y
+
+
+def test_grad_matches_fp64(stlib, cuda):
+    import torch
+    rng = np.random.default_rng(0)
+    p = omlp.init_params(3)
+    X, y = _records(rng, 3000)
+    g = torch.zeros(stlib.MLP_PARAMS, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    stlib.st_mlp_grad(torch.tensor(p, device="cuda"), torch.tensor(X, device="cuda"), torch.tensor(y, device="cuda"),
+                      g, loss)
+    torch.cuda.synchronize()
+    ref_g = omlp.grad(p, X, y)
+    ref_l = omlp.loss(p, X, y)
+    assert float(loss.item()) == pytest.approx(ref_l, rel=1e-4)
+    got = g.cpu().numpy().astype(np.float64)
+    scale = np.abs(ref_g).max()
+    assert np.abs(got - ref_g).max() <= 1e-3 * scale
+
+
+def test_adam_step(stlib, cuda):
+    import torch
+    p0 = omlp.init_params(4)
+    g = np.random.default_rng(1).normal(size=stlib.MLP_PARAMS).astype(np.float32)
+    P = torch.tensor(p0, device="cuda")
+    m = torch.zeros_like(P); v = torch.zeros_like(P)
+    stlib.st_mlp_adam(P, torch.tensor(g, device="cuda"), m, v, 1, 0.01, grad_scale=0.5)
+    torch.cuda.synchronize()
+    # first bias-corrected Adam step moves every parameter by lr * sign(g)
+    want = p0 - 0.01 * np.sign(g) * (np.abs(g * 0.5) / (np.abs(g * 0.5) + 1e-8))
+    assert np.allclose(P.cpu().numpy(), want, atol=1e-6)
+
+
+def test_tensor_core_inference_matches_bf16_reference(stlib, cuda):
+    import torch
+    rng = np.random.default_rng(5)
+    p = omlp.init_params(7) + rng.normal(scale=0.1, size=stlib.MLP_PARAMS).astype(np.float32)
+    X, _ = _records(rng, 1000)
+    packed = torch.tensor(stlib.st_mlp_pack(p), device="cuda")
+    om = torch.empty(1000, device="cuda")
+    stlib.st_mlp_infer(packed, torch.tensor(X, device="cuda"), om)
+    torch.cuda.synchronize()
+    ref = omlp.forward_bf16(p, X)
+    got = om.cpu().numpy()
+    assert np.all((got >= 1) & (got <= 2))
+    assert np.abs(got - ref).max() < 5e-3
+    # and close to the unrounded FP64 network
+    assert np.abs(got - omlp.forward(p, X)).mean() < 2e-2
+
+
+def test_recording_single_sphere_head_on(stlib, cuda):
+    # A sphere seen head-on: along the central rays the field falls at rate
+    # |d| per unit of t, so consecutive plain steps give k = 1/L and the
+    # label 0.97 * 2 / (1 + 1/L) for every step.
+    import torch
+    s = sg.single_primitive(sg.SPHERE, [0.0, 0.0, 0.0, 0.3])
+    cam = sg.default_camera(33, 33)
+    h = stlib.st_scene_create(s)
+    try:
+        t = stlib.st_build_tiles(h, cam, 16)
+        W = H = 33
+        out = [torch.empty(n, dtype=dt, device="cuda") for n, dt in
+               ((H * W, torch.float32), (H * W * 3, torch.float32), (H * W, torch.int32), (H * W, torch.uint8))]
+        recs = torch.zeros(20000 * 8, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        stlib.st_trace_record(h, cam, t, stlib.make_opts(), *out, recs, cnt, 1)
+        torch.cuda.synchronize()
+        n = int(cnt.item())
+        r = recs[:n * 8].view(n, 8).cpu().numpy()
+    finally:
+        stlib.st_scene_destroy(h)
+    assert n > 100
+    assert np.all((r[:, 6] >= 1) & (r[:, 6] <= 2))
+    assert np.all(np.isfinite(r[:, :6]))
+    head_on = 0.97 * 2 / (1 + 1 / 1.45)
+    # the field of a sphere never falls faster than head-on (k <= 1/L), and
+    # the central rays reach that rate: the smallest labels are the head-on one
+    assert r[:, 6].min() >= head_on - 2e-3
+    assert r[:, 6].min() <= head_on + 1e-2
+
+
+@pytest.mark.parametrize("which", ["random", "trained"])
+def test_learned_trace_parity(stlib, orc, cuda, which):
+    import torch
+    from paper_2304_09673_b300 import learn
+    if which == "trained":
+        if not learn.WEIGHTS.exists():
+            pytest.skip("no trained weights committed yet")
+        p = learn.load()
+    else:
+        p = omlp.init_params(11)
+    packed = torch.tensor(stlib.st_mlp_pack(p), device="cuda")
+    for seed in (0, 2):
+        s = sg.workload_small(seed)
+        cam = sg.default_camera(256, 256)
+        g = render(stlib, s, cam, step_mode=stlib.ST_STEP_LEARNED, mlp=packed.data_ptr())
+        ref = orc.trace(s, cam)
+        _parity(orc, s, cam, g, ref)
+        assert g["counters"][7] == 0
+
+
+def test_overrelaxed_trace_parity(stlib, orc, cuda):
+    s = sg.workload_small(1)
+    cam = sg.default_camera(256, 256)
+    g = render(stlib, s, cam, step_mode=stlib.ST_STEP_OVERRELAX, omega=1.7)
+    ref = orc.trace(s, cam)
+    _parity(orc, s, cam, g, ref)
