@@ -70,80 +70,96 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t *>(&v);
 }
 
-// Warp-collective: evaluates the MLP on 64 rows (row s * 32 + lane holds
-// feature vector x[s] of this lane, s = 0, 1) and returns omega per row.
+// One 16-row tile of the network: A fragments in, output column 0 of rows
+// g and g + 8 (valid in lanes with t == 0).
+__device__ __forceinline__ void mlp_tile(const MlpSmem &W, const uint32_t (&a)[4], int g, int t, float &o_lo,
+                                         float &o_hi) {
+  float h1[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float bl = W.b1[8 * q + 2 * t], bh = W.b1[8 * q + 2 * t + 1];
+    h1[q][0] = bl; h1[q][1] = bh; h1[q][2] = bl; h1[q][3] = bh;
+    mma_bf16(h1[q], a, W.w1[(8 * q + g) * 8 + t], W.w1[(8 * q + g) * 8 + t + 4]);
+  }
+  uint32_t a2[2][4];
+#pragma unroll
+  for (int kt = 0; kt < 2; ++kt) {
+    a2[kt][0] = pack_bf16(fmaxf(h1[2 * kt][0], 0.f), fmaxf(h1[2 * kt][1], 0.f));
+    a2[kt][1] = pack_bf16(fmaxf(h1[2 * kt][2], 0.f), fmaxf(h1[2 * kt][3], 0.f));
+    a2[kt][2] = pack_bf16(fmaxf(h1[2 * kt + 1][0], 0.f), fmaxf(h1[2 * kt + 1][1], 0.f));
+    a2[kt][3] = pack_bf16(fmaxf(h1[2 * kt + 1][2], 0.f), fmaxf(h1[2 * kt + 1][3], 0.f));
+  }
+  float h2[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float bl = W.b2[8 * q + 2 * t], bh = W.b2[8 * q + 2 * t + 1];
+    h2[q][0] = bl; h2[q][1] = bh; h2[q][2] = bl; h2[q][3] = bh;
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt)
+      mma_bf16(h2[q], a2[kt], W.w2[(8 * q + g) * 16 + 8 * kt + t], W.w2[(8 * q + g) * 16 + 8 * kt + t + 4]);
+  }
+  uint32_t a3[2][4];
+#pragma unroll
+  for (int kt = 0; kt < 2; ++kt) {
+    a3[kt][0] = pack_bf16(fmaxf(h2[2 * kt][0], 0.f), fmaxf(h2[2 * kt][1], 0.f));
+    a3[kt][1] = pack_bf16(fmaxf(h2[2 * kt][2], 0.f), fmaxf(h2[2 * kt][3], 0.f));
+    a3[kt][2] = pack_bf16(fmaxf(h2[2 * kt + 1][0], 0.f), fmaxf(h2[2 * kt + 1][1], 0.f));
+    a3[kt][3] = pack_bf16(fmaxf(h2[2 * kt + 1][2], 0.f), fmaxf(h2[2 * kt + 1][3], 0.f));
+  }
+  float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int kt = 0; kt < 2; ++kt) mma_bf16(o, a3[kt], W.w3[g * 16 + 8 * kt + t], W.w3[g * 16 + 8 * kt + t + 4]);
+  o_lo = o[0] + W.b3;
+  o_hi = o[2] + W.b3;
+}
+
+// Warp-collective: evaluates the MLP on the rows of live slots (row
+// s * 32 + lane holds feature vector x[s] of this lane, s = 0, 1; slot s of
+// the lane is live when bit s of `live` is set) and returns omega per slot
+// (1 for dead slots).  16-row tiles without a live row are skipped.
 // xs: per-warp shared scratch of 64 x 16 bf16 (2 KB), os: 64 floats.
 __device__ __forceinline__ void mlp_omega_warp(const MlpSmem &W, const float (&x)[2][6], float (&omega)[2],
-                                               __nv_bfloat16 *xs, float *os) {
+                                               __nv_bfloat16 *xs, float *os, uint32_t live = 3u) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
+  uint32_t tiles = 0;   // bit mt: tile mt (rows 16 mt .. 16 mt + 15) has a live row
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
-    uint32_t *row = reinterpret_cast<uint32_t *>(xs + (s * 32 + lane) * 16);
-    row[0] = pack_bf16(x[s][0], x[s][1]);
-    row[1] = pack_bf16(x[s][2], x[s][3]);
-    row[2] = pack_bf16(x[s][4], x[s][5]);
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, (live >> s) & 1u);
+    tiles |= ((m & 0xFFFFu) ? 1u : 0u) << (2 * s);
+    tiles |= ((m >> 16) ? 1u : 0u) << (2 * s + 1);
+    if ((live >> s) & 1u) {
+      uint32_t *row = reinterpret_cast<uint32_t *>(xs + (s * 32 + lane) * 16);
+      row[0] = pack_bf16(x[s][0], x[s][1]);
+      row[1] = pack_bf16(x[s][2], x[s][3]);
+      row[2] = pack_bf16(x[s][4], x[s][5]);
 #pragma unroll
-    for (int k = 3; k < 8; ++k) row[k] = 0u;
+      for (int k = 3; k < 8; ++k) row[k] = 0u;
+    }
   }
   __syncwarp();
   const uint32_t *xu = reinterpret_cast<const uint32_t *>(xs);
 #pragma unroll 1
   for (int mt = 0; mt < 4; ++mt) {
+    if (!((tiles >> mt) & 1u)) continue;
     uint32_t a[4];
-    a[0] = xu[(mt * 16 + g) * 8 + t];
-    a[1] = xu[(mt * 16 + g + 8) * 8 + t];
-    a[2] = xu[(mt * 16 + g) * 8 + t + 4];
-    a[3] = xu[(mt * 16 + g + 8) * 8 + t + 4];
-    // layer 1: 16 inputs (6 used) -> 32
-    float h1[4][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float bl = W.b1[8 * q + 2 * t], bh = W.b1[8 * q + 2 * t + 1];
-      h1[q][0] = bl; h1[q][1] = bh; h1[q][2] = bl; h1[q][3] = bh;
-      mma_bf16(h1[q], a, W.w1[(8 * q + g) * 8 + t], W.w1[(8 * q + g) * 8 + t + 4]);
-    }
-    uint32_t a2[2][4];
-#pragma unroll
-    for (int kt = 0; kt < 2; ++kt) {
-      a2[kt][0] = pack_bf16(fmaxf(h1[2 * kt][0], 0.f), fmaxf(h1[2 * kt][1], 0.f));
-      a2[kt][1] = pack_bf16(fmaxf(h1[2 * kt][2], 0.f), fmaxf(h1[2 * kt][3], 0.f));
-      a2[kt][2] = pack_bf16(fmaxf(h1[2 * kt + 1][0], 0.f), fmaxf(h1[2 * kt + 1][1], 0.f));
-      a2[kt][3] = pack_bf16(fmaxf(h1[2 * kt + 1][2], 0.f), fmaxf(h1[2 * kt + 1][3], 0.f));
-    }
-    // layer 2: 32 -> 32
-    float h2[4][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float bl = W.b2[8 * q + 2 * t], bh = W.b2[8 * q + 2 * t + 1];
-      h2[q][0] = bl; h2[q][1] = bh; h2[q][2] = bl; h2[q][3] = bh;
-#pragma unroll
-      for (int kt = 0; kt < 2; ++kt)
-        mma_bf16(h2[q], a2[kt], W.w2[(8 * q + g) * 16 + 8 * kt + t], W.w2[(8 * q + g) * 16 + 8 * kt + t + 4]);
-    }
-    uint32_t a3[2][4];
-#pragma unroll
-    for (int kt = 0; kt < 2; ++kt) {
-      a3[kt][0] = pack_bf16(fmaxf(h2[2 * kt][0], 0.f), fmaxf(h2[2 * kt][1], 0.f));
-      a3[kt][1] = pack_bf16(fmaxf(h2[2 * kt][2], 0.f), fmaxf(h2[2 * kt][3], 0.f));
-      a3[kt][2] = pack_bf16(fmaxf(h2[2 * kt + 1][0], 0.f), fmaxf(h2[2 * kt + 1][1], 0.f));
-      a3[kt][3] = pack_bf16(fmaxf(h2[2 * kt + 1][2], 0.f), fmaxf(h2[2 * kt + 1][3], 0.f));
-    }
-    // layer 3: 32 -> 1 (column 0 of an 8-wide tile)
-    float o[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int kt = 0; kt < 2; ++kt)
-      mma_bf16(o, a3[kt], W.w3[g * 16 + 8 * kt + t], W.w3[g * 16 + 8 * kt + t + 4]);
+    const int m0 = 16 * mt;
+    a[0] = xu[(m0 + g) * 8 + t];
+    a[1] = xu[(m0 + g + 8) * 8 + t];
+    a[2] = xu[(m0 + g) * 8 + t + 4];
+    a[3] = xu[(m0 + g + 8) * 8 + t + 4];
+    float lo, hi;
+    mlp_tile(W, a, g, t, lo, hi);
     if (t == 0) {
-      os[mt * 16 + g] = o[0] + W.b3;
-      os[mt * 16 + g + 8] = o[2] + W.b3;
+      os[m0 + g] = lo;
+      os[m0 + g + 8] = hi;
     }
   }
   __syncwarp();
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const float v = os[s * 32 + lane];
-    omega[s] = 1.f + 1.f / (1.f + __expf(-v));
+    omega[s] = ((live >> s) & 1u) ? 1.f + 1.f / (1.f + __expf(-v)) : 1.f;
   }
   __syncwarp();
 }

@@ -50,7 +50,7 @@ constexpr int kMaxLevels = 64;   // operator levels of a view usable by the tail
 
 __host__ __device__ inline size_t work_bytes(const TraceLaunch &L) {
   return align16((size_t)L.act_cap * 4) * 4 + 2 * align16((size_t)L.view_cap * 4) +
-         2 * align16((size_t)L.view_cap * 8) + 2 * align16((size_t)(kMaxLevels + 1) * 4);
+         2 * align16((size_t)L.act_cap * 8) + 2 * align16((size_t)(kMaxLevels + 1) * 4);
 }
 __host__ __device__ inline size_t smem_per_cta(const TraceLaunch &L) {
   return smem_fixed_bytes(L) + (L.work_in_smem ? work_bytes(L) : 0);
@@ -96,8 +96,8 @@ __device__ CtaWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork
   w.act_ze[1] = (float *)q; q += a;
   w.view[0] = (uint32_t *)q; q += align16((size_t)L.view_cap * 4);
   w.view[1] = (uint32_t *)q; q += align16((size_t)L.view_cap * 4);
-  w.ops[0] = (uint2 *)q; q += align16((size_t)L.view_cap * 8);
-  w.ops[1] = (uint2 *)q; q += align16((size_t)L.view_cap * 8);
+  w.ops[0] = (uint2 *)q; q += align16((size_t)L.act_cap * 8);
+  w.ops[1] = (uint2 *)q; q += align16((size_t)L.act_cap * 8);
   w.lvl_off[0] = (int *)q; q += align16((size_t)(kMaxLevels + 1) * 4);
   w.lvl_off[1] = (int *)q;
   return w;
@@ -565,6 +565,10 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
     fpv[s] = fpp[s] = dpp[s] = 0.f; hv[s] = 0;
   }
   const float inv_l = 1.f / M.tp->lipschitz;
+  // Per-subfrustum features of the learned step (see step_features).
+  const float feat_prim = log2f(1.f + (float)inf.n_prim) * 0.125f;
+  const float feat_len = log2f(1.f + (float)LC.list_len) * 0.125f;
+  float om_cache[kR] = {1.f, 1.f};   // last proposed factor per slot (tail mode reuses it)
   const float omega_c = MODE == ST_STEP_OVERRELAX ? M.tp->omega : 1.f;
   bool drained = false;
   uint32_t live_steps = 0;
@@ -720,20 +724,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
                               M.cam->o[2] + zz * __shfl_sync(0xFFFFFFFFu, d[s][2], owner)};
           const float f = tail_eval(view, inf.n_view, ops, lvl_off, inf.n_lvl, src, p, wvals);
           float om_t = omega_c;
-          if (MODE == ST_STEP_LEARNED) {
-            const float dzo = __shfl_sync(0xFFFFFFFFu, dzp[s], owner);
-            const float ilo = __shfl_sync(0xFFFFFFFFu, inv_ld[s], owner);
-            const float fpo = __shfl_sync(0xFFFFFFFFu, fpv[s], owner);
-            const uint32_t sto = __shfl_sync(0xFFFFFFFFu, steps[s], owner);
-            float x[2][6], omt[2];
-            const float dist = dzo > 0.f ? dzo / (M.tp->lipschitz * ilo) : 0.f;
-            step_features(f, fpo, dist, dzo > 0.f, sto + 1, inf.n_prim, LC.list_len, inv_l, x[0]);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) x[1][k] = x[0][k];
-            __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(wvals);
-            mlp_omega_warp(LC.W, x, omt, xs, wvals + 64 * 16 / 2);
-            om_t = omt[0];
-          }
+          if (MODE == ST_STEP_LEARNED) om_t = om_cache[s];   // owner's last proposal, verified as usual
           bool hit = false, exit = false;
           if (lane == owner) step_slot(s, f, om_t, hit, exit);
           retire(s, hit, exit);
@@ -755,16 +746,25 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
 #pragma unroll
     for (int s = 0; s < kR; ++s) om[s] = omega_c;
     if (MODE == ST_STEP_LEARNED) {
-      // One BF16 tensor-core MLP pass for the warp's 64 slots (the
+      // One BF16 tensor-core MLP pass over the warp's live slots (the
       // evaluation stack memory is free again and holds the fragments).
       float x[2][6];
+      uint32_t live = 0u;
 #pragma unroll
       for (int s = 0; s < kR; ++s) {
         const float dist = dzp[s] > 0.f ? dzp[s] / (M.tp->lipschitz * inv_ld[s]) : 0.f;
-        step_features(f[s], fpv[s], dist, dzp[s] > 0.f, steps[s] + 1, inf.n_prim, LC.list_len, inv_l, x[s]);
+        x[s][0] = 8.f * f[s] * inv_l;
+        x[s][1] = 8.f * (dzp[s] > 0.f ? fpv[s] : f[s]) * inv_l;
+        x[s][2] = dzp[s] > 0.f ? 8.f * dist : 0.f;
+        x[s][3] = (float)(steps[s] + 1) * (1.f / 64.f);
+        x[s][4] = feat_prim;
+        x[s][5] = feat_len;
+        live |= (ray[s] >= 0 ? 1u : 0u) << s;
       }
       __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(wvals);
-      mlp_omega_warp(LC.W, x, om, xs, wvals + 64 * 16 / 2);
+      mlp_omega_warp(LC.W, x, om, xs, wvals + 64 * 16 / 2, live);
+#pragma unroll
+      for (int s = 0; s < kR; ++s) om_cache[s] = om[s];
     }
 #pragma unroll
     for (int s = 0; s < kR; ++s) {
@@ -842,8 +842,10 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
 }
 
 // ---- the tracing kernel ----------------------------------------------------------
+// Four CTAs per SM (128 registers) except the learned step, whose MLP
+// fragments need more registers; its extra shared memory limits it to three.
 template <int MODE>
-__global__ void __launch_bounds__(kWarps * 32, 4)
+__global__ void __launch_bounds__(kWarps * 32, 3)
 k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_item;
