@@ -3,9 +3,13 @@
 
 One step = the whole hot path on one frame: st_build_tiles (per-tile culling
 into the A-buffer) + st_trace (synchronized sphere tracing with sparse
-pruning), inputs resident in HBM.  Prints one JSON line (rank 0).
+pruning), inputs resident in HBM.  The headline mode is the learned
+relaxation step; the plain step and fixed omega = 1.7 (Sec. 10) are timed in
+the same run with identical eps, Lipschitz bound and subfrustum sizes.
+Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload 1080p|small|clustered|clustered1080p] [--modes learned,plain,overrelax]
 
 Multi-GPU: one independent replica per rank (the path has no exchange step);
 value = all ranks' rays / max-over-ranks time ("scaling": "weak").
@@ -38,7 +42,7 @@ def workload(name: str):
     if name == "1080p":
         return sg.workload_1080p(100), sg.default_camera(1920, 1080), dict(
             workload="1,024-primitive seeded blobtree (depth<=14, seed 100), 1920x1080, tile 16, "
-                     "plain synchronized sphere tracing, eps 1e-4, max 256 steps", prims=1024,
+                     "synchronized sphere tracing, eps 1e-4, max 256 steps", prims=1024,
             resolution="1920x1080", tile=16)
     if name == "small":
         return sg.workload_small(0), sg.default_camera(256, 256), dict(
@@ -119,15 +123,15 @@ def measured_peaks() -> dict:
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("st_trace.cu", "st_field.cuh", "st_geom.cuh", "st_internal.h"):
+    for f in ("st_trace.cu", "st_field.cuh", "st_geom.cuh", "st_internal.h", "st_mlp.cuh", "st_kernels.h"):
         h.update((ROOT / "paper_2304_09673_b300" / "csrc" / f).read_bytes())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_name: str):
+def recorded_traffic(workload_name: str, mode: str):
     """DRAM bytes per trace launch from a committed ncu summary, valid only
     while the traced kernel's sources are unchanged."""
-    p = ROOT / "profiles" / f"trace_{workload_name}_traffic.json"
+    p = ROOT / "profiles" / f"trace_{mode}_{workload_name}_traffic.json"
     if not p.exists():
         return None
     try:
@@ -196,6 +200,47 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def mode_opts(st, name: str, mlp, max_new: int):
+    """Trace options of one step mode; eps, L, step cap and subfrustum sizes are identical across modes."""
+    if name == "learned":
+        return st.make_opts(step_mode=st.ST_STEP_LEARNED, mlp=mlp.data_ptr(), max_new_per_turn=max_new)
+    if name == "overrelax":
+        return st.make_opts(step_mode=st.ST_STEP_OVERRELAX, omega=1.7, max_new_per_turn=max_new)
+    if name == "plain":
+        return st.make_opts(step_mode=st.ST_STEP_PLAIN, max_new_per_turn=max_new)
+    raise SystemExit(f"unknown step mode {name}")
+
+
+def timed_loop(st, r, cam, opts, steps: int, warmup: int, flush, stream):
+    """warmup untimed steps, then `steps` timed steps (tiles + trace), L2
+    flushed before each; returns per-step and per-trace ms, counters, launches."""
+    import numpy as np
+    import torch
+    for _ in range(warmup):
+        r.build_tiles()
+        r.trace(opts)
+    torch.cuda.synchronize()
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(steps)]
+    cnts = [torch.zeros_like(r.counters) for _ in range(steps)]
+    launches0 = st.st_kernel_launches()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()                     # L2 flush between timed steps (outside the events)
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        r.build_tiles()
+        e1.record(stream)
+        st.st_trace(r.h, cam, r.tiles, opts, r.depth, r.normal, r.evals, r.flags, cnts[k], stream)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    launches = st.st_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(c) for a, _, c in ev]
+    trace_ms = [m.elapsed_time(c) for _, m, c in ev]
+    tiles_ms = [a.elapsed_time(m) for a, m, _ in ev]
+    cnt = torch.stack(cnts).cpu().numpy().astype(np.float64)
+    return dict(step_ms=step_ms, trace_ms=trace_ms, tiles_ms=tiles_ms, cnt=cnt, launches=launches)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -209,71 +254,61 @@ def run_ours(args):
         torch.cuda.set_device(0)
     from paper_2304_09673_b300 import build as b
     b.build()
-    from paper_2304_09673_b300 import scenegen as sg
+    from paper_2304_09673_b300 import learn
     from paper_2304_09673_b300 import st
 
     scene, cam, cfg = workload(args.workload)
+    modes = [m.strip() for m in args.modes.split(",") if m.strip()]
+    head = modes[0]
     stream = torch.cuda.current_stream()
     r = st.Renderer(scene, cam, tile=cfg["tile"], stream=stream)
-    opts = st.make_opts(step_mode=st.ST_STEP_PLAIN)
+    mlp = learn.packed_device(learn.load())
     W, H = cam.width, cam.height
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def step(count=True):
-        r.build_tiles()
-        r.trace(opts, counters=count)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
     props = torch.cuda.get_device_properties(0)
-    gpu_id = None
     try:
-        gpu_id = "GPU-" + str(props.uuid) if not str(props.uuid).startswith("GPU-") else str(props.uuid)
+        gpu_id = str(props.uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
     except Exception:
         gpu_id = None
-    sampler = ClockSampler(gpu_id) if rank == 0 else None
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    counters = []
-    launches0 = st.st_kernel_launches()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.zero_()                     # L2 flush between timed steps (outside the events)
-        r.counters.zero_()
-        e0, e1, e2 = ev[k]
-        e0.record(stream)
-        r.build_tiles()
-        e1.record(stream)
-        st.st_trace(r.h, cam, r.tiles, opts, r.depth, r.normal, r.evals, r.flags, r.counters, stream)
-        e2.record(stream)
-        counters.append(r.counters)       # read after the loop
-        r.counters = torch.zeros_like(r.counters)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    launches = st.st_kernel_launches() - launches0
-    clocks = sampler.stop() if sampler else None
-    step_ms = [a.elapsed_time(c) for a, _, c in ev]
-    trace_ms = [m.elapsed_time(c) for _, m, c in ev]
-    total_ms = sum(step_ms)
-    cnt = torch.stack(counters).cpu().numpy().astype(np.float64)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    rays = W * H * world
-    value = rays / (ms_per_step / 1e3)
-    prim_evals = cnt[:, 1].mean()
-    flops = cnt[:, 3].mean()
-    trace_s = statistics.mean(trace_ms) / 1e3
+    results, images = {}, {}
+    clocks = None
+    for name in modes:
+        opts = mode_opts(st, name, mlp, args.max_new)
+        if world > 1:
+            dist.barrier()
+        sampler = ClockSampler(gpu_id) if (rank == 0 and name == head) else None
+        res = timed_loop(st, r, cam, opts, args.steps, args.warmup, flush, stream)
+        if sampler:
+            clocks = sampler.stop()
+        total_ms = sum(res["step_ms"])
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        res["ms_per_step"] = total_ms / args.steps
+        results[name] = res
+        images[name] = (r.flags.clone(), r.depth.clone())
 
-    # ---- end to end through the public API with host buffers ----
+    # Agreement of every mode with the plain tracer at the same eps: hit masks
+    # and planar hit depths (scene units) on the pixels both modes hit.
+    agreement = {}
+    if "plain" in images:
+        fp, dp = images["plain"]
+        for name, (f, d) in images.items():
+            if name == "plain":
+                continue
+            hp, hm = (fp & 1).bool(), (f & 1).bool()
+            both = hp & hm
+            dd = (d - dp).abs()[both]
+            agreement[name] = {
+                "mask_mismatch_frac": float((hp != hm).float().mean().item()),
+                "depth_diff_p99": float(torch.quantile(dd[:1 << 24].float(), 0.99).item()) if dd.numel() else 0.0,
+                "depth_diff_max": float(dd.max().item()) if dd.numel() else 0.0}
+
+    # ---- end to end through the public API with host buffers (headline mode) ----
+    opts = mode_opts(st, head, mlp, args.max_new)
     ids = np.flatnonzero(scene.kind < 16).astype(np.int32)
     params = np.ascontiguousarray(scene.params[ids])
     words = {0: 1, 1: 4, 2: 3}
@@ -310,30 +345,51 @@ def run_ours(args):
         e2e_s = float(t.item())
 
     if rank == 0:
+        rays = W * H * world
         peaks = measured_peaks()
         sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
         peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-        achieved = flops / trace_s / 1e12
-        traffic = recorded_traffic(args.workload)
+
+        def summary(res):
+            cnt = res["cnt"]
+            ms = res["ms_per_step"]
+            trace_s = statistics.mean(res["trace_ms"]) / 1e3
+            return {"rays_per_s": rays / (ms / 1e3), "ms_per_step": ms,
+                    "prim_evals_per_s": cnt[:, 1].mean() * world / (ms / 1e3),
+                    "trace_ms": trace_s * 1e3, "build_tiles_ms": statistics.mean(res["tiles_ms"]),
+                    "steps_per_ray": cnt[:, 0].mean() / (W * H),
+                    "rejected_steps_per_ray": cnt[:, 5].mean() / (W * H),
+                    "fp32_tflops": cnt[:, 3].mean() / trace_s / 1e12,
+                    "device_error_flags": int(cnt[:, 7].max())}
+
+        per_mode = {name: summary(res) for name, res in results.items()}
+        hs = per_mode[head]
+        achieved = hs["fp32_tflops"]
+        traffic = recorded_traffic(args.workload, head)
         line = {
-            "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(cfg, step_mode="plain", parallelism="replicas" if world > 1 else "single GPU",
+            "metric": METRIC, "value": hs["rays_per_s"], "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": hs["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(cfg, step_mode=head, max_new_per_turn=args.max_new,
+                           parallelism="replicas" if world > 1 else "single GPU",
                            l2="flushed between timed steps (256 MB write outside the timed events)"),
-            "prim_evals_per_s": prim_evals * world / (ms_per_step / 1e3),
-            "trace_ms": statistics.mean(trace_ms),
-            "build_tiles_ms": statistics.mean(a.elapsed_time(m) for a, m, _ in ev),
-            "steps_per_ray": cnt[:, 0].mean() / (W * H),
-            "roofline": {"bound": "alu", "kernel": "k_trace", "achieved": achieved, "peak": peak_tflops,
+            "prim_evals_per_s": hs["prim_evals_per_s"],
+            "modes": per_mode,
+            "roofline": {"bound": "alu", "kernel": f"k_trace<{head}>", "achieved": achieved, "peak": peak_tflops,
                          "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                          "peak_note": f"FP32 FMA pipe: {props.multi_processor_count} SMs x 128 lanes x 2 flops x "
-                                      f"{sm_mhz:.0f} MHz (measured max SM clock)"},
+                                      f"{sm_mhz:.0f} MHz (max SM clock); achieved = useful field-evaluation "
+                                      "flops (fixed per-node counts) / st_trace event time"},
             "e2e": {"value": rays / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
+            "gpu_launches": results[head]["launches"],
             "clocks": clocks,
         }
+        if "plain" in per_mode and head != "plain":
+            line["learned_vs_plain" if head == "learned" else f"{head}_vs_plain"] = (
+                hs["rays_per_s"] / per_mode["plain"]["rays_per_s"])
+        if agreement:
+            line["agreement_with_plain"] = agreement
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(scene, cam, args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -349,6 +405,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="1080p")
+    ap.add_argument("--modes", default="learned,plain,overrelax",
+                    help="step modes to time; the first one is the headline value")
+    ap.add_argument("--max-new", type=int, default=24, help="new primitives per subfrustum")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-pixels", type=int, default=256)

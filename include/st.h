@@ -130,7 +130,8 @@ typedef struct {
     int32_t step_mode;      /* ST_STEP_* [plain]                            */
     float depth_slab_frac;  /* subfrustum depth limit d as a fraction of the
                                scene diameter [0.05 = 1:20, Sec. 8]        */
-    int32_t max_new_per_turn; /* new primitives per subfrustum [6, Sec. 8] */
+    int32_t max_new_per_turn; /* new primitives fetched per subfrustum, at
+                                 most 32 [24; Sec. 8 uses 6]            */
     int32_t newton_iters;   /* Newton refinements of a hit [4]             */
     float newton_clamp;     /* Newton step bound, distance units [64 eps]  */
     const void *mlp;        /* ST_STEP_LEARNED: device pointer (16-byte
