@@ -129,7 +129,8 @@ typedef struct {
     int32_t max_steps;      /* per-ray field evaluation cap [256]          */
     int32_t step_mode;      /* ST_STEP_* [plain]                            */
     float depth_slab_frac;  /* subfrustum depth limit d as a fraction of the
-                               scene diameter [0.05 = 1:20, Sec. 8]        */
+                               scene diameter measured at st_scene_create
+                               (edits keep it) [0.05 = 1:20, Sec. 8]       */
     int32_t max_new_per_turn; /* new primitives fetched per subfrustum, at
                                  most 32 [24; Sec. 8 uses 6]            */
     int32_t newton_iters;   /* Newton refinements of a hit [4]             */
@@ -159,7 +160,8 @@ typedef struct {
  *   [4] subfrustums processed
  *   [5] rejected learned steps
  *   [6] finalisation field evaluations (Newton + normal)
- *   [7] device error flags (bit 0: view capacity, bit 1: stack overflow) */
+ *   [7] device error flags (bit 0: view capacity, bit 1: stack overflow,
+ *       bit 2: a tile list longer than the launch's capacity) */
 #define ST_NUM_COUNTERS 8
 
 /* ---- scenes --------------------------------------------------------------
@@ -219,6 +221,74 @@ int st_trace(st_scene *scene, const st_camera *cam, const st_tiles *tiles,
  * then the stream is synchronised. */
 int st_tiles_copy(const st_tiles *tiles, uint32_t *offsets, float *z_in, float *z_out, uint32_t *prim,
                   void *stream);
+
+/* ---- batched rendering of many scenes ------------------------------------------
+ * Not a paper step: the paper renders one scene per frame.  A batch renders
+ * n scenes (each with its own camera, resolution and output buffers) with
+ * the same per-scene results as st_build_tiles + st_trace: culling, sorting
+ * and tracing of all scenes run as batched launches over a concatenated
+ * primitive / tile space, and tracing is ONE persistent launch whose CTAs
+ * pull (scene, tile) items from a single queue.  The launch sequence is
+ * captured once in a CUDA graph and replayed by every st_batch_render.
+ *
+ * Per-scene tile size (8, 16 or 32), new primitives per subfrustum and the
+ * subfrustum depth slab come from an autotuner (st_autotune) whose results
+ * are kept in a JSON cache file keyed by st_tune_key; other trace options
+ * (eps, Lipschitz bound, step cap and mode, MLP) are the caller's opts for
+ * every scene.  Outputs per scene are identical, bit for bit, to
+ * st_build_tiles(tile) + st_trace with those parameters.
+ *
+ * st_tune: one tuned configuration; ms = measured tiles + trace time of the
+ * scene it was tuned on (informative).
+ * st_tune_key: "m<mode>_n<round(log2 n_prims)>_<W>x<H>" into key[0..cap).
+ * st_tune_load / st_tune_store: look up / insert-or-replace one entry of
+ * the cache file (host only; store rewrites the whole file).  load returns
+ * ST_ERR_INVALID when the file or key is absent or malformed.
+ * st_autotune: times every candidate (tile 8/16/32 x max_new 12/24/32 x
+ * depth slab 0.05/0.15 of the scene diameter) on `scene` seen by `cam`
+ * with `opts` (1 untimed + 2 timed runs each, CUDA events on `stream`),
+ * writes the fastest to *out and, when cache_path is not NULL, stores it.
+ * Synchronises `stream`.
+ *
+ * st_batch_create: plans a batch.  scenes/cams: host arrays of n; depth,
+ * normal, evals, flags: host arrays of n device pointers (per scene layout as
+ * st_trace).  autotune_cache: JSON cache path, or NULL for tile 16 and the
+ * opts' subfrustum parameters; a scene whose key is missing from an existing
+ * cache path is tuned (st_autotune) and stored.  The plan runs the culling
+ * once to size its buffers (entries x 1.5, longest list x 1.25), then
+ * captures the graph.  Synchronises `stream`.  Scenes must outlive the
+ * batch; their primitive parameters may change between renders
+ * (st_scene_update_prims), their tree may not.
+ * st_batch_render: replays the graph on the plan's stream, then synchronises
+ * it and checks the batch status word; when an edit made the lists outgrow
+ * the planned buffers it re-plans, re-captures and renders again (at most
+ * twice), else returns ST_ERR_CAPACITY.  counters: optional host
+ * uint64[ST_NUM_COUNTERS] receiving the counters of the render.
+ * st_batch_tiles: the tile size chosen for scene i (0 when out of range).
+ * st_batch_graph_kernels: kernel launches one render replays.
+ * st_render_batch: create + render + destroy in one call. */
+typedef struct {
+    int32_t tile;
+    int32_t max_new_per_turn;
+    float depth_slab_frac;
+    float ms;
+} st_tune;
+typedef struct st_batch st_batch;
+int st_tune_key(int n_prims, int width, int height, int step_mode, char *key, int cap);
+int st_tune_load(const char *path, const char *key, st_tune *out);
+int st_tune_store(const char *path, const char *key, const st_tune *t);
+int st_autotune(st_scene *scene, const st_camera *cam, const st_trace_opts *opts, const char *cache_path,
+                st_tune *out, void *stream);
+int st_batch_create(st_scene *const *scenes, const st_camera *cams, int n, const st_trace_opts *opts,
+                    float *const *depth, float *const *normal, uint32_t *const *evals,
+                    uint8_t *const *flags, const char *autotune_cache, st_batch **out, void *stream);
+int st_batch_render(st_batch *batch, uint64_t *counters);
+int st_batch_tiles(const st_batch *batch, int i);
+int st_batch_graph_kernels(const st_batch *batch);
+void st_batch_destroy(st_batch *batch);
+int st_render_batch(st_scene *const *scenes, const st_camera *cams, int n, const st_trace_opts *opts,
+                    float *const *depth, float *const *normal, uint32_t *const *evals,
+                    uint8_t *const *flags, const char *autotune_cache, void *stream);
 
 /* ---- learned relaxation factor (MLP 6 -> 32 -> 32 -> 1) ---------------------------
  * Not part of the paper: a small network proposes the relaxation factor

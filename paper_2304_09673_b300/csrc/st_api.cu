@@ -14,6 +14,7 @@ namespace st {
 int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_trace_opts &o, float *depth,
                  float *normal, uint32_t *evals, uint8_t *flags, uint64_t *counters, void *stream, float *records,
                  uint32_t rec_cap, uint32_t *rec_count, int rec_stride);
+TraceParams make_trace_params(const st_trace_opts &o, double diameter);
 
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
@@ -22,6 +23,8 @@ int count_launch() {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return 0;
 }
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 #define ST_CK(call)                                                        \
   do {                                                                     \
@@ -353,6 +356,22 @@ int st_trace_record(st_scene *s, const st_camera *cam, const st_tiles *tl, const
 
 namespace st {
 
+// Trace parameters of st_trace_opts, with the documented defaults.
+TraceParams make_trace_params(const st_trace_opts &o, double diameter) {
+  TraceParams tp;
+  tp.eps = o.eps > 0.f ? o.eps : 1e-4f;
+  tp.lipschitz = o.lipschitz > 0.f ? o.lipschitz : 1.45f;
+  tp.max_steps = o.max_steps > 0 ? o.max_steps : 256;
+  tp.step_mode = o.step_mode;
+  const float frac = o.depth_slab_frac > 0.f ? o.depth_slab_frac : 0.05f;
+  tp.depth_slab = std::max(frac * (float)diameter, 1e-6f);
+  tp.max_new = o.max_new_per_turn > 0 ? std::min(o.max_new_per_turn, 32) : 24;
+  tp.newton_iters = o.newton_iters > 0 ? o.newton_iters : (o.newton_iters < 0 ? 0 : 4);
+  tp.newton_clamp = o.newton_clamp > 0.f ? o.newton_clamp : 64.f * tp.eps;
+  tp.omega = o.omega > 1.f ? std::min(o.omega, 2.f) : 1.7f;
+  return tp;
+}
+
 int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_trace_opts &o, float *depth,
                  float *normal, uint32_t *evals, uint8_t *flags, uint64_t *counters, void *stream, float *records,
                  uint32_t rec_cap, uint32_t *rec_count, int rec_stride) {
@@ -377,16 +396,7 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
   job.out.evals = evals;
   job.out.flags = flags;
   TraceParams &tp = job.tp;
-  tp.eps = o.eps > 0.f ? o.eps : 1e-4f;
-  tp.lipschitz = o.lipschitz > 0.f ? o.lipschitz : 1.45f;
-  tp.max_steps = o.max_steps > 0 ? o.max_steps : 256;
-  tp.step_mode = o.step_mode;
-  const float frac = o.depth_slab_frac > 0.f ? o.depth_slab_frac : 0.05f;
-  tp.depth_slab = std::max(frac * (float)s->prep.diameter, 1e-6f);
-  tp.max_new = o.max_new_per_turn > 0 ? std::min(o.max_new_per_turn, 32) : 24;
-  tp.newton_iters = o.newton_iters > 0 ? o.newton_iters : (o.newton_iters < 0 ? 0 : 4);
-  tp.newton_clamp = o.newton_clamp > 0.f ? o.newton_clamp : 64.f * tp.eps;
-  tp.omega = o.omega > 1.f ? std::min(o.omega, 2.f) : 1.7f;
+  tp = make_trace_params(o, s->prep.diameter);
   job.tile_base = 0;
   cudaStream_t st = (cudaStream_t)stream;
 

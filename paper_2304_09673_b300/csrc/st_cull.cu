@@ -245,14 +245,32 @@ k_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_p
   }
 }
 
+// `abort` (optional): a status word; the kernel does nothing when its
+// capacity bit is set (a batch whose buffers turned out too small).
+__device__ __forceinline__ bool aborted(const uint32_t *abort) {
+  return abort && (*(volatile const uint32_t *)abort & ST_STATUS_CAPACITY);
+}
+
 __global__ void k_scatter(const Pair *pairs, const uint32_t *pair_counter, uint32_t pair_cap,
-                          const uint32_t *offsets, uint64_t *keys, float *z_out) {
+                          const uint32_t *offsets, uint64_t *keys, float *z_out, const uint32_t *abort) {
+  if (aborted(abort)) return;
   uint32_t n = min(*pair_counter, pair_cap);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     Pair p = pairs[i];
     uint32_t dst = offsets[p.tile] + p.rank;
+    if (dst >= pair_cap) continue;
     keys[dst] = ((uint64_t)__float_as_uint(p.z_in) << 32) | (uint64_t)p.addr;
     z_out[dst] = p.z_out;
+  }
+}
+
+// Capacity check of a batch's fixed buffers, after the tile scan: entries
+// beyond the pair buffer, or a list longer than the planned sort / active-set
+// capacity, set the capacity bit of the status word.
+__global__ void k_check_capacity(const uint32_t *pair_counter, uint32_t pair_cap, const uint32_t *max_overlap,
+                                 uint32_t overlap_cap, uint32_t *status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (*pair_counter > pair_cap || *max_overlap > overlap_cap) atomicOr(status, ST_STATUS_CAPACITY);
   }
 }
 
@@ -260,7 +278,8 @@ __global__ void k_scatter(const Pair *pairs, const uint32_t *pair_counter, uint3
 // len in (min_len, max_len] only (two launches cover short and long lists).
 __global__ void k_tile_sort(const uint32_t *offsets, uint32_t n_tiles, const uint64_t *keys,
                             const float *z_out_in, float *z_in, float *z_out, uint32_t *prim,
-                            uint32_t min_len, uint32_t max_len) {
+                            uint32_t min_len, uint32_t max_len, const uint32_t *abort) {
+  if (aborted(abort)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);
   for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
@@ -302,7 +321,9 @@ __global__ void k_tile_sort(const uint32_t *offsets, uint32_t n_tiles, const uin
 
 // Lists of length 0 or 1 need no sort: copy straight through.
 __global__ void k_tile_copy_short(const uint32_t *offsets, uint32_t n_tiles, const uint64_t *keys,
-                                  const float *z_out_in, float *z_in, float *z_out, uint32_t *prim) {
+                                  const float *z_out_in, float *z_in, float *z_out, uint32_t *prim,
+                                  const uint32_t *abort) {
+  if (aborted(abort)) return;
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
     uint32_t beg = offsets[t];
     if (offsets[t + 1] - beg == 1) {
@@ -430,10 +451,11 @@ void launch_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, ui
 void launch_scatter_sort(const Pair *pairs, const uint32_t *pair_counter, uint32_t pair_cap,
                          const uint32_t *offsets, uint32_t n_tiles, uint32_t max_overlap,
                          uint64_t *keys, float *z_out_tmp, float *z_in, float *z_out, uint32_t *prim,
-                         int n_sm, cudaStream_t s) {
-  count_launch(), k_scatter<<<n_sm * 8, 256, 0, s>>>(pairs, pair_counter, pair_cap, offsets, keys, z_out_tmp);
+                         int n_sm, cudaStream_t s, const uint32_t *abort) {
+  count_launch(), k_scatter<<<n_sm * 8, 256, 0, s>>>(pairs, pair_counter, pair_cap, offsets, keys, z_out_tmp, abort);
   if (!n_tiles) return;
-  count_launch(), k_tile_copy_short<<<(n_tiles + 255) / 256, 256, 0, s>>>(offsets, n_tiles, keys, z_out_tmp, z_in, z_out, prim);
+  count_launch(), k_tile_copy_short<<<(n_tiles + 255) / 256, 256, 0, s>>>(offsets, n_tiles, keys, z_out_tmp, z_in,
+                                                                          z_out, prim, abort);
   // Short lists: up to kSortSmall entries (48 KB of shared memory).
   const uint32_t small = kSortSmall;
   if (max_overlap > 1) {
@@ -442,15 +464,20 @@ void launch_scatter_sort(const Pair *pairs, const uint32_t *pair_counter, uint32
     while (n2 < cap) n2 <<= 1;
     size_t sm = (size_t)n2 * 12;
     count_launch(), k_tile_sort<<<n_tiles < 65535u ? n_tiles : 65535u, 256, sm, s>>>(offsets, n_tiles, keys, z_out_tmp, z_in,
-                                                                     z_out, prim, 1, small);
+                                                                     z_out, prim, 1, small, abort);
   }
   if (max_overlap > small) {
     uint32_t n2 = 1;
     while (n2 < max_overlap) n2 <<= 1;
     size_t sm = (size_t)n2 * 12;
     count_launch(), k_tile_sort<<<n_sm, 1024, sm, s>>>(offsets, n_tiles, keys, z_out_tmp, z_in, z_out, prim, small,
-                                       kSortLarge);
+                                       kSortLarge, abort);
   }
+}
+
+void launch_check_capacity(const uint32_t *pair_counter, uint32_t pair_cap, const uint32_t *max_overlap,
+                           uint32_t overlap_cap, uint32_t *status, cudaStream_t s) {
+  count_launch(), k_check_capacity<<<1, 32, 0, s>>>(pair_counter, pair_cap, max_overlap, overlap_cap, status);
 }
 
 cudaError_t cull_set_attributes() {

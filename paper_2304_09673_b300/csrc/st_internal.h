@@ -125,7 +125,10 @@ void prim_words(int kind, const float *q, float *words /* 4 * rec_words */);
 void camera_basis(const st_camera &c, DevCamera &out);
 
 void set_error(const std::string &msg);
-// Host-side count of kernel launches issued by the library.
+// Host-side count of kernel launches issued by the library (a CUDA graph
+// replay adds the kernel nodes it launches).
 int count_launch();
+void count_launches(uint64_t n);
+uint64_t launches_so_far();
 
 }  // namespace st

@@ -26,8 +26,16 @@ void launch_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, ui
                        uint32_t pair_cap, uint32_t *pair_counter, int n_sm, cudaStream_t s);
 void launch_scatter_sort(const Pair *pairs, const uint32_t *pair_counter, uint32_t pair_cap,
                          const uint32_t *offsets, uint32_t n_tiles, uint32_t max_overlap, uint64_t *keys,
-                         float *z_out_tmp, float *z_in, float *z_out, uint32_t *prim, int n_sm, cudaStream_t s);
+                         float *z_out_tmp, float *z_in, float *z_out, uint32_t *prim, int n_sm, cudaStream_t s,
+                         const uint32_t *abort = nullptr);
+void launch_check_capacity(const uint32_t *pair_counter, uint32_t pair_cap, const uint32_t *max_overlap,
+                           uint32_t overlap_cap, uint32_t *status, cudaStream_t s);
 cudaError_t cull_set_attributes();
+
+// Status word bits of batched launches (device, OR-accumulated).
+constexpr uint32_t ST_STATUS_VIEW = 1u;       // a pruned view exceeded its capacity
+constexpr uint32_t ST_STATUS_STACK = 2u;      // evaluation stack overflow
+constexpr uint32_t ST_STATUS_CAPACITY = 4u;   // entries / list length beyond the planned buffers
 
 // Tracing: per-warp working set layout is computed by trace_layout().
 struct TraceLaunch {
@@ -49,6 +57,8 @@ struct TraceLaunch {
   uint32_t rec_cap;
   uint32_t *rec_count;     // device counter (zeroed by the caller)
   int32_t rec_stride;      // record rays whose pixel index % stride == 0
+  uint32_t *status;        // optional status word (ST_STATUS_*); the kernel
+                           // returns at once when the capacity bit is set
 };
 
 constexpr int ST_STEP_RECORD = 3;   // plain stepping that records training data
@@ -56,6 +66,12 @@ constexpr int ST_STEP_RECORD = 3;   // plain stepping that records training data
 size_t trace_smem_per_warp(const TraceLaunch &L);
 uint32_t trace_work_words(const TraceLaunch &L);
 cudaError_t trace_launch(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s);
+// Split form for graph capture: trace_plan sets the kernel attributes and
+// returns the persistent grid and shared memory size (call before capture);
+// trace_launch_planned only enqueues the launch.
+cudaError_t trace_plan(const TraceLaunch &L, int n_sm, int *grid, size_t *smem);
+cudaError_t trace_launch_planned(const Job *jobs, int n_jobs, const TraceLaunch &L, int grid, size_t smem,
+                                 cudaStream_t s);
 int trace_warps_per_cta();
 int trace_ctas_per_sm(const TraceLaunch &L);
 void launch_pruned_view(const DevScene &sc, const uint32_t *act, int n, uint32_t *view, uint32_t *vaddr,

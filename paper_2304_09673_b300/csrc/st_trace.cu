@@ -568,7 +568,6 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
   // Per-subfrustum features of the learned step (see step_features).
   const float feat_prim = log2f(1.f + (float)inf.n_prim) * 0.125f;
   const float feat_len = log2f(1.f + (float)LC.list_len) * 0.125f;
-  float om_cache[kR] = {1.f, 1.f};   // last proposed factor per slot (tail mode reuses it)
   const float omega_c = MODE == ST_STEP_OVERRELAX ? M.tp->omega : 1.f;
   bool drained = false;
   uint32_t live_steps = 0;
@@ -710,44 +709,44 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
     for (int s = 0; s < kR; ++s) n_live += __popc(__ballot_sync(0xFFFFFFFFu, ray[s] >= 0));
     if (n_live == 0) break;
 
+    float f[kR];
     if (drained && tail_ok && n_live * tail_cost < inf.n_view) {
-      // ---- tail: evaluate each remaining ray with the whole warp ----
+      // ---- tail: evaluate each remaining ray with the whole warp; the
+      // owner lane receives its ray's value ----
 #pragma unroll
       for (int s = 0; s < kR; ++s) {
+        f[s] = 0.f;
         uint32_t m = __ballot_sync(0xFFFFFFFFu, ray[s] >= 0);
         while (m) {
           const int owner = __ffs(m) - 1;
           m &= m - 1;
           const float zz = __shfl_sync(0xFFFFFFFFu, z[s], owner);
-          const float p[3] = {M.cam->o[0] + zz * __shfl_sync(0xFFFFFFFFu, d[s][0], owner),
-                              M.cam->o[1] + zz * __shfl_sync(0xFFFFFFFFu, d[s][1], owner),
-                              M.cam->o[2] + zz * __shfl_sync(0xFFFFFFFFu, d[s][2], owner)};
-          const float f = tail_eval(view, inf.n_view, ops, lvl_off, inf.n_lvl, src, p, wvals);
-          float om_t = omega_c;
-          if (MODE == ST_STEP_LEARNED) om_t = om_cache[s];   // owner's last proposal, verified as usual
-          bool hit = false, exit = false;
-          if (lane == owner) step_slot(s, f, om_t, hit, exit);
-          retire(s, hit, exit);
+          const float pt[3] = {M.cam->o[0] + zz * __shfl_sync(0xFFFFFFFFu, d[s][0], owner),
+                               M.cam->o[1] + zz * __shfl_sync(0xFFFFFFFFu, d[s][1], owner),
+                               M.cam->o[2] + zz * __shfl_sync(0xFFFFFFFFu, d[s][2], owner)};
+          const float fv = tail_eval(view, inf.n_view, ops, lvl_off, inf.n_lvl, src, pt, wvals);
+          if (lane == owner) f[s] = fv;
         }
       }
-      continue;
-    }
-
-    // ---- one lockstep field evaluation per slot (Algorithm 3 over the view) ----
-    float p[kR][3], f[kR];
+    } else {
+      // ---- one lockstep field evaluation per slot (Algorithm 3 over the view) ----
+      float p[kR][3];
 #pragma unroll
-    for (int s = 0; s < kR; ++s) {
-      p[s][0] = M.cam->o[0] + z[s] * d[s][0];
-      p[s][1] = M.cam->o[1] + z[s] * d[s][1];
-      p[s][2] = M.cam->o[2] + z[s] * d[s][2];
+      for (int s = 0; s < kR; ++s) {
+        p[s][0] = M.cam->o[0] + z[s] * d[s][0];
+        p[s][1] = M.cam->o[1] + z[s] * d[s][1];
+        p[s][2] = M.cam->o[2] + z[s] * d[s][2];
+      }
+      eval_view_r<kR, float>(view, inf.n_view, src, p, f, stk);
     }
-    eval_view_r<kR, float>(view, inf.n_view, src, p, f, stk);
     float om[kR];
 #pragma unroll
     for (int s = 0; s < kR; ++s) om[s] = omega_c;
     if (MODE == ST_STEP_LEARNED) {
       // One BF16 tensor-core MLP pass over the warp's live slots (the
       // evaluation stack memory is free again and holds the fragments).
+      // The factor of a step depends on its ray's state alone, whichever
+      // evaluation path produced f.
       float x[2][6];
       uint32_t live = 0u;
 #pragma unroll
@@ -763,8 +762,6 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       }
       __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(wvals);
       mlp_omega_warp(LC.W, x, om, xs, wvals + 64 * 16 / 2, live);
-#pragma unroll
-      for (int s = 0; s < kR; ++s) om_cache[s] = om[s];
     }
 #pragma unroll
     for (int s = 0; s < kR; ++s) {
@@ -866,6 +863,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
 
   uint64_t c_steps = 0, c_prim = 0, c_op = 0, c_flops = 0, c_sub = 0, c_fin = 0, c_rej = 0;
   uint32_t c_err = 0;
+  if (L.status && (*(volatile const uint32_t *)L.status & ST_STATUS_CAPACITY)) return;
 
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(L.item_counter, 1u);
@@ -888,6 +886,14 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     const int th = min(T, job.cam.H - M.y0);
     const int nr = M.tw * th;
     const uint32_t lbeg = job.tl.offsets[tile], len = job.tl.offsets[tile + 1] - lbeg;
+    if (len > (uint32_t)L.act_cap) {
+      // A list longer than the launch's active-set capacity (only possible
+      // when a captured batch is replayed on edited scenes): report, no output.
+      for (int r = threadIdx.x; r < nr; r += blockDim.x) write_miss(M, r, 0u, 0);
+      c_err |= ST_STATUS_CAPACITY;
+      __syncthreads();
+      continue;
+    }
     LC.list_len = len;
     const float *zin_l = job.tl.z_in + lbeg;
     const float *zout_l = job.tl.z_out + lbeg;
@@ -1003,6 +1009,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     __syncthreads();
   }
 
+  if (L.status && c_err && lane == 0) atomicOr(L.status, c_err);
   if (L.counters) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1086,6 +1093,39 @@ static cudaError_t trace_launch_mode(const Job *jobs, int n_jobs, const TraceLau
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   count_launch(), k_trace<MODE><<<n_sm * per_sm, kWarps * 32, smem, s>>>(jobs, n_jobs, L);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t trace_plan_mode(const TraceLaunch &L, int n_sm, int *grid, size_t *smem) {
+  *smem = smem_per_cta(L);
+  cudaError_t e = cudaFuncSetAttribute(k_trace<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<MODE>, kWarps * 32, *smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  *grid = n_sm * per_sm;
+  return cudaSuccess;
+}
+
+cudaError_t trace_plan(const TraceLaunch &L, int n_sm, int *grid, size_t *smem) {
+  switch (L.step_mode) {
+    case ST_STEP_OVERRELAX: return trace_plan_mode<ST_STEP_OVERRELAX>(L, n_sm, grid, smem);
+    case ST_STEP_LEARNED: return trace_plan_mode<ST_STEP_LEARNED>(L, n_sm, grid, smem);
+    case ST_STEP_RECORD: return trace_plan_mode<ST_STEP_RECORD>(L, n_sm, grid, smem);
+    default: return trace_plan_mode<ST_STEP_PLAIN>(L, n_sm, grid, smem);
+  }
+}
+
+cudaError_t trace_launch_planned(const Job *jobs, int n_jobs, const TraceLaunch &L, int grid, size_t smem,
+                                 cudaStream_t s) {
+  switch (L.step_mode) {
+    case ST_STEP_OVERRELAX: count_launch(), k_trace<ST_STEP_OVERRELAX><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
+    case ST_STEP_LEARNED: count_launch(), k_trace<ST_STEP_LEARNED><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
+    case ST_STEP_RECORD: count_launch(), k_trace<ST_STEP_RECORD><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
+    default: count_launch(), k_trace<ST_STEP_PLAIN><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
+  }
   return cudaGetLastError();
 }
 

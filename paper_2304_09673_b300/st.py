@@ -56,6 +56,11 @@ class st_trace_opts(C.Structure):
                 ("omega", C.c_float)]
 
 
+class st_tune(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("max_new_per_turn", C.c_int32), ("depth_slab_frac", C.c_float),
+                ("ms", C.c_float)]
+
+
 _P = C.c_void_p
 _lib.st_last_error.restype = C.c_char_p
 _lib.st_version.restype = C.c_char_p
@@ -82,12 +87,26 @@ _lib.st_mlp_grad.argtypes = [_P, _P, _P, C.c_int, _P, _P, _P]
 _lib.st_mlp_adam.argtypes = [_P, _P, _P, _P, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, _P]
 _lib.st_mlp_infer.argtypes = [_P, _P, C.c_int, _P, _P]
 _lib.st_prep_tree.argtypes = [C.POINTER(st_scene_desc), _P, _P, _P, _P]
+_lib.st_tune_key.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_char_p, C.c_int]
+_lib.st_tune_load.argtypes = [C.c_char_p, C.c_char_p, C.POINTER(st_tune)]
+_lib.st_tune_store.argtypes = [C.c_char_p, C.c_char_p, C.POINTER(st_tune)]
+_lib.st_autotune.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_trace_opts), C.c_char_p, C.POINTER(st_tune), _P]
+_lib.st_batch_create.argtypes = [_P, _P, C.c_int, C.POINTER(st_trace_opts), _P, _P, _P, _P, C.c_char_p,
+                                 C.POINTER(C.c_void_p), _P]
+_lib.st_batch_render.argtypes = [_P, _P]
+_lib.st_batch_tiles.argtypes = [_P, C.c_int]
+_lib.st_batch_graph_kernels.argtypes = [_P]
+_lib.st_batch_destroy.argtypes = [_P]
+_lib.st_batch_destroy.restype = None
+_lib.st_render_batch.argtypes = [_P, _P, C.c_int, C.POINTER(st_trace_opts), _P, _P, _P, _P, C.c_char_p, _P]
 
 EXPORTED = ("st_scene_create", "st_scene_update_prims", "st_scene_addresses", "st_scene_destroy",
             "st_build_tiles", "st_trace", "st_tiles_copy", "st_pruned_view", "st_eval_pruned", "st_prep_tree", "st_last_error",
             "st_version", "st_kernel_launches", "st_trace_noalloc", "st_trace_noalloc_scratch_bytes",
             "st_trace_record", "st_mlp_pack_size", "st_mlp_param_count", "st_mlp_pack", "st_mlp_grad",
-            "st_mlp_adam", "st_mlp_infer")
+            "st_mlp_adam", "st_mlp_infer", "st_tune_key", "st_tune_load", "st_tune_store", "st_autotune",
+            "st_batch_create", "st_batch_render", "st_batch_tiles", "st_batch_graph_kernels", "st_batch_destroy",
+            "st_render_batch")
 
 
 def lib():
@@ -342,3 +361,81 @@ class Renderer:
             self.close()
         except Exception:
             pass
+
+
+# ---- batched rendering and the autotuner ---------------------------------------------
+def st_tune_key(n_prims: int, width: int, height: int, step_mode: int = ST_STEP_PLAIN) -> str:
+    buf = C.create_string_buffer(96)
+    _check(_lib.st_tune_key(n_prims, width, height, step_mode, buf, 96), "st_tune_key")
+    return buf.value.decode()
+
+
+def st_tune_load(path, key: str) -> st_tune | None:
+    """The cached entry, or None when the file or key is absent."""
+    t = st_tune()
+    rc = _lib.st_tune_load(str(path).encode(), key.encode(), C.byref(t))
+    return t if rc == ST_OK else None
+
+
+def st_tune_store(path, key: str, t: st_tune) -> None:
+    _check(_lib.st_tune_store(str(path).encode(), key.encode(), C.byref(t)), "st_tune_store")
+
+
+def st_autotune(h, cam, opts=None, cache_path=None, stream=None) -> st_tune:
+    c = make_camera(cam)
+    o = opts if opts is not None else make_opts()
+    t = st_tune()
+    _check(_lib.st_autotune(h, C.byref(c), C.byref(o), None if cache_path is None else str(cache_path).encode(),
+                            C.byref(t), _stream(stream)), "st_autotune")
+    return t
+
+
+def _batch_arrays(handles, cams, depth, normal, evals, flags):
+    n = len(handles)
+    if not (len(cams) == len(depth) == len(normal) == len(evals) == len(flags) == n):
+        raise ValueError("batch argument lists differ in length")
+    hs = (C.c_void_p * n)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    cs = (st_camera * n)(*[make_camera(c) for c in cams])
+    ptrs = [(C.c_void_p * n)(*[t.data_ptr() for t in lst]) for lst in (depth, normal, evals, flags)]
+    return n, hs, cs, ptrs
+
+
+def st_batch_create(handles, cams, opts, depth, normal, evals, flags, autotune_cache=None, stream=None):
+    """Plans a batch (CUDA graph).  Output lists: one torch CUDA tensor per scene."""
+    n, hs, cs, ptrs = _batch_arrays(handles, cams, depth, normal, evals, flags)
+    o = opts if opts is not None else make_opts()
+    b = C.c_void_p()
+    _check(_lib.st_batch_create(hs, cs, n, C.byref(o), *ptrs,
+                                None if autotune_cache is None else str(autotune_cache).encode(), C.byref(b),
+                                _stream(stream)), "st_batch_create")
+    return b
+
+
+def st_batch_render(b, counters: bool = False):
+    """Replays the batch graph; returns the host counters when asked."""
+    if counters:
+        out = np.zeros(ST_NUM_COUNTERS, np.uint64)
+        _check(_lib.st_batch_render(b, out.ctypes.data), "st_batch_render")
+        return out
+    _check(_lib.st_batch_render(b, None), "st_batch_render")
+    return None
+
+
+def st_batch_tiles(b, i: int) -> int:
+    return _lib.st_batch_tiles(b, i)
+
+
+def st_batch_graph_kernels(b) -> int:
+    return _lib.st_batch_graph_kernels(b)
+
+
+def st_batch_destroy(b) -> None:
+    _lib.st_batch_destroy(b)
+
+
+def st_render_batch(handles, cams, opts, depth, normal, evals, flags, autotune_cache=None, stream=None) -> None:
+    n, hs, cs, ptrs = _batch_arrays(handles, cams, depth, normal, evals, flags)
+    o = opts if opts is not None else make_opts()
+    _check(_lib.st_render_batch(hs, cs, n, C.byref(o), *ptrs,
+                                None if autotune_cache is None else str(autotune_cache).encode(), _stream(stream)),
+           "st_render_batch")
