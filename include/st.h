@@ -145,7 +145,9 @@ typedef struct {
                                view; [7] A-buffer list length; [12]
                                refinement cycles / 16 summed over warps;
                                [13] sum of view lengths, [14] sum of
-                               operator levels; [8-11], [15] zero
+                               operator levels; [8] discard, [9] fetch,
+                               [10] view build, [11] parameter cache fill
+                               cycles / 16 (first warp); [15] zero
                                (NULL = off)                                */
     float omega;            /* relaxation factor of ST_STEP_OVERRELAX [1.7,
                                Sec. 10]                                    */
@@ -363,8 +365,13 @@ size_t st_trace_noalloc_scratch_bytes(void);
 
 /* ---- inspection of the hot-path steps ----------------------------------------
  * st_pruned_view: the pruned tree view of an active set, built on the device
- * by the same code st_trace uses (Algorithm 1 with fast ancestor pointers,
- * clamping, popRequiredA / popRequiredB and the usage rewrite of Sec. 9).
+ * by the same code st_trace uses: the warp-parallel form of Algorithm 1 (the
+ * operators of the view are the lowest common ancestors of consecutive
+ * active primitives; the usage rewrite of Sec. 9 through each node's nearest
+ * blocking ancestor).
+ * st_pruned_view_alg1: the same view by Algorithm 1 as stated (one thread,
+ * fast ancestor pointers, clamping, popRequiredA / popRequiredB and the
+ * usage rewrite); same arguments and outputs.
  *   act        device uint32[n], post-order addresses of active primitives,
  *              strictly ascending, 1 <= n <= number of primitives
  *   view       device uint32[2n-1] out: bits 28..31 node code (0 sphere,
@@ -384,6 +391,8 @@ size_t st_trace_noalloc_scratch_bytes(void);
  * gradient (then the IEEE square root is used). */
 int st_pruned_view(const st_scene *scene, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
                    int32_t *info, void *stream);
+int st_pruned_view_alg1(const st_scene *scene, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
+                        int32_t *info, void *stream);
 int st_eval_pruned(const st_scene *scene, const uint32_t *view, const int32_t *info, const float *pts,
                    int npts, float *f, float *grad, void *stream);
 

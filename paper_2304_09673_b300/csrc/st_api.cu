@@ -73,7 +73,7 @@ struct st_scene {
   int n_nodes = 0, n_prims = 0;
   float voi_pad = 1e-5f;
   // scene arrays
-  DBuf<uint32_t> blob, rec_off, prim_addr;
+  DBuf<uint32_t> blob, rec_off, prim_addr, blk, lift;
   DBuf<float4> rec;
   DBuf<float> d_prim;
   // culling buffers
@@ -108,6 +108,9 @@ static DevScene dev_scene(const st_scene *s) {
   d.rec = s->rec.p;
   d.prim_addr = s->prim_addr.p;
   d.d_prim = s->d_prim.p;
+  d.blk = s->blk.p;
+  d.lift = s->lift.p;
+  d.lift_levels = s->prep.lift_levels;
   d.n_nodes = s->n_nodes;
   d.n_prims = s->n_prims;
   d.stack_depth = s->prep.stack_depth;
@@ -172,6 +175,8 @@ int st_scene_create(const st_scene_desc *desc, st_scene **out, void *stream) {
   if ((e = s->rec.ensure(nw)) != cudaSuccess) return fail(e);
   if ((e = s->prim_addr.ensure(p.prim_addr.size())) != cudaSuccess) return fail(e);
   if ((e = s->d_prim.ensure(p.d_prim.size())) != cudaSuccess) return fail(e);
+  if ((e = s->blk.ensure(p.blk.size())) != cudaSuccess) return fail(e);
+  if ((e = s->lift.ensure(p.lift.size())) != cudaSuccess) return fail(e);
   if ((e = s->small.ensure(16)) != cudaSuccess) return fail(e);
   if ((e = s->item_counter.ensure(4)) != cudaSuccess) return fail(e);
   if ((e = s->job.ensure(1)) != cudaSuccess) return fail(e);
@@ -180,6 +185,8 @@ int st_scene_create(const st_scene_desc *desc, st_scene **out, void *stream) {
   if ((e = cudaMemcpyAsync(s->rec.p, p.rec.data(), nw * 16, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
   if ((e = cudaMemcpyAsync(s->prim_addr.p, p.prim_addr.data(), p.prim_addr.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
   if ((e = cudaMemcpyAsync(s->d_prim.p, p.d_prim.data(), p.d_prim.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpyAsync(s->blk.p, p.blk.data(), p.blk.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpyAsync(s->lift.p, p.lift.data(), p.lift.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
   *out = s;
   return ST_OK;
@@ -188,6 +195,7 @@ int st_scene_create(const st_scene_desc *desc, st_scene **out, void *stream) {
 void st_scene_destroy(st_scene *s) {
   if (!s) return;
   s->blob.release(); s->rec_off.release(); s->prim_addr.release(); s->rec.release(); s->d_prim.release();
+  s->blk.release(); s->lift.release();
   s->cand_count.release(); s->cand_off.release(); s->tile_count.release(); s->offsets.release();
   s->scan_sums.release(); s->small.release(); s->rects.release(); s->pairs.release(); s->keys.release();
   s->ztmp.release(); s->z_in.release(); s->z_out.release(); s->prim.release(); s->job.release();
@@ -439,15 +447,26 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
 
 extern "C" {
 
-int st_pruned_view(const st_scene *s, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
-                   int32_t *info, void *stream) {
+static int pruned_view_common(const st_scene *s, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
+                              int32_t *info, void *stream, int method) {
   if (!s || !act || n < 1 || n > s->n_prims || !view || !info) { set_error("invalid arguments"); return ST_ERR_INVALID; }
   cudaStream_t st = (cudaStream_t)stream;
   st_scene *m = const_cast<st_scene *>(s);
-  ST_CK(m->g_work.ensure(ST_MAX_STACK + 2));
-  launch_pruned_view(dev_scene(s), act, n, view, view_addr, info, m->g_work.p, ST_MAX_STACK + 2, st);
+  const int cap = ST_MAX_STACK + 2;
+  ST_CK(m->g_work.ensure(pruned_view_scratch_words(n, cap)));
+  launch_pruned_view(dev_scene(s), act, n, view, view_addr, info, m->g_work.p, cap, method, st);
   ST_CK(cudaGetLastError());
   return ST_OK;
+}
+
+int st_pruned_view(const st_scene *s, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
+                   int32_t *info, void *stream) {
+  return pruned_view_common(s, act, n, view, view_addr, info, stream, 0);
+}
+
+int st_pruned_view_alg1(const st_scene *s, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
+                        int32_t *info, void *stream) {
+  return pruned_view_common(s, act, n, view, view_addr, info, stream, 1);
 }
 
 int st_eval_pruned(const st_scene *s, const uint32_t *view, const int32_t *info, const float *pts, int npts,

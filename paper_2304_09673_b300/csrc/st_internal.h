@@ -66,7 +66,11 @@ struct DevScene {
   const float4 *rec;         // record words
   const uint32_t *prim_addr; // [n_prims] post-order address of primitive j
   const float *d_prim;       // [n_prims] range-of-interest bound (Sec. 5)
-  int32_t n_nodes, n_prims, stack_depth;
+  const uint32_t *blk;       // [n_nodes] nearest ancestor that does not pass a
+                             // lone operand from this node's side (kNoAnc: none)
+  const uint32_t *lift;      // [lift_levels][n_nodes] ancestor 2^k levels up
+                             // (level 0 = parent; 0xFFFFFFFF above the root)
+  int32_t n_nodes, n_prims, stack_depth, lift_levels;
   float diameter, voi_pad;
 };
 
@@ -111,6 +115,9 @@ struct Job {
 struct Prep {
   std::vector<int32_t> po_of_desc, desc_of_po, parent;
   std::vector<uint32_t> blob, rec_off, prim_addr;
+  std::vector<uint32_t> blk;    // nearest blocking ancestor (see DevScene::blk)
+  std::vector<uint32_t> lift;   // binary-lifting ancestor table (see DevScene::lift)
+  int lift_levels = 1;
   std::vector<float> roi, d_prim, rec;  // rec: 4 floats per word
   std::vector<int32_t> prim_desc;       // description index of primitive j
   int stack_depth = 0;

@@ -75,7 +75,8 @@ cudaError_t trace_launch_planned(const Job *jobs, int n_jobs, const TraceLaunch 
 int trace_warps_per_cta();
 int trace_ctas_per_sm(const TraceLaunch &L);
 void launch_pruned_view(const DevScene &sc, const uint32_t *act, int n, uint32_t *view, uint32_t *vaddr,
-                        int32_t *info, uint32_t *bstk, int stack_cap, cudaStream_t s);
+                        int32_t *info, uint32_t *scratch, int stack_cap, int method, cudaStream_t s);
+size_t pruned_view_scratch_words(int n, int stack_cap);
 void launch_eval_view(const DevScene &sc, const uint32_t *view, const int32_t *info, const float *pts, int npts,
                       float *f, float *grad, cudaStream_t s);
 

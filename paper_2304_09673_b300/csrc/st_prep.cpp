@@ -168,6 +168,37 @@ int prepare(const st_scene_desc &d, Prep &p, std::string &err) {
     fast[a] = f;
   }
 
+  // Nearest blocking ancestor, top-down: the first ancestor at which a lone
+  // operand coming up from this node's side is not passed through (Sec. 9
+  // usage rule); a usage bit climbing from node v to an ancestor w survives
+  // iff blk(v) >= w.
+  p.blk.assign(n, kNoAnc);
+  for (int a = root - 1; a >= 0; --a) {
+    const int A = p.parent[a];
+    const uint32_t m = ignore_mode(kind_po[A]);
+    const bool passes = !(m & (isl_po[a] ? 1u : 2u));
+    p.blk[a] = passes ? p.blk[A] : (uint32_t)A;
+  }
+  // Binary-lifting ancestor table: lift[k][a] = ancestor 2^k levels above a.
+  {
+    std::vector<int32_t> lvl(n, 0);
+    int max_lvl = 0;
+    for (int a = root - 1; a >= 0; --a) {
+      lvl[a] = lvl[p.parent[a]] + 1;
+      max_lvl = std::max(max_lvl, lvl[a]);
+    }
+    int K = 1;
+    while ((1 << K) <= max_lvl) ++K;
+    p.lift_levels = K;
+    p.lift.assign((size_t)K * n, 0xFFFFFFFFu);
+    for (int a = 0; a < n; ++a) p.lift[a] = p.parent[a] < 0 ? 0xFFFFFFFFu : (uint32_t)p.parent[a];
+    for (int k = 1; k < K; ++k)
+      for (int a = 0; a < n; ++a) {
+        const uint32_t mid = p.lift[(size_t)(k - 1) * n + a];
+        p.lift[(size_t)k * n + a] = mid == 0xFFFFFFFFu ? mid : p.lift[(size_t)(k - 1) * n + mid];
+      }
+  }
+
   // Post-order evaluation stack depth (Algorithm 3).
   std::vector<int32_t> depth(n, 1);
   for (int a = 0; a < n; ++a) {

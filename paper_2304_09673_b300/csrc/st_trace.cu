@@ -36,6 +36,9 @@ int trace_warps_per_cta() { return kWarps; }
 enum RayStatus : uint32_t { R_ALIVE = 0, R_HIT = 1, R_UNCONV = 2 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+// View-build stacks: value stack (uint2) and pending-operator stack (uint4),
+// stack_slots + 2 entries each.
+__host__ __device__ inline size_t bstk_words(const TraceLaunch &L) { return 6 * (size_t)(L.stack_slots + 2); }
 
 // Shared memory of a CTA: ray state, two pending-ray lists, per-warp hit
 // lists, per-warp evaluation stacks (float2 slots), the Algorithm 1 stack,
@@ -43,14 +46,15 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 __host__ __device__ inline size_t smem_fixed_bytes(const TraceLaunch &L) {
   const size_t r = (size_t)L.max_tile_rays;
   return align16(r * 4) + align16(r * 4) + 2 * align16(r * 2) + (size_t)kWarps * align16(r * 2) +
-         (size_t)kWarps * align16((size_t)L.stack_slots * 32 * 8) + align16((size_t)(L.stack_slots + 2) * 4) +
+         (size_t)kWarps * align16((size_t)L.stack_slots * 32 * 8) + align16(bstk_words(L) * 4) +
          2 * (size_t)L.dc_words * 16 + (L.mlp ? kMlpPackBytes : 0);
 }
 constexpr int kMaxLevels = 64;   // operator levels of a view usable by the tail mode
 
 __host__ __device__ inline size_t work_bytes(const TraceLaunch &L) {
   return align16((size_t)L.act_cap * 4) * 4 + 2 * align16((size_t)L.view_cap * 4) +
-         2 * align16((size_t)L.act_cap * 8) + 2 * align16((size_t)(kMaxLevels + 1) * 4);
+         2 * align16((size_t)L.act_cap * 8) + 2 * align16((size_t)(kMaxLevels + 1) * 4) +
+         align16((size_t)L.act_cap * 8);
 }
 __host__ __device__ inline size_t smem_per_cta(const TraceLaunch &L) {
   return smem_fixed_bytes(L) + (L.work_in_smem ? work_bytes(L) : 0);
@@ -72,6 +76,7 @@ struct CtaWork {
   unsigned char *mlp;  // packed MLP weights (learned step) or null
   uint2 *ops[2];       // operators of each view sorted by level: (self | left << 16, right)
   int *lvl_off[2];     // [kMaxLevels + 1] level offsets into ops
+  uint2 *sort_tmp;     // view build: level-sort scratch [act_cap]
 };
 
 __device__ CtaWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork) {
@@ -83,7 +88,7 @@ __device__ CtaWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork
   w.alive[1] = (uint16_t *)p; p += align16(r * 2);
   w.hits = (uint16_t *)p; p += (size_t)kWarps * align16(r * 2);
   w.stk = (float2 *)p; p += (size_t)kWarps * align16((size_t)L.stack_slots * 32 * 8);
-  w.bstk = (uint32_t *)p; p += align16((size_t)(L.stack_slots + 2) * 4);
+  w.bstk = (uint32_t *)p; p += align16(bstk_words(L) * 4);
   w.dc[0] = (float4 *)p; p += (size_t)L.dc_words * 16;
   w.dc[1] = (float4 *)p; p += (size_t)L.dc_words * 16;
   w.mlp = nullptr;
@@ -99,7 +104,8 @@ __device__ CtaWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork
   w.ops[0] = (uint2 *)q; q += align16((size_t)L.act_cap * 8);
   w.ops[1] = (uint2 *)q; q += align16((size_t)L.act_cap * 8);
   w.lvl_off[0] = (int *)q; q += align16((size_t)(kMaxLevels + 1) * 4);
-  w.lvl_off[1] = (int *)q;
+  w.lvl_off[1] = (int *)q; q += align16((size_t)(kMaxLevels + 1) * 4);
+  w.sort_tmp = (uint2 *)q;
   return w;
 }
 
@@ -211,6 +217,186 @@ __device__ __forceinline__ ViewInfo build_view(const DevScene &sc, const uint32_
   vi.n_view = nv;
   vi.root_used = sp == 1 ? (int)(bstk[0] >> 31) : 0;
   if (sp != 1) vi.err = 1;
+  return vi;
+}
+
+// ---- pruned view by lowest common ancestors (warp-collective) -------------------
+// The same view as Algorithm 1, built for a GPU warp.  In post-order, the
+// operators that Algorithm 1 emits (those with active primitives under both
+// operands) are exactly the lowest common ancestors X_i of consecutive active
+// primitives A_i < A_i+1, and the view is A and X merged in address order.
+// A usage bit climbing from a view node v to its view parent X survives the
+// lone-operand nodes in between iff blk(v) >= X, so the usage rewrite of
+// Sec. 9 needs no tree walk.  The active set is processed in chunks of
+// kViewChunk entries staged in shared memory:
+//   phase 1 (all lanes): X_i = first ancestor of A_i at or above A_i+1, by
+//     binary lifting (four interleaved searches per lane), and the words the
+//     merge needs;
+//   phase 2 (lane 0, shared memory only): merge in address order with a
+//     value stack (usage, blk, height) and a stack of pending X_i carrying
+//     their own words; emit view words, operator codes and the unsorted
+//     level schedule;
+// then phase 3 (all lanes): counting sort of the operators by height into
+// `ops` / `lvl_off` for the tail mode.
+// Returns the view info in every lane; *n_lvl_out = levels of the schedule
+// (0 when it does not fit kMaxLevels or 16-bit indices).
+constexpr int kViewChunk = 128;
+struct ViewChunk {       // shared staging of one chunk (warp 0 of a CTA)
+  uint4 a[kViewChunk];   // (X_i, blk(X_i), blk(A_i), kind(X_i) | ignoreMod(X_i) << 8)
+  uint2 b[kViewChunk];   // (view word of A_i, global flag | record offset of X_i)
+};
+
+__device__ __forceinline__ ViewInfo build_view_lca(const DevScene &sc, const uint32_t *act, int n, uint32_t *view,
+                                                   ViewChunk &ch, uint2 *ops, uint2 *sort_tmp, int *lvl_off,
+                                                   int *lvl_cur, uint32_t *stk, int stack_cap, uint32_t *vaddr,
+                                                   int *n_lvl_out) {
+  const int lane = threadIdx.x & 31;
+  constexpr uint32_t kNone = 0xFFFFFFFFu;
+  constexpr int kPer = kViewChunk / 32;
+  ViewInfo vi = {0, 0, 0, 0, 0u, 0};
+  int nop = 0, maxh = 0;
+  // lane 0's merge state
+  // stk: 16-byte aligned, 6 (stack_cap + 2) words
+  uint4 *ps = reinterpret_cast<uint4 *>(stk);                       // pending operators: (X, blk, kind | igm << 8, word)
+  uint2 *vs = reinterpret_cast<uint2 *>(stk + 4 * (stack_cap + 2)); // value stack: (blk | u << 23 | h << 24, index)
+  int vsp = 0, psp = 0, nv = 0;
+  if (n < 1) vi.err = 1;
+  for (int c0 = 0; c0 < n; c0 += kViewChunk) {
+    // ---- phase 1 ----
+    uint32_t a[kPer], nxt[kPer], x[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = c0 + q * 32 + lane;
+      a[q] = i < n ? act[i] : 0u;
+      nxt[q] = i + 1 < n ? act[i + 1] : 0u;   // 0: no search
+      x[q] = a[q];
+    }
+    for (int k = sc.lift_levels - 1; k >= 0; --k) {
+      const uint32_t *lk = sc.lift + (size_t)k * (uint32_t)sc.n_nodes;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        if (nxt[q]) {
+          const uint32_t y = __ldg(lk + x[q]);
+          if (y < nxt[q]) x[q] = y;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = c0 + q * 32 + lane;
+      if (i < n) {
+        const uint32_t ab = __ldg(sc.blob + a[q]);
+        const uint32_t leaf = (blob_kind(ab) << kViewCodeShift) | kViewGlobal | __ldg(sc.rec_off + a[q]);
+        const uint32_t lb = __ldg(sc.blk + a[q]);
+        uint32_t X = kNone, xw = 0u, xblk = kNoAnc, xrec = 0u;
+        if (nxt[q]) {
+          X = __ldg(sc.lift + x[q]);   // parent of the highest ancestor below A_i+1
+          if (X < (uint32_t)sc.n_nodes) {
+            const uint32_t xb = __ldg(sc.blob + X);
+            xw = blob_kind(xb) | (blob_igm(xb) << 8);
+            xblk = __ldg(sc.blk + X);
+            xrec = __ldg(sc.rec_off + X);
+          }
+        }
+        ch.a[q * 32 + lane] = make_uint4(X, min(xblk, kNoAnc), min(lb, kNoAnc), xw);
+        ch.b[q * 32 + lane] = make_uint2(leaf, kViewGlobal | xrec);
+      }
+    }
+    __syncwarp();
+    // ---- phase 2 ----
+    if (lane == 0) {
+      const int c1 = min(n, c0 + kViewChunk);
+      for (int i = c0; i < c1 && !vi.err; ++i) {
+        const uint4 t = ch.a[i - c0];
+        const uint2 w = ch.b[i - c0];
+        if (vsp >= stack_cap + 2) { vi.err = 2; break; }
+        if (vaddr) vaddr[nv] = act[i];
+        view[nv] = w.x;
+        vi.flops += node_flops(w.x >> kViewCodeShift);
+        vs[vsp++] = make_uint2(t.z | (1u << 23), (uint32_t)nv);
+        ++nv;
+        const uint32_t xnext = i + 1 < n ? t.x : kNone;
+        if (i + 1 < n && xnext >= (uint32_t)sc.n_nodes) { vi.err = 1; break; }
+        while (psp > 0) {
+          const uint4 pj = ps[psp - 1];
+          if (pj.x >= xnext) break;
+          --psp;
+          if (vsp < 2) { vi.err = 1; break; }
+          const uint2 R = vs[--vsp], Lv = vs[--vsp];
+          const uint32_t X = pj.x;
+          const uint32_t uL = (((Lv.x >> 23) & 1u) && (Lv.x & kNoAnc) >= X) ? 1u : 0u;
+          const uint32_t uR = (((R.x >> 23) & 1u) && (R.x & kNoAnc) >= X) ? 1u : 0u;
+          const uint32_t b = (uL << 1) | uR, m = (pj.z >> 8) & 3u, kind = pj.z & 31u;
+          const bool ok = ((~b) & m & 3u) == 0u;
+          uint32_t code;
+          if (ok && b == 3u) code = kind - ST_OP_UNION + V_UNION;
+          else if (!ok || b == 0u) code = V_INF;
+          else code = b == 1u ? V_RIGHT : V_LEFT;
+          if (vaddr) vaddr[nv] = X;
+          view[nv] = (code << kViewCodeShift) | pj.w;
+          vi.flops += node_flops(code);
+          const uint32_t h = min(max(Lv.x >> 24, R.x >> 24) + 1u, 255u);
+          maxh = max(maxh, (int)h);
+          ops[nop++] = make_uint2((uint32_t)nv | (Lv.y << 16), (R.y & 0xFFFFu) | (h << 16));
+          const uint32_t u = (ok && b != 0u) ? 1u : 0u;
+          vs[vsp++] = make_uint2(pj.y | (u << 23) | (h << 24), (uint32_t)nv);
+          ++nv;
+        }
+        if (vi.err) break;
+        if (i + 1 < n) {
+          if (psp >= stack_cap + 2) { vi.err = 2; break; }
+          ps[psp++] = make_uint4(t.x, t.y, t.w, w.y);
+        }
+      }
+    }
+    __syncwarp();
+    if (__shfl_sync(0xFFFFFFFFu, vi.err, 0)) break;
+  }
+  if (lane == 0) {
+    if (!vi.err) {
+      if (vsp != 1 || psp != 0) vi.err = 1;
+      else vi.root_used = (((vs[0].x >> 23) & 1u) && (vs[0].x & kNoAnc) == kNoAnc) ? 1 : 0;
+    }
+    vi.n_view = nv;
+    vi.n_prim = n;
+    vi.n_op = nop;
+  }
+  vi.n_view = __shfl_sync(0xFFFFFFFFu, vi.n_view, 0);
+  vi.root_used = __shfl_sync(0xFFFFFFFFu, vi.root_used, 0);
+  vi.n_prim = __shfl_sync(0xFFFFFFFFu, vi.n_prim, 0);
+  vi.n_op = __shfl_sync(0xFFFFFFFFu, vi.n_op, 0);
+  vi.flops = __shfl_sync(0xFFFFFFFFu, vi.flops, 0);
+  vi.err = __shfl_sync(0xFFFFFFFFu, vi.err, 0);
+  nop = __shfl_sync(0xFFFFFFFFu, nop, 0);
+  maxh = __shfl_sync(0xFFFFFFFFu, maxh, 0);
+  int n_lvl = 0;
+  if (!vi.err && vi.root_used && vi.n_view <= 65535 && maxh <= kMaxLevels) {
+    for (int h = lane; h <= kMaxLevels; h += 32) lvl_off[h] = 0;
+    __syncwarp();
+    for (int k = lane; k < nop; k += 32) atomicAdd(&lvl_off[ops[k].y >> 16], 1);
+    __syncwarp();
+    if (lane == 0) {
+      int acc = 0;
+      lvl_off[0] = 0;
+      for (int h = 1; h <= maxh; ++h) {
+        const int c = lvl_off[h];
+        lvl_cur[h] = acc;
+        acc += c;
+        lvl_off[h] = acc;
+      }
+    }
+    __syncwarp();
+    for (int k = lane; k < nop; k += 32) {
+      const uint2 o = ops[k];
+      const int pos = atomicAdd(&lvl_cur[o.y >> 16], 1);
+      sort_tmp[pos] = make_uint2(o.x, o.y & 0xFFFFu);
+    }
+    __syncwarp();
+    for (int k = lane; k < nop; k += 32) ops[k] = sort_tmp[k];
+    __syncwarp();
+    n_lvl = maxh;
+  }
+  *n_lvl_out = n_lvl;
   return vi;
 }
 
@@ -327,9 +513,18 @@ __device__ __forceinline__ int build_schedule(const uint32_t *view, int n_view, 
 // pruned view into `view`.  Warp-collective; lane 0 writes *out.
 __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, const DevScene &sc, const TraceParams &tp,
                             const float *zin_l, const float *zout_l, const uint32_t *prim_l, uint32_t len,
-                            int vb, int stack_slots, int dc_words, SubInfo *out) {
+                            int vb, int stack_slots, int dc_words, SubInfo *out, int *lvl_cur, ViewChunk *vch,
+                            unsigned long long *dbg) {
   uint32_t *view = pick(C.view, vb);
   const int lane = threadIdx.x & 31;
+  long long tc = dbg ? clock64() : 0;
+  auto lap = [&](int slot) {   // per-phase cycle counters (tile diagnostics)
+    if (dbg) {
+      const long long t = clock64();
+      if (lane == 0) dbg[slot] += (unsigned long long)(t - tc);
+      tc = t;
+    }
+  };
   // ---- discard ----
   {
     int kept = 0;
@@ -354,6 +549,7 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
     sg.maxze = warp_max(mz);
     __syncwarp();
   }
+  lap(0);
   SubInfo info;
   info.done = (sg.n_act == 0 && sg.next >= len) ? 1 : 0;
   info.err = 0;
@@ -418,22 +614,21 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
     info.z_begin = z_begin;
     info.z_end = sg.z_end;
     __syncwarp();
-    // ---- pruned view (Algorithm 1), one lane ----
-    ViewInfo vi;
-    if (lane == 0) {
-      vi = build_view(sc, pick(C.act, sg.cur), sg.n_act, view, C.bstk, stack_slots);
-      info.n_view = vi.n_view;
-      info.root_used = vi.root_used;
-      info.n_prim = vi.n_prim;
-      info.n_op = vi.n_op;
-      info.flops = vi.flops;
-      info.err = vi.err;
-      if (!vi.err && vi.root_used) info.n_lvl = build_schedule(view, vi.n_view, pick(C.ops, vb), pick(C.lvl_off, vb), C.bstk, stack_slots);
-    }
-    __syncwarp();
-    const int nv = __shfl_sync(0xFFFFFFFFu, info.n_view, 0);
-    const int used = __shfl_sync(0xFFFFFFFFu, info.root_used, 0);
-    if (used) fill_dcache(view, nv, sc.rec, pick(C.dc, vb), dc_words);
+    lap(1);
+    // ---- pruned view (the lowest-common-ancestor form of Algorithm 1) ----
+    int n_lvl = 0;
+    const ViewInfo vi = build_view_lca(sc, pick(C.act, sg.cur), sg.n_act, view, *vch, pick(C.ops, vb), C.sort_tmp,
+                                       pick(C.lvl_off, vb), lvl_cur, C.bstk, stack_slots, nullptr, &n_lvl);
+    info.n_view = vi.n_view;
+    info.root_used = vi.root_used;
+    info.n_prim = vi.n_prim;
+    info.n_op = vi.n_op;
+    info.flops = vi.flops;
+    info.err = vi.err;
+    info.n_lvl = (!vi.err && vi.root_used) ? n_lvl : 0;
+    lap(2);
+    if (!vi.err && vi.root_used) fill_dcache(view, vi.n_view, sc.rec, pick(C.dc, vb), dc_words);
+    lap(3);
   }
   if (lane == 0) *out = info;
   __syncwarp();
@@ -847,6 +1042,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_item;
   __shared__ SubInfo s_info[2];
+  __shared__ int s_lvl_cur[kMaxLevels + 1];   // level cursors of the view build (warp 0)
+  __shared__ ViewChunk s_vchunk;               // view build staging (warp 0)
   __shared__ int s_qhead[3], s_nctr[3];
   __shared__ uint32_t s_steps;
   __shared__ unsigned long long s_dbg[8];
@@ -917,7 +1114,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     sg.next = 0; sg.n_act = 0; sg.cur = 0; sg.z_end = 0.f; sg.maxze = -INFINITY;
     if (warp == 0) {
       const long long t0 = clock64();
-      prepare_sub(sg, C, sc, job.tp, zin_l, zout_l, prim_l, len, 0, L.stack_slots, L.dc_words, &s_info[0]);
+      prepare_sub(sg, C, sc, job.tp, zin_l, zout_l, prim_l, len, 0, L.stack_slots, L.dc_words, &s_info[0], s_lvl_cur, &s_vchunk,
+                  L.tile_stats ? s_dbg : nullptr);
       t_prep += clock64() - t0;
     }
     __syncthreads();
@@ -937,7 +1135,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         // The next subfrustum's view is built while the other warps march.
         const long long t0 = clock64();
         prepare_sub(sg, C, sc, job.tp, zin_l, zout_l, prim_l, len, (k + 1) & 1, L.stack_slots, L.dc_words,
-                    &s_info[(k + 1) & 1]);
+                    &s_info[(k + 1) & 1], s_lvl_cur, &s_vchunk, L.tile_stats ? s_dbg : nullptr);
         t_prep += clock64() - t0;
         c_sub += 1;
         s_sub += 1;
@@ -989,8 +1187,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     __syncthreads();
     if (L.tile_stats && threadIdx.x == 0) {
       uint32_t *ts = L.tile_stats + (size_t)item * 16;
-      ts[8] = (uint32_t)s_dbg[0];
-      ts[9] = (uint32_t)s_dbg[1];
+      ts[8] = (uint32_t)(s_dbg[0] >> 4);
+      ts[9] = (uint32_t)(s_dbg[1] >> 4);
       ts[10] = (uint32_t)(s_dbg[2] >> 4);
       ts[11] = (uint32_t)(s_dbg[3] >> 4);
       ts[12] = (uint32_t)(s_dbg[4] >> 4);
@@ -1034,14 +1232,36 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
 }
 
 // ---- inspection kernels: the same view build and evaluator as k_trace ----------
+// method 0: the tracer's warp-parallel builder (build_view_lca); method 1:
+// Algorithm 1 as stated (one lane, fast ancestor pointers).  One warp;
+// `scratch` holds the builder's work arrays (pruned_view_scratch_words).
 __global__ void k_pruned_view(DevScene sc, const uint32_t *act, int n, uint32_t *view, uint32_t *vaddr,
-                              int32_t *info, uint32_t *bstk, int stack_cap) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  ViewInfo vi = build_view(sc, act, n, view, bstk, stack_cap, vaddr);
-  info[0] = vi.n_view;
-  info[1] = vi.root_used;
-  info[2] = vi.err;
-  info[3] = vi.n_prim;
+                              int32_t *info, uint32_t *scratch, int stack_cap, int method) {
+  if (blockIdx.x != 0) return;
+  ViewInfo vi;
+  int n_lvl = 0;
+  if (method == 0) {
+    __shared__ ViewChunk vch;
+    uint32_t *stk = scratch;   // 16-byte aligned (device allocation base)
+    uint2 *ops = reinterpret_cast<uint2 *>(scratch + align16((size_t)6 * (stack_cap + 2) * 4) / 4);
+    uint2 *sort_tmp = ops + n;
+    int *lvl_off = reinterpret_cast<int *>(sort_tmp + n);
+    int *lvl_cur = lvl_off + kMaxLevels + 1;
+    vi = build_view_lca(sc, act, n, view, vch, ops, sort_tmp, lvl_off, lvl_cur, stk, stack_cap, vaddr, &n_lvl);
+  } else {
+    if (threadIdx.x != 0) return;
+    vi = build_view(sc, act, n, view, scratch, stack_cap, vaddr);
+  }
+  if (threadIdx.x == 0) {
+    info[0] = vi.n_view;
+    info[1] = vi.root_used;
+    info[2] = vi.err;
+    info[3] = vi.n_prim;
+  }
+}
+
+size_t pruned_view_scratch_words(int n, int stack_cap) {
+  return align16((size_t)6 * (stack_cap + 2) * 4) / 4 + (size_t)n * 4 + 2 * (kMaxLevels + 1) + 16;
 }
 
 // f_A (and optionally its forward-mode gradient) at arbitrary points for a
@@ -1074,8 +1294,8 @@ __global__ void k_eval_view(DevScene sc, const uint32_t *view, const int32_t *in
 }
 
 void launch_pruned_view(const DevScene &sc, const uint32_t *act, int n, uint32_t *view, uint32_t *vaddr,
-                        int32_t *info, uint32_t *bstk, int stack_cap, cudaStream_t s) {
-  count_launch(), k_pruned_view<<<1, 32, 0, s>>>(sc, act, n, view, vaddr, info, bstk, stack_cap);
+                        int32_t *info, uint32_t *scratch, int stack_cap, int method, cudaStream_t s) {
+  count_launch(), k_pruned_view<<<1, 32, 0, s>>>(sc, act, n, view, vaddr, info, scratch, stack_cap, method);
 }
 
 void launch_eval_view(const DevScene &sc, const uint32_t *view, const int32_t *info, const float *pts, int npts,

@@ -74,6 +74,7 @@ _lib.st_trace.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINT
                           _P, _P, _P, _P, _P, _P]
 _lib.st_tiles_copy.argtypes = [C.POINTER(st_tiles), _P, _P, _P, _P, _P]
 _lib.st_pruned_view.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
+_lib.st_pruned_view_alg1.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
 _lib.st_eval_pruned.argtypes = [_P, _P, _P, _P, C.c_int, _P, _P, _P]
 _lib.st_kernel_launches.restype = C.c_uint64
 _lib.st_trace_noalloc.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINTER(st_trace_opts),
@@ -101,7 +102,7 @@ _lib.st_batch_destroy.restype = None
 _lib.st_render_batch.argtypes = [_P, _P, C.c_int, C.POINTER(st_trace_opts), _P, _P, _P, _P, C.c_char_p, _P]
 
 EXPORTED = ("st_scene_create", "st_scene_update_prims", "st_scene_addresses", "st_scene_destroy",
-            "st_build_tiles", "st_trace", "st_tiles_copy", "st_pruned_view", "st_eval_pruned", "st_prep_tree", "st_last_error",
+            "st_build_tiles", "st_trace", "st_tiles_copy", "st_pruned_view", "st_pruned_view_alg1", "st_eval_pruned", "st_prep_tree", "st_last_error",
             "st_version", "st_kernel_launches", "st_trace_noalloc", "st_trace_noalloc_scratch_bytes",
             "st_trace_record", "st_mlp_pack_size", "st_mlp_param_count", "st_mlp_pack", "st_mlp_grad",
             "st_mlp_adam", "st_mlp_infer", "st_tune_key", "st_tune_load", "st_tune_store", "st_autotune",
@@ -269,6 +270,11 @@ def st_mlp_infer(packed, x, omega, stream=None) -> None:
 def st_pruned_view(h, act, view, view_addr, info, stream=None) -> None:
     _check(_lib.st_pruned_view(h, _ptr(act), int(act.numel()), _ptr(view), _ptr(view_addr), _ptr(info),
                                _stream(stream)), "st_pruned_view")
+
+
+def st_pruned_view_alg1(h, act, view, view_addr, info, stream=None) -> None:
+    _check(_lib.st_pruned_view_alg1(h, _ptr(act), int(act.numel()), _ptr(view), _ptr(view_addr), _ptr(info),
+                                    _stream(stream)), "st_pruned_view_alg1")
 
 
 def st_eval_pruned(h, view, info, pts, f, grad=None, stream=None) -> None:

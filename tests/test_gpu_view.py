@@ -1,5 +1,7 @@
-"""Pruned tree views built on the GPU (Algorithm 1 with fast pointers) and
-their FP32 evaluation (Algorithm 3) against the oracle's definitions."""
+"""Pruned tree views built on the GPU -- the tracer's warp-parallel
+lowest-common-ancestor builder (st_pruned_view) and Algorithm 1 as stated
+with fast pointers (st_pruned_view_alg1) -- and their FP32 evaluation
+(Algorithm 3) against the oracle's definitions."""
 import numpy as np
 import pytest
 
@@ -11,22 +13,24 @@ pytestmark = pytest.mark.gpu
 CODE_TO_OP = {0: 3, 1: 3, 2: 3, 3: 3, 4: 3, 5: 3, 6: 3, 7: 3, 8: 3, 9: 0, 10: 1, 11: 2}
 
 
-def gpu_view(st, h, act_po, torch):
+def gpu_view(st, h, act_po, torch, method="lca"):
     act = torch.tensor(np.sort(act_po).astype(np.int32), device="cuda")
     n = len(act_po)
     view = torch.zeros(2 * n - 1, dtype=torch.int32, device="cuda")
     vaddr = torch.zeros(2 * n - 1, dtype=torch.int32, device="cuda")
     info = torch.zeros(4, dtype=torch.int32, device="cuda")
-    st.st_pruned_view(h, act, view, vaddr, info)
+    fn = st.st_pruned_view if method == "lca" else st.st_pruned_view_alg1
+    fn(h, act, view, vaddr, info)
     torch.cuda.synchronize()
     return view, vaddr, info
 
 
+@pytest.mark.parametrize("method", ["lca", "alg1"])
 @pytest.mark.parametrize("seed", range(4))
-def test_view_matches_definition(stlib, orc, cuda, seed):
+def test_view_matches_definition(stlib, orc, cuda, seed, method):
     import torch
     rng = np.random.default_rng(seed)
-    s = sg.make_scene(int(rng.integers(20, 400)), 14, 800 + seed, op_mix=(0.5, 0.25, 0.25))
+    s = sg.make_scene(int(rng.integers(20, 400)), 14, 800 + seed, op_mix=(0.5, 0.25, 0.25), sharp=seed % 2 == 1)
     st_ = orc.structure(s)
     h = stlib.st_scene_create(s)
     try:
@@ -36,7 +40,7 @@ def test_view_matches_definition(stlib, orc, cuda, seed):
             act = np.zeros(s.n_nodes, bool)
             act[rng.choice(prims, size=m, replace=False)] = True
             addr, opc, ru = orc.pruned_view(s, act)
-            view, vaddr, info = gpu_view(stlib, h, st_["po_of"][act], torch)
+            view, vaddr, info = gpu_view(stlib, h, st_["po_of"][act], torch, method)
             info = info.cpu().numpy()
             assert info[2] == 0
             assert info[0] == len(addr) and info[3] == m
@@ -114,5 +118,60 @@ def test_gradient_matches_central_differences(stlib, orc, cuda):
         a = angle(gg[smooth], cd[0][smooth])
         assert smooth.sum() > 300
         assert np.percentile(a, 99) < 1e-3 and a.max() < 5e-3
+    finally:
+        stlib.st_scene_destroy(h)
+
+
+def _comb(n, seed):
+    """A left comb of n primitives (tree depth n - 1) with mixed operators:
+    long ancestor chains for the binary-lifting search."""
+    base = sg.make_scene(n, None, seed)
+    prims = np.flatnonzero(base.kind < 16)[:n]
+    kinds = list(base.kind[prims])
+    params = [base.params[i] for i in prims]
+    rng = np.random.default_rng(seed)
+    left, right = [-1] * n, [-1] * n
+    cur = 0
+    for j in range(1, n):
+        op = [sg.OP_UNION, sg.OP_INTER, sg.OP_DIFF][int(rng.choice(3, p=[0.6, 0.2, 0.2]))]
+        k = rng.uniform(0.02, 0.1)
+        q = np.zeros(16, np.float32)
+        q[0], q[1] = k, 1.5 * k
+        kinds.append(op)
+        params.append(q)
+        left.append(cur)
+        right.append(j)
+        cur = len(kinds) - 1
+    return sg.Scene(kind=np.array(kinds, np.int32), left=np.array(left, np.int32), right=np.array(right, np.int32),
+                    params=np.array(params, np.float32), root=cur)
+
+
+@pytest.mark.parametrize("shape", ["comb", "clustered"])
+def test_lca_builder_equals_algorithm_1(stlib, orc, cuda, shape):
+    """Word-for-word identical views (codes and record offsets) from both
+    builders on deep trees and on large active sets of a 10,000-primitive
+    clustered scene."""
+    import torch
+    if shape == "comb":
+        s = _comb(300, 5)
+    else:
+        s = sg.workload_clustered(200)
+    st_ = orc.structure(s)
+    h = stlib.st_scene_create(s)
+    rng = np.random.default_rng(7)
+    try:
+        prims = np.flatnonzero(s.kind < 16)
+        for m in (1, 2, 3, 17, 200, min(len(prims), 3000)):
+            act = np.zeros(s.n_nodes, bool)
+            act[rng.choice(prims, size=m, replace=False)] = True
+            a = gpu_view(stlib, h, st_["po_of"][act], torch, "lca")
+            b = gpu_view(stlib, h, st_["po_of"][act], torch, "alg1")
+            ia, ib = a[2].cpu().numpy(), b[2].cpu().numpy()
+            assert ia.tolist() == ib.tolist() and ia[2] == 0
+            n = int(ia[0])
+            assert torch.equal(a[0][:n], b[0][:n]) and torch.equal(a[1][:n], b[1][:n])
+            if shape == "comb" and m <= 200:
+                addr, opc, ru = orc.pruned_view(s, act)
+                assert np.array_equal(a[1].cpu().numpy()[:n], addr) and int(ia[1]) == ru
     finally:
         stlib.st_scene_destroy(h)
