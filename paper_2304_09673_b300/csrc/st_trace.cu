@@ -987,20 +987,36 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
     pixel_ray(cam, M.x0 + r % M.tw, M.y0 + r / M.tw, d);
     const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     const float lim = M.tp->newton_clamp / dn;
-    bool beyond = false;
+    // Newton on f_A along the ray; a ray stops at its own convergence
+    // (|step| <= 1e-6 z, a few FP32 ulps of z), so its result does not
+    // depend on the other rays of the warp.
+    bool beyond = false, done = !v;
+    int n_eval = 0;
     for (int it = 0; it < M.tp->newton_iters; ++it) {
+      if (!__any_sync(0xFFFFFFFFu, !done)) break;
       Dual<1> pd[1][3], fd[1];
 #pragma unroll
       for (int k = 0; k < 3; ++k) { pd[0][k].v = cam.o[k] + zz * d[k]; pd[0][k].g[0] = d[k]; }
       eval_view_r<1, Dual<1>>(view, inf.n_view, src, pd, fd, stk);
-      beyond = false;
-      if (fd[0].g[0] != 0.f && isfinite(fd[0].v)) {
-        float step = -fd[0].v / fd[0].g[0];
-        step = fminf(fmaxf(step, -lim), lim);
-        beyond = zz + step > inf.z_end && fd[0].v > 0.f;
-        zz = fminf(fmaxf(zz + step, inf.z_begin), inf.z_end);
+      if (!done) {
+        ++n_eval;
+        beyond = false;
+        if (fd[0].g[0] != 0.f && isfinite(fd[0].v)) {
+          float step = -fd[0].v / fd[0].g[0];
+          step = fminf(fmaxf(step, -lim), lim);
+          beyond = zz + step > inf.z_end && fd[0].v > 0.f;
+          const float zn = fminf(fmaxf(zz + step, inf.z_begin), inf.z_end);
+          if (fabsf(zn - zz) <= 1e-6f * zz) done = true;
+          zz = zn;
+        } else {
+          done = true;
+        }
       }
     }
+    // Normal: gradient of f_A from three axis derivatives at the final point
+    // (not reusing the last Newton derivative: the field's gradient has kinks
+    // where the blend range b_r reaches zero, and the previous Newton point
+    // may lie across one).
     float g[3] = {0.f, 0.f, 0.f};
 #pragma unroll 1
     for (int k = 0; k < 3; ++k) {
@@ -1012,6 +1028,7 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
       g[1] = k == 1 ? fd[0].g[0] : g[1];
       g[2] = k == 2 ? fd[0].g[0] : g[2];
     }
+    n_eval += 3;
     const bool back = v && beyond;
     if (back) {
       C.ray_z[r] = inf.z_end;
@@ -1028,7 +1045,7 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
       M.out->normal[3 * o + 2] = g[2] * ig;
       M.out->evals[o] = C.ray_st[r] & 0xFFFFFFu;
       M.out->flags[o] = 1;
-      c_fin += (uint64_t)M.tp->newton_iters + 3;
+      c_fin += (uint64_t)n_eval;
     }
   }
 }
