@@ -65,3 +65,63 @@ def angle(a, b):
     nb = np.linalg.norm(b, axis=-1)
     c = np.sum(a * b, axis=-1) / np.maximum(na * nb, 1e-300)
     return np.arccos(np.clip(c, -1, 1))
+
+
+def parity(orc, s, cam, g, ref, pix=None, normal_tol=1e-3):
+    H, W = cam.height, cam.width
+    _, _, diam = orc.scene_bounds(s)
+    if pix is None:
+        band = band_mask(orc, s, cam, ref)
+        pi, pj = ref["pi"], ref["pj"]
+    else:
+        pi, pj = pix
+        band = np.zeros(len(pi), bool)
+    gf = g["flags"][pj, pi]
+    unconv = (gf & 2) != 0
+    assert unconv.mean() <= 1e-3, unconv.mean()
+    ghit = (gf & 1) != 0
+    ohit = (ref["flags"] & 1) != 0
+    band = band.reshape(-1) if pix is None else band
+    keep = ~band & ~unconv
+    mism = (ghit != ohit) & keep
+    assert mism.sum() == 0, f"{mism.sum()} mask mismatches of {keep.sum()}"
+    both = ghit & ohit & keep
+    dd = np.abs(g["depth"][pj, pi][both].astype(np.float64) - ref["depth"][both])
+    assert dd.max(initial=0) <= 1e-4 * diam, dd.max()
+    # normals: GPU normal vs FP64 central differences at the GPU's hit point
+    d64, _ = orc.camera_rays(cam, pi[both], pj[both])
+    o = np.array(cam.eye, np.float64)
+    t = g["depth"][pj, pi][both].astype(np.float64) / np.linalg.norm(d64, axis=1)
+    P = o + t[:, None] * d64
+    hh = 1e-6
+    c = np.zeros_like(P)
+    for k in range(3):
+        e = np.zeros(3); e[k] = hh
+        c[:, k] = (orc.field(s, P + e) - orc.field(s, P - e)) / (2 * hh)
+    a = angle(g["normal"][pj, pi][both].astype(np.float64), c)
+    # exclude creases (normal not defined): central differences disagree across h
+    c2 = np.zeros_like(P)
+    for k in range(3):
+        e = np.zeros(3); e[k] = 1e-5
+        c2[:, k] = (orc.field(s, P + e) - orc.field(s, P - e)) / 2e-5
+    smooth = angle(c, c2) < 1e-4
+    assert np.all(a[smooth] < normal_tol), np.sort(a[smooth])[-5:]
+    return dict(n_hit=int(both.sum()), band=int(band.sum()), max_depth_err=float(dd.max(initial=0)))
+
+
+def sampled_parity(orc, s, cam, g, n, seed=1, normal_tol=1e-3):
+    """parity() on n random pixels of a frame too large for a full oracle
+    frame; the band test is per pixel from the oracle's own hit and min f."""
+    rng = np.random.default_rng(seed)
+    pi = rng.integers(0, cam.width, n).astype(np.int32)
+    pj = rng.integers(0, cam.height, n).astype(np.int32)
+    ref = orc.trace(s, cam, pi, pj)
+    _, _, diam = orc.scene_bounds(s)
+    d64, _ = orc.camera_rays(cam, pi, pj)
+    cosn = np.abs(np.sum(ref["normal"] * d64 / np.linalg.norm(d64, axis=1, keepdims=True), axis=1))
+    ohit = (ref["flags"] & 1) != 0
+    band = (ohit & (cosn < 0.05)) | (~ohit & (ref["min_f"] < 1e-4 * diam)) | near_miss(ref)
+    keep = ~band
+    sub = dict(flags=ref["flags"][keep], depth=ref["depth"][keep], normal=ref["normal"][keep],
+               min_f=ref["min_f"][keep], resid=ref["resid"][keep], pi=pi[keep], pj=pj[keep])
+    return parity(orc, s, cam, g, sub, pix=(pi[keep], pj[keep]), normal_tol=normal_tol)

@@ -8,7 +8,7 @@ import pytest
 from oracle import mlp as omlp
 from paper_2304_09673_b300 import scenegen as sg
 from gpu_util import render
-from test_gpu_trace import _parity
+from gpu_util import parity as _parity
 
 pytestmark = pytest.mark.gpu
 

@@ -5,51 +5,10 @@ import numpy as np
 import pytest
 
 from paper_2304_09673_b300 import scenegen as sg
-from gpu_util import angle, band_mask, near_miss, render
+from gpu_util import near_miss, render, sampled_parity
+from gpu_util import parity as _parity
 
 pytestmark = pytest.mark.gpu
-
-
-def _parity(orc, s, cam, g, ref, pix=None, normal_tol=1e-3):
-    H, W = cam.height, cam.width
-    _, _, diam = orc.scene_bounds(s)
-    if pix is None:
-        band = band_mask(orc, s, cam, ref)
-        pi, pj = ref["pi"], ref["pj"]
-    else:
-        pi, pj = pix
-        band = np.zeros(len(pi), bool)
-    gf = g["flags"][pj, pi]
-    unconv = (gf & 2) != 0
-    assert unconv.mean() <= 1e-3, unconv.mean()
-    ghit = (gf & 1) != 0
-    ohit = (ref["flags"] & 1) != 0
-    band = band.reshape(-1) if pix is None else band
-    keep = ~band & ~unconv
-    mism = (ghit != ohit) & keep
-    assert mism.sum() == 0, f"{mism.sum()} mask mismatches of {keep.sum()}"
-    both = ghit & ohit & keep
-    dd = np.abs(g["depth"][pj, pi][both].astype(np.float64) - ref["depth"][both])
-    assert dd.max(initial=0) <= 1e-4 * diam, dd.max()
-    # normals: GPU normal vs FP64 central differences at the GPU's hit point
-    d64, _ = orc.camera_rays(cam, pi[both], pj[both])
-    o = np.array(cam.eye, np.float64)
-    t = g["depth"][pj, pi][both].astype(np.float64) / np.linalg.norm(d64, axis=1)
-    P = o + t[:, None] * d64
-    hh = 1e-6
-    c = np.zeros_like(P)
-    for k in range(3):
-        e = np.zeros(3); e[k] = hh
-        c[:, k] = (orc.field(s, P + e) - orc.field(s, P - e)) / (2 * hh)
-    a = angle(g["normal"][pj, pi][both].astype(np.float64), c)
-    # exclude creases (normal not defined): central differences disagree across h
-    c2 = np.zeros_like(P)
-    for k in range(3):
-        e = np.zeros(3); e[k] = 1e-5
-        c2[:, k] = (orc.field(s, P + e) - orc.field(s, P - e)) / 2e-5
-    smooth = angle(c, c2) < 1e-4
-    assert np.all(a[smooth] < normal_tol), np.sort(a[smooth])[-5:]
-    return dict(n_hit=int(both.sum()), band=int(band.sum()), max_depth_err=float(dd.max(initial=0)))
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -102,18 +61,5 @@ def test_trace_1080p_sampled(stlib, orc, cuda):
     s = sg.workload_1080p(100)
     cam = sg.default_camera(1920, 1080)
     g = render(stlib, s, cam)
-    rng = np.random.default_rng(1)
-    pi = rng.integers(0, 1920, 800).astype(np.int32)
-    pj = rng.integers(0, 1080, 800).astype(np.int32)
-    ref = orc.trace(s, cam, pi, pj)
-    # sampled pixels: band test per pixel from the oracle's own hit / min f
-    _, _, diam = orc.scene_bounds(s)
-    d64, _ = orc.camera_rays(cam, pi, pj)
-    cosn = np.abs(np.sum(ref["normal"] * d64 / np.linalg.norm(d64, axis=1, keepdims=True), axis=1))
-    ohit = (ref["flags"] & 1) != 0
-    band = (ohit & (cosn < 0.05)) | (~ohit & (ref["min_f"] < 1e-4 * diam)) | near_miss(ref)
-    keep = ~band
-    sub = dict(flags=ref["flags"][keep], depth=ref["depth"][keep], normal=ref["normal"][keep],
-               min_f=ref["min_f"][keep], resid=ref["resid"][keep], pi=pi[keep], pj=pj[keep])
-    _parity(orc, s, cam, g, sub, pix=(pi[keep], pj[keep]))
+    sampled_parity(orc, s, cam, g, 800, seed=1)
     assert (g["flags"] & 2).mean() <= 1e-3
