@@ -85,7 +85,7 @@ struct st_scene {
   DBuf<uint32_t> prim;
   DBuf<Job> job;
   // tracing
-  DBuf<uint32_t> g_work, item_counter;
+  DBuf<uint32_t> g_work, item_counter, order;
   // updates
   DBuf<float4> upd_words;
   DBuf<uint32_t> upd_index;
@@ -199,7 +199,8 @@ void st_scene_destroy(st_scene *s) {
   s->cand_count.release(); s->cand_off.release(); s->tile_count.release(); s->offsets.release();
   s->scan_sums.release(); s->small.release(); s->rects.release(); s->pairs.release(); s->keys.release();
   s->ztmp.release(); s->z_in.release(); s->z_out.release(); s->prim.release(); s->job.release();
-  s->g_work.release(); s->item_counter.release(); s->upd_words.release(); s->upd_index.release();
+  s->g_work.release(); s->item_counter.release(); s->order.release(); s->upd_words.release();
+  s->upd_index.release();
   delete s;
 }
 
@@ -439,6 +440,9 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
   ST_CK(s->job.ensure(1));
   ST_CK(cudaMemcpyAsync(s->job.p, &job, sizeof(Job), cudaMemcpyHostToDevice, st));
   ST_CK(cudaMemsetAsync(s->item_counter.p, 0, 4, st));
+  ST_CK(s->order.ensure(L.n_items));
+  launch_tile_order(s->job.p, 1, L.n_items, s->order.p, st);
+  L.order = s->order.p;
   ST_CK(trace_launch(s->job.p, 1, L, s->n_sm, st));
   return ST_OK;
 }

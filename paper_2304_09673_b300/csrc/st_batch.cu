@@ -222,7 +222,7 @@ struct st_batch {
   uint32_t n_prims = 0, n_tiles = 0;
   std::vector<Job> jobs;
   Buf<Job> d_jobs;
-  Buf<uint32_t> cand_count, cand_off, tile_count, offsets, scan_sums, small, item_counter, status, g_work;
+  Buf<uint32_t> cand_count, cand_off, tile_count, offsets, scan_sums, small, item_counter, status, g_work, order;
   Buf<int4> rects;
   Buf<Pair> pairs;
   Buf<uint64_t> keys, counters;
@@ -302,6 +302,7 @@ int plan(st_batch *b) {
   BK(b->rects.ensure(b->n_prims));
   BK(b->tile_count.ensure(b->n_tiles));
   BK(b->offsets.ensure((size_t)b->n_tiles + 1));
+  BK(b->order.ensure(b->n_tiles));
   BK(b->scan_sums.ensure(std::max(scan_block_count(b->n_prims), scan_block_count(b->n_tiles)) + 2));
   BK(b->small.ensure(16));
   BK(b->item_counter.ensure(1));
@@ -357,6 +358,7 @@ int plan(st_batch *b) {
   L.item_counter = b->item_counter.p;
   L.counters = b->counters.p;
   L.status = b->status.p;
+  L.order = b->order.p;
   L.step_mode = b->opts.step_mode;
   L.mlp = L.step_mode == ST_STEP_LEARNED ? b->opts.mlp : nullptr;
   if (L.step_mode == ST_STEP_LEARNED && L.stack_slots < 10) L.stack_slots = 10;
@@ -382,6 +384,7 @@ int plan(st_batch *b) {
   launch_check_capacity(b->small.p + 1, b->pair_cap, b->small.p + 2, b->overlap_cap, b->status.p, cs);
   launch_scatter_sort(b->pairs.p, b->small.p + 1, b->pair_cap, b->offsets.p, b->n_tiles, b->overlap_cap, b->keys.p,
                       b->ztmp.p, b->z_in.p, b->z_out.p, b->prim.p, b->n_sm, cs, b->status.p);
+  launch_tile_order(b->d_jobs.p, n, b->n_tiles, b->order.p, cs);
   cudaError_t le = trace_launch_planned(b->d_jobs.p, n, L, b->grid, b->smem, cs);
   cudaGraph_t g = nullptr;
   cudaError_t ce = cudaStreamEndCapture(cs, &g);
@@ -403,7 +406,7 @@ void destroy(st_batch *b) {
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   b->d_jobs.release(); b->cand_count.release(); b->cand_off.release(); b->tile_count.release();
   b->offsets.release(); b->scan_sums.release(); b->small.release(); b->item_counter.release();
-  b->status.release(); b->g_work.release(); b->rects.release(); b->pairs.release(); b->keys.release();
+  b->status.release(); b->g_work.release(); b->order.release(); b->rects.release(); b->pairs.release(); b->keys.release();
   b->counters.release(); b->ztmp.release(); b->z_in.release(); b->z_out.release(); b->prim.release();
   delete b;
 }

@@ -59,6 +59,8 @@ struct TraceLaunch {
   int32_t rec_stride;      // record rays whose pixel index % stride == 0
   uint32_t *status;        // optional status word (ST_STATUS_*); the kernel
                            // returns at once when the capacity bit is set
+  const uint32_t *order;   // optional [n_items] global tile per work item
+                           // (launch_tile_order: longest list first)
 };
 
 constexpr int ST_STEP_RECORD = 3;   // plain stepping that records training data
@@ -73,6 +75,10 @@ cudaError_t trace_plan(const TraceLaunch &L, int n_sm, int *grid, size_t *smem);
 cudaError_t trace_launch_planned(const Job *jobs, int n_jobs, const TraceLaunch &L, int grid, size_t smem,
                                  cudaStream_t s);
 int trace_warps_per_cta();
+// Work order of a trace launch: the jobs' n_tiles global tiles sorted by
+// A-buffer list length, longest first (counting sort; equal lengths in any
+// order -- results do not depend on the order tiles are traced in).
+void launch_tile_order(const Job *jobs, int n_jobs, uint32_t n_tiles, uint32_t *order, cudaStream_t s);
 int trace_ctas_per_sm(const TraceLaunch &L);
 void launch_pruned_view(const DevScene &sc, const uint32_t *act, int n, uint32_t *view, uint32_t *vaddr,
                         int32_t *info, uint32_t *scratch, int stack_cap, int method, cudaStream_t s);

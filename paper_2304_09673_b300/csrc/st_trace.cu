@@ -1084,10 +1084,11 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     __syncthreads();
     const uint32_t item = s_item;
     if (item >= L.n_items) break;
-    const int jb = find_job_tile(jobs, n_jobs, item);
+    const uint32_t gtile = L.order ? L.order[item] : item;
+    const int jb = find_job_tile(jobs, n_jobs, gtile);
     const Job &job = jobs[jb];
     const DevScene &sc = job.sc;
-    const uint32_t tile = item - job.tile_base;
+    const uint32_t tile = gtile - job.tile_base;
     const int T = job.tl.tile;
     const int tx = (int)(tile % (uint32_t)job.tl.tiles_x), ty = (int)(tile / (uint32_t)job.tl.tiles_x);
     MarchCtx M;
@@ -1203,7 +1204,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     }
     __syncthreads();
     if (L.tile_stats && threadIdx.x == 0) {
-      uint32_t *ts = L.tile_stats + (size_t)item * 16;
+      uint32_t *ts = L.tile_stats + (size_t)gtile * 16;
       ts[8] = (uint32_t)(s_dbg[0] >> 4);
       ts[9] = (uint32_t)(s_dbg[1] >> 4);
       ts[10] = (uint32_t)(s_dbg[2] >> 4);
@@ -1246,6 +1247,64 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       if (c_err) atomicOr((unsigned long long *)&L.counters[7], (unsigned long long)c_err);
     }
   }
+}
+
+// ---- work order: longest tile lists first ----------------------------------------
+// One CTA: histogram of list lengths (4096 bins, longer lists share the
+// last), bins scanned from the longest down, tiles scattered.  Heavy tiles
+// then start while every SM is free instead of finishing last.
+__global__ void __launch_bounds__(1024) k_tile_order(const Job *jobs, int n_jobs, uint32_t n_tiles, uint32_t *order) {
+  constexpr int kBins = 4096;
+  __shared__ uint32_t cnt[kBins];
+  __shared__ uint32_t s_warp[32];
+  auto tile_bin = [&](uint32_t g) -> uint32_t {
+    const Job &job = jobs[find_job_tile(jobs, n_jobs, g)];
+    const uint32_t t = g - job.tile_base;
+    return min(job.tl.offsets[t + 1] - job.tl.offsets[t], (uint32_t)kBins - 1u);
+  };
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) cnt[i] = 0u;
+  __syncthreads();
+  for (uint32_t g = threadIdx.x; g < n_tiles; g += blockDim.x) atomicAdd(&cnt[tile_bin(g)], 1u);
+  __syncthreads();
+  // exclusive scan over bins in descending order: thread t owns 4 bins
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t v[4], sum = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[q] = cnt[kBins - 1 - (threadIdx.x * 4 + q)];
+    sum += v[q];
+  }
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = s_warp[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  uint32_t base = (warp > 0 ? s_warp[warp - 1] : 0u) + x - sum;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    cnt[kBins - 1 - (threadIdx.x * 4 + q)] = base;   // start of the bin in the order
+    base += v[q];
+  }
+  __syncthreads();
+  for (uint32_t g = threadIdx.x; g < n_tiles; g += blockDim.x) order[atomicAdd(&cnt[tile_bin(g)], 1u)] = g;
+}
+
+void launch_tile_order(const Job *jobs, int n_jobs, uint32_t n_tiles, uint32_t *order, cudaStream_t s) {
+  if (n_tiles) count_launch(), k_tile_order<<<1, 1024, 0, s>>>(jobs, n_jobs, n_tiles, order);
 }
 
 // ---- inspection kernels: the same view build and evaluator as k_trace ----------
