@@ -63,6 +63,22 @@ def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The slowest rank's time (replicas: every rank runs the same work)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units processed by all ranks / the max-over-ranks time."""
+    return units_per_rank * world / seconds
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason sampling during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -282,11 +298,7 @@ def run_ours(args):
         res = timed_loop(st, r, cam, opts, args.steps, args.warmup, flush, stream)
         if sampler:
             clocks = sampler.stop()
-        total_ms = sum(res["step_ms"])
-        if world > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(res["step_ms"]), world)
         res["ms_per_step"] = total_ms / args.steps
         results[name] = res
         images[name] = (r.flags.clone(), r.depth.clone())
@@ -338,14 +350,10 @@ def run_ours(args):
         t0 = time.perf_counter()
         e2e_step()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = statistics.mean(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(statistics.mean(e2e_times), world)
 
     if rank == 0:
-        rays = W * H * world
+        rays = W * H * world   # whole job: every rank traces the same frame
         peaks = measured_peaks()
         sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
         peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
@@ -354,7 +362,7 @@ def run_ours(args):
             cnt = res["cnt"]
             ms = res["ms_per_step"]
             trace_s = statistics.mean(res["trace_ms"]) / 1e3
-            return {"rays_per_s": rays / (ms / 1e3), "ms_per_step": ms,
+            return {"rays_per_s": whole_job_rate(W * H, world, ms / 1e3), "ms_per_step": ms,
                     "prim_evals_per_s": cnt[:, 1].mean() * world / (ms / 1e3),
                     "trace_ms": trace_s * 1e3, "build_tiles_ms": statistics.mean(res["tiles_ms"]),
                     "steps_per_ray": cnt[:, 0].mean() / (W * H),
@@ -380,7 +388,7 @@ def run_ours(args):
                          "peak_note": f"FP32 FMA pipe: {props.multi_processor_count} SMs x 128 lanes x 2 flops x "
                                       f"{sm_mhz:.0f} MHz (max SM clock); achieved = useful field-evaluation "
                                       "flops (fixed per-node counts) / st_trace event time"},
-            "e2e": {"value": rays / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": whole_job_rate(W * H, world, e2e_s), "unit": "rays/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": results[head]["launches"],
             "clocks": clocks,
