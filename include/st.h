@@ -147,7 +147,8 @@ typedef struct {
                                [13] sum of view lengths, [14] sum of
                                operator levels; [8] discard, [9] fetch,
                                [10] view build, [11] parameter cache fill
-                               cycles / 16 (first warp); [15] zero
+                               cycles / 16 (first warp); [15] marching
+                               cycles / 16 summed over warps
                                (NULL = off)                                */
     float omega;            /* relaxation factor of ST_STEP_OVERRELAX [1.7,
                                Sec. 10]                                    */

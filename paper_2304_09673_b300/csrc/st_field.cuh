@@ -100,6 +100,22 @@ template <int N> __device__ __forceinline__ Dual<N> max_(const Dual<N> &a, const
 template <int N> __device__ __forceinline__ Dual<N> max_(const Dual<N> &a, float b) { return b > a.v ? Dual<N>(b) : a; }
 template <int N> __device__ __forceinline__ Dual<N> min_(const Dual<N> &a, float b) { return b < a.v ? Dual<N>(b) : a; }
 
+// Explicitly rounded FP32 arithmetic.  The field is evaluated by several code
+// paths (lockstep over two rays per lane, the warp-wide tail evaluation) and
+// a ray's trajectory must not depend on which one steps it, so the fusion of
+// products and sums into FMA is written out instead of left to the compiler.
+// Dual numbers (single code path, refinement only) use their operators.
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <class A, class B> __device__ __forceinline__ auto add_(const A &a, const B &b) { return a + b; }
+template <class A, class B> __device__ __forceinline__ auto sub_(const A &a, const B &b) { return a - b; }
+template <class A, class B> __device__ __forceinline__ auto mul_(const A &a, const B &b) { return a * b; }
+template <class A, class B, class C> __device__ __forceinline__ auto fma_(const A &a, const B &b, const C &c) {
+  return a * b + c;
+}
+
 // Record word k of a view node: from the view's shared parameter cache or,
 // for nodes that did not fit, from the scene's global record array.
 struct RecSrc {
@@ -115,31 +131,31 @@ __device__ __forceinline__ float4 ldrec(const float4 *q) { return *q; }
 // ---- primitives (exact SDFs, Lipschitz 1); records preloaded ----------------------
 template <class T>
 __device__ __forceinline__ T sd_sphere(const float4 a, const T p[3]) {
-  T dx = p[0] - a.x, dy = p[1] - a.y, dz = p[2] - a.z;
-  return sqrt_(dx * dx + dy * dy + dz * dz) - a.w;
+  const T dx = sub_(p[0], a.x), dy = sub_(p[1], a.y), dz = sub_(p[2], a.z);
+  return sub_(sqrt_(fma_(dx, dx, fma_(dy, dy, mul_(dz, dz)))), a.w);
 }
 
 // q = |M (p - c)| - b ; |max(q, 0)| + min(max_i q_i, 0) - r_round
 template <class T>
 __device__ __forceinline__ T sd_rbox(const float4 a0, const float4 a1, const float4 a2, const float4 a3,
                                      const T p[3]) {
-  T wx = p[0] - a0.x, wy = p[1] - a0.y, wz = p[2] - a0.z;
-  T q0 = abs_(wx * a1.x + wy * a1.y + wz * a1.z) - a1.w;
-  T q1 = abs_(wx * a2.x + wy * a2.y + wz * a2.z) - a2.w;
-  T q2 = abs_(wx * a3.x + wy * a3.y + wz * a3.z) - a3.w;
-  T m0 = max_(q0, 0.f), m1 = max_(q1, 0.f), m2 = max_(q2, 0.f);
-  T inner = min_(max_(q0, max_(q1, q2)), 0.f);
-  return sqrt_(m0 * m0 + m1 * m1 + m2 * m2) + inner - a0.w;
+  const T wx = sub_(p[0], a0.x), wy = sub_(p[1], a0.y), wz = sub_(p[2], a0.z);
+  const T q0 = sub_(abs_(fma_(wx, a1.x, fma_(wy, a1.y, mul_(wz, a1.z)))), a1.w);
+  const T q1 = sub_(abs_(fma_(wx, a2.x, fma_(wy, a2.y, mul_(wz, a2.z)))), a2.w);
+  const T q2 = sub_(abs_(fma_(wx, a3.x, fma_(wy, a3.y, mul_(wz, a3.z)))), a3.w);
+  const T m0 = max_(q0, 0.f), m1 = max_(q1, 0.f), m2 = max_(q2, 0.f);
+  const T inner = min_(max_(q0, max_(q1, q2)), 0.f);
+  return sub_(add_(sqrt_(fma_(m0, m0, fma_(m1, m1, mul_(m2, m2)))), inner), a0.w);
 }
 
 // distance to segment [a, b] minus r; records [a, r] and [b - a, 1/|b-a|^2]
 template <class T>
 __device__ __forceinline__ T sd_capsule(const float4 a0, const float4 a2, const T p[3]) {
-  T px = p[0] - a0.x, py = p[1] - a0.y, pz = p[2] - a0.z;
-  T h = (px * a2.x + py * a2.y + pz * a2.z) * a2.w;
+  const T px = sub_(p[0], a0.x), py = sub_(p[1], a0.y), pz = sub_(p[2], a0.z);
+  T h = mul_(fma_(px, a2.x, fma_(py, a2.y, mul_(pz, a2.z))), a2.w);
   h = min_(max_(h, 0.f), 1.f);
-  T dx = px - h * a2.x, dy = py - h * a2.y, dz = pz - h * a2.z;
-  return sqrt_(dx * dx + dy * dy + dz * dz) - a0.w;
+  const T dx = fma_(h, -a2.x, px), dy = fma_(h, -a2.y, py), dz = fma_(h, -a2.z, pz);
+  return sub_(sqrt_(fma_(dx, dx, fma_(dy, dy, mul_(dz, dz)))), a0.w);
 }
 
 // ---- compact smooth operators G_op (Sec. 5) -------------------------------------
@@ -147,11 +163,16 @@ __device__ __forceinline__ T sd_capsule(const float4 a0, const float4 a2, const 
 // d(f0, f1, k) = k/6 max(1 - a/k, 0)^3 with a = |f0 - f1|; transition
 // b_r(x) = k max(1 - c1 x, 0); a non-positive blend range gives no blend.
 template <class T>
-__device__ __forceinline__ T disp_range(const T &kr, const T &a) {
+__device__ __forceinline__ T cube_(const T &x) { return mul_(x, mul_(x, x)); }
+
+// Displacement with blend range kr, as (kr / 6) and max(1 - a/kr, 0)^3 for a
+// fused m -/+ (kr/6) x^3; a non-positive range gives no displacement.
+template <class T>
+__device__ __forceinline__ void disp_terms(const T &kr, const T &a, T &kr6, T &x3) {
   const bool pos = val(kr) > 1e-30f;
-  T x = max_(kr - a, 0.f) * rcp_(pos ? kr : T(1.f));
-  T d = (kr * (1.f / 6.f)) * (x * x * x);
-  return pos ? d : T(0.f);
+  const T x = mul_(max_(sub_(kr, a), 0.f), rcp_(pos ? kr : T(1.f)));
+  kr6 = pos ? mul_(kr, 1.f / 6.f) : T(0.f);
+  x3 = cube_(x);
 }
 
 // Branch-free: the blended value is always computed and selected by the
@@ -159,31 +180,36 @@ __device__ __forceinline__ T disp_range(const T &kr, const T &a) {
 template <uint32_t CODE, class T>
 __device__ __forceinline__ T op_compact(float4 c, const T &f0, const T &f1) {
   const bool inside = val(f0) <= c.y && val(f1) <= c.y;
+  const float k6 = mul_(c.x, 1.f / 6.f);
+  T kr6, x3;
   if (CODE == V_UNION) {
-    T m = min_(f0, f1);
-    T a = abs_(f0 - f1);
-    T x = max_(c.x - a, 0.f) * c.w;
-    T g = m - (c.x * (1.f / 6.f)) * (x * x * x);
-    T kr = c.x * max_(1.f - g * c.z, 0.f);
-    T res = m - disp_range(kr, a);
+    const T m = min_(f0, f1);
+    const T a = abs_(sub_(f0, f1));
+    const T x = mul_(max_(sub_(c.x, a), 0.f), c.w);
+    const T g = fma_(cube_(x), -k6, m);
+    const T kr = mul_(max_(fma_(g, -c.z, 1.f), 0.f), c.x);
+    disp_terms(kr, a, kr6, x3);
+    const T res = fma_(-kr6, x3, m);
     return inside ? res : m;
   } else if (CODE == V_INTER) {
-    T m = max_(f0, f1);
-    T a = abs_(f0 - f1);
-    T x = max_(c.x - a, 0.f) * c.w;
-    T g = m + (c.x * (1.f / 6.f)) * (x * x * x);
-    T kr = min_(c.x * max_(1.f - g * c.z, 0.f), c.x);
-    T res = m + disp_range(kr, a);
+    const T m = max_(f0, f1);
+    const T a = abs_(sub_(f0, f1));
+    const T x = mul_(max_(sub_(c.x, a), 0.f), c.w);
+    const T g = fma_(cube_(x), k6, m);
+    const T kr = min_(mul_(max_(fma_(g, -c.z, 1.f), 0.f), c.x), c.x);
+    disp_terms(kr, a, kr6, x3);
+    const T res = fma_(kr6, x3, m);
     return inside ? res : m;
   } else {
     // difference: csg max(f0, -f1), displacement d(f0, -f1, .)
-    T nf1 = -f1;
-    T m = max_(f0, nf1);
-    T a = abs_(f0 - nf1);
-    T x = max_(c.x - a, 0.f) * c.w;
-    T g = m + (c.x * (1.f / 6.f)) * (x * x * x);
-    T kr = min_(abs_(c.x * max_(1.f - g * c.z, 0.f)), c.x);
-    T res = m + disp_range(kr, a);
+    const T nf1 = -f1;
+    const T m = max_(f0, nf1);
+    const T a = abs_(sub_(f0, nf1));
+    const T x = mul_(max_(sub_(c.x, a), 0.f), c.w);
+    const T g = fma_(cube_(x), k6, m);
+    const T kr = min_(abs_(mul_(max_(fma_(g, -c.z, 1.f), 0.f), c.x)), c.x);
+    disp_terms(kr, a, kr6, x3);
+    const T res = fma_(kr6, x3, m);
     return inside ? res : m;
   }
 }

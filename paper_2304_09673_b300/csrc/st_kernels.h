@@ -36,6 +36,7 @@ cudaError_t cull_set_attributes();
 constexpr uint32_t ST_STATUS_VIEW = 1u;       // a pruned view exceeded its capacity
 constexpr uint32_t ST_STATUS_STACK = 2u;      // evaluation stack overflow
 constexpr uint32_t ST_STATUS_CAPACITY = 4u;   // entries / list length beyond the planned buffers
+constexpr uint32_t ST_STATUS_WAIT = 8u;       // a bounded wait inside a CTA expired
 
 // Tracing: per-warp working set layout is computed by trace_layout().
 struct TraceLaunch {

@@ -46,6 +46,7 @@ __host__ __device__ inline size_t bstk_words(const TraceLaunch &L) { return 6 * 
 __host__ __device__ inline size_t smem_fixed_bytes(const TraceLaunch &L) {
   const size_t r = (size_t)L.max_tile_rays;
   return align16(r * 4) + align16(r * 4) + 2 * align16(r * 2) + (size_t)kWarps * align16(r * 2) +
+         align16(r * 16) + align16(r * 8) + align16(r * 8) +
          (size_t)kWarps * align16((size_t)L.stack_slots * 32 * 8) + align16(bstk_words(L) * 4) +
          2 * (size_t)L.dc_words * 16 + (L.mlp ? kMlpPackBytes : 0);
 }
@@ -67,6 +68,9 @@ struct CtaWork {
   uint32_t *ray_st;   // [rays] steps | status << 24
   uint16_t *alive[2]; // pending rays, read list / append list (alternating)
   uint16_t *hits;     // [kWarps][rays] rays that hit in the current subfrustum
+  float4 *rs4;        // [rays] state of a ray handed to another warp: rp, dzp, zf, zs
+  float2 *rs2;        // [rays] ... rs, f at the previous point
+  unsigned long long *tq;  // [rays] shared tail queue: (tag << 32) | ray
   float2 *stk;        // [kWarps][stack_slots][32]
   uint32_t *bstk;     // Algorithm 1 stack
   uint32_t *act[2];
@@ -87,6 +91,9 @@ __device__ CtaWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork
   w.alive[0] = (uint16_t *)p; p += align16(r * 2);
   w.alive[1] = (uint16_t *)p; p += align16(r * 2);
   w.hits = (uint16_t *)p; p += (size_t)kWarps * align16(r * 2);
+  w.rs4 = (float4 *)p; p += align16(r * 16);
+  w.rs2 = (float2 *)p; p += align16(r * 8);
+  w.tq = (unsigned long long *)p; p += align16(r * 8);
   w.stk = (float2 *)p; p += (size_t)kWarps * align16((size_t)L.stack_slots * 32 * 8);
   w.bstk = (uint32_t *)p; p += align16(bstk_words(L) * 4);
   w.dc[0] = (float4 *)p; p += (size_t)L.dc_words * 16;
@@ -695,7 +702,7 @@ __device__ __forceinline__ void load_ray(const MarchCtx &M, const CtaWork &C, in
   z = fmaxf(C.ray_z[r], z_begin);
   steps = C.ray_st[r] & 0xFFFFFFu;
   pixel_ray(*M.cam, M.x0 + r % M.tw, M.y0 + r / M.tw, d);
-  inv_ld = 1.0f / (M.tp->lipschitz * sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+  inv_ld = 1.0f / mul_(M.tp->lipschitz, sqrtf(fma_(d[0], d[0], fma_(d[1], d[1], mul_(d[2], d[2])))));
 }
 
 __device__ __forceinline__ void write_miss(const MarchCtx &M, int r, uint32_t steps, uint8_t flag) {
@@ -719,6 +726,34 @@ __device__ __forceinline__ void append_rays(bool want, int r, uint16_t *list, in
   if (want) list[base + __popc(m & lanemask_lt())] = (uint16_t)r;
 }
 
+// ---- tail sharing between the warps of a tile ----------------------------------
+// A warp that is down to a few rays of a subfrustum keeps one and hands the
+// others to a shared queue (state saved per ray in shared memory); warps
+// without rays pop them instead of waiting at the end of the subfrustum.  A
+// ray's trajectory does not depend on the warp that steps it.  Entries are
+// (tag << 32) | ray with a tag unique per subfrustum of the CTA, so a popper
+// can wait for the pusher's store; every wait is bounded.
+constexpr uint32_t kIdleSpinLimit = 1u << 22;
+constexpr uint32_t kEntrySpinLimit = 1u << 16;
+
+__device__ __forceinline__ int tq_pop(unsigned long long *tq, int *tail, int *head, uint32_t tag, int cap,
+                                      uint32_t &err) {
+  const int t = *(volatile int *)tail;
+  const int h = *(volatile int *)head;
+  if (h >= t || h >= cap) return -1;
+  if (atomicCAS(head, h, h + 1) != h) return -1;
+  for (uint32_t it = 0; it < kEntrySpinLimit; ++it) {
+    const unsigned long long e = *(volatile unsigned long long *)(tq + h);
+    if ((uint32_t)(e >> 32) == tag) {
+      __threadfence_block();
+      return (int)(uint32_t)(e & 0xFFFFFFFFull);
+    }
+    __nanosleep(20);
+  }
+  err |= ST_STATUS_WAIT;
+  return -1;
+}
+
 // Returns the number of live ray-steps taken by this lane.  `wvals` is the
 // warp's evaluation-stack memory viewed as floats (tail mode scratch).
 struct LearnCtx {      // learned step / recording context of a subfrustum
@@ -732,7 +767,11 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
                               const uint32_t *view, const uint2 *ops, const int *lvl_off, const uint16_t *alive_in,
                               int n_in, int *q_head, uint16_t *alive_out, int *n_out, uint16_t *hits, int &n_hits,
                               float2 *stk_lane, float *wvals, int vals_cap, uint64_t &c_rej,
-                              const LearnCtx &LC) {
+                              const LearnCtx &LC, int *tq_tail, int *tq_head, int *n_done, int *n_idle,
+                              uint32_t tag, uint32_t &c_err) {
+  constexpr bool kShare = MODE != ST_STEP_RECORD;
+  uint32_t idle_spins = 0;
+  bool idle = false;   // this warp is registered in *n_idle (waiting for handed-over rays)
   uint32_t rejected = 0;
   const int lane = threadIdx.x & 31;
   const float eps = M.tp->eps;
@@ -810,12 +849,14 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         }
       }
       fpp[s] = fpv[s];
-      dpp[s] = fs * inv_l;   // the plain step taken from this point, in distance units
+      dpp[s] = mul_(fs, inv_l);   // the plain step taken from this point, in distance units
       fpv[s] = fs;
       hv[s] = hv[s] < 2 ? hv[s] + 1 : 2;
     }
-    const float r = fabsf(fs) * inv_ld[s];   // surface-free radius along the ray
-    if (MODE != ST_STEP_PLAIN && MODE != ST_STEP_RECORD && r + rp[s] < dzp[s]) {
+    // Explicit rounding throughout: the two slots are separate unrolled
+    // copies of this code, and a ray may move between slots and warps.
+    const float r = mul_(fabsf(fs), inv_ld[s]);   // surface-free radius along the ray
+    if (MODE != ST_STEP_PLAIN && MODE != ST_STEP_RECORD && add_(r, rp[s]) < dzp[s]) {
       // The unbounding spheres of the last two points do not overlap: the
       // relaxed step may have skipped a crossing.  Keep the landing sphere,
       // return to the previous point and take the plain step from there.
@@ -825,8 +866,8 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       dzp[s] = 0.f;
       relax_off |= bit;
       ++rejected;
-      if (z[s] >= zs[s] - rs[s]) {
-        z[s] = zs[s] + rs[s];
+      if (z[s] >= sub_(zs[s], rs[s])) {
+        z[s] = add_(zs[s], rs[s]);
         rs[s] = -1.f;
         relax_off &= ~bit;
       }
@@ -840,21 +881,21 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       return;
     }
     if (MODE == ST_STEP_PLAIN || MODE == ST_STEP_RECORD) {
-      z[s] += r;
+      z[s] = add_(z[s], r);
       leave_or_cap(s, exit);
       return;
     }
     fpv[s] = fs;   // value at the point the (possibly relaxed) step starts from
     float om = (relax_off & bit) ? 1.f : om_prop;
-    float dz = om * r;
-    if (om > 1.f && z[s] + dz >= z_end) { om = 1.f; dz = r; }   // relaxed steps never cross z_end
-    zf[s] = z[s] + r;
+    float dz = mul_(om, r);
+    if (om > 1.f && add_(z[s], dz) >= z_end) { om = 1.f; dz = r; }   // relaxed steps never cross z_end
+    zf[s] = add_(z[s], r);
     rp[s] = r;
     dzp[s] = dz;
-    z[s] += dz;
-    if ((relax_off & bit) && rs[s] >= 0.f && z[s] >= zs[s] - rs[s]) {
+    z[s] = add_(z[s], dz);
+    if ((relax_off & bit) && rs[s] >= 0.f && z[s] >= sub_(zs[s], rs[s])) {
       // Plain stepping reached the stored surface-free sphere: cross it.
-      z[s] = fmaxf(z[s], zs[s] + rs[s]);
+      z[s] = fmaxf(z[s], add_(zs[s], rs[s]));
       rs[s] = -1.f;
       relax_off &= ~bit;
       dzp[s] = 0.f;
@@ -899,13 +940,80 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         off += __popc(need_m[s]);
       }
     }
+    if (kShare && drained && !__any_sync(0xFFFFFFFFu, ray[0] >= 0 || ray[1] >= 0)) {
+      // Out of rays: take one handed over by another warp.
+      if (!idle && lane == 0) atomicAdd(n_idle, 1);
+      idle = true;
+      int got = -1;
+      if (lane == 0) got = tq_pop(C.tq, tq_tail, tq_head, tag, LC.L->max_tile_rays, c_err);
+      got = __shfl_sync(0xFFFFFFFFu, got, 0);
+      if (got >= 0) {
+        if (lane == 0) atomicSub(n_idle, 1);
+        idle = false;
+      }
+      if (got >= 0 && lane == 0) {
+        ray[0] = got;
+        load_ray(M, C, got, z_begin, z[0], steps[0], d[0], inv_ld[0]);
+        const float4 a = C.rs4[got];
+        const float2 b = C.rs2[got];
+        rp[0] = a.x; dzp[0] = a.y; zf[0] = a.z; zs[0] = a.w;
+        rs[0] = b.x; fpv[0] = b.y;
+        relax_off = rs[0] >= 0.f ? (relax_off | 1u) : (relax_off & ~1u);
+        hv[0] = 0;
+      }
+    }
     int n_live = 0;
 #pragma unroll
     for (int s = 0; s < kR; ++s) n_live += __popc(__ballot_sync(0xFFFFFFFFu, ray[s] >= 0));
-    if (n_live == 0) break;
+    if (n_live == 0) {
+      if (!kShare) break;
+      // Every ray of the subfrustum finished?  Else wait for handed-over rays.
+      if (*(volatile int *)n_done >= n_in || ++idle_spins > kIdleSpinLimit) {
+        if (idle_spins > kIdleSpinLimit) c_err |= ST_STATUS_WAIT;
+        if (idle && lane == 0) atomicSub(n_idle, 1);
+        break;
+      }
+      __nanosleep(64);
+      continue;
+    }
 
     float f[kR];
     if (drained && tail_ok && n_live * tail_cost < inf.n_view) {
+      int n_give = 0;
+      if (kShare && n_live > 1) n_give = min(n_live - 1, *(volatile int *)n_idle);
+      n_give = __shfl_sync(0xFFFFFFFFu, n_give, 0);
+      if (n_give > 0) {
+        // Keep the first live ray, hand up to one ray per idle warp over.
+        const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, ray[0] >= 0), m1 = __ballot_sync(0xFFFFFFFFu, ray[1] >= 0);
+        const int keep_s = m0 ? 0 : 1;
+        const int keep_l = __ffs(m0 ? m0 : m1) - 1;
+        int given = 0;
+#pragma unroll
+        for (int s = 0; s < kR; ++s) {
+          const bool cand = ray[s] >= 0 && !(s == keep_s && lane == keep_l);
+          const uint32_t cm = __ballot_sync(0xFFFFFFFFu, cand);
+          const bool give = cand && given + __popc(cm & lanemask_lt()) < n_give;
+          given += __popc(cm);
+          const uint32_t gm = __ballot_sync(0xFFFFFFFFu, give);
+          if (!gm) continue;
+          if (give) {
+            const int r = ray[s];
+            C.ray_z[r] = z[s];
+            C.ray_st[r] = steps[s];
+            C.rs4[r] = make_float4(rp[s], dzp[s], zf[s], zs[s]);
+            C.rs2[r] = make_float2(rs[s], fpv[s]);
+          }
+          __threadfence_block();
+          int base = 0;
+          if (lane == __ffs(gm) - 1) base = atomicAdd(tq_tail, __popc(gm));
+          base = __shfl_sync(0xFFFFFFFFu, base, __ffs(gm) - 1);
+          const int idx = base + __popc(gm & lanemask_lt());
+          if (give && idx < LC.L->max_tile_rays) {
+            *(volatile unsigned long long *)(C.tq + idx) = ((unsigned long long)tag << 32) | (uint32_t)ray[s];
+            ray[s] = -1;
+          }
+        }
+      }
       // ---- tail: evaluate each remaining ray with the whole warp; the
       // owner lane receives its ray's value ----
 #pragma unroll
@@ -916,9 +1024,9 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
           const int owner = __ffs(m) - 1;
           m &= m - 1;
           const float zz = __shfl_sync(0xFFFFFFFFu, z[s], owner);
-          const float pt[3] = {M.cam->o[0] + zz * __shfl_sync(0xFFFFFFFFu, d[s][0], owner),
-                               M.cam->o[1] + zz * __shfl_sync(0xFFFFFFFFu, d[s][1], owner),
-                               M.cam->o[2] + zz * __shfl_sync(0xFFFFFFFFu, d[s][2], owner)};
+          const float pt[3] = {fma_(zz, __shfl_sync(0xFFFFFFFFu, d[s][0], owner), M.cam->o[0]),
+                               fma_(zz, __shfl_sync(0xFFFFFFFFu, d[s][1], owner), M.cam->o[1]),
+                               fma_(zz, __shfl_sync(0xFFFFFFFFu, d[s][2], owner), M.cam->o[2])};
           const float fv = tail_eval(view, inf.n_view, ops, lvl_off, inf.n_lvl, src, pt, wvals);
           if (lane == owner) f[s] = fv;
         }
@@ -928,9 +1036,9 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       float p[kR][3];
 #pragma unroll
       for (int s = 0; s < kR; ++s) {
-        p[s][0] = M.cam->o[0] + z[s] * d[s][0];
-        p[s][1] = M.cam->o[1] + z[s] * d[s][1];
-        p[s][2] = M.cam->o[2] + z[s] * d[s][2];
+        p[s][0] = fma_(z[s], d[s][0], M.cam->o[0]);
+        p[s][1] = fma_(z[s], d[s][1], M.cam->o[1]);
+        p[s][2] = fma_(z[s], d[s][2], M.cam->o[2]);
       }
       eval_view_r<kR, float>(view, inf.n_view, src, p, f, stk);
     }
@@ -946,11 +1054,11 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       uint32_t live = 0u;
 #pragma unroll
       for (int s = 0; s < kR; ++s) {
-        const float dist = dzp[s] > 0.f ? dzp[s] / (M.tp->lipschitz * inv_ld[s]) : 0.f;
-        x[s][0] = 8.f * f[s] * inv_l;
-        x[s][1] = 8.f * (dzp[s] > 0.f ? fpv[s] : f[s]) * inv_l;
-        x[s][2] = dzp[s] > 0.f ? 8.f * dist : 0.f;
-        x[s][3] = (float)(steps[s] + 1) * (1.f / 64.f);
+        const float dist = dzp[s] > 0.f ? __fdiv_rn(dzp[s], mul_(M.tp->lipschitz, inv_ld[s])) : 0.f;
+        x[s][0] = mul_(mul_(8.f, f[s]), inv_l);
+        x[s][1] = mul_(mul_(8.f, dzp[s] > 0.f ? fpv[s] : f[s]), inv_l);
+        x[s][2] = dzp[s] > 0.f ? mul_(8.f, dist) : 0.f;
+        x[s][3] = mul_((float)(steps[s] + 1), 1.f / 64.f);
         x[s][4] = feat_prim;
         x[s][5] = feat_len;
         live |= (ray[s] >= 0 ? 1u : 0u) << s;
@@ -958,12 +1066,16 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(wvals);
       mlp_omega_warp(LC.W, x, om, xs, wvals + 64 * 16 / 2, live);
     }
+    int n_fin = 0;
 #pragma unroll
     for (int s = 0; s < kR; ++s) {
       bool hit, exit;
+      const bool was = ray[s] >= 0;
       step_slot(s, f[s], om[s], hit, exit);
+      n_fin += __popc(__ballot_sync(0xFFFFFFFFu, was && (hit || exit || ray[s] < 0)));
       retire(s, hit, exit);
     }
+    if (kShare && n_fin && lane == 0) atomicAdd(n_done, n_fin);
   }
   c_rej += rejected;
   return live_steps;
@@ -1062,6 +1174,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   __shared__ int s_lvl_cur[kMaxLevels + 1];   // level cursors of the view build (warp 0)
   __shared__ ViewChunk s_vchunk;               // view build staging (warp 0)
   __shared__ int s_qhead[3], s_nctr[3];
+  __shared__ int s_tqt[3], s_tqh[3], s_ndone[3], s_nidle[3];   // tail sharing per subfrustum slot
   __shared__ uint32_t s_steps;
   __shared__ unsigned long long s_dbg[8];
   const int lane = threadIdx.x & 31;
@@ -1077,6 +1190,10 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
 
   uint64_t c_steps = 0, c_prim = 0, c_op = 0, c_flops = 0, c_sub = 0, c_fin = 0, c_rej = 0;
   uint32_t c_err = 0;
+  uint32_t g_sub = 0;   // subfrustums this CTA has started (tail-queue tag)
+  // Shared memory is not cleared at launch: zero the tail queue so that no
+  // stale entry can carry a tag of this launch (tags start at 1).
+  for (int i = threadIdx.x; i < L.max_tile_rays; i += blockDim.x) C.tq[i] = 0ull;
   if (L.status && (*(volatile const uint32_t *)L.status & ST_STATUS_CAPACITY)) return;
 
   for (;;) {
@@ -1125,6 +1242,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     if (threadIdx.x == 0) {
       s_nctr[0] = nr; s_nctr[1] = 0; s_nctr[2] = 0;
       s_qhead[0] = 0; s_qhead[1] = 0; s_qhead[2] = 0;
+      for (int i = 0; i < 3; ++i) { s_tqt[i] = 0; s_tqh[i] = 0; s_ndone[i] = 0; s_nidle[i] = 0; }
       s_steps = 0u;
       for (int i = 0; i < 8; ++i) s_dbg[i] = 0ull;
     }
@@ -1148,7 +1266,10 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       const int rd = k % 3, wr = (k + 1) % 3, rs = (k + 2) % 3;
       const uint16_t *alive_in = pick(C.alive, k & 1);
       uint16_t *alive_out = pick(C.alive, (k + 1) & 1);
-      if (threadIdx.x == 0) { s_nctr[rs] = 0; s_qhead[rs] = 0; }
+      if (threadIdx.x == 0) {
+        s_nctr[rs] = 0; s_qhead[rs] = 0; s_tqt[rs] = 0; s_tqh[rs] = 0; s_ndone[rs] = 0; s_nidle[rs] = 0;
+      }
+      ++g_sub;
       if (warp == 0) {
         // The next subfrustum's view is built while the other warps march.
         const long long t0 = clock64();
@@ -1165,7 +1286,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         const RecSrc src{sc.rec, pick(C.dc, k & 1)};
         const uint32_t ls = march_sub<MODE>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
                                       n_pending, &s_qhead[rd], alive_out, &s_nctr[wr], my_hits, n_hits, stk_lane,
-                                      wvals, 2 * L.stack_slots * 32, c_rej, LC);
+                                      wvals, 2 * L.stack_slots * 32, c_rej, LC, &s_tqt[rd], &s_tqh[rd], &s_ndone[rd],
+                                      &s_nidle[rd], g_sub, c_err);
         const long long t1 = clock64();
         c_steps += ls;
         c_prim += (uint64_t)ls * inf.n_prim;
@@ -1174,6 +1296,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         finalize_hits(M, C, src, inf, pick(C.view, k & 1), my_hits, n_hits, alive_out, &s_nctr[wr], stk_lane, c_fin);
         if (L.tile_stats && lane == 0) {
           atomicAdd(&s_dbg[4], (unsigned long long)(clock64() - t1));
+          atomicAdd(&s_dbg[7], (unsigned long long)(t1 - t0));
           if (warp == 0) {
             atomicAdd(&s_dbg[5], (unsigned long long)inf.n_view);
             atomicAdd(&s_dbg[6], (unsigned long long)inf.n_lvl);
@@ -1212,7 +1335,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       ts[12] = (uint32_t)(s_dbg[4] >> 4);
       ts[13] = (uint32_t)s_dbg[5];
       ts[14] = (uint32_t)s_dbg[6];
-      ts[15] = 0;
+      ts[15] = (uint32_t)(s_dbg[7] >> 4);
       ts[0] = (uint32_t)((clock64() - t_tile0) >> 4);
       ts[1] = (uint32_t)(t_prep >> 4);
       ts[2] = (uint32_t)(t_march >> 4);
