@@ -164,7 +164,8 @@ typedef struct {
  *   [5] rejected learned steps
  *   [6] finalisation field evaluations (Newton + normal)
  *   [7] device error flags (bit 0: view capacity, bit 1: stack overflow,
- *       bit 2: a tile list longer than the launch's capacity) */
+ *       bit 2: a tile list longer than the launch's capacity, bit 3: a
+ *       bounded wait between the warps of a tile expired) */
 #define ST_NUM_COUNTERS 8
 
 /* ---- scenes --------------------------------------------------------------
