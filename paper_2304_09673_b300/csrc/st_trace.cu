@@ -1101,46 +1101,49 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
     const float lim = M.tp->newton_clamp / dn;
     // Newton on f_A along the ray; a ray stops at its own convergence
     // (|step| <= 1e-6 z, a few FP32 ulps of z), so its result does not
-    // depend on the other rays of the warp.
+    // depend on the other rays of the warp.  Then the normal: gradient of f_A
+    // from three axis derivatives at the final point (not reusing the last
+    // Newton derivative: the field's gradient has kinks where the blend range
+    // b_r reaches zero, and the previous Newton point may lie across one).
+    // One evaluation call site serves both phases (instruction cache).
     bool beyond = false, done = !v;
     int n_eval = 0;
-    for (int it = 0; it < M.tp->newton_iters; ++it) {
-      if (!__any_sync(0xFFFFFFFFu, !done)) break;
+    float g[3] = {0.f, 0.f, 0.f};
+    const int n_newton = M.tp->newton_iters;
+#pragma unroll 1
+    for (int it = 0; it < n_newton + 3; ++it) {
+      const bool newton = it < n_newton;
+      if (newton && !__any_sync(0xFFFFFFFFu, !done)) { it = n_newton - 1; continue; }
+      const int k = it - n_newton;   // gradient axis (newton: < 0)
       Dual<1> pd[1][3], fd[1];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) { pd[0][k].v = cam.o[k] + zz * d[k]; pd[0][k].g[0] = d[k]; }
+      for (int j = 0; j < 3; ++j) {
+        pd[0][j].v = cam.o[j] + zz * d[j];
+        pd[0][j].g[0] = newton ? d[j] : (j == k ? 1.f : 0.f);
+      }
       eval_view_r<1, Dual<1>>(view, inf.n_view, src, pd, fd, stk);
-      if (!done) {
-        ++n_eval;
-        beyond = false;
-        if (fd[0].g[0] != 0.f && isfinite(fd[0].v)) {
-          float step = -fd[0].v / fd[0].g[0];
-          step = fminf(fmaxf(step, -lim), lim);
-          beyond = zz + step > inf.z_end && fd[0].v > 0.f;
-          const float zn = fminf(fmaxf(zz + step, inf.z_begin), inf.z_end);
-          if (fabsf(zn - zz) <= 1e-6f * zz) done = true;
-          zz = zn;
-        } else {
-          done = true;
+      if (newton) {
+        if (!done) {
+          ++n_eval;
+          beyond = false;
+          if (fd[0].g[0] != 0.f && isfinite(fd[0].v)) {
+            float step = -fd[0].v / fd[0].g[0];
+            step = fminf(fmaxf(step, -lim), lim);
+            beyond = zz + step > inf.z_end && fd[0].v > 0.f;
+            const float zn = fminf(fmaxf(zz + step, inf.z_begin), inf.z_end);
+            if (fabsf(zn - zz) <= 1e-6f * zz) done = true;
+            zz = zn;
+          } else {
+            done = true;
+          }
         }
+      } else {
+        g[0] = k == 0 ? fd[0].g[0] : g[0];
+        g[1] = k == 1 ? fd[0].g[0] : g[1];
+        g[2] = k == 2 ? fd[0].g[0] : g[2];
+        ++n_eval;
       }
     }
-    // Normal: gradient of f_A from three axis derivatives at the final point
-    // (not reusing the last Newton derivative: the field's gradient has kinks
-    // where the blend range b_r reaches zero, and the previous Newton point
-    // may lie across one).
-    float g[3] = {0.f, 0.f, 0.f};
-#pragma unroll 1
-    for (int k = 0; k < 3; ++k) {
-      Dual<1> pd[1][3], fd[1];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) { pd[0][j].v = cam.o[j] + zz * d[j]; pd[0][j].g[0] = j == k ? 1.f : 0.f; }
-      eval_view_r<1, Dual<1>>(view, inf.n_view, src, pd, fd, stk);
-      g[0] = k == 0 ? fd[0].g[0] : g[0];
-      g[1] = k == 1 ? fd[0].g[0] : g[1];
-      g[2] = k == 2 ? fd[0].g[0] : g[2];
-    }
-    n_eval += 3;
     const bool back = v && beyond;
     if (back) {
       C.ray_z[r] = inf.z_end;
