@@ -1251,37 +1251,45 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     }
     SegState sg;
     sg.next = 0; sg.n_act = 0; sg.cur = 0; sg.z_end = 0.f; sg.maxze = -INFINITY;
-    if (warp == 0) {
-      const long long t0 = clock64();
-      prepare_sub(sg, C, sc, job.tp, zin_l, zout_l, prim_l, len, 0, L.stack_slots, L.dc_words, &s_info[0], s_lvl_cur, &s_vchunk,
-                  L.tile_stats ? s_dbg : nullptr);
-      t_prep += clock64() - t0;
-    }
-    __syncthreads();
     int n_pending = nr;
-    int k = 0;
+    int k = -1;
+    // k = -1 only prepares subfrustum 0; one call site for the preparation
+    // keeps the kernel's code (and instruction-fetch stalls) smaller.
     for (;; ++k) {
-      const SubInfo inf = s_info[k & 1];
-      if (inf.done || inf.err || n_pending == 0) {
-        if (inf.err) c_err |= (uint32_t)inf.err;
-        break;
+      const bool run = k >= 0;
+      SubInfo inf{};
+      if (run) {
+        inf = s_info[k & 1];
+        if (inf.done || inf.err || n_pending == 0) {
+          if (inf.err) c_err |= (uint32_t)inf.err;
+          break;
+        }
       }
-      const int rd = k % 3, wr = (k + 1) % 3, rs = (k + 2) % 3;
-      const uint16_t *alive_in = pick(C.alive, k & 1);
-      uint16_t *alive_out = pick(C.alive, (k + 1) & 1);
-      if (threadIdx.x == 0) {
-        s_nctr[rs] = 0; s_qhead[rs] = 0; s_tqt[rs] = 0; s_tqh[rs] = 0; s_ndone[rs] = 0; s_nidle[rs] = 0;
+      const int kk = run ? k : 0;
+      const int rd = kk % 3, wr = (kk + 1) % 3, rs = (kk + 2) % 3;
+      const uint16_t *alive_in = pick(C.alive, kk & 1);
+      uint16_t *alive_out = pick(C.alive, (kk + 1) & 1);
+      if (run) {
+        if (threadIdx.x == 0) {
+          s_nctr[rs] = 0; s_qhead[rs] = 0; s_tqt[rs] = 0; s_tqh[rs] = 0; s_ndone[rs] = 0; s_nidle[rs] = 0;
+        }
+        ++g_sub;
       }
-      ++g_sub;
       if (warp == 0) {
         // The next subfrustum's view is built while the other warps march.
         const long long t0 = clock64();
         prepare_sub(sg, C, sc, job.tp, zin_l, zout_l, prim_l, len, (k + 1) & 1, L.stack_slots, L.dc_words,
                     &s_info[(k + 1) & 1], s_lvl_cur, &s_vchunk, L.tile_stats ? s_dbg : nullptr);
         t_prep += clock64() - t0;
-        c_sub += 1;
-        s_sub += 1;
-        s_maxview = max(s_maxview, (uint32_t)inf.n_view);
+        if (run) {
+          c_sub += 1;
+          s_sub += 1;
+          s_maxview = max(s_maxview, (uint32_t)inf.n_view);
+        }
+      }
+      if (!run) {
+        __syncthreads();
+        continue;
       }
       if (inf.root_used) {
         const long long t0 = clock64();
