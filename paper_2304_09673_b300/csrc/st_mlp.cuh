@@ -65,21 +65,32 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// m16n8k8: layer 1 has 6 inputs, so K = 8 covers them (columns 6, 7 zero).
+__device__ __forceinline__ void mma_bf16_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(b0));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t *>(&v);
 }
 
-// One 16-row tile of the network: A fragments in, output column 0 of rows
-// g and g + 8 (valid in lanes with t == 0).
-__device__ __forceinline__ void mlp_tile(const MlpSmem &W, const uint32_t (&a)[4], int g, int t, float &o_lo,
+// One 16-row tile of the network: layer-1 A fragments (rows g and g + 8,
+// input columns 2t, 2t + 1) in, output column 0 of rows g and g + 8 out
+// (valid in lanes with t == 0).
+__device__ __forceinline__ void mlp_tile(const MlpSmem &W, uint32_t a0, uint32_t a1, int g, int t, float &o_lo,
                                          float &o_hi) {
+  const float2 *b1 = reinterpret_cast<const float2 *>(W.b1);
+  const float2 *b2 = reinterpret_cast<const float2 *>(W.b2);
   float h1[4][4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const float bl = W.b1[8 * q + 2 * t], bh = W.b1[8 * q + 2 * t + 1];
-    h1[q][0] = bl; h1[q][1] = bh; h1[q][2] = bl; h1[q][3] = bh;
-    mma_bf16(h1[q], a, W.w1[(8 * q + g) * 8 + t], W.w1[(8 * q + g) * 8 + t + 4]);
+    const float2 b = b1[4 * q + t];
+    h1[q][0] = b.x; h1[q][1] = b.y; h1[q][2] = b.x; h1[q][3] = b.y;
+    mma_bf16_k8(h1[q], a0, a1, W.w1[(8 * q + g) * 8 + t]);
   }
   uint32_t a2[2][4];
 #pragma unroll
@@ -92,8 +103,8 @@ __device__ __forceinline__ void mlp_tile(const MlpSmem &W, const uint32_t (&a)[4
   float h2[4][4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const float bl = W.b2[8 * q + 2 * t], bh = W.b2[8 * q + 2 * t + 1];
-    h2[q][0] = bl; h2[q][1] = bh; h2[q][2] = bl; h2[q][3] = bh;
+    const float2 b = b2[4 * q + t];
+    h2[q][0] = b.x; h2[q][1] = b.y; h2[q][2] = b.x; h2[q][3] = b.y;
 #pragma unroll
     for (int kt = 0; kt < 2; ++kt)
       mma_bf16(h2[q], a2[kt], W.w2[(8 * q + g) * 16 + 8 * kt + t], W.w2[(8 * q + g) * 16 + 8 * kt + t + 4]);
@@ -113,15 +124,24 @@ __device__ __forceinline__ void mlp_tile(const MlpSmem &W, const uint32_t (&a)[4
   o_hi = o[2] + W.b3;
 }
 
+// 1 + sigmoid(v) = 1.5 + tanh(v / 2) / 2 (one MUFU tanh).
+__device__ __forceinline__ float omega_of(float v) {
+  float th;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(0.5f * v));
+  return 1.5f + 0.5f * th;
+}
+
 // Warp-collective: evaluates the MLP on the rows of live slots (row
 // s * 32 + lane holds feature vector x[s] of this lane, s = 0, 1; slot s of
 // the lane is live when bit s of `live` is set) and returns omega per slot
 // (1 for dead slots).  16-row tiles without a live row are skipped.
-// xs: per-warp shared scratch of 64 x 16 bf16 (2 KB), os: 64 floats.
+// xs: per-warp shared scratch of 64 rows x 4 words (1 KB; words 0..2 hold
+// the six BF16 features), os: 64 floats.
 __device__ __forceinline__ void mlp_omega_warp(const MlpSmem &W, const float (&x)[2][6], float (&omega)[2],
                                                __nv_bfloat16 *xs, float *os, uint32_t live = 3u) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
+  uint32_t *xu = reinterpret_cast<uint32_t *>(xs);
   uint32_t tiles = 0;   // bit mt: tile mt (rows 16 mt .. 16 mt + 15) has a live row
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
@@ -129,27 +149,22 @@ __device__ __forceinline__ void mlp_omega_warp(const MlpSmem &W, const float (&x
     tiles |= ((m & 0xFFFFu) ? 1u : 0u) << (2 * s);
     tiles |= ((m >> 16) ? 1u : 0u) << (2 * s + 1);
     if ((live >> s) & 1u) {
-      uint32_t *row = reinterpret_cast<uint32_t *>(xs + (s * 32 + lane) * 16);
+      uint32_t *row = xu + (s * 32 + lane) * 4;
       row[0] = pack_bf16(x[s][0], x[s][1]);
       row[1] = pack_bf16(x[s][2], x[s][3]);
       row[2] = pack_bf16(x[s][4], x[s][5]);
-#pragma unroll
-      for (int k = 3; k < 8; ++k) row[k] = 0u;
     }
   }
   __syncwarp();
-  const uint32_t *xu = reinterpret_cast<const uint32_t *>(xs);
 #pragma unroll 1
   for (int mt = 0; mt < 4; ++mt) {
     if (!((tiles >> mt) & 1u)) continue;
-    uint32_t a[4];
     const int m0 = 16 * mt;
-    a[0] = xu[(m0 + g) * 8 + t];
-    a[1] = xu[(m0 + g + 8) * 8 + t];
-    a[2] = xu[(m0 + g) * 8 + t + 4];
-    a[3] = xu[(m0 + g + 8) * 8 + t + 4];
+    // Rows of dead slots hold stale words; their outputs are never used.
+    const uint32_t a0 = t < 3 ? xu[(m0 + g) * 4 + t] : 0u;
+    const uint32_t a1 = t < 3 ? xu[(m0 + g + 8) * 4 + t] : 0u;
     float lo, hi;
-    mlp_tile(W, a, g, t, lo, hi);
+    mlp_tile(W, a0, a1, g, t, lo, hi);
     if (t == 0) {
       os[m0 + g] = lo;
       os[m0 + g + 8] = hi;
@@ -159,7 +174,7 @@ __device__ __forceinline__ void mlp_omega_warp(const MlpSmem &W, const float (&x
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const float v = os[s * 32 + lane];
-    omega[s] = ((live >> s) & 1u) ? 1.f + 1.f / (1.f + __expf(-v)) : 1.f;
+    omega[s] = ((live >> s) & 1u) ? omega_of(v) : 1.f;
   }
   __syncwarp();
 }

@@ -1054,7 +1054,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       uint32_t live = 0u;
 #pragma unroll
       for (int s = 0; s < kR; ++s) {
-        const float dist = dzp[s] > 0.f ? __fdiv_rn(dzp[s], mul_(M.tp->lipschitz, inv_ld[s])) : 0.f;
+        const float dist = dzp[s] > 0.f ? mul_(dzp[s], frcp(mul_(M.tp->lipschitz, inv_ld[s]))) : 0.f;
         x[s][0] = mul_(mul_(8.f, f[s]), inv_l);
         x[s][1] = mul_(mul_(8.f, dzp[s] > 0.f ? fpv[s] : f[s]), inv_l);
         x[s][2] = dzp[s] > 0.f ? mul_(8.f, dist) : 0.f;
@@ -1064,7 +1064,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         live |= (ray[s] >= 0 ? 1u : 0u) << s;
       }
       __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(wvals);
-      mlp_omega_warp(LC.W, x, om, xs, wvals + 64 * 16 / 2, live);
+      mlp_omega_warp(LC.W, x, om, xs, wvals + 64 * 4, live);
     }
     int n_fin = 0;
 #pragma unroll
