@@ -175,50 +175,34 @@ __device__ __forceinline__ void disp_terms(const T &kr, const T &a, T &kr6, T &x
   x3 = cube_(x);
 }
 
-// Branch-free: the blended value is always computed and selected by the
-// range test (no divergence inside a warp that evaluates the same node).
-template <uint32_t CODE, class T>
-__device__ __forceinline__ T op_compact(float4 c, const T &f0, const T &f1) {
+// The three compact operators G_op (union, intersection, difference) as one
+// branch-free body: the (warp-uniform) operator code selects min / max, the
+// sign of the displacement and the clamp of the blend range (k' <= k for the
+// intersection and the difference, |k'| for the difference), so the
+// interpreter has one case for all three.  The blended value is always
+// computed and selected by the range test f0 <= d_o and f1 <= d_o.
+template <class T>
+__device__ __forceinline__ T op_compact_any(uint32_t code, float4 c, const T &f0, const T &f1) {
+  const bool uni = code == V_UNION, dif = code == V_DIFF;
   const bool inside = val(f0) <= c.y && val(f1) <= c.y;
   const float k6 = mul_(c.x, 1.f / 6.f);
+  const T g1 = dif ? -f1 : f1;
+  const T m = uni ? min_(f0, g1) : max_(f0, g1);
+  const T a = abs_(sub_(f0, g1));
+  const T x = mul_(max_(sub_(c.x, a), 0.f), c.w);
+  const T g = fma_(cube_(x), uni ? -k6 : k6, m);
+  const T kb = mul_(max_(fma_(g, -c.z, 1.f), 0.f), c.x);
+  const T kr = uni ? kb : min_(dif ? abs_(kb) : kb, c.x);
   T kr6, x3;
-  if (CODE == V_UNION) {
-    const T m = min_(f0, f1);
-    const T a = abs_(sub_(f0, f1));
-    const T x = mul_(max_(sub_(c.x, a), 0.f), c.w);
-    const T g = fma_(cube_(x), -k6, m);
-    const T kr = mul_(max_(fma_(g, -c.z, 1.f), 0.f), c.x);
-    disp_terms(kr, a, kr6, x3);
-    const T res = fma_(-kr6, x3, m);
-    return inside ? res : m;
-  } else if (CODE == V_INTER) {
-    const T m = max_(f0, f1);
-    const T a = abs_(sub_(f0, f1));
-    const T x = mul_(max_(sub_(c.x, a), 0.f), c.w);
-    const T g = fma_(cube_(x), k6, m);
-    const T kr = min_(mul_(max_(fma_(g, -c.z, 1.f), 0.f), c.x), c.x);
-    disp_terms(kr, a, kr6, x3);
-    const T res = fma_(kr6, x3, m);
-    return inside ? res : m;
-  } else {
-    // difference: csg max(f0, -f1), displacement d(f0, -f1, .)
-    const T nf1 = -f1;
-    const T m = max_(f0, nf1);
-    const T a = abs_(sub_(f0, nf1));
-    const T x = mul_(max_(sub_(c.x, a), 0.f), c.w);
-    const T g = fma_(cube_(x), k6, m);
-    const T kr = min_(abs_(mul_(max_(fma_(g, -c.z, 1.f), 0.f), c.x)), c.x);
-    disp_terms(kr, a, kr6, x3);
-    const T res = fma_(kr6, x3, m);
-    return inside ? res : m;
-  }
+  disp_terms(kr, a, kr6, x3);
+  const T res = fma_(uni ? -kr6 : kr6, x3, m);
+  return inside ? res : m;
 }
 
-template <uint32_t CODE, class T>
-__device__ __forceinline__ T op_sharp(const T &f0, const T &f1) {
-  if (CODE == V_SUNION) return min_(f0, f1);
-  if (CODE == V_SINTER) return max_(f0, f1);
-  return max_(f0, -f1);
+template <class T>
+__device__ __forceinline__ T op_sharp_any(uint32_t code, const T &f0, const T &f1) {
+  const T g1 = code == V_SDIFF ? -f1 : f1;
+  return code == V_SUNION ? min_(f0, g1) : max_(f0, g1);
 }
 
 __device__ __forceinline__ uint32_t node_flops(uint32_t code) {
@@ -270,49 +254,19 @@ __device__ __forceinline__ void eval_view_r(const uint32_t *view, int n_view, co
         for (int r = 0; r < R; ++r) acc[r] = sd_capsule<T>(a0, a2, p[r]);
         break;
       }
-      case V_UNION: {
+      case V_UNION: case V_INTER: case V_DIFF: {
         const float4 c = ldrec(q);
         T l[R];
         stk.pop(--sp, l);
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = op_compact<V_UNION, T>(c, l[r], acc[r]);
+        for (int r = 0; r < R; ++r) acc[r] = op_compact_any<T>(code, c, l[r], acc[r]);
         break;
       }
-      case V_INTER: {
-        const float4 c = ldrec(q);
+      case V_SUNION: case V_SINTER: case V_SDIFF: {
         T l[R];
         stk.pop(--sp, l);
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = op_compact<V_INTER, T>(c, l[r], acc[r]);
-        break;
-      }
-      case V_DIFF: {
-        const float4 c = ldrec(q);
-        T l[R];
-        stk.pop(--sp, l);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = op_compact<V_DIFF, T>(c, l[r], acc[r]);
-        break;
-      }
-      case V_SUNION: {
-        T l[R];
-        stk.pop(--sp, l);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = op_sharp<V_SUNION, T>(l[r], acc[r]);
-        break;
-      }
-      case V_SINTER: {
-        T l[R];
-        stk.pop(--sp, l);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = op_sharp<V_SINTER, T>(l[r], acc[r]);
-        break;
-      }
-      case V_SDIFF: {
-        T l[R];
-        stk.pop(--sp, l);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = op_sharp<V_SDIFF, T>(l[r], acc[r]);
+        for (int r = 0; r < R; ++r) acc[r] = op_sharp_any<T>(code, l[r], acc[r]);
         break;
       }
       case V_INF: {

@@ -669,13 +669,10 @@ __device__ __forceinline__ float tail_eval(const uint32_t *view, int n_view, con
       const float f0 = vals[li], f1 = vals[ri];
       const float4 *q = rec_ptr(src, w);
       float v;
-      switch (w >> kViewCodeShift) {
-        case V_UNION: v = op_compact<V_UNION, float>(ldrec(q), f0, f1); break;
-        case V_INTER: v = op_compact<V_INTER, float>(ldrec(q), f0, f1); break;
-        case V_DIFF: v = op_compact<V_DIFF, float>(ldrec(q), f0, f1); break;
-        case V_SUNION: v = op_sharp<V_SUNION, float>(f0, f1); break;
-        case V_SINTER: v = op_sharp<V_SINTER, float>(f0, f1); break;
-        case V_SDIFF: v = op_sharp<V_SDIFF, float>(f0, f1); break;
+      const uint32_t code = w >> kViewCodeShift;
+      switch (code) {
+        case V_UNION: case V_INTER: case V_DIFF: v = op_compact_any<float>(code, ldrec(q), f0, f1); break;
+        case V_SUNION: case V_SINTER: case V_SDIFF: v = op_sharp_any<float>(code, f0, f1); break;
         case V_INF: v = INFINITY; break;
         case V_RIGHT: v = f1; break;
         default: v = f0; break;
