@@ -253,6 +253,7 @@ struct ViewChunk {       // shared staging of one chunk (warp 0 of a CTA)
   uint2 b[kViewChunk];   // (view word of A_i, global flag | record offset of X_i)
 };
 
+template <bool kAddr>
 __device__ __forceinline__ ViewInfo build_view_lca(const DevScene &sc, const uint32_t *act, int n, uint32_t *view,
                                                    ViewChunk &ch, uint2 *ops, uint2 *sort_tmp, int *lvl_off,
                                                    int *lvl_cur, uint32_t *stk, int stack_cap, uint32_t *vaddr,
@@ -267,6 +268,9 @@ __device__ __forceinline__ ViewInfo build_view_lca(const DevScene &sc, const uin
   uint4 *ps = reinterpret_cast<uint4 *>(stk);                       // pending operators: (X, blk, kind | igm << 8, word)
   uint2 *vs = reinterpret_cast<uint2 *>(stk + 4 * (stack_cap + 2)); // value stack: (blk | u << 23 | h << 24, index)
   int vsp = 0, psp = 0, nv = 0;
+  uint32_t leaf_flops = 0;   // per lane, reduced after the chunks
+  uint2 vt0 = make_uint2(0u, 0u), vt1 = make_uint2(0u, 0u);   // cached value-stack top, second
+  uint4 pt = make_uint4(0u, 0u, 0u, 0u);                       // cached pending-operator top
   if (n < 1) vi.err = 1;
   for (int c0 = 0; c0 < n; c0 += kViewChunk) {
     // ---- phase 1 ----
@@ -307,52 +311,64 @@ __device__ __forceinline__ ViewInfo build_view_lca(const DevScene &sc, const uin
         }
         ch.a[q * 32 + lane] = make_uint4(X, min(xblk, kNoAnc), min(lb, kNoAnc), xw);
         ch.b[q * 32 + lane] = make_uint2(leaf, kViewGlobal | xrec);
+        leaf_flops += node_flops(blob_kind(ab));
       }
     }
     __syncwarp();
     // ---- phase 2 ----
+    // The top two value-stack entries (vt0 = top) and the top pending
+    // operator (pt) live in registers; deeper entries stay in shared memory
+    // at their own indices.  This keeps the merge's dependency chain in
+    // registers.
     if (lane == 0) {
       const int c1 = min(n, c0 + kViewChunk);
       for (int i = c0; i < c1 && !vi.err; ++i) {
         const uint4 t = ch.a[i - c0];
         const uint2 w = ch.b[i - c0];
         if (vsp >= stack_cap + 2) { vi.err = 2; break; }
-        if (vaddr) vaddr[nv] = act[i];
+        if (kAddr) vaddr[nv] = act[i];
         view[nv] = w.x;
-        vi.flops += node_flops(w.x >> kViewCodeShift);
-        vs[vsp++] = make_uint2(t.z | (1u << 23), (uint32_t)nv);
+        if (vsp >= 2) vs[vsp - 2] = vt1;
+        vt1 = vt0;
+        vt0 = make_uint2(t.z | (1u << 23), (uint32_t)nv);
+        ++vsp;
         ++nv;
         const uint32_t xnext = i + 1 < n ? t.x : kNone;
         if (i + 1 < n && xnext >= (uint32_t)sc.n_nodes) { vi.err = 1; break; }
-        while (psp > 0) {
-          const uint4 pj = ps[psp - 1];
-          if (pj.x >= xnext) break;
+        while (psp > 0 && pt.x < xnext) {
+          const uint4 pj = pt;
           --psp;
+          if (psp > 0) pt = ps[psp - 1];
           if (vsp < 2) { vi.err = 1; break; }
-          const uint2 R = vs[--vsp], Lv = vs[--vsp];
+          const uint2 R = vt0, Lv = vt1;
+          vsp -= 2;
+          const uint2 below = vsp >= 1 ? vs[vsp - 1] : make_uint2(0u, 0u);
           const uint32_t X = pj.x;
           const uint32_t uL = (((Lv.x >> 23) & 1u) && (Lv.x & kNoAnc) >= X) ? 1u : 0u;
           const uint32_t uR = (((R.x >> 23) & 1u) && (R.x & kNoAnc) >= X) ? 1u : 0u;
           const uint32_t b = (uL << 1) | uR, m = (pj.z >> 8) & 3u, kind = pj.z & 31u;
           const bool ok = ((~b) & m & 3u) == 0u;
-          uint32_t code;
-          if (ok && b == 3u) code = kind - ST_OP_UNION + V_UNION;
-          else if (!ok || b == 0u) code = V_INF;
-          else code = b == 1u ? V_RIGHT : V_LEFT;
-          if (vaddr) vaddr[nv] = X;
+          const bool keep = ok && b == 3u;
+          const uint32_t code = keep ? kind - ST_OP_UNION + V_UNION
+                                     : ((!ok || b == 0u) ? (uint32_t)V_INF : (b == 1u ? (uint32_t)V_RIGHT : (uint32_t)V_LEFT));
+          if (kAddr) vaddr[nv] = X;
           view[nv] = (code << kViewCodeShift) | pj.w;
-          vi.flops += node_flops(code);
+          vi.flops += keep ? (kind <= ST_OP_DIFF ? kFlopsCompactOp : kFlopsSharpOp) : 0u;
           const uint32_t h = min(max(Lv.x >> 24, R.x >> 24) + 1u, 255u);
           maxh = max(maxh, (int)h);
           ops[nop++] = make_uint2((uint32_t)nv | (Lv.y << 16), (R.y & 0xFFFFu) | (h << 16));
           const uint32_t u = (ok && b != 0u) ? 1u : 0u;
-          vs[vsp++] = make_uint2(pj.y | (u << 23) | (h << 24), (uint32_t)nv);
+          vt1 = below;
+          vt0 = make_uint2(pj.y | (u << 23) | (h << 24), (uint32_t)nv);
+          ++vsp;
           ++nv;
         }
         if (vi.err) break;
         if (i + 1 < n) {
           if (psp >= stack_cap + 2) { vi.err = 2; break; }
-          ps[psp++] = make_uint4(t.x, t.y, t.w, w.y);
+          if (psp >= 1) ps[psp - 1] = pt;
+          pt = make_uint4(t.x, t.y, t.w, w.y);
+          ++psp;
         }
       }
     }
@@ -362,7 +378,7 @@ __device__ __forceinline__ ViewInfo build_view_lca(const DevScene &sc, const uin
   if (lane == 0) {
     if (!vi.err) {
       if (vsp != 1 || psp != 0) vi.err = 1;
-      else vi.root_used = (((vs[0].x >> 23) & 1u) && (vs[0].x & kNoAnc) == kNoAnc) ? 1 : 0;
+      else vi.root_used = (((vt0.x >> 23) & 1u) && (vt0.x & kNoAnc) == kNoAnc) ? 1 : 0;
     }
     vi.n_view = nv;
     vi.n_prim = n;
@@ -372,7 +388,9 @@ __device__ __forceinline__ ViewInfo build_view_lca(const DevScene &sc, const uin
   vi.root_used = __shfl_sync(0xFFFFFFFFu, vi.root_used, 0);
   vi.n_prim = __shfl_sync(0xFFFFFFFFu, vi.n_prim, 0);
   vi.n_op = __shfl_sync(0xFFFFFFFFu, vi.n_op, 0);
-  vi.flops = __shfl_sync(0xFFFFFFFFu, vi.flops, 0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) leaf_flops += __shfl_xor_sync(0xFFFFFFFFu, leaf_flops, o);
+  vi.flops = __shfl_sync(0xFFFFFFFFu, vi.flops, 0) + leaf_flops;
   vi.err = __shfl_sync(0xFFFFFFFFu, vi.err, 0);
   nop = __shfl_sync(0xFFFFFFFFu, nop, 0);
   maxh = __shfl_sync(0xFFFFFFFFu, maxh, 0);
@@ -624,7 +642,7 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
     lap(1);
     // ---- pruned view (the lowest-common-ancestor form of Algorithm 1) ----
     int n_lvl = 0;
-    const ViewInfo vi = build_view_lca(sc, pick(C.act, sg.cur), sg.n_act, view, *vch, pick(C.ops, vb), C.sort_tmp,
+    const ViewInfo vi = build_view_lca<false>(sc, pick(C.act, sg.cur), sg.n_act, view, *vch, pick(C.ops, vb), C.sort_tmp,
                                        pick(C.lvl_off, vb), lvl_cur, C.bstk, stack_slots, nullptr, &n_lvl);
     info.n_view = vi.n_view;
     info.root_used = vi.root_used;
@@ -1454,7 +1472,8 @@ __global__ void k_pruned_view(DevScene sc, const uint32_t *act, int n, uint32_t 
     uint2 *sort_tmp = ops + n;
     int *lvl_off = reinterpret_cast<int *>(sort_tmp + n);
     int *lvl_cur = lvl_off + kMaxLevels + 1;
-    vi = build_view_lca(sc, act, n, view, vch, ops, sort_tmp, lvl_off, lvl_cur, stk, stack_cap, vaddr, &n_lvl);
+    vi = vaddr ? build_view_lca<true>(sc, act, n, view, vch, ops, sort_tmp, lvl_off, lvl_cur, stk, stack_cap, vaddr, &n_lvl)
+               : build_view_lca<false>(sc, act, n, view, vch, ops, sort_tmp, lvl_off, lvl_cur, stk, stack_cap, vaddr, &n_lvl);
   } else {
     if (threadIdx.x != 0) return;
     vi = build_view(sc, act, n, view, scratch, stack_cap, vaddr);
