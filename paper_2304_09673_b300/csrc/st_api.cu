@@ -415,7 +415,7 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
   L.act_cap = (int)std::max<uint32_t>(tl->max_overlap, 1u);
   L.view_cap = 2 * L.act_cap;
   L.stack_slots = s->prep.stack_depth + 2;
-  L.dc_words = 640;
+  L.dc_words = L.view_cap > 2048 ? 2048 : 640;   // big views: larger parameter cache (2 CTAs per SM)
   L.n_items = (uint32_t)(tiles_x * tiles_y);
   L.counters = counters;
   L.tile_stats = o.tile_stats;

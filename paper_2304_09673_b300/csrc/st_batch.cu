@@ -353,7 +353,7 @@ int plan(st_batch *b) {
   L.act_cap = (int)b->overlap_cap;
   L.view_cap = 2 * L.act_cap;
   L.stack_slots = stack_slots;
-  L.dc_words = 640;
+  L.dc_words = L.view_cap > 2048 ? 2048 : 640;   // big views: larger parameter cache (2 CTAs per SM)
   L.n_items = b->n_tiles;
   L.item_counter = b->item_counter.p;
   L.counters = b->counters.p;
