@@ -305,6 +305,11 @@ struct SmemStack2 {   // R = 2 float points
     a[1] = v.y;
   }
 };
+struct SmemStack1 {   // R = 1 float point (the .x half of SmemStack2's slots)
+  float2 *base;
+  __device__ __forceinline__ void push(int s, const float (&a)[1]) { reinterpret_cast<float *>(base + s * 32)[0] = a[0]; }
+  __device__ __forceinline__ void pop(int s, float (&a)[1]) const { a[0] = reinterpret_cast<const float *>(base + s * 32)[0]; }
+};
 struct SmemStackD1 {  // R = 1 dual number (value, derivative)
   float2 *base;
   __device__ __forceinline__ void push(int s, const Dual<1> (&a)[1]) { base[s * 32] = make_float2(a[0].v, a[0].g[0]); }

@@ -1048,14 +1048,35 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       }
     } else {
       // ---- one lockstep field evaluation per slot (Algorithm 3 over the view) ----
-      float p[kR][3];
-#pragma unroll
-      for (int s = 0; s < kR; ++s) {
-        p[s][0] = fma_(z[s], d[s][0], M.cam->o[0]);
-        p[s][1] = fma_(z[s], d[s][1], M.cam->o[1]);
-        p[s][2] = fma_(z[s], d[s][2], M.cam->o[2]);
+      // A lane whose first slot is empty takes its second slot's ray; when no
+      // lane has a second ray left, one evaluation chain per lane suffices.
+      const bool mv = ray[0] < 0 && ray[1] >= 0;
+      if (mv) {
+        ray[0] = ray[1]; z[0] = z[1]; inv_ld[0] = inv_ld[1]; steps[0] = steps[1];
+        d[0][0] = d[1][0]; d[0][1] = d[1][1]; d[0][2] = d[1][2];
+        rp[0] = rp[1]; dzp[0] = dzp[1]; zf[0] = zf[1]; zs[0] = zs[1]; rs[0] = rs[1];
+        fpv[0] = fpv[1]; fpp[0] = fpp[1]; dpp[0] = dpp[1]; hv[0] = hv[1];
+        relax_off = (relax_off & ~3u) | ((relax_off >> 1) & 1u);
+        ray[1] = -1;
       }
-      eval_view_r<kR, float>(view, inf.n_view, src, p, f, stk);
+      if (!__any_sync(0xFFFFFFFFu, ray[1] >= 0)) {
+        float p1[1][3] = {{fma_(z[0], d[0][0], M.cam->o[0]), fma_(z[0], d[0][1], M.cam->o[1]),
+                           fma_(z[0], d[0][2], M.cam->o[2])}};
+        float f1[1];
+        SmemStack1 stk1{stk.base};
+        eval_view_r<1, float>(view, inf.n_view, src, p1, f1, stk1);
+        f[0] = f1[0];
+        f[1] = 0.f;
+      } else {
+        float p[kR][3];
+#pragma unroll
+        for (int s = 0; s < kR; ++s) {
+          p[s][0] = fma_(z[s], d[s][0], M.cam->o[0]);
+          p[s][1] = fma_(z[s], d[s][1], M.cam->o[1]);
+          p[s][2] = fma_(z[s], d[s][2], M.cam->o[2]);
+        }
+        eval_view_r<kR, float>(view, inf.n_view, src, p, f, stk);
+      }
     }
     float om[kR];
 #pragma unroll
