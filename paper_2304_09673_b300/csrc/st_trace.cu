@@ -136,6 +136,17 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// Position of the k-th (0-based) set bit of m (k < popc(m)).
+__device__ __forceinline__ int kth_set_bit(uint32_t m, int k) {
+  int pos = 0;
+#pragma unroll
+  for (int b = 16; b >= 1; b >>= 1) {
+    const uint32_t low = pos + b >= 32 ? m : (m & ((1u << (pos + b)) - 1u));
+    if (__popc(low) <= k) pos += b;
+  }
+  return pos;
+}
+
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
@@ -1048,6 +1059,46 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       }
     } else {
       // ---- one lockstep field evaluation per slot (Algorithm 3 over the view) ----
+      // At most 32 rays left but some lane holds two: lanes with two rays hand
+      // their second ray to lanes with none (warp shuffles), so that one
+      // evaluation chain per lane suffices.
+      {
+        const uint32_t two = __ballot_sync(0xFFFFFFFFu, ray[0] >= 0 && ray[1] >= 0);
+        const uint32_t none = __ballot_sync(0xFFFFFFFFu, ray[0] < 0 && ray[1] < 0);
+        if (two && n_live <= 32) {
+          const int rank_t = __popc(none & lanemask_lt());
+          const bool take = ((none >> lane) & 1u) && rank_t < __popc(two);
+          const int src_l = take ? kth_set_bit(two, rank_t) : lane;
+          const bool give = ((two >> lane) & 1u) && __popc(two & lanemask_lt()) < __popc(none);
+          const int r_r = __shfl_sync(0xFFFFFFFFu, ray[1], src_l);
+          const float z_r = __shfl_sync(0xFFFFFFFFu, z[1], src_l);
+          const float d0_r = __shfl_sync(0xFFFFFFFFu, d[1][0], src_l);
+          const float d1_r = __shfl_sync(0xFFFFFFFFu, d[1][1], src_l);
+          const float d2_r = __shfl_sync(0xFFFFFFFFu, d[1][2], src_l);
+          const float il_r = __shfl_sync(0xFFFFFFFFu, inv_ld[1], src_l);
+          const uint32_t st_r = __shfl_sync(0xFFFFFFFFu, steps[1], src_l);
+          const float rp_r = __shfl_sync(0xFFFFFFFFu, rp[1], src_l);
+          const float dzp_r = __shfl_sync(0xFFFFFFFFu, dzp[1], src_l);
+          const float zf_r = __shfl_sync(0xFFFFFFFFu, zf[1], src_l);
+          const float zs_r = __shfl_sync(0xFFFFFFFFu, zs[1], src_l);
+          const float rs_r = __shfl_sync(0xFFFFFFFFu, rs[1], src_l);
+          const float fpv_r = __shfl_sync(0xFFFFFFFFu, fpv[1], src_l);
+          const float fpp_r = __shfl_sync(0xFFFFFFFFu, fpp[1], src_l);
+          const float dpp_r = __shfl_sync(0xFFFFFFFFu, dpp[1], src_l);
+          const int hv_r = __shfl_sync(0xFFFFFFFFu, hv[1], src_l);
+          const uint32_t ro_r = __shfl_sync(0xFFFFFFFFu, (relax_off >> 1) & 1u, src_l);
+          if (take) {
+            ray[0] = r_r; z[0] = z_r; d[0][0] = d0_r; d[0][1] = d1_r; d[0][2] = d2_r; inv_ld[0] = il_r;
+            steps[0] = st_r; rp[0] = rp_r; dzp[0] = dzp_r; zf[0] = zf_r; zs[0] = zs_r; rs[0] = rs_r;
+            fpv[0] = fpv_r; fpp[0] = fpp_r; dpp[0] = dpp_r; hv[0] = hv_r;
+            relax_off = (relax_off & ~1u) | ro_r;
+          }
+          if (give) {
+            ray[1] = -1;
+            relax_off &= ~2u;
+          }
+        }
+      }
       // A lane whose first slot is empty takes its second slot's ray; when no
       // lane has a second ray left, one evaluation chain per lane suffices.
       const bool mv = ray[0] < 0 && ray[1] >= 0;
