@@ -4,19 +4,26 @@
 // Algorithm 3.
 //
 // Execution model (own design for sm_103a):
-//   * persistent CTAs of kWarps warps; every warp is an independent tile
-//     worker pulling (job, tile) items from a global queue;
-//   * per tile, the warp walks the depth-sorted A-buffer list, segmenting the
-//     tile frustum into subfrustums [z_begin, z_end] with a fixed active
-//     primitive set (Sec. 8 "tracking active primitives"; discard, fetch and
-//     sorted merge are warp-parallel);
-//   * one lane rebuilds the pruned view from the active set (Algorithm 1 with
-//     fast ancestor pointers, clamping and popRequiredA / popRequiredB);
-//   * all lanes then sphere-trace the subfrustum in lockstep over the same
-//     view (warp-uniform node sequence, no divergence in the interpreter);
-//     a lane whose ray hits, leaves the subfrustum or reaches the step cap
-//     immediately takes the next pending ray of the tile (compaction of
-//     finished rays), so lanes stay busy until the tile's queue drains;
+//   * persistent CTAs of kWarps warps, three per SM; a CTA traces one tile at
+//     a time, tiles handed out longest A-buffer list first from a global
+//     counter (one launch can cover the tiles of many scenes);
+//   * warp 0 walks the tile's depth-sorted A-buffer list, segmenting the tile
+//     frustum into subfrustums [z_begin, z_end] with a fixed active primitive
+//     set (Sec. 8 "tracking active primitives"; discard, fetch and sorted
+//     merge are warp-parallel), builds the pruned view of subfrustum k + 1
+//     (lowest common ancestors of consecutive active primitives, the same
+//     view as Algorithm 1) and fills its shared parameter cache while all
+//     warps march subfrustum k;
+//   * each warp sphere-traces up to two rays per lane in lockstep over the
+//     same view (warp-uniform node sequence, no divergence in the
+//     interpreter); a lane whose ray hits, leaves the subfrustum or reaches
+//     the step cap takes the next pending ray of the tile; with few rays left
+//     a warp compacts them to one evaluation chain per lane, then evaluates
+//     each remaining ray with the whole warp (tail mode) and hands rays to
+//     idle warps of the tile;
+//   * step modes: plain f / (L |d|); fixed or learned over-relaxation, every
+//     relaxed step verified by the sphere-overlap test (Sec. 10); recording
+//     of plain steps for training;
 //   * hits are refined with Newton steps on the ray (dual numbers) and get
 //     the normalised forward-mode gradient of f_A as normal.
 #include <cstdint>
@@ -1253,8 +1260,8 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
 }
 
 // ---- the tracing kernel ----------------------------------------------------------
-// Four CTAs per SM (128 registers) except the learned step, whose MLP
-// fragments need more registers; its extra shared memory limits it to three.
+// Three CTAs per SM: up to 170 registers per thread (the learned step's MLP
+// fragments need 166) with ~57 KB of shared memory per CTA.
 template <int MODE>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
