@@ -9,7 +9,7 @@ the same run with identical eps, Lipschitz bound and subfrustum sizes.
 Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 1080p|small|clustered|clustered1080p] [--modes learned,plain,overrelax]
+                  [--workload 1080p|small|clustered|clustered1080p] [--modes learned,plain,overrelax,crossing]
 
 Multi-GPU: one independent replica per rank (the path has no exchange step);
 value = all ranks' rays / max-over-ranks time ("scaling": "weak").
@@ -224,6 +224,10 @@ def mode_opts(st, name: str, mlp, max_new: int):
         return st.make_opts(step_mode=st.ST_STEP_OVERRELAX, omega=1.7, max_new_per_turn=max_new)
     if name == "plain":
         return st.make_opts(step_mode=st.ST_STEP_PLAIN, max_new_per_turn=max_new)
+    if name == "crossing":
+        # Sec. 10's own ray processing: omega = 1.7 with sphere reuse, minimum
+        # step instead of eps and step cap (hits are crossings, f <= 0)
+        return st.make_opts(step_mode=st.ST_STEP_CROSSING, omega=1.7, max_new_per_turn=max_new)
     raise SystemExit(f"unknown step mode {name}")
 
 
@@ -504,7 +508,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="1080p")
-    ap.add_argument("--modes", default="learned,plain,overrelax",
+    ap.add_argument("--modes", default="learned,plain,overrelax,crossing",
                     help="step modes to time; the first one is the headline value")
     ap.add_argument("--max-new", type=int, default=24, help="new primitives per subfrustum")
     ap.add_argument("--batch-scenes", type=int, default=64, help="scenes of the batch64 workload")

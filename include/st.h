@@ -123,6 +123,14 @@ typedef struct {
                                   previous point, takes the plain step and
                                   relaxes again once it has crossed the stored
                                   landing sphere (Sec. 10)                 */
+#define ST_STEP_CROSSING 3     /* the ray processing of Sec. 10 as stated:
+                                  ST_STEP_OVERRELAX's verified relaxed steps,
+                                  every step at least min_step long, a hit at
+                                  the first sample with f <= 0 (eps unused),
+                                  no step cap (max_steps unused).  A relaxed
+                                  step that lands inside the solid is
+                                  rejected and plain steps bracket the
+                                  crossing                                 */
 typedef struct {
     float eps;              /* hit when f <= eps [1e-4]                    */
     float lipschitz;        /* L of the step f / L [1.45, Sec. 10]         */
@@ -150,8 +158,12 @@ typedef struct {
                                cycles / 16 (first warp); [15] marching
                                cycles / 16 summed over warps
                                (NULL = off)                                */
-    float omega;            /* relaxation factor of ST_STEP_OVERRELAX [1.7,
-                               Sec. 10]                                    */
+    float omega;            /* relaxation factor of ST_STEP_OVERRELAX and
+                               ST_STEP_CROSSING [1.7, Sec. 10]             */
+    float min_step;         /* ST_STEP_CROSSING: shortest step, distance
+                               units [1/32000 of the largest extent of the
+                               primitives' bounding box measured at
+                               st_scene_create, Sec. 10]                   */
 } st_trace_opts;
 
 /* Optional per-call counters (device pointer to 8 uint64, accumulated with
@@ -345,7 +357,8 @@ int st_mlp_infer(const void *packed, const float *x, int n, float *omega, void *
  * at draw time: render loops that run under a fixed memory budget or must
  * not stall on an allocation (cudaMalloc can synchronise the device), and
  * hosts whose device memory is owned by another allocator.  The paper has no
- * counterpart to this call.
+ * counterpart to this call.  Step modes ST_STEP_PLAIN, ST_STEP_OVERRELAX and
+ * ST_STEP_CROSSING; ST_STEP_LEARNED returns ST_ERR_INVALID.
  *
  * Its scratch memory (the work-queue counter, the job record and, for long
  * tile lists, the per-CTA work areas) is one fixed 32 MiB device array

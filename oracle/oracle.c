@@ -26,7 +26,8 @@
  *     that the GPU culling kernel documents (the integer hit decisions are
  *     taken in the same precision on both sides)
  *   - naive dense sphere tracing (Sec. 2.2, Sec. 10) with Newton polish and
- *     central-difference normals
+ *     central-difference normals, and the over-relaxed variant with sphere
+ *     reuse, minimum step and iso-crossing detection that Sec. 10 states
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no fast-math).
  */
@@ -787,6 +788,39 @@ static void grad_at(const Tree *t, const double p[3], double h, double g[3]) {
     }
 }
 
+/* Depth, normal and residual of one traced ray.  A hit at z is refined by
+ * up to `newton` Newton steps along the ray (step clamped to +-newton_clamp in
+ * distance); depth = z |d| (Euclidean distance to the eye); the normal is the
+ * normalised central-difference gradient (h = 1e-6); resid is the field value
+ * at the refined point.  A miss gets depth = resid = +inf and a zero normal. */
+static void finish_ray(const Tree *t, const Cam *c, const double d[3], double dn, double z, int hit,
+                       int newton, double newton_clamp, double *depth, double *normal, double *resid) {
+    if (!hit) {
+        *depth = INFINITY;
+        *resid = INFINITY;
+        for (int k = 0; k < 3; ++k) normal[k] = 0.0;
+        return;
+    }
+    for (int it = 0; it < newton; ++it) {
+        double p[3] = {c->o[0] + z * d[0], c->o[1] + z * d[1], c->o[2] + z * d[2]}, g[3];
+        double fz = field_rec(t, t->root, p, NULL);
+        grad_at(t, p, 1e-6, g);
+        double gd = g[0] * d[0] + g[1] * d[1] + g[2] * d[2];
+        if (gd == 0.0) break;
+        double dz = -fz / gd;
+        double lim = newton_clamp / dn;
+        if (dz > lim) dz = lim;
+        if (dz < -lim) dz = -lim;
+        z += dz;
+    }
+    double p[3] = {c->o[0] + z * d[0], c->o[1] + z * d[1], c->o[2] + z * d[2]}, g[3];
+    grad_at(t, p, 1e-6, g);
+    double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    *resid = field_rec(t, t->root, p, NULL);
+    *depth = z * dn;
+    for (int k = 0; k < 3; ++k) normal[k] = gn > 0 ? g[k] / gn : 0.0;
+}
+
 /* Per pixel (i, j):  z starts at z_near and advances by f / (L |d|) until
  * f <= eps (hit), z > z_far (miss: exit of the bounding sphere of the
  * primitives' bounds) or max_steps.  A hit is refined by up to `newton`
@@ -832,30 +866,94 @@ void or_trace(int n, int root, const int32_t *kind, const int32_t *left, const i
                 if (z > zfar) break;
             }
         }
-        if (fl & 1) {
-            for (int it = 0; it < newton; ++it) {
-                double p[3] = {c.o[0] + z * d[0], c.o[1] + z * d[1], c.o[2] + z * d[2]}, g[3];
-                double fz = field_rec(&t, root, p, NULL);
-                grad_at(&t, p, 1e-6, g);
-                double gd = g[0] * d[0] + g[1] * d[1] + g[2] * d[2];
-                if (gd == 0.0) break;
-                double dz = -fz / gd;
-                double lim = newton_clamp / dn;
-                if (dz > lim) dz = lim;
-                if (dz < -lim) dz = -lim;
+        finish_ray(&t, &c, d, dn, z, fl & 1, newton, newton_clamp, depth + px, normal + 3 * (size_t)px,
+                   resid + px);
+        steps[px] = st;
+        flags[px] = fl;
+        min_f[px] = mf;
+    }
+    tree_free(&t);
+}
+
+/* The ray processing stated in Sec. 10 ("Ray processing"), over the dense
+ * field: over-relaxed sphere tracing with factor omega, where a step whose
+ * end sphere does not overlap the sphere it started from is undone; the end
+ * sphere is kept and over-relaxation stays off until plain steps reach it,
+ * whereupon the ray jumps across it (the sphere is free of surface).  No
+ * step cap; instead every step is at least min_step long (distance units),
+ * and a hit is the first sample with f <= 0 (iso-crossing detection), then
+ * refined and shaded as in or_trace.
+ * Readings where Sec. 10 is silent: a plain or minimum-length step is never
+ * undone (only relaxed steps are tested); an undone step whose end point lies
+ * inside the solid (f <= 0) stores no sphere to jump across (a crossing lies
+ * before it, which plain steps will bracket).  max_steps only guards against
+ * a broken field (flag bit1); steps counts field evaluations. */
+void or_trace_relaxed(int n, int root, const int32_t *kind, const int32_t *left, const int32_t *right,
+                      const float *params, const float *cam, double lipschitz, double omega,
+                      double min_step, int max_steps, int newton, double newton_clamp, int npx,
+                      const int32_t *pi, const int32_t *pj, double *depth, double *normal,
+                      int32_t *steps, uint8_t *flags, double *min_f, double *resid) {
+    Tree t;
+    tree_init(&t, n, root, kind, left, right, params);
+    Cam c;
+    cam_init(&c, cam);
+    double lo[3], hi[3];
+    double diag = or_scene_bounds(n, kind, params, lo, hi);
+    double bc[3] = {0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2])};
+    double br = 0.5 * diag;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int px = 0; px < npx; ++px) {
+        double d[3];
+        cam_ray64(&c, pi[px], pj[px], d);
+        double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double h = min_step / dn;            /* shortest step in ray parameter */
+        double t0, t1, mf = INFINITY;
+        int st = 0;
+        uint8_t fl = 0;
+        double z = 0.01;
+        if (ray_sphere64(c.o, d, bc, br, &t0, &t1) && t1 > z) {
+            if (t0 > z) z = t0;
+            double zfar = t1;
+            double rp = 0.0;                 /* surface-free radius at the previous sample */
+            double dzp = 0.0;                /* last relaxed step (0: none to verify) */
+            double zf = z;                   /* where the plain step from the previous sample lands */
+            double zs = 0.0, rs = -1.0;      /* stored sphere (rs < 0: none) */
+            int relax = 1;
+            for (;;) {
+                if (st >= max_steps) { fl |= 2; break; }
+                double f = field_at(&t, c.o, d, z);
+                ++st;
+                if (f < mf) mf = f;
+                double r = fabs(f) / (lipschitz * dn);
+                if (dzp > 0.0 && r + rp < dzp) {
+                    /* undo the relaxed step */
+                    if (f > 0.0) { zs = z; rs = r; } else { zs = INFINITY; rs = 0.0; }
+                    relax = 0;
+                    z = zf;
+                    dzp = 0.0;
+                    if (rs >= 0.0 && z >= zs - rs) { z = zs + rs; rs = -1.0; relax = 1; }
+                    if (z > zfar) break;
+                    continue;
+                }
+                if (f <= 0.0) { fl |= 1; break; }
+                double om = relax ? omega : 1.0;
+                double dz = om * r;
+                if (dz <= h) { dz = h; om = 1.0; }
+                zf = z + (r > h ? r : h);
+                rp = r;
+                dzp = om > 1.0 ? dz : 0.0;
                 z += dz;
+                if (!relax && rs >= 0.0 && z >= zs - rs) {
+                    if (z < zs + rs) z = zs + rs;
+                    rs = -1.0;
+                    relax = 1;
+                    dzp = 0.0;
+                }
+                if (z > zfar) break;
             }
-            double p[3] = {c.o[0] + z * d[0], c.o[1] + z * d[1], c.o[2] + z * d[2]}, g[3];
-            grad_at(&t, p, 1e-6, g);
-            double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-            resid[px] = field_rec(&t, root, p, NULL);
-            depth[px] = z * dn;
-            for (int k = 0; k < 3; ++k) normal[3 * (size_t)px + k] = gn > 0 ? g[k] / gn : 0.0;
-        } else {
-            depth[px] = INFINITY;
-            resid[px] = INFINITY;
-            for (int k = 0; k < 3; ++k) normal[3 * (size_t)px + k] = 0.0;
         }
+        finish_ray(&t, &c, d, dn, z, fl & 1, newton, newton_clamp, depth + px, normal + 3 * (size_t)px,
+                   resid + px);
         steps[px] = st;
         flags[px] = fl;
         min_f[px] = mf;

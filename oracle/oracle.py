@@ -69,6 +69,8 @@ def _declare(L):
     L.or_cull.restype = I
     L.or_trace.argtypes = [I, I, P, P, P, P, P, D, D, I, I, D, I, P, P, P, P, P, P, P, P]
     L.or_trace.restype = None
+    L.or_trace_relaxed.argtypes = [I, I, P, P, P, P, P, D, D, D, I, I, D, I, P, P, P, P, P, P, P, P]
+    L.or_trace_relaxed.restype = None
     L.or_march.argtypes = [I, I, P, P, P, P, P, D, I, P, P, P, P]
     L.or_march.restype = None
     L.or_num_threads.argtypes = []
@@ -222,6 +224,41 @@ def trace(scene, cam, pi=None, pj=None, eps: float = EPS, lipschitz: float = LIP
     ca = cam_array(cam)
     lib().or_trace(*sa, _p(ca), eps, lipschitz, max_steps, newton, newton_clamp, n, _p(pi),
                    _p(pj), _p(depth), _p(normal), _p(steps), _p(flags), _p(min_f), _p(resid))
+    return dict(depth=depth, normal=normal, steps=steps, flags=flags, min_f=min_f, resid=resid,
+                pi=pi, pj=pj)
+
+
+def min_step_default(scene) -> float:
+    """Sec. 10: the minimum step is about 1/32000 of the largest dimension
+    of the scene's bounding box."""
+    lo, hi, _ = scene_bounds(scene)
+    return float(np.max(hi - lo)) / 32000.0
+
+
+def trace_relaxed(scene, cam, pi=None, pj=None, lipschitz: float = LIPSCHITZ, omega: float = 1.7,
+                  min_step: float | None = None, max_steps: int = 10_000_000, newton: int = 4,
+                  newton_clamp: float = 64 * EPS):
+    """Sec. 10's ray processing (over-relaxation with sphere reuse, minimum
+    step, hit at the first f <= 0) over the dense FP64 field, for the pixels
+    (pi, pj) (all if None).  Returns the same dict as trace()."""
+    if pi is None:
+        jj, ii = np.mgrid[0:cam.height, 0:cam.width]
+        pi, pj = ii.reshape(-1), jj.reshape(-1)
+    pi = np.ascontiguousarray(pi, np.int32)
+    pj = np.ascontiguousarray(pj, np.int32)
+    if min_step is None:
+        min_step = min_step_default(scene)
+    n = len(pi)
+    depth = np.empty(n, np.float64)
+    normal = np.empty((n, 3), np.float64)
+    steps = np.empty(n, np.int32)
+    flags = np.empty(n, np.uint8)
+    min_f = np.empty(n, np.float64)
+    resid = np.empty(n, np.float64)
+    keep, sa = _scene_args(scene)
+    ca = cam_array(cam)
+    lib().or_trace_relaxed(*sa, _p(ca), lipschitz, omega, min_step, max_steps, newton, newton_clamp, n,
+                           _p(pi), _p(pj), _p(depth), _p(normal), _p(steps), _p(flags), _p(min_f), _p(resid))
     return dict(depth=depth, normal=normal, steps=steps, flags=flags, min_f=min_f, resid=resid,
                 pi=pi, pj=pj)
 

@@ -14,7 +14,7 @@ namespace st {
 int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_trace_opts &o, float *depth,
                  float *normal, uint32_t *evals, uint8_t *flags, uint64_t *counters, void *stream, float *records,
                  uint32_t rec_cap, uint32_t *rec_count, int rec_stride);
-TraceParams make_trace_params(const st_trace_opts &o, double diameter);
+TraceParams make_trace_params(const st_trace_opts &o, double diameter, double extent);
 
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
@@ -120,10 +120,11 @@ static DevScene dev_scene(const st_scene *s) {
 }
 
 // Read-only facts of a scene for entry points defined in other files.
-void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, int *n_sm) {
+void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, double *extent, int *n_sm) {
   *sc = dev_scene(s);
   *stack_depth = s->prep.stack_depth;
   *diameter = s->prep.diameter;
+  *extent = s->prep.extent;
   *n_sm = s->n_sm;
 }
 
@@ -333,7 +334,8 @@ int st_trace(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_tra
   st_trace_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.step_mode != ST_STEP_PLAIN && o.step_mode != ST_STEP_OVERRELAX && o.step_mode != ST_STEP_LEARNED) {
+  if (o.step_mode != ST_STEP_PLAIN && o.step_mode != ST_STEP_OVERRELAX && o.step_mode != ST_STEP_LEARNED &&
+      o.step_mode != ST_STEP_CROSSING) {
     set_error("unknown step mode");
     return ST_ERR_INVALID;
   }
@@ -366,7 +368,7 @@ int st_trace_record(st_scene *s, const st_camera *cam, const st_tiles *tl, const
 namespace st {
 
 // Trace parameters of st_trace_opts, with the documented defaults.
-TraceParams make_trace_params(const st_trace_opts &o, double diameter) {
+TraceParams make_trace_params(const st_trace_opts &o, double diameter, double extent) {
   TraceParams tp;
   tp.eps = o.eps > 0.f ? o.eps : 1e-4f;
   tp.lipschitz = o.lipschitz > 0.f ? o.lipschitz : 1.45f;
@@ -378,6 +380,7 @@ TraceParams make_trace_params(const st_trace_opts &o, double diameter) {
   tp.newton_iters = o.newton_iters > 0 ? o.newton_iters : (o.newton_iters < 0 ? 0 : 4);
   tp.newton_clamp = o.newton_clamp > 0.f ? o.newton_clamp : 64.f * tp.eps;
   tp.omega = o.omega > 1.f ? std::min(o.omega, 2.f) : 1.7f;
+  tp.min_step = o.min_step > 0.f ? o.min_step : std::max((float)(extent / 32000.0), 1e-7f);
   return tp;
 }
 
@@ -405,7 +408,7 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
   job.out.evals = evals;
   job.out.flags = flags;
   TraceParams &tp = job.tp;
-  tp = make_trace_params(o, s->prep.diameter);
+  tp = make_trace_params(o, s->prep.diameter, s->prep.extent);
   job.tile_base = 0;
   cudaStream_t st = (cudaStream_t)stream;
 
@@ -415,7 +418,7 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
   L.act_cap = (int)std::max<uint32_t>(tl->max_overlap, 1u);
   L.view_cap = 2 * L.act_cap;
   L.stack_slots = s->prep.stack_depth + 2;
-  L.dc_words = L.view_cap > 2048 ? 2048 : 640;   // big views: larger parameter cache (2 CTAs per SM)
+  L.dc_words = trace_dcache_words(L.view_cap, tl->max_overlap, tl->n_entries, s->n_sm);
   L.n_items = (uint32_t)(tiles_x * tiles_y);
   L.counters = counters;
   L.tile_stats = o.tile_stats;

@@ -22,8 +22,8 @@
 #include "st_kernels.h"
 
 namespace st {
-void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, int *n_sm);
-TraceParams make_trace_params(const st_trace_opts &o, double diameter);
+void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, double *extent, int *n_sm);
+TraceParams make_trace_params(const st_trace_opts &o, double diameter, double extent);
 }  // namespace st
 
 using namespace st;
@@ -229,6 +229,7 @@ struct st_batch {
   Buf<float> ztmp, z_in, z_out;
   Buf<uint32_t> prim;
   uint32_t pair_cap = 0, overlap_cap = 0;
+  uint32_t longest_seen = 0, entries_seen = 0;   // sizing pass: longest list, entry total
   TraceLaunch L;
   int grid = 0;
   size_t smem = 0;
@@ -270,8 +271,8 @@ int plan(st_batch *b) {
     Job &j = b->jobs[i];
     std::memset(&j, 0, sizeof(Job));
     int sd = 0, nsm = 1;
-    double diam = 0;
-    scene_facts(b->scenes[i], &j.sc, &sd, &diam, &nsm);
+    double diam = 0, ext = 0;
+    scene_facts(b->scenes[i], &j.sc, &sd, &diam, &ext, &nsm);
     b->n_sm = nsm;
     camera_basis(b->cams[i], j.cam);
     const int T = b->tune[i].tile;
@@ -281,7 +282,7 @@ int plan(st_batch *b) {
     st_trace_opts o = b->opts;
     o.max_new_per_turn = b->tune[i].max_new_per_turn;
     o.depth_slab_frac = b->tune[i].depth_slab_frac;
-    j.tp = make_trace_params(o, diam);
+    j.tp = make_trace_params(o, diam, ext);
     j.out.depth = b->depth[i];
     j.out.normal = b->normal[i];
     j.out.evals = b->evals[i];
@@ -328,6 +329,8 @@ int plan(st_batch *b) {
     set_error("st_batch: a tile list exceeds the sort capacity (16384 entries)");
     return ST_ERR_CAPACITY;
   }
+  b->longest_seen = host_small[2];
+  b->entries_seen = host_small[3];
   // Headroom for edits between renders.
   b->pair_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, (uint64_t)host_small[1] * 3 / 2 + 4096);
   b->overlap_cap = std::min<uint32_t>(kSortLarge, std::max<uint32_t>(host_small[2] + host_small[2] / 4 + 16, 64));
@@ -353,7 +356,7 @@ int plan(st_batch *b) {
   L.act_cap = (int)b->overlap_cap;
   L.view_cap = 2 * L.act_cap;
   L.stack_slots = stack_slots;
-  L.dc_words = L.view_cap > 2048 ? 2048 : 640;   // big views: larger parameter cache (2 CTAs per SM)
+  L.dc_words = trace_dcache_words(L.view_cap, b->longest_seen, b->entries_seen, b->n_sm);
   L.n_items = b->n_tiles;
   L.item_counter = b->item_counter.p;
   L.counters = b->counters.p;
@@ -510,8 +513,8 @@ int st_autotune(st_scene *scene, const st_camera *cam, const st_trace_opts *opts
   if (cache_path) {
     DevScene sc;
     int sd = 0, nsm = 0;
-    double diam = 0;
-    scene_facts(scene, &sc, &sd, &diam, &nsm);
+    double diam = 0, ext = 0;
+    scene_facts(scene, &sc, &sd, &diam, &ext, &nsm);
     char key[96];
     rc = st_tune_key(sc.n_prims, cam->width, cam->height, o.step_mode, key, (int)sizeof(key));
     if (rc == ST_OK) rc = st_tune_store(cache_path, key, &best);
@@ -531,7 +534,8 @@ int st_batch_create(st_scene *const *scenes, const st_camera *cams, int n, const
   st_trace_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.step_mode != ST_STEP_PLAIN && o.step_mode != ST_STEP_OVERRELAX && o.step_mode != ST_STEP_LEARNED) {
+  if (o.step_mode != ST_STEP_PLAIN && o.step_mode != ST_STEP_OVERRELAX && o.step_mode != ST_STEP_LEARNED &&
+      o.step_mode != ST_STEP_CROSSING) {
     set_error("st_batch_create: unknown step mode");
     return ST_ERR_INVALID;
   }
@@ -561,8 +565,8 @@ int st_batch_create(st_scene *const *scenes, const st_camera *cams, int n, const
     if (autotune_cache) {
       DevScene sc;
       int sd = 0, nsm = 0;
-      double diam = 0;
-      scene_facts(scenes[i], &sc, &sd, &diam, &nsm);
+      double diam = 0, ext = 0;
+      scene_facts(scenes[i], &sc, &sd, &diam, &ext, &nsm);
       char key[96];
       int rc = st_tune_key(sc.n_prims, cams[i].width, cams[i].height, o.step_mode, key, (int)sizeof(key));
       if (rc == ST_OK && st_tune_load(autotune_cache, key, &t) != ST_OK)

@@ -95,7 +95,8 @@ struct DevOut {
 struct TraceParams {
   float eps, lipschitz, depth_slab, newton_clamp;
   int32_t max_steps, max_new, newton_iters, step_mode;
-  float omega;   // relaxation factor of ST_STEP_OVERRELAX
+  float omega;      // relaxation factor of ST_STEP_OVERRELAX / ST_STEP_CROSSING
+  float min_step;   // ST_STEP_CROSSING: shortest step, distance units
 };
 
 // One culling or tracing job (a scene seen by a camera).
@@ -121,7 +122,8 @@ struct Prep {
   std::vector<float> roi, d_prim, rec;  // rec: 4 floats per word
   std::vector<int32_t> prim_desc;       // description index of primitive j
   int stack_depth = 0;
-  double diameter = 0;
+  double diameter = 0;   // diagonal of the primitives' bounding box
+  double extent = 0;     // its largest edge
 };
 
 // Returns ST_OK or ST_ERR_INVALID with `err` set.

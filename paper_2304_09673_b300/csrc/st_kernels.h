@@ -64,10 +64,14 @@ struct TraceLaunch {
                            // (launch_tile_order: longest list first)
 };
 
-constexpr int ST_STEP_RECORD = 3;   // plain stepping that records training data
+constexpr int ST_STEP_RECORD = 15;  // plain stepping that records training data (internal)
 
 size_t trace_smem_per_warp(const TraceLaunch &L);
 uint32_t trace_work_words(const TraceLaunch &L);
+// Parameter cache words per view buffer for a launch whose views hold up to
+// view_cap nodes, whose longest tile list has max_overlap entries out of
+// n_entries in all, on n_sm SMs.
+int trace_dcache_words(int view_cap, uint32_t max_overlap, uint64_t n_entries, int n_sm);
 cudaError_t trace_launch(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s);
 // Split form for graph capture: trace_plan sets the kernel attributes and
 // returns the persistent grid and shared memory size (call before capture);

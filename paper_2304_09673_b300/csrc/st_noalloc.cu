@@ -10,7 +10,8 @@
 #include "st_kernels.h"
 
 namespace st {
-void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, int *n_sm);
+void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, double *extent, int *n_sm);
+TraceParams make_trace_params(const st_trace_opts &o, double diameter, double extent);
 }
 
 namespace {
@@ -96,7 +97,7 @@ extern "C" int st_trace_noalloc(st_scene *s, const st_camera *cam, const st_tile
   st_trace_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.step_mode != ST_STEP_PLAIN && o.step_mode != ST_STEP_OVERRELAX) {
+  if (o.step_mode != ST_STEP_PLAIN && o.step_mode != ST_STEP_OVERRELAX && o.step_mode != ST_STEP_CROSSING) {
     set_error("st_trace_noalloc: step mode not available");
     return ST_ERR_INVALID;
   }
@@ -107,8 +108,8 @@ extern "C" int st_trace_noalloc(st_scene *s, const st_camera *cam, const st_tile
   Job job;
   std::memset(&job, 0, sizeof(job));
   int stack_depth = 0, n_sm = 1;
-  double diameter = 0;
-  scene_facts(s, &job.sc, &stack_depth, &diameter, &n_sm);
+  double diameter = 0, extent = 0;
+  scene_facts(s, &job.sc, &stack_depth, &diameter, &extent, &n_sm);
   camera_basis(*cam, job.cam);
   job.tl.tile = tl->tile;
   job.tl.tiles_x = tl->tiles_x;
@@ -121,17 +122,7 @@ extern "C" int st_trace_noalloc(st_scene *s, const st_camera *cam, const st_tile
   job.out.normal = normal;
   job.out.evals = evals;
   job.out.flags = flags;
-  TraceParams &tp = job.tp;
-  tp.eps = o.eps > 0.f ? o.eps : 1e-4f;
-  tp.lipschitz = o.lipschitz > 0.f ? o.lipschitz : 1.45f;
-  tp.max_steps = o.max_steps > 0 ? o.max_steps : 256;
-  tp.step_mode = o.step_mode;
-  const float frac = o.depth_slab_frac > 0.f ? o.depth_slab_frac : 0.05f;
-  tp.depth_slab = std::max(frac * (float)diameter, 1e-6f);
-  tp.max_new = o.max_new_per_turn > 0 ? std::min(o.max_new_per_turn, 32) : 24;
-  tp.newton_iters = o.newton_iters > 0 ? o.newton_iters : (o.newton_iters < 0 ? 0 : 4);
-  tp.newton_clamp = o.newton_clamp > 0.f ? o.newton_clamp : 64.f * tp.eps;
-  tp.omega = o.omega > 1.f ? std::min(o.omega, 2.f) : 1.7f;
+  job.tp = make_trace_params(o, diameter, extent);
   job.tile_base = 0;
 
   TraceLaunch L;
@@ -144,7 +135,7 @@ extern "C" int st_trace_noalloc(st_scene *s, const st_camera *cam, const st_tile
   L.n_items = (uint32_t)(tiles_x * tiles_y);
   L.counters = counters;
   L.tile_stats = o.tile_stats;
-  L.step_mode = tp.step_mode;
+  L.step_mode = job.tp.step_mode;
   L.work_in_smem = 1;
   if (trace_smem_per_warp(L) * 16 > 200 * 1024) L.work_in_smem = 0;
 

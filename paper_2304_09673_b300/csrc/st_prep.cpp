@@ -250,9 +250,13 @@ int prepare(const st_scene_desc &d, Prep &p, std::string &err) {
     }
   }
   if (p.rec.size() / 4 > kViewOffMask) return fail("too many record words");
-  double s = 0;
-  for (int j = 0; j < 3; ++j) s += (hi[j] - lo[j]) * (hi[j] - lo[j]);
+  double s = 0, e = 0;
+  for (int j = 0; j < 3; ++j) {
+    s += (hi[j] - lo[j]) * (hi[j] - lo[j]);
+    e = std::fmax(e, hi[j] - lo[j]);
+  }
   p.diameter = std::sqrt(s);
+  p.extent = e;
   return ST_OK;
 }
 

@@ -41,6 +41,9 @@ constexpr int kR = 2;       // rays per lane (shared node decode, two evaluation
 int trace_warps_per_cta() { return kWarps; }
 
 enum RayStatus : uint32_t { R_ALIVE = 0, R_HIT = 1, R_UNCONV = 2 };
+// ray_st keeps a ray's step count in its low 24 bits: the step cap of the
+// modes without one.
+constexpr int kStepFieldMax = 0xFFFFFF;
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 // View-build stacks: value stack (uint2) and pending-operator stack (uint4),
@@ -69,6 +72,20 @@ __host__ __device__ inline size_t smem_per_cta(const TraceLaunch &L) {
 }
 size_t trace_smem_per_warp(const TraceLaunch &L) { return smem_per_cta(L) / kWarps; }
 uint32_t trace_work_words(const TraceLaunch &L) { return (uint32_t)(work_bytes(L) / 4); }
+
+// The larger cache (2048 float4 words, twice) holds the parameters of views
+// of ~600 primitives but leaves room for two CTAs per SM instead of three.
+// That pays when the launch is bound by its heaviest tiles, whose long lists
+// make large views and many subfrustums (their warps then get a larger share
+// of the SM), not when the work is spread over many more tiles than CTAs:
+// measured on B300, 10k clustered primitives at 1920x1080 gain 4-10 %
+// (5k: 22 %) and at 3840x2160 lose 25-40 %.  The test compares the longest
+// list with the entries per CTA.
+int trace_dcache_words(int view_cap, uint32_t max_overlap, uint64_t n_entries, int n_sm) {
+  if (view_cap <= 2048) return 640;
+  const double per_cta = (double)n_entries / (3.0 * std::max(n_sm, 1));
+  return (double)max_overlap > 0.3 * per_cta ? 2048 : 640;
+}
 
 struct CtaWork {
   float *ray_z;       // [rays] depth reached by each ray
@@ -835,7 +852,10 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
   // Per-subfrustum features of the learned step (see step_features).
   const float feat_prim = log2f(1.f + (float)inf.n_prim) * 0.125f;
   const float feat_len = log2f(1.f + (float)LC.list_len) * 0.125f;
-  const float omega_c = MODE == ST_STEP_OVERRELAX ? M.tp->omega : 1.f;
+  const float omega_c = MODE == ST_STEP_OVERRELAX || MODE == ST_STEP_CROSSING ? M.tp->omega : 1.f;
+  // Shortest step of ST_STEP_CROSSING times L: with inv_ld = 1 / (L |d|) the
+  // step along the ray parameter is min_l x inv_ld.
+  const float min_l = MODE == ST_STEP_CROSSING ? mul_(M.tp->min_step, M.tp->lipschitz) : 0.f;
   bool drained = false;
   uint32_t live_steps = 0;
   SmemStack2 stk{stk_lane};
@@ -851,7 +871,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       exit = true;
       C.ray_z[ray[s]] = z_end;
       C.ray_st[ray[s]] = steps[s];
-    } else if ((int)steps[s] >= M.tp->max_steps) {
+    } else if ((int)steps[s] >= (MODE == ST_STEP_CROSSING ? kStepFieldMax : M.tp->max_steps)) {
       C.ray_st[ray[s]] = steps[s] | (R_UNCONV << 24);
       write_miss(M, ray[s], steps[s], 2);
       ray[s] = -1;
@@ -895,6 +915,13 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       // return to the previous point and take the plain step from there.
       zs[s] = z[s];
       rs[s] = r;
+      if (MODE == ST_STEP_CROSSING && fs <= 0.f) {
+        // Landed inside the solid: a crossing lies before this point, so
+        // plain steps go on until they bracket it (a sphere that is never
+        // reached keeps relaxation off, and none is jumped over).
+        zs[s] = __int_as_float(0x7f800000);
+        rs[s] = 0.f;
+      }
       z[s] = zf[s];
       dzp[s] = 0.f;
       relax_off |= bit;
@@ -907,7 +934,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       leave_or_cap(s, exit);
       return;
     }
-    if (fs <= eps) {
+    if (MODE == ST_STEP_CROSSING ? fs <= 0.f : fs <= eps) {
       hit = true;
       C.ray_z[ray[s]] = z[s];
       C.ray_st[ray[s]] = steps[s] | (R_HIT << 24);
@@ -922,9 +949,18 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
     float om = (relax_off & bit) ? 1.f : om_prop;
     float dz = mul_(om, r);
     if (om > 1.f && add_(z[s], dz) >= z_end) { om = 1.f; dz = r; }   // relaxed steps never cross z_end
-    zf[s] = add_(z[s], r);
+    float dz_plain = r;
+    if (MODE == ST_STEP_CROSSING) {
+      // Shortest step: it may cross the surface (by less than min_step), and
+      // the sign test at the next sample detects the crossing; a step that
+      // the minimum lengthened is not a relaxed step and is never rejected.
+      const float h = mul_(min_l, inv_ld[s]);
+      if (dz <= h) { dz = h; om = 1.f; }
+      dz_plain = fmaxf(r, h);
+    }
+    zf[s] = add_(z[s], dz_plain);
     rp[s] = r;
-    dzp[s] = dz;
+    dzp[s] = (MODE == ST_STEP_CROSSING && om <= 1.f) ? r : dz;
     z[s] = add_(z[s], dz);
     if ((relax_off & bit) && rs[s] >= 0.f && z[s] >= sub_(zs[s], rs[s])) {
       // Plain stepping reached the stored surface-free sphere: cross it.
@@ -1637,6 +1673,7 @@ static cudaError_t trace_plan_mode(const TraceLaunch &L, int n_sm, int *grid, si
 cudaError_t trace_plan(const TraceLaunch &L, int n_sm, int *grid, size_t *smem) {
   switch (L.step_mode) {
     case ST_STEP_OVERRELAX: return trace_plan_mode<ST_STEP_OVERRELAX>(L, n_sm, grid, smem);
+    case ST_STEP_CROSSING: return trace_plan_mode<ST_STEP_CROSSING>(L, n_sm, grid, smem);
     case ST_STEP_LEARNED: return trace_plan_mode<ST_STEP_LEARNED>(L, n_sm, grid, smem);
     case ST_STEP_RECORD: return trace_plan_mode<ST_STEP_RECORD>(L, n_sm, grid, smem);
     default: return trace_plan_mode<ST_STEP_PLAIN>(L, n_sm, grid, smem);
@@ -1647,6 +1684,7 @@ cudaError_t trace_launch_planned(const Job *jobs, int n_jobs, const TraceLaunch 
                                  cudaStream_t s) {
   switch (L.step_mode) {
     case ST_STEP_OVERRELAX: count_launch(), k_trace<ST_STEP_OVERRELAX><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
+    case ST_STEP_CROSSING: count_launch(), k_trace<ST_STEP_CROSSING><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
     case ST_STEP_LEARNED: count_launch(), k_trace<ST_STEP_LEARNED><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
     case ST_STEP_RECORD: count_launch(), k_trace<ST_STEP_RECORD><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
     default: count_launch(), k_trace<ST_STEP_PLAIN><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
@@ -1657,6 +1695,7 @@ cudaError_t trace_launch_planned(const Job *jobs, int n_jobs, const TraceLaunch 
 cudaError_t trace_launch(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s) {
   switch (L.step_mode) {
     case ST_STEP_OVERRELAX: return trace_launch_mode<ST_STEP_OVERRELAX>(jobs, n_jobs, L, n_sm, s);
+    case ST_STEP_CROSSING: return trace_launch_mode<ST_STEP_CROSSING>(jobs, n_jobs, L, n_sm, s);
     case ST_STEP_LEARNED: return trace_launch_mode<ST_STEP_LEARNED>(jobs, n_jobs, L, n_sm, s);
     case ST_STEP_RECORD: return trace_launch_mode<ST_STEP_RECORD>(jobs, n_jobs, L, n_sm, s);
     default: return trace_launch_mode<ST_STEP_PLAIN>(jobs, n_jobs, L, n_sm, s);
@@ -1676,6 +1715,7 @@ static int ctas_per_sm_mode(const TraceLaunch &L) {
 int trace_ctas_per_sm(const TraceLaunch &L) {
   switch (L.step_mode) {
     case ST_STEP_OVERRELAX: return ctas_per_sm_mode<ST_STEP_OVERRELAX>(L);
+    case ST_STEP_CROSSING: return ctas_per_sm_mode<ST_STEP_CROSSING>(L);
     case ST_STEP_LEARNED: return ctas_per_sm_mode<ST_STEP_LEARNED>(L);
     case ST_STEP_RECORD: return ctas_per_sm_mode<ST_STEP_RECORD>(L);
     default: return ctas_per_sm_mode<ST_STEP_PLAIN>(L);

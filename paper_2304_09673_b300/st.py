@@ -19,7 +19,7 @@ if not LIB_PATH.exists():
 _lib = C.CDLL(str(LIB_PATH))
 
 ST_OK, ST_ERR_INVALID, ST_ERR_CAPACITY, ST_ERR_CUDA, ST_ERR_TIMEOUT, ST_ERR_NOMEM = 0, -1, -2, -3, -4, -5
-ST_STEP_PLAIN, ST_STEP_LEARNED, ST_STEP_OVERRELAX = 0, 1, 2
+ST_STEP_PLAIN, ST_STEP_LEARNED, ST_STEP_OVERRELAX, ST_STEP_CROSSING = 0, 1, 2, 3
 ST_NUM_COUNTERS = 8
 ST_REC_FLOATS = 16
 
@@ -53,7 +53,7 @@ class st_trace_opts(C.Structure):
                 ("step_mode", C.c_int32), ("depth_slab_frac", C.c_float),
                 ("max_new_per_turn", C.c_int32), ("newton_iters", C.c_int32),
                 ("newton_clamp", C.c_float), ("mlp", C.c_void_p), ("tile_stats", C.c_void_p),
-                ("omega", C.c_float)]
+                ("omega", C.c_float), ("min_step", C.c_float)]
 
 
 class st_tune(C.Structure):
@@ -158,9 +158,9 @@ def make_camera(cam) -> st_camera:
 
 def make_opts(eps=1e-4, lipschitz=1.45, max_steps=256, step_mode=ST_STEP_PLAIN, depth_slab_frac=0.05,
               max_new_per_turn=24, newton_iters=4, newton_clamp=0.0, mlp=None, tile_stats=None,
-              omega=1.7) -> st_trace_opts:
+              omega=1.7, min_step=0.0) -> st_trace_opts:
     o = st_trace_opts(eps, lipschitz, max_steps, step_mode, depth_slab_frac, max_new_per_turn,
-                      newton_iters, newton_clamp, mlp, None, omega)
+                      newton_iters, newton_clamp, mlp, None, omega, min_step)
     if tile_stats is not None:
         o.tile_stats = tile_stats.data_ptr()
         o._keep = tile_stats

@@ -109,13 +109,14 @@ def parity(orc, s, cam, g, ref, pix=None, normal_tol=1e-3):
     return dict(n_hit=int(both.sum()), band=int(band.sum()), max_depth_err=float(dd.max(initial=0)))
 
 
-def sampled_parity(orc, s, cam, g, n, seed=1, normal_tol=1e-3):
+def sampled_parity(orc, s, cam, g, n, seed=1, normal_tol=1e-3, tracer="trace"):
     """parity() on n random pixels of a frame too large for a full oracle
-    frame; the band test is per pixel from the oracle's own hit and min f."""
+    frame; the band test is per pixel from the oracle's own hit and min f.
+    `tracer` names the oracle tracer (trace or trace_relaxed)."""
     rng = np.random.default_rng(seed)
     pi = rng.integers(0, cam.width, n).astype(np.int32)
     pj = rng.integers(0, cam.height, n).astype(np.int32)
-    ref = orc.trace(s, cam, pi, pj)
+    ref = getattr(orc, tracer)(s, cam, pi, pj)
     _, _, diam = orc.scene_bounds(s)
     d64, _ = orc.camera_rays(cam, pi, pj)
     cosn = np.abs(np.sum(ref["normal"] * d64 / np.linalg.norm(d64, axis=1, keepdims=True), axis=1))

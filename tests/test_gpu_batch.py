@@ -66,11 +66,14 @@ def _setup(stlib, torch):
     return scenes, cams, handles, _outputs(cams, torch)
 
 
-@pytest.mark.parametrize("mode", ["plain", "learned"])
+@pytest.mark.parametrize("mode", ["plain", "learned", "crossing"])
 def test_batch_equals_per_scene_bitwise(stlib, cuda, tmp_path, mode):
     import torch
     kw = {}
     m = stlib.ST_STEP_PLAIN
+    if mode == "crossing":
+        m = stlib.ST_STEP_CROSSING
+        kw = dict(step_mode=m)
     if mode == "learned":
         from paper_2304_09673_b300 import learn
         packed = learn.packed_device(learn.load())

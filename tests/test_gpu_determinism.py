@@ -9,7 +9,7 @@ from paper_2304_09673_b300 import scenegen as sg
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("mode", ["plain", "learned", "overrelax"])
+@pytest.mark.parametrize("mode", ["plain", "learned", "overrelax", "crossing"])
 @pytest.mark.parametrize("n,depth,seed,W,H,tile", [(300, 12, 3, 200, 120, 8), (900, 14, 7, 320, 180, 16),
                                                    (150, 10, 9, 128, 128, 32)])
 def test_repeated_launches_identical(stlib, cuda, mode, n, depth, seed, W, H, tile):
@@ -21,6 +21,8 @@ def test_repeated_launches_identical(stlib, cuda, mode, n, depth, seed, W, H, ti
         kw = dict(step_mode=stlib.ST_STEP_LEARNED, mlp=packed.data_ptr())
     elif mode == "overrelax":
         kw = dict(step_mode=stlib.ST_STEP_OVERRELAX)
+    elif mode == "crossing":
+        kw = dict(step_mode=stlib.ST_STEP_CROSSING)
     s = sg.make_scene(n, depth, seed)
     cam = sg.default_camera(W, H)
     h = stlib.st_scene_create(s)

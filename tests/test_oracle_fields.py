@@ -94,11 +94,17 @@ def _angle(a, b):
     return np.arccos(np.clip(a @ b, -1, 1))
 
 
-def test_trace_single_sphere_analytic(orc):
+# Both oracle tracers: dense sphere tracing with the eps test, and Sec. 10's
+# over-relaxed variant with minimum step and iso-crossing detection.
+TRACERS = ["trace", "trace_relaxed"]
+
+
+@pytest.mark.parametrize("tracer", TRACERS)
+def test_trace_single_sphere_analytic(orc, tracer):
     c, r = np.array([0.1, -0.05, 0.2]), 0.3
     s = sg.single_primitive(sg.SPHERE, list(c) + [r])
     cam = sg.default_camera(48, 40)
-    res = orc.trace(s, cam)
+    res = getattr(orc, tracer)(s, cam)
     d64, _ = orc.camera_rays(cam, res["pi"], res["pj"])
     o = np.array(cam.eye, np.float64)
     c32 = s.params[0, :3].astype(np.float64)
@@ -109,7 +115,9 @@ def test_trace_single_sphere_analytic(orc):
         t = _ray_sphere(o, d, c32, r32)
         hit = bool(res["flags"][k] & 1)
         if t is None:
-            # a miss may only be reported hit if the ray grazes within eps
+            # a miss may only be reported hit if the ray grazes within eps;
+            # the crossing test never reports a ray that misses
+            assert not (hit and tracer == "trace_relaxed")
             if hit:
                 w = c32 - o
                 dist = np.linalg.norm(np.cross(w, d / np.linalg.norm(d)))
@@ -127,12 +135,13 @@ def test_trace_single_sphere_analytic(orc):
     assert nchk > 100
 
 
-def test_trace_single_box_analytic(orc):
+@pytest.mark.parametrize("tracer", TRACERS)
+def test_trace_single_box_analytic(orc, tracer):
     R = _rot(11)
     c, b = np.array([0.05, 0.0, -0.05]), np.array([0.25, 0.15, 0.2])
     s = sg.single_primitive(sg.RBOX, list(c) + list(R.T.reshape(-1)) + list(b) + [0.0])
     cam = sg.default_camera(72, 72)
-    res = orc.trace(s, cam)
+    res = getattr(orc, tracer)(s, cam)
     d64, _ = orc.camera_rays(cam, res["pi"], res["pj"])
     o = np.array(cam.eye, np.float64)
     M = s.params[0, 3:12].astype(np.float64).reshape(3, 3)
@@ -166,11 +175,12 @@ def test_trace_single_box_analytic(orc):
     assert nchk > 100
 
 
-def test_trace_single_capsule_analytic(orc):
+@pytest.mark.parametrize("tracer", TRACERS)
+def test_trace_single_capsule_analytic(orc, tracer):
     a, b, r = np.array([-0.25, -0.1, 0.0]), np.array([0.2, 0.2, -0.1]), 0.15
     s = sg.single_primitive(sg.CAPSULE, list(a) + list(b) + [r])
     cam = sg.default_camera(72, 72)
-    res = orc.trace(s, cam)
+    res = getattr(orc, tracer)(s, cam)
     d64, _ = orc.camera_rays(cam, res["pi"], res["pj"])
     o = np.array(cam.eye, np.float64)
     a32, b32, r32 = (s.params[0, 0:3].astype(np.float64), s.params[0, 3:6].astype(np.float64),
@@ -293,12 +303,14 @@ def test_union_only_exact_inside(orc):
     assert n_in > 10
 
 
-def test_first_hit_no_earlier_crossing(orc):
+@pytest.mark.parametrize("tracer", TRACERS)
+def test_first_hit_no_earlier_crossing(orc, tracer):
     # Sphere tracing reports the first crossing: fine FP64 marching finds no
-    # f <= 0 sample before the reported hit (sampled rays).
+    # f <= 0 sample before the reported hit (sampled rays).  For the relaxed
+    # tracer this checks that undone steps and sphere reuse skip no crossing.
     s = sg.workload_small(1)
     cam = sg.default_camera(64, 64)
-    res = orc.trace(s, cam)
+    res = getattr(orc, tracer)(s, cam)
     hit = np.flatnonzero(res["flags"] & 1)[::7][:40]
     d64, _ = orc.camera_rays(cam, res["pi"][hit], res["pj"][hit])
     t_hit = res["depth"][hit] / np.linalg.norm(d64, axis=1)
