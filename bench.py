@@ -4,12 +4,15 @@
 One step = the whole hot path on one frame: st_build_tiles (per-tile culling
 into the A-buffer) + st_trace (synchronized sphere tracing with sparse
 pruning), inputs resident in HBM.  The headline mode is the learned
-relaxation step; the plain step and fixed omega = 1.7 (Sec. 10) are timed in
-the same run with identical eps, Lipschitz bound and subfrustum sizes.
+relaxation step; the plain step, fixed omega = 1.7 and the paper's own ray
+processing (Sec. 10: omega = 1.7, minimum step, crossing test, no step cap) are
+timed in the same run with identical Lipschitz bound and subfrustum sizes.
+--workload table1 times the synchronized pipeline against the paper's
+per-pixel comparison variants (Table 1).
 Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 1080p|small|clustered|clustered1080p] [--modes learned,plain,overrelax,crossing]
+                  [--workload 1080p|small|clustered|clustered1080p|batch64|table1] [--modes learned,plain,overrelax,crossing]
 
 Multi-GPU: one independent replica per rank (the path has no exchange step);
 value = all ranks' rays / max-over-ranks time ("scaling": "weak").
@@ -501,6 +504,92 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def run_table1(args):
+    """The structure of the paper's Table 1 on synthetic stand-ins for its
+    models: frame time (A-buffer + tracing, plain step, same eps) of the
+    synchronized pipeline (st_build_tiles + st_trace) against per-pixel
+    processing over a full-resolution A-buffer with f_A evaluated at every
+    step by Algorithm 1 with fast ancestor pointers ("FastPtr/Full") or parent
+    pointers ("ParentPtr/Full"): st_build_tiles + st_build_dexels +
+    st_trace_dexels."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2304_09673_b300 import build as b
+    b.build()
+    from paper_2304_09673_b300 import scenegen as sg
+    from paper_2304_09673_b300 import st
+    cases = [("150-primitive seeded blobtree (depth <= 12, seed 150), 1720x1376", sg.make_scene(150, 12, 150),
+              sg.default_camera(1720, 1376)),
+             ("150-primitive left comb (left-heavy tree, depth 149, seed 150), 1720x1376", sg.make_comb(150, 150),
+              sg.default_camera(1720, 1376)),
+             ("1,024-primitive seeded blobtree (depth <= 14, seed 100), 1920x1080", sg.workload_1080p(100),
+              sg.default_camera(1920, 1080))]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    opts = st.make_opts()
+    sampler = ClockSampler(None)
+    launches0 = st.st_kernel_launches()
+    results = []
+    for what, scene, cam in cases:
+        W, H = cam.width, cam.height
+        r = st.Renderer(scene, cam, tile=16, stream=stream)
+
+        def sync_step():
+            r.build_tiles()
+            st.st_trace(r.h, cam, r.tiles, opts, r.depth, r.normal, r.evals, r.flags, r.counters, stream)
+
+        def dexel_step(trav):
+            def fn():
+                t = st.st_build_tiles(r.h, cam, 16, stream)
+                dx = st.st_build_dexels(r.h, cam, t, stream)
+                st.st_trace_dexels(r.h, cam, dx, opts, trav, r.depth, r.normal, r.evals, r.flags, r.counters,
+                                   stream)
+            return fn
+
+        row = {"workload": what}
+        masks = {}
+        for name, fn in (("synchronized", sync_step), ("fastptr_full", dexel_step(st.ST_TRAVERSE_FAST)),
+                         ("parentptr_full", dexel_step(st.ST_TRAVERSE_PARENT))):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            ms, cnt = [], None
+            for _ in range(args.steps):
+                flush.zero_()
+                r.counters.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                cnt = r.counters.cpu().numpy().astype(np.float64)
+            masks[name] = (r.flags & 1).clone()
+            row[name] = {"ms_per_frame": statistics.mean(ms), "rays_per_s": W * H / (statistics.mean(ms) / 1e3),
+                         "steps_per_ray": cnt[0] / (W * H), "prim_evals_per_ray": cnt[1] / (W * H),
+                         "device_error_flags": int(cnt[7])}
+            if name != "synchronized":
+                row[name]["operator_visits_per_ray"] = cnt[2] / (W * H)
+        base = row["synchronized"]["ms_per_frame"]
+        row["fastptr_over_synchronized"] = row["fastptr_full"]["ms_per_frame"] / base
+        row["parentptr_over_synchronized"] = row["parentptr_full"]["ms_per_frame"] / base
+        row["mask_mismatch_frac_vs_synchronized"] = {
+            k: float((masks[k] != masks["synchronized"]).float().mean().item()) for k in ("fastptr_full", "parentptr_full")}
+        results.append(row)
+        r.close()
+    clocks = sampler.stop()
+    line = {"metric": "frame time of per-pixel ParentPtr/Full over the synchronized pipeline (Table 1 structure)",
+            "value": results[0]["parentptr_over_synchronized"], "unit": "x", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": results[0]["synchronized"]["ms_per_frame"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Table 1 variants on two seeded scenes (plain step, eps 1e-4, max 256 steps, "
+                                   "tile 16 for the synchronized A-buffer)",
+                       "l2": "flushed between timed steps (256 MB write outside the timed events)"},
+            "cases": results, "gpu_launches": st.st_kernel_launches() - launches0, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,6 +611,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "table1":
+        run_table1(args)
     else:
         run_ours(args)
 

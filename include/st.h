@@ -378,6 +378,51 @@ int st_trace_noalloc(st_scene *scene, const st_camera *cam, const st_tiles *tile
                      uint8_t *flags, uint64_t *counters, void *stream);
 size_t st_trace_noalloc_scratch_bytes(void);
 
+/* ---- the non-synchronized variants of Table 1 ---------------------------------
+ * The paper measures its pipeline against per-pixel processing over a
+ * full-resolution A-buffer ("dexel" buffer) in which every field evaluation
+ * runs the sparse bottom-up traversal of Algorithm 1 on the ray's own active
+ * primitives, with parent pointers (Sec. 7.1, "ParentPtr/Full") or fast
+ * ancestor pointers (Sec. 7.2, "FastPtr/Full").  These calls provide them
+ * for comparison; st_build_tiles + st_trace is the method.
+ *
+ * st_build_dexels: one list per pixel of every primitive whose volume of
+ * interest the pixel's centre ray hits (FP32 tests of the tile culling), with
+ * entry and exit depths, sorted by (z_in, post-order address).  `tiles` must
+ * come from st_build_tiles for the same scene, camera and primitive
+ * parameters (their lists hold every primitive hit by a ray of the tile).
+ * *out: tile = 1, tiles_x = width, tiles_y = height, CSR over pixels
+ * (row-major), library-owned device buffers valid until the next call on the
+ * scene; max_overlap = longest pixel list.  Synchronises `stream` once (to
+ * size the buffers).
+ *
+ * st_trace_dexels: per-pixel sphere tracing (one thread per ray): the ray's
+ * own list is cut into subintervals by the rule st_trace applies per tile
+ * (Sec. 8: discard, fetch up to max_new_per_turn with no empty space and
+ * within the depth slab), a step never passes a subinterval's end, and each
+ * step evaluates f_A by Algorithm 1 with field values, with
+ * traversal ST_TRAVERSE_PARENT or ST_TRAVERSE_FAST.  Step ST_STEP_PLAIN only
+ * (eps, L, max_steps, Newton refinement and normals as st_trace).  Outputs as
+ * st_trace.  Counters: [0] tracing steps, [1] primitive evaluations, [2]
+ * operators reached by the traversals' climbs, [3] operators evaluated, [4]
+ * active-set changes, [7] error bits (1 malformed traversal, 2 stack).
+ * Library-owned scratch of max_overlap x 8 bytes per thread of a persistent
+ * grid.
+ *
+ * st_eval_sparse: f_A at points (device float[npts][3] -> f device
+ * float[npts]) by the same traversal over the active primitives `act`
+ * (device, ascending post-order addresses); equal bit for bit to
+ * st_eval_pruned over the pruned view of the same set.  status: device
+ * uint32, error bits OR-ed in (zero it first). */
+#define ST_TRAVERSE_PARENT 0
+#define ST_TRAVERSE_FAST 1
+int st_build_dexels(st_scene *scene, const st_camera *cam, const st_tiles *tiles, st_tiles *out, void *stream);
+int st_trace_dexels(st_scene *scene, const st_camera *cam, const st_tiles *dexels, const st_trace_opts *opts,
+                    int traversal, float *depth, float *normal, uint32_t *evals, uint8_t *flags,
+                    uint64_t *counters, void *stream);
+int st_eval_sparse(const st_scene *scene, const uint32_t *act, int n, const float *pts, int npts, int traversal,
+                   float *f, uint32_t *status, void *stream);
+
 /* ---- inspection of the hot-path steps ----------------------------------------
  * st_pruned_view: the pruned tree view of an active set, built on the device
  * by the same code st_trace uses: the warp-parallel form of Algorithm 1 (the

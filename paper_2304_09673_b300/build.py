@@ -10,7 +10,8 @@ PKG = Path(__file__).resolve().parent
 ROOT = PKG.parent
 CSRC = PKG / "csrc"
 LIB = PKG / "libst.so"
-SOURCES = ["st_api.cu", "st_cull.cu", "st_trace.cu", "st_prep.cpp", "st_noalloc.cu", "st_mlp.cu", "st_batch.cu"]
+SOURCES = ["st_api.cu", "st_cull.cu", "st_trace.cu", "st_prep.cpp", "st_noalloc.cu", "st_mlp.cu", "st_batch.cu",
+           "st_dexel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -73,9 +73,14 @@ struct st_scene {
   int n_nodes = 0, n_prims = 0;
   float voi_pad = 1e-5f;
   // scene arrays
-  DBuf<uint32_t> blob, rec_off, prim_addr, blk, lift;
+  DBuf<uint32_t> blob, rec_off, prim_addr, blk, lift, prim_index;
   DBuf<float4> rec;
   DBuf<float> d_prim;
+  // full-resolution A-buffer and per-pixel tracing (st_build_dexels / st_trace_dexels)
+  DBuf<uint32_t> dx_count, dx_offsets, dx_prim, dx_small;
+  DBuf<uint64_t> dx_keys;
+  DBuf<float> dx_ztmp, dx_zin, dx_zout;
+  DBuf<uint2> dx_act;
   // culling buffers
   DBuf<uint32_t> cand_count, cand_off, tile_count, offsets, scan_sums, small;  // small: counters
   DBuf<int4> rects;
@@ -110,6 +115,7 @@ static DevScene dev_scene(const st_scene *s) {
   d.d_prim = s->d_prim.p;
   d.blk = s->blk.p;
   d.lift = s->lift.p;
+  d.prim_index = s->prim_index.p;
   d.lift_levels = s->prep.lift_levels;
   d.n_nodes = s->n_nodes;
   d.n_prims = s->n_prims;
@@ -178,6 +184,7 @@ int st_scene_create(const st_scene_desc *desc, st_scene **out, void *stream) {
   if ((e = s->d_prim.ensure(p.d_prim.size())) != cudaSuccess) return fail(e);
   if ((e = s->blk.ensure(p.blk.size())) != cudaSuccess) return fail(e);
   if ((e = s->lift.ensure(p.lift.size())) != cudaSuccess) return fail(e);
+  if ((e = s->prim_index.ensure(p.prim_index.size())) != cudaSuccess) return fail(e);
   if ((e = s->small.ensure(16)) != cudaSuccess) return fail(e);
   if ((e = s->item_counter.ensure(4)) != cudaSuccess) return fail(e);
   if ((e = s->job.ensure(1)) != cudaSuccess) return fail(e);
@@ -188,6 +195,7 @@ int st_scene_create(const st_scene_desc *desc, st_scene **out, void *stream) {
   if ((e = cudaMemcpyAsync(s->d_prim.p, p.d_prim.data(), p.d_prim.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
   if ((e = cudaMemcpyAsync(s->blk.p, p.blk.data(), p.blk.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
   if ((e = cudaMemcpyAsync(s->lift.p, p.lift.data(), p.lift.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpyAsync(s->prim_index.p, p.prim_index.data(), p.prim_index.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
   *out = s;
   return ST_OK;
@@ -201,7 +209,9 @@ void st_scene_destroy(st_scene *s) {
   s->scan_sums.release(); s->small.release(); s->rects.release(); s->pairs.release(); s->keys.release();
   s->ztmp.release(); s->z_in.release(); s->z_out.release(); s->prim.release(); s->job.release();
   s->g_work.release(); s->item_counter.release(); s->order.release(); s->upd_words.release();
-  s->upd_index.release();
+  s->upd_index.release(); s->prim_index.release();
+  s->dx_count.release(); s->dx_offsets.release(); s->dx_prim.release(); s->dx_small.release();
+  s->dx_keys.release(); s->dx_ztmp.release(); s->dx_zin.release(); s->dx_zout.release(); s->dx_act.release();
   delete s;
 }
 
@@ -481,6 +491,126 @@ int st_eval_pruned(const st_scene *s, const uint32_t *view, const int32_t *info,
   if (!s || !view || !info || (npts > 0 && (!pts || !f)) || npts < 0) { set_error("invalid arguments"); return ST_ERR_INVALID; }
   launch_eval_view(dev_scene(s), view, info, pts, npts, f, grad, (cudaStream_t)stream);
   ST_CK(cudaGetLastError());
+  return ST_OK;
+}
+
+int st_build_dexels(st_scene *s, const st_camera *cam, const st_tiles *tl, st_tiles *out, void *stream) {
+  if (!s || !tl || !out) { set_error("null argument"); return ST_ERR_INVALID; }
+  int rc = check_camera(cam);
+  if (rc != ST_OK) return rc;
+  if (tl->tile != 8 && tl->tile != 16 && tl->tile != 32) { set_error("tile lists must have tile 8, 16 or 32"); return ST_ERR_INVALID; }
+  const int tiles_x = (cam->width + tl->tile - 1) / tl->tile, tiles_y = (cam->height + tl->tile - 1) / tl->tile;
+  if (tl->tiles_x != tiles_x || tl->tiles_y != tiles_y) {
+    set_error("tile buffer does not match the camera");
+    return ST_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t n_pix = (uint32_t)cam->width * (uint32_t)cam->height;
+  static thread_local bool attr_done = false;
+  if (!attr_done) { ST_CK(cull_set_attributes()); attr_done = true; }
+  Job job;
+  std::memset(&job, 0, sizeof(job));
+  job.sc = dev_scene(s);
+  camera_basis(*cam, job.cam);
+  job.tl.tile = tl->tile;
+  job.tl.tiles_x = tl->tiles_x;
+  job.tl.tiles_y = tl->tiles_y;
+  job.tl.offsets = tl->offsets;
+  job.tl.z_in = tl->z_in;
+  job.tl.z_out = tl->z_out;
+  job.tl.prim = tl->prim;
+  ST_CK(s->dx_count.ensure(n_pix));
+  ST_CK(s->dx_offsets.ensure((size_t)n_pix + 1));
+  ST_CK(s->dx_small.ensure(4));
+  ST_CK(s->scan_sums.ensure(scan_block_count(n_pix) + 2));
+  ST_CK(cudaMemsetAsync(s->dx_small.p, 0, 4 * sizeof(uint32_t), st));
+  launch_dexel_pass(job, false, s->dx_count.p, nullptr, nullptr, nullptr, st);
+  scan_u32(s->dx_count.p, s->dx_offsets.p, n_pix, s->scan_sums.p, s->dx_small.p, s->dx_small.p + 1,
+           s->dx_offsets.p + n_pix, st);
+  ST_CK(cudaGetLastError());
+  uint32_t host_small[2] = {0, 0};
+  ST_CK(cudaMemcpyAsync(host_small, s->dx_small.p, sizeof(host_small), cudaMemcpyDeviceToHost, st));
+  ST_CK(cudaStreamSynchronize(st));
+  const uint32_t n_entries = host_small[0], max_len = host_small[1];
+  ST_CK(s->dx_keys.ensure((size_t)n_entries + 1));
+  ST_CK(s->dx_ztmp.ensure((size_t)n_entries + 1));
+  ST_CK(s->dx_zin.ensure((size_t)n_entries + 1));
+  ST_CK(s->dx_zout.ensure((size_t)n_entries + 1));
+  ST_CK(s->dx_prim.ensure((size_t)n_entries + 1));
+  launch_dexel_pass(job, true, nullptr, s->dx_offsets.p, s->dx_keys.p, s->dx_ztmp.p, st);
+  launch_segment_sort(s->dx_offsets.p, n_pix, max_len, s->dx_keys.p, s->dx_ztmp.p, s->dx_zin.p, s->dx_zout.p,
+                      s->dx_prim.p, s->n_sm, st);
+  ST_CK(cudaGetLastError());
+  out->tile = 1;
+  out->tiles_x = cam->width;
+  out->tiles_y = cam->height;
+  out->offsets = s->dx_offsets.p;
+  out->z_in = s->dx_zin.p;
+  out->z_out = s->dx_zout.p;
+  out->prim = s->dx_prim.p;
+  out->n_entries = n_entries;
+  out->max_overlap = max_len;
+  return ST_OK;
+}
+
+int st_trace_dexels(st_scene *s, const st_camera *cam, const st_tiles *dx, const st_trace_opts *opts, int traversal,
+                    float *depth, float *normal, uint32_t *evals, uint8_t *flags, uint64_t *counters, void *stream) {
+  if (!s || !dx || !depth || !normal || !evals || !flags) { set_error("null argument"); return ST_ERR_INVALID; }
+  int rc = check_camera(cam);
+  if (rc != ST_OK) return rc;
+  if (dx->tile != 1 || dx->tiles_x != cam->width || dx->tiles_y != cam->height) {
+    set_error("st_trace_dexels: the dexel buffer (tile 1) does not match the camera");
+    return ST_ERR_INVALID;
+  }
+  if (traversal != ST_TRAVERSE_PARENT && traversal != ST_TRAVERSE_FAST) {
+    set_error("st_trace_dexels: unknown traversal");
+    return ST_ERR_INVALID;
+  }
+  st_trace_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.step_mode != ST_STEP_PLAIN) {
+    set_error("st_trace_dexels: only ST_STEP_PLAIN");
+    return ST_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Job job;
+  std::memset(&job, 0, sizeof(job));
+  job.sc = dev_scene(s);
+  camera_basis(*cam, job.cam);
+  job.out.depth = depth;
+  job.out.normal = normal;
+  job.out.evals = evals;
+  job.out.flags = flags;
+  job.tp = make_trace_params(o, s->prep.diameter, s->prep.extent);
+  int grid = 0;
+  ST_CK(dexel_trace_grid(traversal == ST_TRAVERSE_FAST, s->n_sm, &grid));
+  DexelLaunch D;
+  std::memset(&D, 0, sizeof(D));
+  D.offsets = dx->offsets;
+  D.z_in = dx->z_in;
+  D.z_out = dx->z_out;
+  D.prim = dx->prim;
+  D.n_threads = (uint32_t)grid * 128u;
+  ST_CK(s->dx_act.ensure((size_t)std::max<uint32_t>(dx->max_overlap, 1u) * D.n_threads));
+  D.act = s->dx_act.p;
+  ST_CK(s->item_counter.ensure(4));
+  D.pixel_counter = s->item_counter.p;
+  D.counters = counters;
+  ST_CK(cudaMemsetAsync(D.pixel_counter, 0, 4, st));
+  ST_CK(launch_trace_dexel(job, D, traversal == ST_TRAVERSE_FAST, grid, st));
+  return ST_OK;
+}
+
+int st_eval_sparse(const st_scene *s, const uint32_t *act, int n, const float *pts, int npts, int traversal, float *f,
+                   uint32_t *status, void *stream) {
+  if (!s || !act || n < 1 || n > s->n_prims || npts < 0 || (npts > 0 && (!pts || !f)) || !status) {
+    set_error("invalid arguments");
+    return ST_ERR_INVALID;
+  }
+  if (traversal != ST_TRAVERSE_PARENT && traversal != ST_TRAVERSE_FAST) { set_error("unknown traversal"); return ST_ERR_INVALID; }
+  ST_CK(launch_eval_sparse(dev_scene(s), act, n, pts, npts, traversal == ST_TRAVERSE_FAST, f, status,
+                           (cudaStream_t)stream));
   return ST_OK;
 }
 

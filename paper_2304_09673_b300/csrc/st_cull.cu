@@ -69,41 +69,6 @@ __device__ void sphere_tile_rect(const DevCamera &cam, int tile, int tiles_x, in
   rect = make_int4(px0 / tile, py0 / tile, px1 / tile, py1 / tile);
 }
 
-// Volume of interest extents in FP32: ((size + d) + pad).
-struct Voi {
-  int kind;
-  float c[3];      // centre (sphere, box) or end a (capsule)
-  float M[9];      // box rotation rows
-  float e[3];      // box half extents
-  float b[3];      // capsule end b
-  float r;         // sphere / capsule radius
-};
-
-__device__ __forceinline__ void load_voi(const DevScene &sc, uint32_t j, Voi &v) {
-  uint32_t a = sc.prim_addr[j];
-  uint32_t kind = blob_kind(sc.blob[a]);
-  const float4 *w = sc.rec + sc.rec_off[a];
-  float dp = sc.d_prim[j], pad = sc.voi_pad;
-  v.kind = (int)kind;
-  float4 w0 = w[0];
-  v.c[0] = w0.x; v.c[1] = w0.y; v.c[2] = w0.z;
-  if (kind == ST_PRIM_SPHERE) {
-    v.r = ieee_add(ieee_add(w0.w, dp), pad);
-  } else if (kind == ST_PRIM_RBOX) {
-    float rr = w0.w;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      float4 m = w[1 + i];
-      v.M[3 * i] = m.x; v.M[3 * i + 1] = m.y; v.M[3 * i + 2] = m.z;
-      v.e[i] = ieee_add(ieee_add(ieee_add(m.w, rr), dp), pad);
-    }
-  } else {
-    float4 w1 = w[1];
-    v.b[0] = w1.x; v.b[1] = w1.y; v.b[2] = w1.z;
-    v.r = ieee_add(ieee_add(w0.w, dp), pad);
-  }
-}
-
 }  // namespace
 
 __global__ void k_prim_bounds(const Job *jobs, int n_jobs, uint32_t n_prims_total,
@@ -174,47 +139,15 @@ k_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_p
       const DevCamera &cam = job.cam;
       Voi v;
       load_voi(job.sc, j, v);
-      // Ray-independent quantities.
-      float w[3], lo3[3];
-      CapsuleConst cc;
-      if (v.kind == ST_PRIM_SPHERE) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) w[i] = ieee_sub(v.c[i], cam.o[i]);
-      } else if (v.kind == ST_PRIM_RBOX) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) w[i] = ieee_sub(cam.o[i], v.c[i]);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) lo3[i] = ieee_dot3(v.M[3 * i], v.M[3 * i + 1], v.M[3 * i + 2], w[0], w[1], w[2]);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          cc.wa[i] = ieee_sub(v.c[i], cam.o[i]);
-          cc.wb[i] = ieee_sub(v.b[i], cam.o[i]);
-          cc.ba[i] = ieee_sub(v.b[i], v.c[i]);
-          w[i] = ieee_sub(cam.o[i], v.c[i]);
-        }
-        cc.bb = ieee_dot3(cc.ba[0], cc.ba[1], cc.ba[2], cc.ba[0], cc.ba[1], cc.ba[2]);
-        cc.r = v.r;
-        if (cc.bb > 0.0f) {
-          cc.wbv = ieee_dot3(w[0], w[1], w[2], cc.ba[0], cc.ba[1], cc.ba[2]);
-          float fw = ieee_div(cc.wbv, cc.bb);
-#pragma unroll
-          for (int i = 0; i < 3; ++i) cc.p[i] = ieee_sub(w[i], ieee_mul(fw, cc.ba[i]));
-        }
-      }
+      VoiRay vq;
+      voi_ray_setup(v, cam, vq);
       uint32_t zin_bits = 0xFFFFFFFFu, zout_bits = 0u;
       for (int s = lane; s < T * T; s += 32) {
         const int px = tx * T + (s % T), py = ty * T + (s / T);
         if (px >= cam.W || py >= cam.H) continue;
         float d[3], t0, t1;
         pixel_ray(cam, px, py, d);
-        bool h;
-        if (v.kind == ST_PRIM_SPHERE) h = ray_sphere32(w, d, v.r, t0, t1);
-        else if (v.kind == ST_PRIM_RBOX) h = ray_obox32(lo3, v.M, v.e, d, t0, t1);
-        else h = ray_capsule32(cc, d, t0, t1);
-        if (!h) continue;
-        t0 = t0 > 0.0f ? t0 : 0.0f;
-        if (!(t1 >= t0)) continue;
+        if (!voi_ray_hit(v, vq, d, t0, t1)) continue;
         // t0, t1 >= 0: float order equals unsigned bit order.
         uint32_t b0 = __float_as_uint(t0), b1 = __float_as_uint(t1);
         zin_bits = b0 < zin_bits ? b0 : zin_bits;
@@ -448,31 +381,46 @@ void launch_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, ui
                                                     tile_count, pairs, pair_cap, pair_counter);
 }
 
+void launch_copy_short(const uint32_t *offsets, uint32_t n_segs, const uint64_t *keys, const float *z_out_tmp,
+                       float *z_in, float *z_out, uint32_t *prim, cudaStream_t s, const uint32_t *abort) {
+  if (!n_segs) return;
+  count_launch(), k_tile_copy_short<<<(n_segs + 255) / 256, 256, 0, s>>>(offsets, n_segs, keys, z_out_tmp, z_in,
+                                                                         z_out, prim, abort);
+}
+
+void launch_tile_sort_range(const uint32_t *offsets, uint32_t n_segs, uint32_t max_len, uint32_t min_len,
+                            const uint64_t *keys, const float *z_out_tmp, float *z_in, float *z_out,
+                            uint32_t *prim, int n_sm, cudaStream_t s, const uint32_t *abort) {
+  // Short lists: up to kSortSmall entries (48 KB of shared memory), a CTA
+  // per list; longer ones up to kSortLarge, fewer and larger CTAs.
+  const uint32_t small = kSortSmall;
+  if (max_len > min_len && min_len < small) {
+    uint32_t cap = max_len < small ? max_len : small;
+    uint32_t n2 = 1;
+    while (n2 < cap) n2 <<= 1;
+    size_t sm = (size_t)n2 * 12;
+    count_launch(), k_tile_sort<<<n_segs < 65535u ? n_segs : 65535u, 256, sm, s>>>(offsets, n_segs, keys, z_out_tmp,
+                                                                               z_in, z_out, prim, min_len, small,
+                                                                               abort);
+  }
+  if (max_len > small) {
+    uint32_t n2 = 1;
+    while (n2 < max_len) n2 <<= 1;
+    size_t sm = (size_t)n2 * 12;
+    count_launch(), k_tile_sort<<<n_sm, 1024, sm, s>>>(offsets, n_segs, keys, z_out_tmp, z_in, z_out, prim,
+                                                       min_len > small ? min_len : small, kSortLarge, abort);
+  }
+}
+
 void launch_scatter_sort(const Pair *pairs, const uint32_t *pair_counter, uint32_t pair_cap,
                          const uint32_t *offsets, uint32_t n_tiles, uint32_t max_overlap,
                          uint64_t *keys, float *z_out_tmp, float *z_in, float *z_out, uint32_t *prim,
                          int n_sm, cudaStream_t s, const uint32_t *abort) {
   count_launch(), k_scatter<<<n_sm * 8, 256, 0, s>>>(pairs, pair_counter, pair_cap, offsets, keys, z_out_tmp, abort);
   if (!n_tiles) return;
-  count_launch(), k_tile_copy_short<<<(n_tiles + 255) / 256, 256, 0, s>>>(offsets, n_tiles, keys, z_out_tmp, z_in,
-                                                                          z_out, prim, abort);
-  // Short lists: up to kSortSmall entries (48 KB of shared memory).
-  const uint32_t small = kSortSmall;
-  if (max_overlap > 1) {
-    uint32_t cap = max_overlap < small ? max_overlap : small;
-    uint32_t n2 = 1;
-    while (n2 < cap) n2 <<= 1;
-    size_t sm = (size_t)n2 * 12;
-    count_launch(), k_tile_sort<<<n_tiles < 65535u ? n_tiles : 65535u, 256, sm, s>>>(offsets, n_tiles, keys, z_out_tmp, z_in,
-                                                                     z_out, prim, 1, small, abort);
-  }
-  if (max_overlap > small) {
-    uint32_t n2 = 1;
-    while (n2 < max_overlap) n2 <<= 1;
-    size_t sm = (size_t)n2 * 12;
-    count_launch(), k_tile_sort<<<n_sm, 1024, sm, s>>>(offsets, n_tiles, keys, z_out_tmp, z_in, z_out, prim, small,
-                                       kSortLarge, abort);
-  }
+  launch_copy_short(offsets, n_tiles, keys, z_out_tmp, z_in, z_out, prim, s, abort);
+  if (max_overlap > 1)
+    launch_tile_sort_range(offsets, n_tiles, max_overlap, 1, keys, z_out_tmp, z_in, z_out, prim, n_sm, s, abort);
 }
 
 void launch_check_capacity(const uint32_t *pair_counter, uint32_t pair_cap, const uint32_t *max_overlap,

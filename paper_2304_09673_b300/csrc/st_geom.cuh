@@ -136,4 +136,88 @@ __device__ __forceinline__ bool ray_capsule32(const CapsuleConst &k, const float
   return true;
 }
 
+// Volume of interest of primitive j (Sec. 6.1: the primitive's bound offset by
+// its range-of-interest bound d_prim), extents in FP32: ((size + d) + pad).
+struct Voi {
+  int kind;
+  float c[3];      // centre (sphere, box) or end a (capsule)
+  float M[9];      // box rotation rows
+  float e[3];      // box half extents
+  float b[3];      // capsule end b
+  float r;         // sphere / capsule radius
+};
+
+__device__ __forceinline__ void load_voi(const DevScene &sc, uint32_t j, Voi &v) {
+  uint32_t a = sc.prim_addr[j];
+  uint32_t kind = blob_kind(sc.blob[a]);
+  const float4 *w = sc.rec + sc.rec_off[a];
+  float dp = sc.d_prim[j], pad = sc.voi_pad;
+  v.kind = (int)kind;
+  float4 w0 = w[0];
+  v.c[0] = w0.x; v.c[1] = w0.y; v.c[2] = w0.z;
+  if (kind == ST_PRIM_SPHERE) {
+    v.r = ieee_add(ieee_add(w0.w, dp), pad);
+  } else if (kind == ST_PRIM_RBOX) {
+    float rr = w0.w;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float4 m = w[1 + i];
+      v.M[3 * i] = m.x; v.M[3 * i + 1] = m.y; v.M[3 * i + 2] = m.z;
+      v.e[i] = ieee_add(ieee_add(ieee_add(m.w, rr), dp), pad);
+    }
+  } else {
+    float4 w1 = w[1];
+    v.b[0] = w1.x; v.b[1] = w1.y; v.b[2] = w1.z;
+    v.r = ieee_add(ieee_add(w0.w, dp), pad);
+  }
+}
+
+// Ray-independent quantities of a volume of interest seen from the eye.
+struct VoiRay {
+  float w[3], lo3[3];
+  CapsuleConst cc;
+};
+
+__device__ __forceinline__ void voi_ray_setup(const Voi &v, const DevCamera &cam, VoiRay &q) {
+  if (v.kind == ST_PRIM_SPHERE) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q.w[i] = ieee_sub(v.c[i], cam.o[i]);
+  } else if (v.kind == ST_PRIM_RBOX) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q.w[i] = ieee_sub(cam.o[i], v.c[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q.lo3[i] = ieee_dot3(v.M[3 * i], v.M[3 * i + 1], v.M[3 * i + 2], q.w[0], q.w[1], q.w[2]);
+  } else {
+    CapsuleConst &cc = q.cc;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      cc.wa[i] = ieee_sub(v.c[i], cam.o[i]);
+      cc.wb[i] = ieee_sub(v.b[i], cam.o[i]);
+      cc.ba[i] = ieee_sub(v.b[i], v.c[i]);
+      q.w[i] = ieee_sub(cam.o[i], v.c[i]);
+    }
+    cc.bb = ieee_dot3(cc.ba[0], cc.ba[1], cc.ba[2], cc.ba[0], cc.ba[1], cc.ba[2]);
+    cc.r = v.r;
+    if (cc.bb > 0.0f) {
+      cc.wbv = ieee_dot3(q.w[0], q.w[1], q.w[2], cc.ba[0], cc.ba[1], cc.ba[2]);
+      float fw = ieee_div(cc.wbv, cc.bb);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) cc.p[i] = ieee_sub(q.w[i], ieee_mul(fw, cc.ba[i]));
+    }
+  }
+}
+
+// Entry and exit of the ray o + t d in the volume of interest, the entry
+// clamped to t >= 0 (the eye may be inside); false when the ray misses it.
+__device__ __forceinline__ bool voi_ray_hit(const Voi &v, const VoiRay &q, const float d[3], float &t0,
+                                            float &t1) {
+  bool h;
+  if (v.kind == ST_PRIM_SPHERE) h = ray_sphere32(q.w, d, v.r, t0, t1);
+  else if (v.kind == ST_PRIM_RBOX) h = ray_obox32(q.lo3, v.M, v.e, d, t0, t1);
+  else h = ray_capsule32(q.cc, d, t0, t1);
+  if (!h) return false;
+  t0 = t0 > 0.0f ? t0 : 0.0f;
+  return t1 >= t0;
+}
+
 }  // namespace st

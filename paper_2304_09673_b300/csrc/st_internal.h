@@ -70,6 +70,8 @@ struct DevScene {
                              // lone operand from this node's side (kNoAnc: none)
   const uint32_t *lift;      // [lift_levels][n_nodes] ancestor 2^k levels up
                              // (level 0 = parent; 0xFFFFFFFF above the root)
+  const uint32_t *prim_index;// [n_nodes] primitive index j of a primitive node
+                             // (0xFFFFFFFF for operators)
   int32_t n_nodes, n_prims, stack_depth, lift_levels;
   float diameter, voi_pad;
 };
@@ -119,6 +121,7 @@ struct Prep {
   std::vector<uint32_t> blk;    // nearest blocking ancestor (see DevScene::blk)
   std::vector<uint32_t> lift;   // binary-lifting ancestor table (see DevScene::lift)
   int lift_levels = 1;
+  std::vector<uint32_t> prim_index;   // see DevScene::prim_index
   std::vector<float> roi, d_prim, rec;  // rec: 4 floats per word
   std::vector<int32_t> prim_desc;       // description index of primitive j
   int stack_depth = 0;

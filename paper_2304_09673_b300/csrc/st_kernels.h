@@ -31,6 +31,36 @@ void launch_scatter_sort(const Pair *pairs, const uint32_t *pair_counter, uint32
 void launch_check_capacity(const uint32_t *pair_counter, uint32_t pair_cap, const uint32_t *max_overlap,
                            uint32_t overlap_cap, uint32_t *status, cudaStream_t s);
 cudaError_t cull_set_attributes();
+// Sort of CSR segments by (z_in, address) keys: copy of 1-entry segments, and
+// shared-memory sorts of segments with min_len < length <= max_len.
+void launch_copy_short(const uint32_t *offsets, uint32_t n_segs, const uint64_t *keys, const float *z_out_tmp,
+                       float *z_in, float *z_out, uint32_t *prim, cudaStream_t s, const uint32_t *abort = nullptr);
+void launch_tile_sort_range(const uint32_t *offsets, uint32_t n_segs, uint32_t max_len, uint32_t min_len,
+                            const uint64_t *keys, const float *z_out_tmp, float *z_in, float *z_out,
+                            uint32_t *prim, int n_sm, cudaStream_t s, const uint32_t *abort = nullptr);
+
+// ---- non-synchronized per-pixel variants (st_dexel.cu) ----
+struct DexelLaunch {
+  const uint32_t *offsets;   // [W * H + 1] per-pixel CSR of the dexel buffer
+  const float *z_in, *z_out;
+  const uint32_t *prim;
+  uint2 *act;                // per-thread active sets: entry i of thread t at
+                             // act[i * n_threads + t] (address, z_out bits)
+  uint32_t n_threads;        // grid threads (stride of act)
+  uint32_t *pixel_counter;   // zeroed before the launch
+  uint64_t *counters;        // optional ST_NUM_COUNTERS
+};
+// Count (fill = false) or write (fill = true) the per-pixel fragments of the
+// tile lists in job.tl; pix_off: exclusive scan of the counts.
+void launch_dexel_pass(const Job &job, bool fill, uint32_t *count, const uint32_t *pix_off, uint64_t *keys,
+                       float *zo_tmp, cudaStream_t s);
+void launch_segment_sort(const uint32_t *offsets, uint32_t n_segs, uint32_t max_len, const uint64_t *keys,
+                         const float *z_out_tmp, float *z_in, float *z_out, uint32_t *prim, int n_sm,
+                         cudaStream_t s);
+cudaError_t launch_eval_sparse(const DevScene &sc, const uint32_t *act, int n, const float *pts, int npts,
+                               int fast, float *f, uint32_t *status, cudaStream_t s);
+cudaError_t dexel_trace_grid(int fast, int n_sm, int *grid);
+cudaError_t launch_trace_dexel(const Job &job, const DexelLaunch &D, int fast, int grid, cudaStream_t s);
 
 // Status word bits of batched launches (device, OR-accumulated).
 constexpr uint32_t ST_STATUS_VIEW = 1u;       // a pruned view exceeded its capacity

@@ -223,6 +223,7 @@ int prepare(const st_scene_desc &d, Prep &p, std::string &err) {
   p.prim_addr.clear();
   p.d_prim.clear();
   p.prim_desc.clear();
+  p.prim_index.assign(n, 0xFFFFFFFFu);
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
   for (int a = 0; a < n; ++a) {
     int i = p.desc_of_po[a];
@@ -233,6 +234,7 @@ int prepare(const st_scene_desc &d, Prep &p, std::string &err) {
       float w[16];
       prim_words(k, q, w);
       p.rec.insert(p.rec.end(), w, w + 4 * rec_words(k));
+      p.prim_index[a] = (uint32_t)p.prim_addr.size();
       p.prim_addr.push_back((uint32_t)a);
       p.d_prim.push_back(p.roi[a]);
       p.prim_desc.push_back(i);

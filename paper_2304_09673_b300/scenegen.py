@@ -188,6 +188,34 @@ def make_scene(n_prims: int, max_depth: int | None, seed: int, *, clusters: int 
                  meta=dict(n_prims=n_prims, max_depth=max_depth, seed=seed, clusters=clusters))
 
 
+def make_comb(n_prims: int, seed: int, op_mix=(0.6, 0.2, 0.2)) -> Scene:
+    """A left comb (left-heavy tree, depth n - 1) over the primitives of a
+    seeded random scene: every operator has the previous comb as left operand
+    and the next primitive as right operand; compact smooth operators drawn
+    with probabilities ``op_mix`` (k ~ U[0.02, 0.1], d_o = 1.5 k)."""
+    base = make_scene(n_prims, None, seed)
+    prims = np.flatnonzero(base.kind < 16)[:n_prims]
+    kinds = list(base.kind[prims])
+    params = [base.params[i] for i in prims]
+    rng = np.random.default_rng(seed)
+    p = np.asarray(op_mix, dtype=np.float64)
+    p = p / p.sum()
+    left, right = [-1] * n_prims, [-1] * n_prims
+    cur = 0
+    for j in range(1, n_prims):
+        op = (OP_UNION, OP_INTER, OP_DIFF)[int(rng.choice(3, p=p))]
+        k = rng.uniform(0.02, 0.1)
+        q = np.zeros(16, np.float32)
+        q[0], q[1] = k, 1.5 * k
+        kinds.append(op)
+        params.append(q)
+        left.append(cur)
+        right.append(j)
+        cur = len(kinds) - 1
+    return Scene(kind=np.array(kinds, np.int32), left=np.array(left, np.int32), right=np.array(right, np.int32),
+                 params=np.array(params, np.float32), root=cur)
+
+
 def single_primitive(kind: int, rec) -> Scene:
     """A one-node scene (for analytic hit tests)."""
     params = np.zeros((1, 16), dtype=np.float32)

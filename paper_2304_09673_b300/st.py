@@ -20,6 +20,7 @@ _lib = C.CDLL(str(LIB_PATH))
 
 ST_OK, ST_ERR_INVALID, ST_ERR_CAPACITY, ST_ERR_CUDA, ST_ERR_TIMEOUT, ST_ERR_NOMEM = 0, -1, -2, -3, -4, -5
 ST_STEP_PLAIN, ST_STEP_LEARNED, ST_STEP_OVERRELAX, ST_STEP_CROSSING = 0, 1, 2, 3
+ST_TRAVERSE_PARENT, ST_TRAVERSE_FAST = 0, 1
 ST_NUM_COUNTERS = 8
 ST_REC_FLOATS = 16
 
@@ -100,6 +101,10 @@ _lib.st_batch_graph_kernels.argtypes = [_P]
 _lib.st_batch_destroy.argtypes = [_P]
 _lib.st_batch_destroy.restype = None
 _lib.st_render_batch.argtypes = [_P, _P, C.c_int, C.POINTER(st_trace_opts), _P, _P, _P, _P, C.c_char_p, _P]
+_lib.st_build_dexels.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINTER(st_tiles), _P]
+_lib.st_trace_dexels.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINTER(st_trace_opts), C.c_int,
+                                 _P, _P, _P, _P, _P, _P]
+_lib.st_eval_sparse.argtypes = [_P, _P, C.c_int, _P, C.c_int, C.c_int, _P, _P, _P]
 
 EXPORTED = ("st_scene_create", "st_scene_update_prims", "st_scene_addresses", "st_scene_destroy",
             "st_build_tiles", "st_trace", "st_tiles_copy", "st_pruned_view", "st_pruned_view_alg1", "st_eval_pruned", "st_prep_tree", "st_last_error",
@@ -107,7 +112,7 @@ EXPORTED = ("st_scene_create", "st_scene_update_prims", "st_scene_addresses", "s
             "st_trace_record", "st_mlp_pack_size", "st_mlp_param_count", "st_mlp_pack", "st_mlp_grad",
             "st_mlp_adam", "st_mlp_infer", "st_tune_key", "st_tune_load", "st_tune_store", "st_autotune",
             "st_batch_create", "st_batch_render", "st_batch_tiles", "st_batch_graph_kernels", "st_batch_destroy",
-            "st_render_batch")
+            "st_render_batch", "st_build_dexels", "st_trace_dexels", "st_eval_sparse")
 
 
 def lib():
@@ -280,6 +285,28 @@ def st_pruned_view_alg1(h, act, view, view_addr, info, stream=None) -> None:
 def st_eval_pruned(h, view, info, pts, f, grad=None, stream=None) -> None:
     _check(_lib.st_eval_pruned(h, _ptr(view), _ptr(info), _ptr(pts), int(pts.numel() // 3), _ptr(f), _ptr(grad),
                                _stream(stream)), "st_eval_pruned")
+
+
+def st_build_dexels(h, cam, tiles: st_tiles, stream=None) -> st_tiles:
+    """Full-resolution A-buffer (one list per pixel) from tile lists of the same camera."""
+    out = st_tiles()
+    c = make_camera(cam)
+    _check(_lib.st_build_dexels(h, C.byref(c), C.byref(tiles), C.byref(out), _stream(stream)), "st_build_dexels")
+    return out
+
+
+def st_trace_dexels(h, cam, dexels: st_tiles, opts: st_trace_opts | None, traversal: int, depth, normal, evals,
+                    flags, counters=None, stream=None) -> None:
+    c = make_camera(cam)
+    o = opts if opts is not None else make_opts()
+    _check(_lib.st_trace_dexels(h, C.byref(c), C.byref(dexels), C.byref(o), int(traversal), _ptr(depth),
+                                _ptr(normal), _ptr(evals), _ptr(flags), _ptr(counters), _stream(stream)),
+           "st_trace_dexels")
+
+
+def st_eval_sparse(h, act, pts, traversal: int, f, status, stream=None) -> None:
+    _check(_lib.st_eval_sparse(h, _ptr(act), int(act.numel()), _ptr(pts), int(pts.numel() // 3), int(traversal),
+                               _ptr(f), _ptr(status), _stream(stream)), "st_eval_sparse")
 
 
 def st_tiles_copy(tiles: st_tiles, stream=None):

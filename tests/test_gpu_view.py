@@ -125,25 +125,7 @@ def test_gradient_matches_central_differences(stlib, orc, cuda):
 def _comb(n, seed):
     """A left comb of n primitives (tree depth n - 1) with mixed operators:
     long ancestor chains for the binary-lifting search."""
-    base = sg.make_scene(n, None, seed)
-    prims = np.flatnonzero(base.kind < 16)[:n]
-    kinds = list(base.kind[prims])
-    params = [base.params[i] for i in prims]
-    rng = np.random.default_rng(seed)
-    left, right = [-1] * n, [-1] * n
-    cur = 0
-    for j in range(1, n):
-        op = [sg.OP_UNION, sg.OP_INTER, sg.OP_DIFF][int(rng.choice(3, p=[0.6, 0.2, 0.2]))]
-        k = rng.uniform(0.02, 0.1)
-        q = np.zeros(16, np.float32)
-        q[0], q[1] = k, 1.5 * k
-        kinds.append(op)
-        params.append(q)
-        left.append(cur)
-        right.append(j)
-        cur = len(kinds) - 1
-    return sg.Scene(kind=np.array(kinds, np.int32), left=np.array(left, np.int32), right=np.array(right, np.int32),
-                    params=np.array(params, np.float32), root=cur)
+    return sg.make_comb(n, seed)
 
 
 @pytest.mark.parametrize("shape", ["comb", "clustered"])
