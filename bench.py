@@ -12,7 +12,7 @@ per-pixel comparison variants (Table 1).
 Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 1080p|small|clustered|clustered1080p|batch64|table1] [--modes learned,plain,overrelax,crossing]
+                  [--workload 1080p|small|clustered|clustered1080p|batch64|table1|blend] [--modes learned,plain,overrelax,crossing]
 
 Multi-GPU: one independent replica per rank (the path has no exchange step);
 value = all ranks' rays / max-over-ranks time ("scaling": "weak").
@@ -590,6 +590,69 @@ def run_table1(args):
     print(json.dumps(line), flush=True)
 
 
+def run_blend(args):
+    """Blend localisation (the paper's blend experiment on 8..16 spheres):
+    frame time (st_build_tiles + st_trace, plain step) at 1920x1080 as
+    spheres are added, for a sharp union, the compact smooth union with two
+    blend ranges and the same smooth union without compact support
+    ("classical": unbounded range of interest, every sphere active
+    everywhere)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2304_09673_b300 import build as b
+    b.build()
+    from paper_2304_09673_b300 import scenegen as sg
+    from paper_2304_09673_b300 import st
+    cam = sg.default_camera(1920, 1080)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    opts = st.make_opts()
+    settings = [("sharp union", "sharp", 0.0), ("compact blend k=0.06", "compact", 0.06),
+                ("compact blend k=0.12", "compact", 0.12), ("classical blend k=0.06", "classical", 0.06)]
+    ns = (8, 10, 12, 14, 16)
+    sampler = ClockSampler(None)
+    launches0 = st.st_kernel_launches()
+    curves = {}
+    for label, blend, k in settings:
+        pts = []
+        for n in ns:
+            r = st.Renderer(sg.blend_spheres(n, blend, k), cam, tile=16, stream=stream)
+            for _ in range(args.warmup):
+                r.render(opts)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                flush.zero_()
+                r.counters.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r.build_tiles()
+                st.st_trace(r.h, cam, r.tiles, opts, r.depth, r.normal, r.evals, r.flags, r.counters, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            c = r.counters.cpu().numpy().astype(np.float64)
+            pts.append({"spheres": n, "ms_per_frame": statistics.mean(ms),
+                        "prim_evals_per_ray": c[1] / (cam.width * cam.height),
+                        "mean_tile_list": float(r.tiles.n_entries) / (r.tiles.tiles_x * r.tiles.tiles_y),
+                        "device_error_flags": int(c[7])})
+            r.close()
+        slope = float(np.polyfit(ns, [q["ms_per_frame"] for q in pts], 1)[0])
+        curves[label] = {"points": pts, "ms_per_added_sphere": slope}
+    clocks = sampler.stop()
+    c16 = {lab: v["points"][-1]["ms_per_frame"] for lab, v in curves.items()}
+    line = {"metric": "frame time with 16 spheres, classical smooth blend over compact blend (blend localisation)",
+            "value": c16["classical blend k=0.06"] / c16["compact blend k=0.06"], "unit": "x", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": c16["compact blend k=0.06"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "8..16 spheres (radius 0.12, 4x4 grid, spacing 0.2) under a balanced union tree, "
+                                   "1920x1080, tile 16, plain step, eps 1e-4",
+                       "l2": "flushed between timed steps (256 MB write outside the timed events)"},
+            "curves": curves, "gpu_launches": st.st_kernel_launches() - launches0, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -613,6 +676,8 @@ def main():
         run_batch(args)
     elif args.workload == "table1":
         run_table1(args)
+    elif args.workload == "blend":
+        run_blend(args)
     else:
         run_ours(args)
 

@@ -216,6 +216,50 @@ def make_comb(n_prims: int, seed: int, op_mix=(0.6, 0.2, 0.2)) -> Scene:
                  params=np.array(params, np.float32), root=cur)
 
 
+# Range of interest standing for "unbounded" (a blend without compact
+# support): every volume of interest covers the scene, and the blend range
+# b_r differs from k by ~1e-5 relative at the scene's field values.
+UNBOUNDED_RANGE = 1.0e4
+
+
+def blend_spheres(n: int, blend: str, k: float = 0.06) -> Scene:
+    """The blend-localisation scenes: n spheres (radius 0.12) filled row by row
+    into a 4 x 4 grid (spacing 0.2) in the image plane of the default camera,
+    combined by a balanced tree of unions: ``blend`` = "sharp" (Eq. 1),
+    "compact" (compact smooth union, d_o = 1.5 k) or "classical" (the same
+    smooth union with an unbounded range of interest)."""
+    if not 1 <= n <= 16:
+        raise ValueError("1..16 spheres")
+    cam = default_camera(64, 64)
+    eye = np.asarray(cam.eye, np.float64)
+    fwd = -eye / np.linalg.norm(eye)
+    right = np.cross(fwd, [0.0, 1.0, 0.0])
+    right /= np.linalg.norm(right)
+    up = np.cross(right, fwd)
+    rng = np.random.default_rng(n)
+    spheres = []
+    for i in range(n):
+        r, c = divmod(i, 4)
+        centre = (c - 1.5) * 0.2 * right + (1.5 - r) * 0.2 * up + rng.normal(scale=0.02, size=3)
+        spheres.append(single_primitive(SPHERE, list(centre) + [0.12]))
+    if blend == "sharp":
+        kind, kk, d_o = OP_SHARP_UNION, 0.0, 0.0
+    elif blend == "compact":
+        kind, kk, d_o = OP_UNION, k, 1.5 * k
+    elif blend == "classical":
+        kind, kk, d_o = OP_UNION, k, UNBOUNDED_RANGE
+    else:
+        raise ValueError(blend)
+
+    def build(lo, hi):
+        if hi - lo == 1:
+            return spheres[lo]
+        mid = (lo + hi + 1) // 2
+        return combine(kind, build(lo, mid), build(mid, hi), kk, d_o)
+
+    return build(0, n)
+
+
 def single_primitive(kind: int, rec) -> Scene:
     """A one-node scene (for analytic hit tests)."""
     params = np.zeros((1, 16), dtype=np.float32)

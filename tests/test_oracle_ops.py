@@ -117,3 +117,21 @@ def test_nan_filter(orc):
     assert math.isfinite(v)
     assert orc.op(OP_UNION, 0.1, 0.15, math.inf, 0.02) == 0.02
     assert orc.op(OP_INTER, 0.1, 0.15, math.inf, 0.02) == math.inf
+
+
+def test_unbounded_range_is_the_classical_blend(orc):
+    # A compact union whose range of interest is unbounded blends everywhere
+    # with k' -> k: it tends to the classical smooth union of Eq. 4-5 (the
+    # "classical" scenes of the blend-localisation experiment use d_o = 1e4).
+    from paper_2304_09673_b300.scenegen import UNBOUNDED_RANGE
+    rng = np.random.default_rng(5)
+    k = 0.06
+    worst = 0.0
+    for f0, f1 in rng.uniform(-0.4, 0.4, size=(400, 2)):
+        a = orc.op(OP_UNION, k, UNBOUNDED_RANGE, f0, f1)
+        b = orc.smooth(OP_UNION, k, f0, f1)
+        worst = max(worst, abs(a - b))
+    assert worst < 1e-6
+    # while the compact range leaves min(f0, f1) beyond d_o
+    assert orc.op(OP_UNION, k, 1.5 * k, 0.2, 0.21) == 0.2
+    assert orc.smooth(OP_UNION, k, 0.2, 0.21) < 0.2
