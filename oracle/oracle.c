@@ -43,6 +43,9 @@
 #define K_SPHERE 0
 #define K_RBOX 1
 #define K_CAPSULE 2
+#define K_TORUS 12
+#define K_SCONE 13
+#define K_ELLIPSOID 14
 #define K_UNION 16
 #define K_INTER 17
 #define K_DIFF 18
@@ -112,11 +115,69 @@ static double sdf_capsule(const float *q, const double p[3]) {
     return sqrt(dx * dx + dy * dy + dz * dz) - (double)q[6];
 }
 
+/* Unit vector of a record's axis (FP64). */
+static void unit3(const float *a, double u[3]) {
+    double n = sqrt((double)a[0] * a[0] + (double)a[1] * a[1] + (double)a[2] * a[2]);
+    for (int k = 0; k < 3; ++k) u[k] = a[k] / n;
+}
+
+/* Torus: points within r of the circle of radius R around the axis through
+ * c; distance to that circle minus r.  The circle's nearest point lies in the
+ * direction of p's component perpendicular to the axis. */
+static double sdf_torus(const float *q, const double p[3]) {
+    double ax[3], v[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+    unit3(q + 3, ax);
+    double h = v[0] * ax[0] + v[1] * ax[1] + v[2] * ax[2];
+    double w[3] = {v[0] - h * ax[0], v[1] - h * ax[1], v[2] - h * ax[2]};
+    double rho = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double dr = rho - (double)q[6];
+    return sqrt(dr * dr + h * h) - (double)q[7];
+}
+
+/* Sphere-cone: the convex hull of the balls (a, r_a) and (b, r_b).  In the
+ * plane through the axis, with y along the axis from a, x >= 0 the distance to
+ * it and h = |b - a|, the hull's side is tangent to both circles: outward
+ * normal n = (cos, sin) with sin = (r_a - r_b) / h, tangent points at
+ * parameter 0 and cos h along the side.  Nearest feature: ball a behind the
+ * first tangent point, ball b beyond the second, the side in between. */
+static double sdf_scone(const float *q, const double p[3]) {
+    double ba[3] = {(double)q[3] - q[0], (double)q[4] - q[1], (double)q[5] - q[2]};
+    double h = sqrt(ba[0] * ba[0] + ba[1] * ba[1] + ba[2] * ba[2]);
+    double ra = q[6], rb = q[7];
+    double sn = (ra - rb) / h, cs = sqrt(1.0 - sn * sn);
+    double v[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+    double y = (v[0] * ba[0] + v[1] * ba[1] + v[2] * ba[2]) / h;
+    double w[3] = {v[0] - y * ba[0] / h, v[1] - y * ba[1] / h, v[2] - y * ba[2] / h};
+    double x = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double lam = cs * y - sn * x;   /* position along the side */
+    if (lam < 0.0) return sqrt(x * x + y * y) - ra;
+    if (lam > cs * h) return sqrt(x * x + (y - h) * (y - h)) - rb;
+    return cs * x + sn * y - ra;
+}
+
+/* Ellipsoid (c, M world -> local, radii r): the Lipschitz-1 bound
+ * min(r) (|M (p - c) / r| - 1); zero exactly on the ellipsoid, negative
+ * inside, and never above the distance to it. */
+static double sdf_ellipsoid(const float *q, const double p[3]) {
+    double w[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+    double s = 0.0, rmin = q[12];
+    for (int i = 0; i < 3; ++i) {
+        double l = q[3 + 3 * i] * w[0] + q[4 + 3 * i] * w[1] + q[5 + 3 * i] * w[2];
+        double z = l / (double)q[12 + i];
+        s += z * z;
+        if (q[12 + i] < rmin) rmin = q[12 + i];
+    }
+    return rmin * (sqrt(s) - 1.0);
+}
+
 static double sdf_prim(int kind, const float *q, const double p[3]) {
     switch (kind) {
     case K_SPHERE: return sdf_sphere(q, p);
     case K_RBOX: return sdf_rbox(q, p);
     case K_CAPSULE: return sdf_capsule(q, p);
+    case K_TORUS: return sdf_torus(q, p);
+    case K_SCONE: return sdf_scone(q, p);
+    case K_ELLIPSOID: return sdf_ellipsoid(q, p);
     }
     return INFINITY;
 }
@@ -362,8 +423,14 @@ int or_pruned_view(int n, int root, const int32_t *kind, const int32_t *left,
 
 /* Sec. 6.1: primitive bounding volume offset by the primitive's range of
  * interest bound d.  Sphere -> sphere (c, r + d); rounded box -> oriented box
- * (c, M, b + r_round + d); capsule -> capsule (a, b, r + d).  Output record:
- * same layout as the primitive record with the enlarged radius / extents. */
+ * (c, M, b + r_round + d); capsule -> capsule (a, b, r + d).  The VOI family
+ * of the further primitives contains their offset volume {f <= d}: torus ->
+ * capped cylinder around its axis (radius R + r + d, half-height r + d, kept
+ * as a capsule-shaped record whose ends are the cap centres, tested without
+ * the spherical caps); sphere-cone -> capsule (a, b, max(r_a, r_b) + d);
+ * ellipsoid -> oriented box (c, M, r (1 + d / min r)), the box around the
+ * ellipsoid that {f <= d} is.  Output record: the family's layout (sphere:
+ * c, r; box: c, M, e at [12:15]; capsule / cylinder: a, b, r at [6]). */
 static void voi_rec(int kind, const float *q, double d, double *v) {
     for (int i = 0; i < NREC; ++i) v[i] = q[i];
     switch (kind) {
@@ -372,6 +439,21 @@ static void voi_rec(int kind, const float *q, double d, double *v) {
         for (int i = 0; i < 3; ++i) v[12 + i] = (double)q[12 + i] + (double)q[15] + d;
         break;
     case K_CAPSULE: v[6] = (double)q[6] + d; break;
+    case K_TORUS: {
+        double ax[3];
+        unit3(q + 3, ax);
+        double hh = (double)q[7] + d;
+        for (int k = 0; k < 3; ++k) { v[k] = q[k] - hh * ax[k]; v[3 + k] = q[k] + hh * ax[k]; }
+        v[6] = (double)q[6] + q[7] + d;
+        break;
+    }
+    case K_SCONE: v[6] = (q[6] > q[7] ? (double)q[6] : (double)q[7]) + d; break;
+    case K_ELLIPSOID: {
+        double rmin = q[12];
+        for (int i = 1; i < 3; ++i) if (q[12 + i] < rmin) rmin = q[12 + i];
+        for (int i = 0; i < 3; ++i) v[12 + i] = (double)q[12 + i] * (1.0 + d / rmin);
+        break;
+    }
     }
 }
 
@@ -385,10 +467,29 @@ static void prim_aabb(int kind, const float *q, double lo[3], double hi[3]) {
             for (int i = 0; i < 3; ++i) e += fabs((double)q[3 + 3 * i + j]) * ((double)q[12 + i] + q[15]);
             lo[j] = q[j] - e; hi[j] = q[j] + e;
         }
-    } else {
+    } else if (kind == K_CAPSULE) {
         for (int j = 0; j < 3; ++j) {
             double a = q[j], b = q[3 + j];
             lo[j] = (a < b ? a : b) - q[6]; hi[j] = (a > b ? a : b) + q[6];
+        }
+    } else if (kind == K_TORUS) {
+        double ax[3];
+        unit3(q + 3, ax);
+        for (int j = 0; j < 3; ++j) {
+            double e = (double)q[6] * sqrt(fmax(0.0, 1.0 - ax[j] * ax[j])) + q[7];
+            lo[j] = q[j] - e; hi[j] = q[j] + e;
+        }
+    } else if (kind == K_SCONE) {
+        for (int j = 0; j < 3; ++j) {
+            double la = q[j] - (double)q[6], lb = q[3 + j] - (double)q[7];
+            double ha = q[j] + (double)q[6], hb = q[3 + j] + (double)q[7];
+            lo[j] = la < lb ? la : lb; hi[j] = ha > hb ? ha : hb;
+        }
+    } else {   /* ellipsoid: inside its oriented box of half extents r */
+        for (int j = 0; j < 3; ++j) {
+            double e = 0;
+            for (int i = 0; i < 3; ++i) e += fabs((double)q[3 + 3 * i + j]) * (double)q[12 + i];
+            lo[j] = q[j] - e; hi[j] = q[j] + e;
         }
     }
 }
@@ -517,6 +618,44 @@ static int ray_obox64(const double o[3], const double d[3], const double *v, dou
     return 1;
 }
 
+/* Ray against the cylinder of radius r around segment [a, b], capped by the
+ * planes through a and b. */
+static int ray_cylinder64(const double o[3], const double d[3], const double *v, double *t0,
+                          double *t1) {
+    double a[3] = {v[0], v[1], v[2]}, b[3] = {v[3], v[4], v[5]}, r = v[6];
+    double ba[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double w[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
+    double bb = ba[0] * ba[0] + ba[1] * ba[1] + ba[2] * ba[2];
+    if (!(bb > 0)) return 0;
+    double wb = w[0] * ba[0] + w[1] * ba[1] + w[2] * ba[2];
+    double db = d[0] * ba[0] + d[1] * ba[1] + d[2] * ba[2];
+    double wp[3], dp[3];
+    for (int k = 0; k < 3; ++k) { wp[k] = w[k] - wb / bb * ba[k]; dp[k] = d[k] - db / bb * ba[k]; }
+    double A = dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2];
+    double c0 = -INFINITY, c1 = INFINITY;
+    if (A > 0) {
+        double tc = -(wp[0] * dp[0] + wp[1] * dp[1] + wp[2] * dp[2]) / A;
+        double h2 = 0;
+        for (int k = 0; k < 3; ++k) { double q = wp[k] + tc * dp[k]; h2 += q * q; }
+        if (h2 > r * r) return 0;
+        double s = sqrt((r * r - h2) / A);
+        c0 = tc - s; c1 = tc + s;
+    } else if (wp[0] * wp[0] + wp[1] * wp[1] + wp[2] * wp[2] > r * r) {
+        return 0;
+    }
+    if (db == 0) {
+        if (wb < 0 || wb > bb) return 0;
+    } else {
+        double ta = -wb / db, tb = (bb - wb) / db;
+        double sa = ta < tb ? ta : tb, sb = ta < tb ? tb : ta;
+        if (sa > c0) c0 = sa;
+        if (sb < c1) c1 = sb;
+        if (c0 > c1) return 0;
+    }
+    *t0 = c0; *t1 = c1;
+    return 1;
+}
+
 /* Ray against capsule (a, b, r) = cylinder between the end planes U two
  * spheres; the capsule is convex so its interval is the hull of the parts. */
 static int ray_capsule64(const double o[3], const double d[3], const double *v, double *t0,
@@ -525,39 +664,7 @@ static int ray_capsule64(const double o[3], const double d[3], const double *v, 
     double a[3] = {v[0], v[1], v[2]}, b[3] = {v[3], v[4], v[5]}, r = v[6];
     if (ray_sphere64(o, d, a, r, &s0, &s1)) { lo = fmin(lo, s0); hi = fmax(hi, s1); }
     if (ray_sphere64(o, d, b, r, &s0, &s1)) { lo = fmin(lo, s0); hi = fmax(hi, s1); }
-    double ba[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-    double w[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
-    double bb = ba[0] * ba[0] + ba[1] * ba[1] + ba[2] * ba[2];
-    if (bb > 0) {
-        double wb = w[0] * ba[0] + w[1] * ba[1] + w[2] * ba[2];
-        double db = d[0] * ba[0] + d[1] * ba[1] + d[2] * ba[2];
-        double wp[3], dp[3];
-        for (int k = 0; k < 3; ++k) { wp[k] = w[k] - wb / bb * ba[k]; dp[k] = d[k] - db / bb * ba[k]; }
-        double A = dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2];
-        int ok = 1;
-        double c0 = -INFINITY, c1 = INFINITY;
-        if (A > 0) {
-            double tc = -(wp[0] * dp[0] + wp[1] * dp[1] + wp[2] * dp[2]) / A;
-            double h2 = 0;
-            for (int k = 0; k < 3; ++k) { double q = wp[k] + tc * dp[k]; h2 += q * q; }
-            if (h2 > r * r) ok = 0;
-            else { double s = sqrt((r * r - h2) / A); c0 = tc - s; c1 = tc + s; }
-        } else {
-            if (wp[0] * wp[0] + wp[1] * wp[1] + wp[2] * wp[2] > r * r) ok = 0;
-        }
-        if (ok) {
-            if (db == 0) {
-                if (wb < 0 || wb > bb) ok = 0;
-            } else {
-                double ta = -wb / db, tb = (bb - wb) / db;
-                double sa = ta < tb ? ta : tb, sb = ta < tb ? tb : ta;
-                if (sa > c0) c0 = sa;
-                if (sb < c1) c1 = sb;
-                if (c0 > c1) ok = 0;
-            }
-        }
-        if (ok) { lo = fmin(lo, c0); hi = fmax(hi, c1); }
-    }
+    if (ray_cylinder64(o, d, v, &s0, &s1)) { lo = fmin(lo, s0); hi = fmax(hi, s1); }
     if (lo > hi) return 0;
     *t0 = lo; *t1 = hi;
     return 1;
@@ -568,7 +675,9 @@ static int ray_voi64(int kind, const double *v, const double o[3], const double 
     switch (kind) {
     case K_SPHERE: { double c[3] = {v[0], v[1], v[2]}; return ray_sphere64(o, d, c, v[3], t0, t1); }
     case K_RBOX: return ray_obox64(o, d, v, t0, t1);
-    case K_CAPSULE: return ray_capsule64(o, d, v, t0, t1);
+    case K_CAPSULE: case K_SCONE: return ray_capsule64(o, d, v, t0, t1);
+    case K_TORUS: return ray_cylinder64(o, d, v, t0, t1);
+    case K_ELLIPSOID: return ray_obox64(o, d, v, t0, t1);
     }
     return 0;
 }
@@ -615,52 +724,64 @@ static int ray_obox32(const float o[3], const float d[3], const float *q, const 
     return 1;
 }
 
+/* The cylinder part of the capsule test (radius r around [a, b], capped by
+ * the end planes), also the torus's volume of interest. */
+static int ray_cylinder32(const float o[3], const float d[3], const float *a, const float *b, float r,
+                          float *t0, float *t1) {
+    float bx = b[0] - a[0], by = b[1] - a[1], bz = b[2] - a[2];
+    float wx = o[0] - a[0], wy = o[1] - a[1], wz = o[2] - a[2];
+    float bb = (bx * bx + by * by) + bz * bz;
+    if (!(bb > 0.0f)) return 0;
+    float wb = (wx * bx + wy * by) + wz * bz;
+    float db = (d[0] * bx + d[1] * by) + d[2] * bz;
+    float fw = wb / bb, fd = db / bb;
+    float px = wx - fw * bx, py = wy - fw * by, pz = wz - fw * bz;
+    float ux = d[0] - fd * bx, uy = d[1] - fd * by, uz = d[2] - fd * bz;
+    float A = (ux * ux + uy * uy) + uz * uz;
+    float r2 = r * r;
+    float c0 = -INFINITY, c1 = INFINITY;
+    if (A > 0.0f) {
+        float pu = (px * ux + py * uy) + pz * uz;
+        float tc = -(pu / A);
+        float hx = px + tc * ux, hy = py + tc * uy, hz = pz + tc * uz;
+        float h2 = (hx * hx + hy * hy) + hz * hz;
+        if (h2 > r2) return 0;
+        float sq = sqrtf((r2 - h2) / A);
+        c0 = tc - sq; c1 = tc + sq;
+    } else {
+        float p2 = (px * px + py * py) + pz * pz;
+        if (p2 > r2) return 0;
+    }
+    if (db == 0.0f) {
+        if (wb < 0.0f || wb > bb) return 0;
+    } else {
+        float ta = -(wb / db), tb = (bb - wb) / db;
+        float sa = ta < tb ? ta : tb, sb = ta < tb ? tb : ta;
+        if (sa > c0) c0 = sa;
+        if (sb < c1) c1 = sb;
+        if (c0 > c1) return 0;
+    }
+    *t0 = c0; *t1 = c1;
+    return 1;
+}
+
 static int ray_capsule32(const float o[3], const float d[3], const float *q, float r,
                          float *t0, float *t1) {
     float lo = INFINITY, hi = -INFINITY, s0, s1;
     const float *a = q, *b = q + 3;
     if (ray_sphere32(o, d, a, r, &s0, &s1)) { if (s0 < lo) lo = s0; if (s1 > hi) hi = s1; }
     if (ray_sphere32(o, d, b, r, &s0, &s1)) { if (s0 < lo) lo = s0; if (s1 > hi) hi = s1; }
-    float bx = b[0] - a[0], by = b[1] - a[1], bz = b[2] - a[2];
-    float wx = o[0] - a[0], wy = o[1] - a[1], wz = o[2] - a[2];
-    float bb = (bx * bx + by * by) + bz * bz;
-    if (bb > 0.0f) {
-        float wb = (wx * bx + wy * by) + wz * bz;
-        float db = (d[0] * bx + d[1] * by) + d[2] * bz;
-        float fw = wb / bb, fd = db / bb;
-        float px = wx - fw * bx, py = wy - fw * by, pz = wz - fw * bz;
-        float ux = d[0] - fd * bx, uy = d[1] - fd * by, uz = d[2] - fd * bz;
-        float A = (ux * ux + uy * uy) + uz * uz;
-        float r2 = r * r;
-        int ok = 1;
-        float c0 = -INFINITY, c1 = INFINITY;
-        if (A > 0.0f) {
-            float pu = (px * ux + py * uy) + pz * uz;
-            float tc = -(pu / A);
-            float hx = px + tc * ux, hy = py + tc * uy, hz = pz + tc * uz;
-            float h2 = (hx * hx + hy * hy) + hz * hz;
-            if (h2 > r2) ok = 0;
-            else { float s = sqrtf((r2 - h2) / A); c0 = tc - s; c1 = tc + s; }
-        } else {
-            float p2 = (px * px + py * py) + pz * pz;
-            if (p2 > r2) ok = 0;
-        }
-        if (ok) {
-            if (db == 0.0f) {
-                if (wb < 0.0f || wb > bb) ok = 0;
-            } else {
-                float ta = -(wb / db), tb = (bb - wb) / db;
-                float sa = ta < tb ? ta : tb, sb = ta < tb ? tb : ta;
-                if (sa > c0) c0 = sa;
-                if (sb < c1) c1 = sb;
-                if (c0 > c1) ok = 0;
-            }
-        }
-        if (ok) { if (c0 < lo) lo = c0; if (c1 > hi) hi = c1; }
-    }
+    if (ray_cylinder32(o, d, a, b, r, &s0, &s1)) { if (s0 < lo) lo = s0; if (s1 > hi) hi = s1; }
     if (lo > hi) return 0;
     *t0 = lo; *t1 = hi;
     return 1;
+}
+
+/* Record words that the library's host preparation derives in FP64 and
+ * rounds once to FP32 (the unit axis of a torus). */
+static void unit3_f32(const float *a, float u[3]) {
+    double n = sqrt((double)a[0] * a[0] + (double)a[1] * a[1] + (double)a[2] * a[2]);
+    for (int k = 0; k < 3; ++k) u[k] = (float)(a[k] / n);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -712,10 +833,24 @@ int or_cull(int n, int root, const int32_t *kind, const int32_t *left, const int
             voi_rec(k, q, roi[i], v64);
             /* FP32 VOI: extents ((size + d) + pad) in single precision. */
             float dp = (float)roi[i];
-            float rr32 = 0, e32[3] = {0, 0, 0};
+            float rr32 = 0, e32[3] = {0, 0, 0}, ca32[3] = {0, 0, 0}, cb32[3] = {0, 0, 0};
             if (k == K_SPHERE) rr32 = (q[3] + dp) + pad;
             else if (k == K_CAPSULE) rr32 = (q[6] + dp) + pad;
-            else for (int a = 0; a < 3; ++a) e32[a] = ((q[12 + a] + q[15]) + dp) + pad;
+            else if (k == K_SCONE) rr32 = ((q[6] > q[7] ? q[6] : q[7]) + dp) + pad;
+            else if (k == K_TORUS) {
+                /* cylinder: radius ((R + r) + d) + pad, half-height (r + d) + pad */
+                float ax[3];
+                unit3_f32(q + 3, ax);
+                rr32 = ((q[6] + q[7]) + dp) + pad;
+                float hh = (q[7] + dp) + pad;
+                for (int a = 0; a < 3; ++a) { ca32[a] = q[a] - hh * ax[a]; cb32[a] = q[a] + hh * ax[a]; }
+            } else if (k == K_ELLIPSOID) {
+                float rmin = q[12];
+                if (q[13] < rmin) rmin = q[13];
+                if (q[14] < rmin) rmin = q[14];
+                float grow = 1.0f + dp / rmin;
+                for (int a = 0; a < 3; ++a) e32[a] = q[12 + a] * grow + pad;
+            } else for (int a = 0; a < 3; ++a) e32[a] = ((q[12 + a] + q[15]) + dp) + pad;
             int hit = 0;
             double zi = INFINITY, zo = -INFINITY;
             float zi32 = INFINITY, zo32 = -INFINITY;
@@ -735,7 +870,8 @@ int or_cull(int n, int root, const int32_t *kind, const int32_t *left, const int
                         int h;
                         cam_ray32(&c, px, py, d);
                         if (k == K_SPHERE) h = ray_sphere32(c.of, d, q, rr32, &t0, &t1);
-                        else if (k == K_RBOX) h = ray_obox32(c.of, d, q, e32, &t0, &t1);
+                        else if (k == K_RBOX || k == K_ELLIPSOID) h = ray_obox32(c.of, d, q, e32, &t0, &t1);
+                        else if (k == K_TORUS) h = ray_cylinder32(c.of, d, ca32, cb32, rr32, &t0, &t1);
                         else h = ray_capsule32(c.of, d, q, rr32, &t0, &t1);
                         if (!h) continue;
                         t0 = t0 > 0.0f ? t0 : 0.0f;

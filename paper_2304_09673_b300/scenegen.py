@@ -22,6 +22,11 @@ leaves"):
   RBOX    (1): [0:3] centre, [3:12] world->local rotation M (row major,
                local = M (x - centre)), [12:15] half extents, [15] rounding
   CAPSULE (2): [0:3] end point a, [3:6] end point b, [6] radius
+  TORUS  (12): [0:3] centre, [3:6] axis, [6] major radius R, [7] minor radius r
+  SCONE  (13): [0:3] centre a, [3:6] centre b, [6] radius r_a, [7] radius r_b
+               (sphere-cone: convex hull of the two balls, |b - a| > |r_a - r_b|)
+  ELLIPSOID (14): [0:3] centre, [3:12] world->local rotation M, [12:15] radii
+(the kind numbers of the last three equal their node codes in a pruned view).
 Operator records: [0] blend range k, [1] operator range bound d_o
   (Sec. 5, Eq. "compact smooth union": R_o = (-inf, d_o]).
 Operator kinds: 16 compact smooth union, 17 compact smooth intersection,
@@ -36,9 +41,11 @@ from dataclasses import dataclass, field
 import numpy as np
 
 SPHERE, RBOX, CAPSULE = 0, 1, 2
+TORUS, SCONE, ELLIPSOID = 12, 13, 14
 OP_UNION, OP_INTER, OP_DIFF = 16, 17, 18
 OP_SHARP_UNION, OP_SHARP_INTER, OP_SHARP_DIFF = 19, 20, 21
 PRIM_KINDS = (SPHERE, RBOX, CAPSULE)
+ALL_PRIM_KINDS = (SPHERE, RBOX, CAPSULE, TORUS, SCONE, ELLIPSOID)
 OP_KINDS = (OP_UNION, OP_INTER, OP_DIFF, OP_SHARP_UNION, OP_SHARP_INTER, OP_SHARP_DIFF)
 
 
@@ -108,13 +115,34 @@ def _draw_primitive(rng: np.random.Generator, centre: np.ndarray, kinds=PRIM_KIN
         rec[3:12] = rot.T.reshape(-1)          # world -> local
         rec[12:15] = rng.uniform(0.03, 0.15, size=3)
         rec[15] = rng.uniform(0.005, 0.03)
-    else:
+    elif kind == CAPSULE:
         rot = _random_rotation(rng)
         half = rng.uniform(0.05, 0.2)
         axis = rot[:, 1]
         rec[0:3] = centre - half * axis
         rec[3:6] = centre + half * axis
         rec[6] = rng.uniform(0.03, 0.1)
+    elif kind == TORUS:
+        rot = _random_rotation(rng)
+        rec[0:3] = centre
+        rec[3:6] = rot[:, 2]
+        rec[6] = rng.uniform(0.06, 0.15)
+        rec[7] = rng.uniform(0.02, 0.05)
+    elif kind == SCONE:
+        rot = _random_rotation(rng)
+        half = rng.uniform(0.05, 0.15)
+        axis = rot[:, 1]
+        rec[0:3] = centre - half * axis
+        rec[3:6] = centre + half * axis
+        rec[6] = rng.uniform(0.04, 0.1)
+        rec[7] = rng.uniform(0.02, 0.06)   # |r_a - r_b| < 0.08 < 2 * half
+    elif kind == ELLIPSOID:
+        rot = _random_rotation(rng)
+        rec[0:3] = centre
+        rec[3:12] = rot.T.reshape(-1)
+        rec[12:15] = rng.uniform(0.04, 0.15, size=3)
+    else:
+        raise ValueError(f"unknown primitive kind {kind}")
     return kind, rec.astype(np.float32)
 
 
@@ -313,6 +341,12 @@ def edit_primitives(scene: Scene, frac: float, rng: np.random.Generator):
 def workload_small(seed: int = 0) -> Scene:
     """64 primitives, complete depth-6 tree (256x256 render)."""
     return make_scene(64, 6, seed)
+
+
+def workload_families(seed: int = 0, n_prims: int = 64, max_depth: int = 6) -> Scene:
+    """All six primitive families (sphere, rounded box, capsule, torus,
+    sphere-cone, ellipsoid) in a random tree (64 primitives, depth 6)."""
+    return make_scene(n_prims, max_depth, seed, kinds=ALL_PRIM_KINDS)
 
 
 def workload_1080p(seed: int = 100) -> Scene:

@@ -251,31 +251,42 @@ def test_all_active_equals_dense(orc):
     assert np.array_equal(orc.field(s, pts, act), orc.field(s, pts))
 
 
+def voi_contains_prim(kind, q, d, p):
+    """Independent point-in-VOI test of one primitive record q with range of
+    interest bound d (sphere / oriented box / capsule / cylinder families)."""
+    q = np.asarray(q, np.float64)
+    if kind == sg.SPHERE:
+        return np.linalg.norm(p - q[:3]) <= q[3] + d
+    if kind in (sg.RBOX, sg.ELLIPSOID):
+        loc = q[3:12].reshape(3, 3) @ (p - q[:3])
+        ext = q[12:15] + q[15] + d if kind == sg.RBOX else q[12:15] * (1 + d / q[12:15].min())
+        return bool(np.all(np.abs(loc) <= ext))
+    if kind == sg.TORUS:
+        ax = q[3:6] / np.linalg.norm(q[3:6])
+        h = (p - q[:3]) @ ax
+        rad = np.linalg.norm(p - q[:3] - h * ax)
+        return abs(h) <= q[7] + d and rad <= q[6] + q[7] + d
+    a, b = q[0:3], q[3:6]
+    ab = b - a
+    h = np.clip((p - a) @ ab / (ab @ ab), 0, 1)
+    r = q[6] if kind == sg.CAPSULE else max(q[6], q[7])
+    return np.linalg.norm(p - a - h * ab) <= r + d
+
+
 def _voi_contains(orc, scene, st, p):
-    """Independent point-in-VOI test (sphere / oriented box / capsule)."""
+    """Independent point-in-VOI test of every primitive of a scene."""
     out = np.zeros(scene.n_nodes, bool)
     for i in np.flatnonzero(scene.kind < 16):
-        q = scene.params[i].astype(np.float64)
-        d = st["roi"][st["po_of"][i]]
-        k = scene.kind[i]
-        if k == sg.SPHERE:
-            out[i] = np.linalg.norm(p - q[:3]) <= q[3] + d
-        elif k == sg.RBOX:
-            loc = q[3:12].reshape(3, 3) @ (p - q[:3])
-            out[i] = np.all(np.abs(loc) <= q[12:15] + q[15] + d)
-        else:
-            a, b = q[0:3], q[3:6]
-            ab = b - a
-            h = np.clip((p - a) @ ab / (ab @ ab), 0, 1)
-            out[i] = np.linalg.norm(p - a - h * ab) <= q[6] + d
+        out[i] = voi_contains_prim(int(scene.kind[i]), scene.params[i], st["roi"][st["po_of"][i]], p)
     return out
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
 def test_local_equivalence_sign(orc, seed):
     # Sec. 3 / Sec. 5: with A = primitives whose volume of interest contains p,
-    # sign(f_A(p)) = sign(f(p)).
-    s = sg.make_scene(48, 7, 900 + seed)
+    # sign(f_A(p)) = sign(f(p)).  Seed 3: all six primitive families.
+    kinds = sg.ALL_PRIM_KINDS if seed == 3 else sg.PRIM_KINDS
+    s = sg.make_scene(48, 7, 900 + seed, kinds=kinds)
     st = orc.structure(s)
     pts = _random_points(s, 400, seed, orc)
     f = orc.field(s, pts)
