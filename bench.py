@@ -12,7 +12,7 @@ per-pixel comparison variants (Table 1).
 Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 1080p|small|clustered|clustered1080p|batch64|table1|blend] [--modes learned,plain,overrelax,crossing]
+                  [--workload 1080p|small|clustered|clustered1080p|families1080p|batch64|table1|blend] [--modes learned,plain,overrelax,crossing]
 
 Multi-GPU: one independent replica per rank (the path has no exchange step);
 value = all ranks' rays / max-over-ranks time ("scaling": "weak").
@@ -59,6 +59,11 @@ def workload(name: str):
         return sg.workload_clustered(200), sg.default_camera(1920, 1080), dict(
             workload="10,000 primitives in 50 Gaussian clusters (sigma 0.05, depth<=20, seed 200), 1920x1080, "
                      "tile 16", prims=10000, resolution="1920x1080", tile=16)
+    if name == "families1080p":
+        return sg.workload_families(100, n_prims=1024, max_depth=14), sg.default_camera(1920, 1080), dict(
+            workload="1,024 primitives of six families (sphere, rounded box, capsule, torus, sphere-cone, "
+                     "ellipsoid; depth<=14, seed 100), 1920x1080, tile 16", prims=1024, resolution="1920x1080",
+            tile=16)
     raise SystemExit(f"unknown workload {name}")
 
 

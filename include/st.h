@@ -49,6 +49,19 @@ extern "C" {
                               M row-major (local = M (x - centre)),
                               rec[12:15] half extents, rec[15] rounding      */
 #define ST_PRIM_CAPSULE 2  /* rec[0:3] end a, rec[3:6] end b, rec[6] radius */
+/* Further families of Sec. 10's primitive list (kind numbers equal their
+ * node codes in a pruned view): */
+#define ST_PRIM_TORUS 12   /* rec[0:3] centre, rec[3:6] axis (any length > 0),
+                              rec[6] major radius R >= 0, rec[7] minor
+                              radius r > 0; exact distance               */
+#define ST_PRIM_SCONE 13   /* sphere-cone, the convex hull of two balls:
+                              rec[0:3] centre a, rec[3:6] centre b, rec[6]
+                              radius r_a, rec[7] radius r_b (>= 0, not both
+                              0, |b - a| > |r_a - r_b|); exact distance   */
+#define ST_PRIM_ELLIPSOID 14 /* rec[0:3] centre, rec[3:12] world->local
+                              rotation M as ST_PRIM_RBOX, rec[12:15] radii
+                              > 0; field min(r) (|M (x - c) / r| - 1), a
+                              Lipschitz-1 bound of the distance           */
 /* Operators (binary): compact smooth operators G_op of Sec. 5 (Eq.
  * "smooth_comp" with the smooth polynomial operators of Eq. 4-7 and the
  * transition b_r), rec[0] = blend range k > 0, rec[1] = operator range bound

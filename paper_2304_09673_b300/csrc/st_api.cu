@@ -234,7 +234,11 @@ int st_scene_update_prims(st_scene *s, const int32_t *ids, const float *params, 
     uint32_t b = s->prep.blob[a];
     if (!blob_isprim(b)) { set_error("node id is not a primitive"); return ST_ERR_INVALID; }
     int kind = (int)blob_kind(b);
-    float w[16];
+    if (const char *e = prim_record_error(kind, params + (size_t)i * ST_REC_FLOATS)) {
+      set_error(std::string("st_scene_update_prims: ") + e);
+      return ST_ERR_INVALID;
+    }
+    float w[20];
     prim_words(kind, params + (size_t)i * ST_REC_FLOATS, w);
     for (int k = 0; k < rec_words(kind); ++k) {
       index.push_back(s->prep.rec_off[a] + k);

@@ -81,13 +81,13 @@ __global__ void k_prim_bounds(const Job *jobs, int n_jobs, uint32_t n_prims_tota
   Voi v;
   load_voi(job.sc, j, v);
   float C[3], rho;
-  if (v.kind == ST_PRIM_SPHERE) {
+  if (v.fam == VOI_SPHERE) {
     C[0] = v.c[0]; C[1] = v.c[1]; C[2] = v.c[2];
     rho = v.r;
-  } else if (v.kind == ST_PRIM_RBOX) {
+  } else if (v.fam == VOI_BOX) {
     C[0] = v.c[0]; C[1] = v.c[1]; C[2] = v.c[2];
     rho = sqrtf(v.e[0] * v.e[0] + v.e[1] * v.e[1] + v.e[2] * v.e[2]);
-  } else {
+  } else {   // capsule and cylinder: the capsule's bounding sphere holds both
     float h[3] = {0.5f * (v.b[0] - v.c[0]), 0.5f * (v.b[1] - v.c[1]), 0.5f * (v.b[2] - v.c[2])};
     C[0] = v.c[0] + h[0]; C[1] = v.c[1] + h[1]; C[2] = v.c[2] + h[2];
     rho = sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]) + v.r;

@@ -123,9 +123,14 @@ struct SparseCount {
 template <class T>
 __device__ __forceinline__ T prim_value(const DevScene &sc, uint32_t a, uint32_t kind, const T p[3]) {
   const float4 *q = sc.rec + __ldg(sc.rec_off + a);
-  if (kind == ST_PRIM_SPHERE) return sd_sphere<T>(q[0], p);
-  if (kind == ST_PRIM_RBOX) return sd_rbox<T>(q[0], q[1], q[2], q[3], p);
-  return sd_capsule<T>(q[0], q[2], p);
+  switch (kind) {
+    case ST_PRIM_SPHERE: return sd_sphere<T>(q[0], p);
+    case ST_PRIM_RBOX: return sd_rbox<T>(q[0], q[1], q[2], q[3], p);
+    case ST_PRIM_CAPSULE: return sd_capsule<T>(q[0], q[2], p);
+    case ST_PRIM_TORUS: return sd_torus<T>(q[0], q[1], p);
+    case ST_PRIM_SCONE: return sd_scone<T>(q[0], q[1], q[2], q[3], p);
+    default: return sd_ellipsoid<T>(q[0], q[1], q[2], q[3], q[4], p);
+  }
 }
 
 template <class T>

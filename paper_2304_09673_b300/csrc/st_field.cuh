@@ -158,6 +158,52 @@ __device__ __forceinline__ T sd_capsule(const float4 a0, const float4 a2, const 
   return sub_(sqrt_(fma_(dx, dx, fma_(dy, dy, mul_(dz, dz)))), a0.w);
 }
 
+// Torus around the unit axis u through c: distance to the circle of radius R
+// minus r; records [c, r] [u, R].  (The radial square root takes a tiny floor
+// so that derivatives stay finite on the axis.)
+template <class T>
+__device__ __forceinline__ T sd_torus(const float4 a0, const float4 a1, const T p[3]) {
+  const T vx = sub_(p[0], a0.x), vy = sub_(p[1], a0.y), vz = sub_(p[2], a0.z);
+  const T h = fma_(vx, a1.x, fma_(vy, a1.y, mul_(vz, a1.z)));
+  const T vv = fma_(vx, vx, fma_(vy, vy, mul_(vz, vz)));
+  const T q = sub_(sqrt_(max_(fma_(h, -h, vv), 1e-30f)), a1.w);
+  return sub_(sqrt_(fma_(q, q, mul_(h, h))), a0.w);
+}
+
+// Sphere-cone (convex hull of the balls (a, r_a), (b, r_b)): in the axial
+// plane (y along u = (b - a)/h from a, x the distance to the axis) the side
+// has outward normal (cos, sin) and spans lam = cos y - sin x in [0, cos h];
+// nearest feature ball a, side or ball b.  Records [a, r_a] [b, r_b] [u, h]
+// [sin, cos, cos h, 0].
+template <class T>
+__device__ __forceinline__ T sd_scone(const float4 a0, const float4 a1, const float4 a2, const float4 a3,
+                                      const T p[3]) {
+  const T vx = sub_(p[0], a0.x), vy = sub_(p[1], a0.y), vz = sub_(p[2], a0.z);
+  const T y = fma_(vx, a2.x, fma_(vy, a2.y, mul_(vz, a2.z)));
+  const T vv = fma_(vx, vx, fma_(vy, vy, mul_(vz, vz)));
+  const T x2 = max_(fma_(y, -y, vv), 1e-30f);
+  const T x = sqrt_(x2);
+  const T lam = fma_(y, a3.y, mul_(x, -a3.x));
+  const T fa = sub_(sqrt_(max_(vv, 1e-30f)), a0.w);
+  const T yb = sub_(y, a2.w);
+  const T fb = sub_(sqrt_(fma_(yb, yb, x2)), a1.w);
+  const T fs = sub_(fma_(x, a3.y, mul_(y, a3.x)), a0.w);
+  return val(lam) < 0.f ? fa : (val(lam) > a3.z ? fb : fs);
+}
+
+// Ellipsoid bound min(r) (|M (p - c) / r| - 1); records [c, min r]
+// [M row i, r_i] x 3 [1/r0, 1/r1, 1/r2, 0].
+template <class T>
+__device__ __forceinline__ T sd_ellipsoid(const float4 a0, const float4 a1, const float4 a2, const float4 a3,
+                                          const float4 a4, const T p[3]) {
+  const T wx = sub_(p[0], a0.x), wy = sub_(p[1], a0.y), wz = sub_(p[2], a0.z);
+  const T z0 = mul_(fma_(wx, a1.x, fma_(wy, a1.y, mul_(wz, a1.z))), a4.x);
+  const T z1 = mul_(fma_(wx, a2.x, fma_(wy, a2.y, mul_(wz, a2.z))), a4.y);
+  const T z2 = mul_(fma_(wx, a3.x, fma_(wy, a3.y, mul_(wz, a3.z))), a4.z);
+  const T s = sqrt_(fma_(z0, z0, fma_(z1, z1, mul_(z2, z2))));
+  return fma_(s, a0.w, -a0.w);
+}
+
 // ---- compact smooth operators G_op (Sec. 5) -------------------------------------
 // Record [k, d_o, c1 = 6 / (6 d_o - k), 1/k].  Smooth displacement of Eq. 5:
 // d(f0, f1, k) = k/6 max(1 - a/k, 0)^3 with a = |f0 - f1|; transition
@@ -210,6 +256,9 @@ __device__ __forceinline__ uint32_t node_flops(uint32_t code) {
     case V_SPHERE: return kFlopsSphere;
     case V_RBOX: return kFlopsRbox;
     case V_CAPSULE: return kFlopsCapsule;
+    case V_TORUS: return kFlopsTorus;
+    case V_SCONE: return kFlopsScone;
+    case V_ELLIPSOID: return kFlopsEllipsoid;
     case V_UNION: case V_INTER: case V_DIFF: return kFlopsCompactOp;
     case V_SUNION: case V_SINTER: case V_SDIFF: return kFlopsSharpOp;
     default: return 0;
@@ -252,6 +301,27 @@ __device__ __forceinline__ void eval_view_r(const uint32_t *view, int n_view, co
         stk.push(sp++, acc);
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = sd_capsule<T>(a0, a2, p[r]);
+        break;
+      }
+      case V_TORUS: {
+        const float4 a0 = ldrec(q), a1 = ldrec(q + 1);
+        stk.push(sp++, acc);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = sd_torus<T>(a0, a1, p[r]);
+        break;
+      }
+      case V_SCONE: {
+        const float4 a0 = ldrec(q), a1 = ldrec(q + 1), a2 = ldrec(q + 2), a3 = ldrec(q + 3);
+        stk.push(sp++, acc);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = sd_scone<T>(a0, a1, a2, a3, p[r]);
+        break;
+      }
+      case V_ELLIPSOID: {
+        const float4 a0 = ldrec(q), a1 = ldrec(q + 1), a2 = ldrec(q + 2), a3 = ldrec(q + 3), a4 = ldrec(q + 4);
+        stk.push(sp++, acc);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = sd_ellipsoid<T>(a0, a1, a2, a3, a4, p[r]);
         break;
       }
       case V_UNION: case V_INTER: case V_DIFF: {

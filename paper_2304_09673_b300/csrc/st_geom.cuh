@@ -82,54 +82,55 @@ struct CapsuleConst {
   float bb, wbv, r;
 };
 
+// The cylinder part of the capsule test: radius k.r around [a, b], capped by
+// the planes through the ends (also the volume of interest of a torus).
+__device__ __forceinline__ bool ray_cylinder32(const CapsuleConst &k, const float d[3], float &t0, float &t1) {
+  if (!(k.bb > 0.0f)) return false;
+  float db = ieee_dot3(d[0], d[1], d[2], k.ba[0], k.ba[1], k.ba[2]);
+  float fd = ieee_div(db, k.bb);
+  float ux = ieee_sub(d[0], ieee_mul(fd, k.ba[0]));
+  float uy = ieee_sub(d[1], ieee_mul(fd, k.ba[1]));
+  float uz = ieee_sub(d[2], ieee_mul(fd, k.ba[2]));
+  float A = ieee_dot3(ux, uy, uz, ux, uy, uz);
+  float r2 = ieee_mul(k.r, k.r);
+  float c0 = -INFINITY, c1 = INFINITY;
+  if (A > 0.0f) {
+    float pu = ieee_dot3(k.p[0], k.p[1], k.p[2], ux, uy, uz);
+    float tc = -ieee_div(pu, A);
+    float hx = ieee_add(k.p[0], ieee_mul(tc, ux));
+    float hy = ieee_add(k.p[1], ieee_mul(tc, uy));
+    float hz = ieee_add(k.p[2], ieee_mul(tc, uz));
+    float h2 = ieee_dot3(hx, hy, hz, hx, hy, hz);
+    if (h2 > r2) return false;
+    float s = ieee_sqrt(ieee_div(ieee_sub(r2, h2), A));
+    c0 = ieee_sub(tc, s);
+    c1 = ieee_add(tc, s);
+  } else {
+    float p2 = ieee_dot3(k.p[0], k.p[1], k.p[2], k.p[0], k.p[1], k.p[2]);
+    if (p2 > r2) return false;
+  }
+  if (db == 0.0f) {
+    if (k.wbv < 0.0f || k.wbv > k.bb) return false;
+  } else {
+    float ta = -ieee_div(k.wbv, db);
+    float tb = ieee_div(ieee_sub(k.bb, k.wbv), db);
+    float sa = ta < tb ? ta : tb;
+    float sb = ta < tb ? tb : ta;
+    if (sa > c0) c0 = sa;
+    if (sb < c1) c1 = sb;
+    if (c0 > c1) return false;
+  }
+  t0 = c0;
+  t1 = c1;
+  return true;
+}
+
 __device__ __forceinline__ bool ray_capsule32(const CapsuleConst &k, const float d[3], float &t0,
                                               float &t1) {
   float lo = INFINITY, hi = -INFINITY, s0, s1;
   if (ray_sphere32(k.wa, d, k.r, s0, s1)) { if (s0 < lo) lo = s0; if (s1 > hi) hi = s1; }
   if (ray_sphere32(k.wb, d, k.r, s0, s1)) { if (s0 < lo) lo = s0; if (s1 > hi) hi = s1; }
-  if (k.bb > 0.0f) {
-    float db = ieee_dot3(d[0], d[1], d[2], k.ba[0], k.ba[1], k.ba[2]);
-    float fd = ieee_div(db, k.bb);
-    float ux = ieee_sub(d[0], ieee_mul(fd, k.ba[0]));
-    float uy = ieee_sub(d[1], ieee_mul(fd, k.ba[1]));
-    float uz = ieee_sub(d[2], ieee_mul(fd, k.ba[2]));
-    float A = ieee_dot3(ux, uy, uz, ux, uy, uz);
-    float r2 = ieee_mul(k.r, k.r);
-    bool ok = true;
-    float c0 = -INFINITY, c1 = INFINITY;
-    if (A > 0.0f) {
-      float pu = ieee_dot3(k.p[0], k.p[1], k.p[2], ux, uy, uz);
-      float tc = -ieee_div(pu, A);
-      float hx = ieee_add(k.p[0], ieee_mul(tc, ux));
-      float hy = ieee_add(k.p[1], ieee_mul(tc, uy));
-      float hz = ieee_add(k.p[2], ieee_mul(tc, uz));
-      float h2 = ieee_dot3(hx, hy, hz, hx, hy, hz);
-      if (h2 > r2) {
-        ok = false;
-      } else {
-        float s = ieee_sqrt(ieee_div(ieee_sub(r2, h2), A));
-        c0 = ieee_sub(tc, s);
-        c1 = ieee_add(tc, s);
-      }
-    } else {
-      float p2 = ieee_dot3(k.p[0], k.p[1], k.p[2], k.p[0], k.p[1], k.p[2]);
-      if (p2 > r2) ok = false;
-    }
-    if (ok) {
-      if (db == 0.0f) {
-        if (k.wbv < 0.0f || k.wbv > k.bb) ok = false;
-      } else {
-        float ta = -ieee_div(k.wbv, db);
-        float tb = ieee_div(ieee_sub(k.bb, k.wbv), db);
-        float sa = ta < tb ? ta : tb;
-        float sb = ta < tb ? tb : ta;
-        if (sa > c0) c0 = sa;
-        if (sb < c1) c1 = sb;
-        if (c0 > c1) ok = false;
-      }
-    }
-    if (ok) { if (c0 < lo) lo = c0; if (c1 > hi) hi = c1; }
-  }
+  if (ray_cylinder32(k, d, s0, s1)) { if (s0 < lo) lo = s0; if (s1 > hi) hi = s1; }
   if (lo > hi) return false;
   t0 = lo;
   t1 = hi;
@@ -138,13 +139,18 @@ __device__ __forceinline__ bool ray_capsule32(const CapsuleConst &k, const float
 
 // Volume of interest of primitive j (Sec. 6.1: the primitive's bound offset by
 // its range-of-interest bound d_prim), extents in FP32: ((size + d) + pad).
+// Families: sphere (sphere); oriented box (rounded box; ellipsoid, the box
+// around {f <= d}, half extents r (1 + d / min r)); capsule (capsule;
+// sphere-cone with radius max(r_a, r_b) + d); capped cylinder (torus: radius
+// (R + r) + d around the axis, half-height r + d).
+enum VoiFamily : int { VOI_SPHERE = 0, VOI_BOX = 1, VOI_CAPSULE = 2, VOI_CYLINDER = 3 };
 struct Voi {
-  int kind;
-  float c[3];      // centre (sphere, box) or end a (capsule)
+  int fam;
+  float c[3];      // centre (sphere, box) or end a (capsule, cylinder)
   float M[9];      // box rotation rows
   float e[3];      // box half extents
-  float b[3];      // capsule end b
-  float r;         // sphere / capsule radius
+  float b[3];      // capsule / cylinder end b
+  float r;         // sphere / capsule / cylinder radius
 };
 
 __device__ __forceinline__ void load_voi(const DevScene &sc, uint32_t j, Voi &v) {
@@ -152,23 +158,40 @@ __device__ __forceinline__ void load_voi(const DevScene &sc, uint32_t j, Voi &v)
   uint32_t kind = blob_kind(sc.blob[a]);
   const float4 *w = sc.rec + sc.rec_off[a];
   float dp = sc.d_prim[j], pad = sc.voi_pad;
-  v.kind = (int)kind;
   float4 w0 = w[0];
   v.c[0] = w0.x; v.c[1] = w0.y; v.c[2] = w0.z;
   if (kind == ST_PRIM_SPHERE) {
+    v.fam = VOI_SPHERE;
     v.r = ieee_add(ieee_add(w0.w, dp), pad);
-  } else if (kind == ST_PRIM_RBOX) {
-    float rr = w0.w;
+  } else if (kind == ST_PRIM_RBOX || kind == ST_PRIM_ELLIPSOID) {
+    v.fam = VOI_BOX;
+    const float rr = w0.w;
+    const float grow = ieee_add(1.0f, ieee_div(dp, rr));   // ellipsoid: rr = min r
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       float4 m = w[1 + i];
       v.M[3 * i] = m.x; v.M[3 * i + 1] = m.y; v.M[3 * i + 2] = m.z;
-      v.e[i] = ieee_add(ieee_add(ieee_add(m.w, rr), dp), pad);
+      v.e[i] = kind == ST_PRIM_RBOX ? ieee_add(ieee_add(ieee_add(m.w, rr), dp), pad)
+                                    : ieee_add(ieee_mul(m.w, grow), pad);
     }
-  } else {
+  } else if (kind == ST_PRIM_TORUS) {
+    v.fam = VOI_CYLINDER;
+    const float4 w1 = w[1];   // unit axis, R
+    const float hh = ieee_add(ieee_add(w0.w, dp), pad);
+    const float ax[3] = {w1.x, w1.y, w1.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float c = v.c[k];
+      v.c[k] = ieee_sub(c, ieee_mul(hh, ax[k]));
+      v.b[k] = ieee_add(c, ieee_mul(hh, ax[k]));
+    }
+    v.r = ieee_add(ieee_add(ieee_add(w1.w, w0.w), dp), pad);
+  } else {   // capsule, sphere-cone
+    v.fam = VOI_CAPSULE;
     float4 w1 = w[1];
     v.b[0] = w1.x; v.b[1] = w1.y; v.b[2] = w1.z;
-    v.r = ieee_add(ieee_add(w0.w, dp), pad);
+    const float rad = kind == ST_PRIM_SCONE ? fmaxf(w0.w, w1.w) : w0.w;
+    v.r = ieee_add(ieee_add(rad, dp), pad);
   }
 }
 
@@ -179,10 +202,10 @@ struct VoiRay {
 };
 
 __device__ __forceinline__ void voi_ray_setup(const Voi &v, const DevCamera &cam, VoiRay &q) {
-  if (v.kind == ST_PRIM_SPHERE) {
+  if (v.fam == VOI_SPHERE) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) q.w[i] = ieee_sub(v.c[i], cam.o[i]);
-  } else if (v.kind == ST_PRIM_RBOX) {
+  } else if (v.fam == VOI_BOX) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) q.w[i] = ieee_sub(cam.o[i], v.c[i]);
 #pragma unroll
@@ -212,9 +235,10 @@ __device__ __forceinline__ void voi_ray_setup(const Voi &v, const DevCamera &cam
 __device__ __forceinline__ bool voi_ray_hit(const Voi &v, const VoiRay &q, const float d[3], float &t0,
                                             float &t1) {
   bool h;
-  if (v.kind == ST_PRIM_SPHERE) h = ray_sphere32(q.w, d, v.r, t0, t1);
-  else if (v.kind == ST_PRIM_RBOX) h = ray_obox32(q.lo3, v.M, v.e, d, t0, t1);
-  else h = ray_capsule32(q.cc, d, t0, t1);
+  if (v.fam == VOI_SPHERE) h = ray_sphere32(q.w, d, v.r, t0, t1);
+  else if (v.fam == VOI_BOX) h = ray_obox32(q.lo3, v.M, v.e, d, t0, t1);
+  else if (v.fam == VOI_CAPSULE) h = ray_capsule32(q.cc, d, t0, t1);
+  else h = ray_cylinder32(q.cc, d, t0, t1);
   if (!h) return false;
   t0 = t0 > 0.0f ? t0 : 0.0f;
   return t1 >= t0;

@@ -33,8 +33,11 @@ enum ViewCode : uint32_t {
   V_UNION = 3, V_INTER = 4, V_DIFF = 5,               // compact smooth G_op
   V_SUNION = 6, V_SINTER = 7, V_SDIFF = 8,            // sharp CSG
   V_INF = 9, V_RIGHT = 10, V_LEFT = 11,               // usage rewrites (Sec. 9)
+  V_TORUS = 12, V_SCONE = 13, V_ELLIPSOID = 14,       // further primitives
 };
 constexpr uint32_t V_FIRST_OP = 3;
+// Primitive view codes (equal to the primitive kinds): 0..2 and 12..14.
+__host__ __device__ inline bool is_prim_code(uint32_t code) { return code < V_FIRST_OP || code >= V_TORUS; }
 constexpr uint32_t kViewCodeShift = 28;
 constexpr uint32_t kViewGlobal = 1u << 27;
 constexpr uint32_t kViewOffMask = (1u << 27) - 1u;
@@ -43,10 +46,23 @@ constexpr uint32_t kViewOffMask = (1u << 27) - 1u;
 //   sphere : [c, r]
 //   rbox   : [c, r_round] [M row0, b.x] [M row1, b.y] [M row2, b.z]
 //   capsule: [a, r] [b, 0] [b - a, 1/|b - a|^2]
+//   torus  : [c, r] [unit axis, R]
+//   sphere-cone: [a, r_a] [b, r_b] [u = (b - a) / h, h = |b - a|]
+//                [sin, cos, cos h, 0] (sin = (r_a - r_b) / h: the side's
+//                outward normal in the axial plane is (cos, sin))
+//   ellipsoid: [c, min r] [M row0, r0] [M row1, r1] [M row2, r2]
+//              [1/r0, 1/r1, 1/r2, 0]
 //   compact operator: [k, d_o, 6 / (6 d_o - k), 1 / k]
 //   sharp operator  : [0, 0, 0, 0]
 __host__ __device__ inline int rec_words(int kind) {
-  return kind == ST_PRIM_RBOX ? 4 : kind == ST_PRIM_CAPSULE ? 3 : 1;
+  switch (kind) {
+    case ST_PRIM_RBOX: return 4;
+    case ST_PRIM_CAPSULE: return 3;
+    case ST_PRIM_TORUS: return 2;
+    case ST_PRIM_SCONE: return 4;
+    case ST_PRIM_ELLIPSOID: return 5;
+    default: return 1;
+  }
 }
 
 // Algorithmic FP32 flop counts per node evaluation (FMA = 2), counted from
@@ -55,6 +71,9 @@ __host__ __device__ inline int rec_words(int kind) {
 constexpr uint32_t kFlopsSphere = 11;
 constexpr uint32_t kFlopsRbox = 40;
 constexpr uint32_t kFlopsCapsule = 25;
+constexpr uint32_t kFlopsTorus = 20;
+constexpr uint32_t kFlopsScone = 27;
+constexpr uint32_t kFlopsEllipsoid = 28;
 constexpr uint32_t kFlopsCompactOp = 30;
 constexpr uint32_t kFlopsSharpOp = 2;
 constexpr uint32_t kFlopsStep = 6;
@@ -133,6 +152,9 @@ struct Prep {
 int prepare(const st_scene_desc &d, Prep &p, std::string &err);
 // Record words of one primitive description record (host-side conversion).
 void prim_words(int kind, const float *q, float *words /* 4 * rec_words */);
+// Checks a primitive record's parameters; returns an error text or nullptr.
+const char *prim_record_error(int kind, const float *q);
+bool is_prim_kind(int kind);
 
 void camera_basis(const st_camera &c, DevCamera &out);
 

@@ -14,7 +14,33 @@
 
 namespace st {
 
-static bool is_prim_kind(int k) { return k == ST_PRIM_SPHERE || k == ST_PRIM_RBOX || k == ST_PRIM_CAPSULE; }
+bool is_prim_kind(int k) {
+  return k == ST_PRIM_SPHERE || k == ST_PRIM_RBOX || k == ST_PRIM_CAPSULE || k == ST_PRIM_TORUS ||
+         k == ST_PRIM_SCONE || k == ST_PRIM_ELLIPSOID;
+}
+
+const char *prim_record_error(int kind, const float *q) {
+  auto norm3 = [](const float *a) {
+    return std::sqrt((double)a[0] * a[0] + (double)a[1] * a[1] + (double)a[2] * a[2]);
+  };
+  switch (kind) {
+    case ST_PRIM_TORUS:
+      if (!(norm3(q + 3) > 0.0)) return "torus: zero axis";
+      if (!(q[6] >= 0.f) || !(q[7] > 0.f)) return "torus: needs R >= 0 and r > 0";
+      return nullptr;
+    case ST_PRIM_SCONE: {
+      const float ba[3] = {q[3] - q[0], q[4] - q[1], q[5] - q[2]};
+      if (!(q[6] >= 0.f) || !(q[7] >= 0.f) || !(q[6] + q[7] > 0.f)) return "sphere-cone: bad radii";
+      if (!(norm3(ba) > std::fabs((double)q[6] - q[7]))) return "sphere-cone: one ball inside the other";
+      return nullptr;
+    }
+    case ST_PRIM_ELLIPSOID:
+      if (!(q[12] > 0.f) || !(q[13] > 0.f) || !(q[14] > 0.f)) return "ellipsoid: radii must be > 0";
+      return nullptr;
+    default:
+      return nullptr;
+  }
+}
 static bool is_op_kind(int k) { return k >= ST_OP_UNION && k <= ST_OP_SHARP_DIFF; }
 static bool is_compact(int k) { return k == ST_OP_UNION || k == ST_OP_INTER || k == ST_OP_DIFF; }
 
@@ -40,12 +66,38 @@ void prim_words(int kind, const float *q, float *w) {
       w[4 + 4 * i + 2] = q[5 + 3 * i];
       w[4 + 4 * i + 3] = q[12 + i];
     }
-  } else {
+  } else if (kind == ST_PRIM_CAPSULE) {
     w[0] = q[0]; w[1] = q[1]; w[2] = q[2]; w[3] = q[6];
     w[4] = q[3]; w[5] = q[4]; w[6] = q[5]; w[7] = 0.f;
     float bx = q[3] - q[0], by = q[4] - q[1], bz = q[5] - q[2];
     float bb = (bx * bx + by * by) + bz * bz;
     w[8] = bx; w[9] = by; w[10] = bz; w[11] = bb > 0.f ? 1.0f / bb : 0.f;
+  } else if (kind == ST_PRIM_TORUS) {
+    // unit axis in FP64, rounded once
+    const double n = std::sqrt((double)q[3] * q[3] + (double)q[4] * q[4] + (double)q[5] * q[5]);
+    w[0] = q[0]; w[1] = q[1]; w[2] = q[2]; w[3] = q[7];
+    for (int k = 0; k < 3; ++k) w[4 + k] = (float)(q[3 + k] / n);
+    w[7] = q[6];
+  } else if (kind == ST_PRIM_SCONE) {
+    const double ba[3] = {(double)q[3] - q[0], (double)q[4] - q[1], (double)q[5] - q[2]};
+    const double h = std::sqrt(ba[0] * ba[0] + ba[1] * ba[1] + ba[2] * ba[2]);
+    const double sn = ((double)q[6] - q[7]) / h, cs = std::sqrt(1.0 - sn * sn);
+    w[0] = q[0]; w[1] = q[1]; w[2] = q[2]; w[3] = q[6];
+    w[4] = q[3]; w[5] = q[4]; w[6] = q[5]; w[7] = q[7];
+    for (int k = 0; k < 3; ++k) w[8 + k] = (float)(ba[k] / h);
+    w[11] = (float)h;
+    w[12] = (float)sn; w[13] = (float)cs; w[14] = (float)(cs * h); w[15] = 0.f;
+  } else {   // ellipsoid
+    const float rmin = std::fmin(q[12], std::fmin(q[13], q[14]));
+    w[0] = q[0]; w[1] = q[1]; w[2] = q[2]; w[3] = rmin;
+    for (int i = 0; i < 3; ++i) {
+      w[4 + 4 * i + 0] = q[3 + 3 * i];
+      w[4 + 4 * i + 1] = q[4 + 3 * i];
+      w[4 + 4 * i + 2] = q[5 + 3 * i];
+      w[4 + 4 * i + 3] = q[12 + i];
+      w[16 + i] = (float)(1.0 / (double)q[12 + i]);
+    }
+    w[19] = 0.f;
   }
 }
 
@@ -58,10 +110,28 @@ static void prim_bounds(int kind, const float *q, double lo[3], double hi[3]) {
       for (int i = 0; i < 3; ++i) e += std::fabs((double)q[3 + 3 * i + j]) * ((double)q[12 + i] + q[15]);
       lo[j] = q[j] - e; hi[j] = q[j] + e;
     }
-  } else {
+  } else if (kind == ST_PRIM_CAPSULE) {
     for (int j = 0; j < 3; ++j) {
       double a = q[j], b = q[3 + j];
       lo[j] = std::fmin(a, b) - q[6]; hi[j] = std::fmax(a, b) + q[6];
+    }
+  } else if (kind == ST_PRIM_TORUS) {
+    const double n = std::sqrt((double)q[3] * q[3] + (double)q[4] * q[4] + (double)q[5] * q[5]);
+    for (int j = 0; j < 3; ++j) {
+      const double a = q[3 + j] / n;
+      const double e = (double)q[6] * std::sqrt(std::fmax(0.0, 1.0 - a * a)) + q[7];
+      lo[j] = q[j] - e; hi[j] = q[j] + e;
+    }
+  } else if (kind == ST_PRIM_SCONE) {
+    for (int j = 0; j < 3; ++j) {
+      lo[j] = std::fmin((double)q[j] - q[6], (double)q[3 + j] - q[7]);
+      hi[j] = std::fmax((double)q[j] + q[6], (double)q[3 + j] + q[7]);
+    }
+  } else {   // ellipsoid: inside its oriented box of half extents r
+    for (int j = 0; j < 3; ++j) {
+      double e = 0;
+      for (int i = 0; i < 3; ++i) e += std::fabs((double)q[3 + 3 * i + j]) * q[12 + i];
+      lo[j] = q[j] - e; hi[j] = q[j] + e;
     }
   }
 }
@@ -78,6 +148,10 @@ int prepare(const st_scene_desc &d, Prep &p, std::string &err) {
     int k = d.kind[i];
     if (is_prim_kind(k)) {
       if (d.left[i] != -1 || d.right[i] != -1) return fail("primitive with children");
+      if (const char *e = prim_record_error(k, d.params + (size_t)i * ST_REC_FLOATS)) {
+        std::ostringstream s; s << "node " << i << ": " << e;
+        return fail(s.str());
+      }
       ++n_prims;
       continue;
     }
@@ -231,7 +305,7 @@ int prepare(const st_scene_desc &d, Prep &p, std::string &err) {
     const float *q = d.params + (size_t)i * ST_REC_FLOATS;
     p.rec_off[a] = (uint32_t)(p.rec.size() / 4);
     if (is_prim_kind(k)) {
-      float w[16];
+      float w[20];
       prim_words(k, q, w);
       p.rec.insert(p.rec.end(), w, w + 4 * rec_words(k));
       p.prim_index[a] = (uint32_t)p.prim_addr.size();

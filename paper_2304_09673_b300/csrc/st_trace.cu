@@ -469,6 +469,9 @@ __device__ __forceinline__ int code_words(uint32_t code) {
     case V_SPHERE: return 1;
     case V_RBOX: return 4;
     case V_CAPSULE: return 3;
+    case V_TORUS: return 2;
+    case V_SCONE: return 4;
+    case V_ELLIPSOID: return 5;
     case V_UNION: case V_INTER: case V_DIFF: return 1;
     default: return 0;
   }
@@ -527,7 +530,7 @@ __device__ __forceinline__ int build_schedule(const uint32_t *view, int n_view, 
   // pass 1: heights and level counts (stack entry: index | level << 16)
   for (int i = 0; i < n_view; ++i) {
     const uint32_t code = view[i] >> kViewCodeShift;
-    if (code < V_FIRST_OP) {
+    if (is_prim_code(code)) {
       if (sp >= stack_cap) return 0;
       bstk[sp++] = (uint32_t)i;
     } else {
@@ -551,7 +554,7 @@ __device__ __forceinline__ int build_schedule(const uint32_t *view, int n_view, 
   sp = 0;
   for (int i = 0; i < n_view; ++i) {
     const uint32_t code = view[i] >> kViewCodeShift;
-    if (code < V_FIRST_OP) {
+    if (is_prim_code(code)) {
       bstk[sp++] = (uint32_t)i;
     } else {
       const uint32_t r = bstk[--sp], l = bstk[--sp];
@@ -704,12 +707,17 @@ __device__ __forceinline__ float tail_eval(const uint32_t *view, int n_view, con
   for (int i = lane; i < n_view; i += 32) {
     const uint32_t w = view[i];
     const uint32_t code = w >> kViewCodeShift;
-    if (code >= V_FIRST_OP) continue;
+    if (!is_prim_code(code)) continue;
     const float4 *q = rec_ptr(src, w);
     float v;
-    if (code == V_SPHERE) v = sd_sphere<float>(ldrec(q), p);
-    else if (code == V_RBOX) v = sd_rbox<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p);
-    else v = sd_capsule<float>(ldrec(q), ldrec(q + 2), p);
+    switch (code) {
+      case V_SPHERE: v = sd_sphere<float>(ldrec(q), p); break;
+      case V_RBOX: v = sd_rbox<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p); break;
+      case V_CAPSULE: v = sd_capsule<float>(ldrec(q), ldrec(q + 2), p); break;
+      case V_TORUS: v = sd_torus<float>(ldrec(q), ldrec(q + 1), p); break;
+      case V_SCONE: v = sd_scone<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p); break;
+      default: v = sd_ellipsoid<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), ldrec(q + 4), p); break;
+    }
     vals[i] = v;
   }
   __syncwarp();
