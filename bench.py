@@ -335,7 +335,7 @@ def run_ours(args):
     opts = mode_opts(st, head, mlp, args.max_new)
     ids = np.flatnonzero(scene.kind < 16).astype(np.int32)
     params = np.ascontiguousarray(scene.params[ids])
-    words = {0: 1, 1: 4, 2: 3}
+    words = {0: 1, 1: 4, 2: 3, 12: 2, 13: 4, 14: 5}   # record words per primitive kind
     h2d = int(sum(words[int(k)] for k in scene.kind[ids]) * 20)
     host = dict(depth=torch.empty(H * W, dtype=torch.float32, pin_memory=True),
                 normal=torch.empty(H * W * 3, dtype=torch.float32, pin_memory=True),

@@ -127,9 +127,7 @@ __device__ __forceinline__ T prim_value(const DevScene &sc, uint32_t a, uint32_t
     case ST_PRIM_SPHERE: return sd_sphere<T>(q[0], p);
     case ST_PRIM_RBOX: return sd_rbox<T>(q[0], q[1], q[2], q[3], p);
     case ST_PRIM_CAPSULE: return sd_capsule<T>(q[0], q[2], p);
-    case ST_PRIM_TORUS: return sd_torus<T>(q[0], q[1], p);
-    case ST_PRIM_SCONE: return sd_scone<T>(q[0], q[1], q[2], q[3], p);
-    default: return sd_ellipsoid<T>(q[0], q[1], q[2], q[3], q[4], p);
+    default: return sd_further<T>(kind, q, p[0], p[1], p[2]);
   }
 }
 

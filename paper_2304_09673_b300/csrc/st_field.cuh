@@ -204,6 +204,18 @@ __device__ __forceinline__ T sd_ellipsoid(const float4 a0, const float4 a1, cons
   return fma_(s, a0.w, -a0.w);
 }
 
+// The further families out of line: one copy per value type instead of one
+// per interpreter instantiation and call site, so scenes without them keep
+// the interpreter's code (and instruction-fetch footprint) of the three
+// basic families.
+template <class T>
+__device__ __noinline__ T sd_further(uint32_t code, const float4 *q, T px, T py, T pz) {
+  const T p[3] = {px, py, pz};
+  if (code == V_TORUS) return sd_torus<T>(ldrec(q), ldrec(q + 1), p);
+  if (code == V_SCONE) return sd_scone<T>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p);
+  return sd_ellipsoid<T>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), ldrec(q + 4), p);
+}
+
 // ---- compact smooth operators G_op (Sec. 5) -------------------------------------
 // Record [k, d_o, c1 = 6 / (6 d_o - k), 1/k].  Smooth displacement of Eq. 5:
 // d(f0, f1, k) = k/6 max(1 - a/k, 0)^3 with a = |f0 - f1|; transition
@@ -303,25 +315,10 @@ __device__ __forceinline__ void eval_view_r(const uint32_t *view, int n_view, co
         for (int r = 0; r < R; ++r) acc[r] = sd_capsule<T>(a0, a2, p[r]);
         break;
       }
-      case V_TORUS: {
-        const float4 a0 = ldrec(q), a1 = ldrec(q + 1);
+      case V_TORUS: case V_SCONE: case V_ELLIPSOID: {
         stk.push(sp++, acc);
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = sd_torus<T>(a0, a1, p[r]);
-        break;
-      }
-      case V_SCONE: {
-        const float4 a0 = ldrec(q), a1 = ldrec(q + 1), a2 = ldrec(q + 2), a3 = ldrec(q + 3);
-        stk.push(sp++, acc);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = sd_scone<T>(a0, a1, a2, a3, p[r]);
-        break;
-      }
-      case V_ELLIPSOID: {
-        const float4 a0 = ldrec(q), a1 = ldrec(q + 1), a2 = ldrec(q + 2), a3 = ldrec(q + 3), a4 = ldrec(q + 4);
-        stk.push(sp++, acc);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = sd_ellipsoid<T>(a0, a1, a2, a3, a4, p[r]);
+        for (int r = 0; r < R; ++r) acc[r] = sd_further<T>(code, q, p[r][0], p[r][1], p[r][2]);
         break;
       }
       case V_UNION: case V_INTER: case V_DIFF: {

@@ -163,16 +163,23 @@ __device__ __forceinline__ void load_voi(const DevScene &sc, uint32_t j, Voi &v)
   if (kind == ST_PRIM_SPHERE) {
     v.fam = VOI_SPHERE;
     v.r = ieee_add(ieee_add(w0.w, dp), pad);
-  } else if (kind == ST_PRIM_RBOX || kind == ST_PRIM_ELLIPSOID) {
+  } else if (kind == ST_PRIM_RBOX) {
     v.fam = VOI_BOX;
     const float rr = w0.w;
-    const float grow = ieee_add(1.0f, ieee_div(dp, rr));   // ellipsoid: rr = min r
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       float4 m = w[1 + i];
       v.M[3 * i] = m.x; v.M[3 * i + 1] = m.y; v.M[3 * i + 2] = m.z;
-      v.e[i] = kind == ST_PRIM_RBOX ? ieee_add(ieee_add(ieee_add(m.w, rr), dp), pad)
-                                    : ieee_add(ieee_mul(m.w, grow), pad);
+      v.e[i] = ieee_add(ieee_add(ieee_add(m.w, rr), dp), pad);
+    }
+  } else if (kind == ST_PRIM_ELLIPSOID) {
+    v.fam = VOI_BOX;
+    const float grow = ieee_add(1.0f, ieee_div(dp, w0.w));   // w0.w = min r
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float4 m = w[1 + i];
+      v.M[3 * i] = m.x; v.M[3 * i + 1] = m.y; v.M[3 * i + 2] = m.z;
+      v.e[i] = ieee_add(ieee_mul(m.w, grow), pad);
     }
   } else if (kind == ST_PRIM_TORUS) {
     v.fam = VOI_CYLINDER;

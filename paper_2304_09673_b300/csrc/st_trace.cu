@@ -714,9 +714,7 @@ __device__ __forceinline__ float tail_eval(const uint32_t *view, int n_view, con
       case V_SPHERE: v = sd_sphere<float>(ldrec(q), p); break;
       case V_RBOX: v = sd_rbox<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p); break;
       case V_CAPSULE: v = sd_capsule<float>(ldrec(q), ldrec(q + 2), p); break;
-      case V_TORUS: v = sd_torus<float>(ldrec(q), ldrec(q + 1), p); break;
-      case V_SCONE: v = sd_scone<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p); break;
-      default: v = sd_ellipsoid<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), ldrec(q + 4), p); break;
+      default: v = sd_further<float>(code, q, p[0], p[1], p[2]); break;
     }
     vals[i] = v;
   }
