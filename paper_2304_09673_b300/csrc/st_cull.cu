@@ -35,9 +35,10 @@ __device__ __forceinline__ int find_job_prim(const Job *jobs, int n_jobs, uint32
   return lo;
 }
 
-// Conservative tile rectangle of a sphere (centre C, radius rho) in view.
-__device__ void sphere_tile_rect(const DevCamera &cam, int tile, int tiles_x, int tiles_y,
-                                 const float C[3], float rho, int4 &rect) {
+// Conservative pixel rectangle of a sphere (centre C, radius rho) in view:
+// returns 0 when it is off screen or behind the eye, 2 when it straddles the
+// eye plane (whole screen), 1 with the rectangle [x0, x1] x [y0, y1].
+__device__ int sphere_pixel_rect(const DevCamera &cam, const float C[3], float rho, int4 &px) {
   rho = rho * 1.001f + 1e-4f;
   float w[3] = {C[0] - cam.o[0], C[1] - cam.o[1], C[2] - cam.o[2]};
   float lr = sqrtf(cam.R[0] * cam.R[0] + cam.R[1] * cam.R[1] + cam.R[2] * cam.R[2]);
@@ -45,9 +46,8 @@ __device__ void sphere_tile_rect(const DevCamera &cam, int tile, int tiles_x, in
   float z = w[0] * cam.F[0] + w[1] * cam.F[1] + w[2] * cam.F[2];
   float x = (w[0] * cam.R[0] + w[1] * cam.R[1] + w[2] * cam.R[2]) / lr;
   float y = (w[0] * cam.U[0] + w[1] * cam.U[1] + w[2] * cam.U[2]) / lu;
-  rect = make_int4(0, 0, tiles_x - 1, tiles_y - 1);
-  if (z < -rho) { rect = make_int4(1, 1, 0, 0); return; }  // behind the eye
-  if (z <= rho * 1.01f) return;                              // straddles the eye plane
+  if (z < -rho) return 0;              // behind the eye
+  if (z <= rho * 1.01f) return 2;      // straddles the eye plane
   float zz = z * z - rho * rho;
   float sx = sqrtf(fmaxf(x * x + zz, 0.f)), sy = sqrtf(fmaxf(y * y + zz, 0.f));
   float mx0 = (x * z - rho * sx) / zz, mx1 = (x * z + rho * sx) / zz;
@@ -59,14 +59,47 @@ __device__ void sphere_tile_rect(const DevCamera &cam, int tile, int tiles_x, in
   float j0 = ((1.f - v1) * cam.H - 1.f) * 0.5f, j1 = ((1.f - v0) * cam.H - 1.f) * 0.5f;
   float fi0 = floorf(i0) - 1.f, fi1 = ceilf(i1) + 1.f;
   float fj0 = floorf(j0) - 1.f, fj1 = ceilf(j1) + 1.f;
-  if (fi1 < 0.f || fj1 < 0.f || fi0 > (float)(cam.W - 1) || fj0 > (float)(cam.H - 1)) {
-    rect = make_int4(1, 1, 0, 0);
-    return;
+  if (fi1 < 0.f || fj1 < 0.f || fi0 > (float)(cam.W - 1) || fj0 > (float)(cam.H - 1)) return 0;
+  px.x = fi0 < 0.f ? 0 : (int)fi0;
+  px.y = fj0 < 0.f ? 0 : (int)fj0;
+  px.z = fi1 > (float)(cam.W - 1) ? cam.W - 1 : (int)fi1;
+  px.w = fj1 > (float)(cam.H - 1) ? cam.H - 1 : (int)fj1;
+  return 1;
+}
+
+// Conservative pixel rectangle of the points c +- e0 a0 +- e1 a1 +- e2 a2 (a
+// box's corners; its projection is their convex hull when all lie in front
+// of the eye): 0 off screen, 2 unusable (a corner near or behind the eye
+// plane), 1 with the rectangle.
+__device__ int box_pixel_rect(const DevCamera &cam, const Voi &v, int4 &px) {
+  const float lr2 = cam.R[0] * cam.R[0] + cam.R[1] * cam.R[1] + cam.R[2] * cam.R[2];
+  const float lu2 = cam.U[0] * cam.U[0] + cam.U[1] * cam.U[1] + cam.U[2] * cam.U[2];
+  float imin = INFINITY, imax = -INFINITY, jmin = INFINITY, jmax = -INFINITY;
+  for (int k = 0; k < 8; ++k) {
+    float w[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      w[q] = v.c[q] - cam.o[q];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) w[q] += ((k >> i) & 1 ? v.e[i] : -v.e[i]) * v.M[3 * i + q];
+    }
+    const float z = w[0] * cam.F[0] + w[1] * cam.F[1] + w[2] * cam.F[2];
+    if (!(z > 1e-3f)) return 2;
+    const float u = (w[0] * cam.R[0] + w[1] * cam.R[1] + w[2] * cam.R[2]) / (lr2 * z);
+    const float vv = (w[0] * cam.U[0] + w[1] * cam.U[1] + w[2] * cam.U[2]) / (lu2 * z);
+    const float i = ((u + 1.f) * cam.W - 1.f) * 0.5f, j = ((1.f - vv) * cam.H - 1.f) * 0.5f;
+    imin = fminf(imin, i); imax = fmaxf(imax, i);
+    jmin = fminf(jmin, j); jmax = fmaxf(jmax, j);
   }
-  int px0 = fi0 < 0.f ? 0 : (int)fi0, py0 = fj0 < 0.f ? 0 : (int)fj0;
-  int px1 = fi1 > (float)(cam.W - 1) ? cam.W - 1 : (int)fi1;
-  int py1 = fj1 > (float)(cam.H - 1) ? cam.H - 1 : (int)fj1;
-  rect = make_int4(px0 / tile, py0 / tile, px1 / tile, py1 / tile);
+  // one pixel plus a relative margin for rounding
+  const float mi = 1.f + 1e-4f * (fabsf(imin) + fabsf(imax)), mj = 1.f + 1e-4f * (fabsf(jmin) + fabsf(jmax));
+  const float fi0 = floorf(imin - mi), fi1 = ceilf(imax + mi), fj0 = floorf(jmin - mj), fj1 = ceilf(jmax + mj);
+  if (fi1 < 0.f || fj1 < 0.f || fi0 > (float)(cam.W - 1) || fj0 > (float)(cam.H - 1)) return 0;
+  px.x = fi0 < 0.f ? 0 : (int)fi0;
+  px.y = fj0 < 0.f ? 0 : (int)fj0;
+  px.z = fi1 > (float)(cam.W - 1) ? cam.W - 1 : (int)fi1;
+  px.w = fj1 > (float)(cam.H - 1) ? cam.H - 1 : (int)fj1;
+  return 1;
 }
 
 }  // namespace
@@ -80,20 +113,50 @@ __global__ void k_prim_bounds(const Job *jobs, int n_jobs, uint32_t n_prims_tota
   uint32_t j = g - job.prim_base;
   Voi v;
   load_voi(job.sc, j, v);
-  float C[3], rho;
+  // Pixel rectangle of the volume of interest: its own projection where it
+  // is cheap (box corners; capsule and cylinder as the union of their end
+  // spheres), else that of a bounding sphere.
+  const DevCamera &cam = job.cam;
+  int4 px = make_int4(0, 0, cam.W - 1, cam.H - 1);
+  int st;
   if (v.fam == VOI_SPHERE) {
-    C[0] = v.c[0]; C[1] = v.c[1]; C[2] = v.c[2];
-    rho = v.r;
+    st = sphere_pixel_rect(cam, v.c, v.r, px);
   } else if (v.fam == VOI_BOX) {
-    C[0] = v.c[0]; C[1] = v.c[1]; C[2] = v.c[2];
-    rho = sqrtf(v.e[0] * v.e[0] + v.e[1] * v.e[1] + v.e[2] * v.e[2]);
-  } else {   // capsule and cylinder: the capsule's bounding sphere holds both
-    float h[3] = {0.5f * (v.b[0] - v.c[0]), 0.5f * (v.b[1] - v.c[1]), 0.5f * (v.b[2] - v.c[2])};
-    C[0] = v.c[0] + h[0]; C[1] = v.c[1] + h[1]; C[2] = v.c[2] + h[2];
-    rho = sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]) + v.r;
+    st = box_pixel_rect(cam, v, px);
+    if (st == 2) {
+      const float rho = sqrtf(v.e[0] * v.e[0] + v.e[1] * v.e[1] + v.e[2] * v.e[2]);
+      st = sphere_pixel_rect(cam, v.c, rho, px);
+    }
+  } else {
+    int4 pa, pb;
+    const int sa = sphere_pixel_rect(cam, v.c, v.r, pa), sb = sphere_pixel_rect(cam, v.b, v.r, pb);
+    if (sa == 2 || sb == 2) {
+      st = 2;
+    } else if (sa == 0 && sb == 0) {
+      // both end spheres off screen: the segment between them may still cross it
+      const float h[3] = {0.5f * (v.b[0] - v.c[0]), 0.5f * (v.b[1] - v.c[1]), 0.5f * (v.b[2] - v.c[2])};
+      const float C[3] = {v.c[0] + h[0], v.c[1] + h[1], v.c[2] + h[2]};
+      st = sphere_pixel_rect(cam, C, sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]) + v.r, px);
+    } else {
+      // the hull of the two spheres projects inside the union of their
+      // rectangles extended to each other
+      if (sa == 0) pa = pb;
+      if (sb == 0) pb = pa;
+      if (sa == 0 || sb == 0) {
+        const float h[3] = {0.5f * (v.b[0] - v.c[0]), 0.5f * (v.b[1] - v.c[1]), 0.5f * (v.b[2] - v.c[2])};
+        const float C[3] = {v.c[0] + h[0], v.c[1] + h[1], v.c[2] + h[2]};
+        st = sphere_pixel_rect(cam, C, sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]) + v.r, px);
+      } else {
+        px = make_int4(min(pa.x, pb.x), min(pa.y, pb.y), max(pa.z, pb.z), max(pa.w, pb.w));
+        st = 1;
+      }
+    }
   }
+  const int T = job.tl.tile;
   int4 rect;
-  sphere_tile_rect(job.cam, job.tl.tile, job.tl.tiles_x, job.tl.tiles_y, C, rho, rect);
+  if (st == 0) rect = make_int4(1, 1, 0, 0);
+  else if (st == 2) rect = make_int4(0, 0, job.tl.tiles_x - 1, job.tl.tiles_y - 1);
+  else rect = make_int4(px.x / T, px.y / T, px.z / T, px.w / T);
   uint32_t n = 0;
   if (rect.z >= rect.x && rect.w >= rect.y) n = (uint32_t)(rect.z - rect.x + 1) * (uint32_t)(rect.w - rect.y + 1);
   cand_count[g] = n;
