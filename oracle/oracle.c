@@ -957,6 +957,11 @@ static void finish_ray(const Tree *t, const Cam *c, const double d[3], double dn
     for (int k = 0; k < 3; ++k) normal[k] = gn > 0 ? g[k] / gn : 0.0;
 }
 
+/* Rays start at planar depth Z_NEAR (the near plane).  A ray whose first
+ * sample there is inside the solid (f < -eps: the eye is inside the shape) is
+ * a hit clipped at the near plane, with no refinement. */
+#define Z_NEAR 0.01
+
 /* Per pixel (i, j):  z starts at z_near and advances by f / (L |d|) until
  * f <= eps (hit), z > z_far (miss: exit of the bounding sphere of the
  * primitives' bounds) or max_steps.  A hit is refined by up to `newton`
@@ -988,22 +993,23 @@ void or_trace(int n, int root, const int32_t *kind, const int32_t *left, const i
         double t0, t1, mf = INFINITY;
         int st = 0;
         uint8_t fl = 0;
-        double z = 0.01, f = INFINITY;
+        double z = Z_NEAR, f = INFINITY;
+        int clip = 0;
         if (ray_sphere64(c.o, d, bc, br, &t0, &t1) && t1 > z) {
             if (t0 > z) z = t0;
             double zfar = t1;
             for (;;) {
                 f = field_at(&t, c.o, d, z);
                 if (f < mf) mf = f;
-                if (f <= eps) { fl |= 1; break; }
+                if (f <= eps) { fl |= 1; clip = st == 0 && z == Z_NEAR && f < -eps; break; }
                 if (st >= max_steps) { fl |= 2; break; }
                 ++st;
                 z += f / (lipschitz * dn);
                 if (z > zfar) break;
             }
         }
-        finish_ray(&t, &c, d, dn, z, fl & 1, newton, newton_clamp, depth + px, normal + 3 * (size_t)px,
-                   resid + px);
+        finish_ray(&t, &c, d, dn, z, fl & 1, clip ? 0 : newton, newton_clamp, depth + px,
+                   normal + 3 * (size_t)px, resid + px);
         steps[px] = st;
         flags[px] = fl;
         min_f[px] = mf;
@@ -1018,14 +1024,15 @@ void or_trace(int n, int root, const int32_t *kind, const int32_t *left, const i
  * whereupon the ray jumps across it (the sphere is free of surface).  No
  * step cap; instead every step is at least min_step long (distance units),
  * and a hit is the first sample with f <= 0 (iso-crossing detection), then
- * refined and shaded as in or_trace.
+ * refined and shaded as in or_trace (a first sample inside the solid at the
+ * near plane with f < -eps is a clipped hit there, as in or_trace).
  * Readings where Sec. 10 is silent: a plain or minimum-length step is never
  * undone (only relaxed steps are tested); an undone step whose end point lies
  * inside the solid (f <= 0) stores no sphere to jump across (a crossing lies
  * before it, which plain steps will bracket).  max_steps only guards against
  * a broken field (flag bit1); steps counts field evaluations. */
 void or_trace_relaxed(int n, int root, const int32_t *kind, const int32_t *left, const int32_t *right,
-                      const float *params, const float *cam, double lipschitz, double omega,
+                      const float *params, const float *cam, double eps, double lipschitz, double omega,
                       double min_step, int max_steps, int newton, double newton_clamp, int npx,
                       const int32_t *pi, const int32_t *pj, double *depth, double *normal,
                       int32_t *steps, uint8_t *flags, double *min_f, double *resid) {
@@ -1046,7 +1053,8 @@ void or_trace_relaxed(int n, int root, const int32_t *kind, const int32_t *left,
         double t0, t1, mf = INFINITY;
         int st = 0;
         uint8_t fl = 0;
-        double z = 0.01;
+        int clip = 0;
+        double z = Z_NEAR;
         if (ray_sphere64(c.o, d, bc, br, &t0, &t1) && t1 > z) {
             if (t0 > z) z = t0;
             double zfar = t1;
@@ -1071,7 +1079,7 @@ void or_trace_relaxed(int n, int root, const int32_t *kind, const int32_t *left,
                     if (z > zfar) break;
                     continue;
                 }
-                if (f <= 0.0) { fl |= 1; break; }
+                if (f <= 0.0) { fl |= 1; clip = st == 1 && z == Z_NEAR && f < -eps; break; }
                 double om = relax ? omega : 1.0;
                 double dz = om * r;
                 if (dz <= h) { dz = h; om = 1.0; }
@@ -1088,8 +1096,8 @@ void or_trace_relaxed(int n, int root, const int32_t *kind, const int32_t *left,
                 if (z > zfar) break;
             }
         }
-        finish_ray(&t, &c, d, dn, z, fl & 1, newton, newton_clamp, depth + px, normal + 3 * (size_t)px,
-                   resid + px);
+        finish_ray(&t, &c, d, dn, z, fl & 1, clip ? 0 : newton, newton_clamp, depth + px,
+                   normal + 3 * (size_t)px, resid + px);
         steps[px] = st;
         flags[px] = fl;
         min_f[px] = mf;

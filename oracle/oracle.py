@@ -69,7 +69,7 @@ def _declare(L):
     L.or_cull.restype = I
     L.or_trace.argtypes = [I, I, P, P, P, P, P, D, D, I, I, D, I, P, P, P, P, P, P, P, P]
     L.or_trace.restype = None
-    L.or_trace_relaxed.argtypes = [I, I, P, P, P, P, P, D, D, D, I, I, D, I, P, P, P, P, P, P, P, P]
+    L.or_trace_relaxed.argtypes = [I, I, P, P, P, P, P, D, D, D, D, I, I, D, I, P, P, P, P, P, P, P, P]
     L.or_trace_relaxed.restype = None
     L.or_march.argtypes = [I, I, P, P, P, P, P, D, I, P, P, P, P]
     L.or_march.restype = None
@@ -237,10 +237,11 @@ def min_step_default(scene) -> float:
 
 def trace_relaxed(scene, cam, pi=None, pj=None, lipschitz: float = LIPSCHITZ, omega: float = 1.7,
                   min_step: float | None = None, max_steps: int = 10_000_000, newton: int = 4,
-                  newton_clamp: float = 64 * EPS):
+                  newton_clamp: float = 64 * EPS, eps: float = EPS):
     """Sec. 10's ray processing (over-relaxation with sphere reuse, minimum
     step, hit at the first f <= 0) over the dense FP64 field, for the pixels
-    (pi, pj) (all if None).  Returns the same dict as trace()."""
+    (pi, pj) (all if None); eps only sets the near-plane clip of rays that
+    start inside the solid.  Returns the same dict as trace()."""
     if pi is None:
         jj, ii = np.mgrid[0:cam.height, 0:cam.width]
         pi, pj = ii.reshape(-1), jj.reshape(-1)
@@ -257,7 +258,7 @@ def trace_relaxed(scene, cam, pi=None, pj=None, lipschitz: float = LIPSCHITZ, om
     resid = np.empty(n, np.float64)
     keep, sa = _scene_args(scene)
     ca = cam_array(cam)
-    lib().or_trace_relaxed(*sa, _p(ca), lipschitz, omega, min_step, max_steps, newton, newton_clamp, n,
+    lib().or_trace_relaxed(*sa, _p(ca), eps, lipschitz, omega, min_step, max_steps, newton, newton_clamp, n,
                            _p(pi), _p(pj), _p(depth), _p(normal), _p(steps), _p(flags), _p(min_f), _p(resid))
     return dict(depth=depth, normal=normal, steps=steps, flags=flags, min_f=min_f, resid=resid,
                 pi=pi, pj=pj)

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(128) k_trace_dexel(Job job, DexelLaunch D) {
     uint32_t nxt = beg, steps = 0;
     int n_act = 0;
     int result = 0;   // 0 miss, 1 hit, 2 step cap
-    float z = 0.f, zend = 0.f, zz = 0.f, g[3] = {0.f, 0.f, 0.f};
+    float z = kZNear, zend = 0.f, zz = 0.f, g[3] = {0.f, 0.f, 0.f};
     while (result == 0) {
       // The subinterval rule of Sec. 8 on the ray's own list: drop fragments
       // that end at or before the previous end, then fetch (up to max_new
@@ -353,6 +353,8 @@ __global__ void __launch_bounds__(128) k_trace_dexel(Job job, DexelLaunch D) {
         SparseCount cnt;
         const Dual<1> fd = eval_sparse<kFast, Dual<1>>(sc, act, n_act, pd, cnt);
         c_err |= cnt.err;
+        // a first sample inside the solid at the near plane: clipped hit
+        if (it == 0 && zz <= kZNear && fd.v < -eps) break;
         beyond = false;
         if (fd.g[0] != 0.f && isfinite(fd.v)) {
           float step = -fd.v / fd.g[0];

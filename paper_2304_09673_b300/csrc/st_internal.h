@@ -78,6 +78,11 @@ constexpr uint32_t kFlopsCompactOp = 30;
 constexpr uint32_t kFlopsSharpOp = 2;
 constexpr uint32_t kFlopsStep = 6;
 
+// Near plane: rays start at planar depth kZNear; a ray whose first sample
+// there is inside the solid (f < -eps) is a hit clipped at the near plane
+// (depth kZNear |d|, no refinement).
+constexpr float kZNear = 0.01f;
+
 // ---- device views of a scene, camera, A-buffer and outputs ---------------------
 struct DevScene {
   const uint32_t *blob;      // [n_nodes] packed node words, post-order

@@ -1259,6 +1259,8 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
       }
       eval_view_r<1, Dual<1>>(view, inf.n_view, src, pd, fd, stk);
       if (newton) {
+        // a first sample inside the solid at the near plane: clipped hit
+        if (it == 0 && zz <= kZNear && fd[0].v < -M.tp->eps) done = true;
         if (!done) {
           ++n_eval;
           beyond = false;
@@ -1374,7 +1376,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     uint32_t s_sub = 0, s_maxview = 0;
 
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-      C.ray_z[r] = 0.f;
+      C.ray_z[r] = kZNear;
       C.ray_st[r] = 0u;
       pick(C.alive, 0)[r] = (uint16_t)r;
     }
