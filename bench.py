@@ -667,7 +667,7 @@ def main():
     ap.add_argument("--workload", default="1080p")
     ap.add_argument("--modes", default="learned,plain,overrelax,crossing",
                     help="step modes to time; the first one is the headline value")
-    ap.add_argument("--max-new", type=int, default=24, help="new primitives per subfrustum")
+    ap.add_argument("--max-new", type=int, default=32, help="new primitives per subfrustum")
     ap.add_argument("--batch-scenes", type=int, default=64, help="scenes of the batch64 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

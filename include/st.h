@@ -153,7 +153,8 @@ typedef struct {
                                scene diameter measured at st_scene_create
                                (edits keep it) [0.05 = 1:20, Sec. 8]       */
     int32_t max_new_per_turn; /* new primitives fetched per subfrustum, at
-                                 most 32 [24; Sec. 8 uses 6]            */
+                                 most 1024; a tile takes at least an eighth
+                                 of its list per turn [32; Sec. 8 uses 6] */
     int32_t newton_iters;   /* Newton refinements of a hit [4]             */
     float newton_clamp;     /* Newton step bound, distance units [64 eps]  */
     const void *mlp;        /* ST_STEP_LEARNED: device pointer (16-byte
@@ -273,7 +274,7 @@ int st_tiles_copy(const st_tiles *tiles, uint32_t *offsets, float *z_in, float *
  * st_tune_load / st_tune_store: look up / insert-or-replace one entry of
  * the cache file (host only; store rewrites the whole file).  load returns
  * ST_ERR_INVALID when the file or key is absent or malformed.
- * st_autotune: times every candidate (tile 8/16/32 x max_new 12/24/32 x
+ * st_autotune: times every candidate (tile 8/16/32 x max_new 16/32/64 x
  * depth slab 0.05/0.15 of the scene diameter) on `scene` seen by `cam`
  * with `opts` (1 untimed + 2 timed runs each, CUDA events on `stream`),
  * writes the fastest to *out and, when cache_path is not NULL, stores it.

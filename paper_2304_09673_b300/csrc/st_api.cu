@@ -390,7 +390,7 @@ TraceParams make_trace_params(const st_trace_opts &o, double diameter, double ex
   tp.step_mode = o.step_mode;
   const float frac = o.depth_slab_frac > 0.f ? o.depth_slab_frac : 0.05f;
   tp.depth_slab = std::max(frac * (float)diameter, 1e-6f);
-  tp.max_new = o.max_new_per_turn > 0 ? std::min(o.max_new_per_turn, 32) : 24;
+  tp.max_new = o.max_new_per_turn > 0 ? std::min(o.max_new_per_turn, 1024) : 32;
   tp.newton_iters = o.newton_iters > 0 ? o.newton_iters : (o.newton_iters < 0 ? 0 : 4);
   tp.newton_clamp = o.newton_clamp > 0.f ? o.newton_clamp : 64.f * tp.eps;
   tp.omega = o.omega > 1.f ? std::min(o.omega, 2.f) : 1.7f;

@@ -96,7 +96,7 @@ struct Json {
 
 bool parse_tune(Json &j, st_tune &t) {
   if (!j.lit('{')) return false;
-  t.tile = 16; t.max_new_per_turn = 24; t.depth_slab_frac = 0.05f; t.ms = 0.f;
+  t.tile = 16; t.max_new_per_turn = 32; t.depth_slab_frac = 0.05f; t.ms = 0.f;
   if (j.lit('}')) return true;
   for (;;) {
     std::string k;
@@ -170,7 +170,7 @@ bool write_cache(const char *path, const std::map<std::string, st_tune> &m) {
 }
 
 bool valid_tune(const st_tune &t) {
-  return (t.tile == 8 || t.tile == 16 || t.tile == 32) && t.max_new_per_turn >= 1 && t.max_new_per_turn <= 32 &&
+  return (t.tile == 8 || t.tile == 16 || t.tile == 32) && t.max_new_per_turn >= 1 && t.max_new_per_turn <= 1024 &&
          t.depth_slab_frac > 0.f && std::isfinite(t.depth_slab_frac);
 }
 
@@ -467,7 +467,7 @@ int st_autotune(st_scene *scene, const st_camera *cam, const st_trace_opts *opts
   BK(cudaEventCreate(&e0));
   BK(cudaEventCreate(&e1));
   const int tiles[3] = {8, 16, 32};
-  const int news[3] = {12, 24, 32};
+  const int news[3] = {16, 32, 64};
   const float slabs[2] = {0.05f, 0.15f};
   st_tune best{16, 24, 0.05f, INFINITY};
   int rc = ST_OK;
@@ -560,7 +560,7 @@ int st_batch_create(st_scene *const *scenes, const st_camera *cams, int n, const
     b->normal.push_back(normal[i]);
     b->evals.push_back(evals[i]);
     b->flags.push_back(flags[i]);
-    st_tune t{16, o.max_new_per_turn > 0 ? std::min(o.max_new_per_turn, 32) : 24,
+    st_tune t{16, o.max_new_per_turn > 0 ? std::min(o.max_new_per_turn, 1024) : 32,
               o.depth_slab_frac > 0.f ? o.depth_slab_frac : 0.05f, 0.f};
     if (autotune_cache) {
       DevScene sc;

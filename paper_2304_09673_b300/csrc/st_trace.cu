@@ -621,11 +621,19 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
   info.z_begin = info.z_end = sg.z_end;
   if (!info.done) {
     // ---- fetch (no empty space, depth slab d, max new per turn; no overlap cap) ----
+    // Candidates are examined 32 at a time (one per lane) until a condition
+    // fails or max_new have been taken.  A tile takes at least an eighth of
+    // its list per turn: long lists (clustered primitives) otherwise split
+    // into many subfrustums, each marching over a large view (measured on
+    // B300: 10k clustered primitives 2.1x faster at 1920x1080, 2.8x at
+    // 3840x2160; no change on short lists).
     float z_begin = sg.z_end;
-    if (sg.next < len) {
-      z_begin = fmaxf(sg.z_end, __ldg(zin_l + sg.next));
+    if (sg.next < len) z_begin = fmaxf(sg.z_end, __ldg(zin_l + sg.next));
+    const int max_new = max(tp.max_new, (int)(len >> 3));
+    for (int fetched = 0; sg.next < len && fetched < max_new;) {
+      const int quota = min(32, max_new - fetched);
       const uint32_t c = sg.next + (uint32_t)lane;
-      const bool valid = lane < tp.max_new && c < len;
+      const bool valid = lane < quota && c < len;
       const float zb = valid ? __ldg(zin_l + c) : INFINITY;
       const float ze = valid ? __ldg(zout_l + c) : -INFINITY;
       const uint32_t pa = valid ? __ldg(prim_l + c) : 0xFFFFFFFFu;
@@ -672,6 +680,9 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
       sg.n_act += take;
       sg.cur ^= 1;
       sg.next += (uint32_t)take;
+      fetched += take;
+      __syncwarp();
+      if (take < quota) break;
     }
     sg.z_end = sg.next < len ? fminf(__ldg(zin_l + sg.next), sg.maxze) : sg.maxze;
     info.z_begin = z_begin;

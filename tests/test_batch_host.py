@@ -39,7 +39,7 @@ def test_cache_written_by_hand_with_extra_fields(stlib, tmp_path):
 
 def test_invalid_entries_and_files_are_rejected(stlib, tmp_path):
     p = tmp_path / "tune.json"
-    for bad in (stlib.st_tune(12, 24, 0.05, 0), stlib.st_tune(16, 0, 0.05, 0), stlib.st_tune(16, 33, 0.05, 0),
+    for bad in (stlib.st_tune(12, 24, 0.05, 0), stlib.st_tune(16, 0, 0.05, 0), stlib.st_tune(16, 1025, 0.05, 0),
                 stlib.st_tune(16, 24, 0.0, 0)):
         with pytest.raises(stlib.StError):
             stlib.st_tune_store(p, "k", bad)

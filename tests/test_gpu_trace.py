@@ -52,7 +52,7 @@ def test_trace_independent_of_segmentation_heuristics(stlib, orc, cuda):
     s = sg.workload_small(6)
     cam = sg.default_camera(128, 128)
     ref = orc.trace(s, cam)
-    for mn, slab in ((1, 0.001), (32, 10.0), (6, 0.05)):
+    for mn, slab in ((1, 0.001), (32, 10.0), (6, 0.05), (200, 10.0), (33, 0.05)):
         g = render(stlib, s, cam, max_new_per_turn=mn, depth_slab_frac=slab)
         _parity(orc, s, cam, g, ref)
 
