@@ -63,3 +63,21 @@ def test_trace_1080p_sampled(stlib, orc, cuda):
     g = render(stlib, s, cam)
     sampled_parity(orc, s, cam, g, 800, seed=1)
     assert (g["flags"] & 2).mean() <= 1e-3
+
+
+@pytest.mark.parametrize("mode", ["plain", "learned"])
+def test_trace_clustered_sampled(stlib, orc, cuda, mode):
+    # 10,000 clustered primitives: tile lists of thousands of entries, views
+    # of thousands of nodes (work areas in global memory, the larger
+    # parameter cache, many primitives fetched per turn)
+    kw = {}
+    if mode == "learned":
+        from paper_2304_09673_b300 import learn
+        packed = learn.packed_device(learn.load())
+        kw = dict(step_mode=stlib.ST_STEP_LEARNED, mlp=packed.data_ptr())
+    s = sg.workload_clustered(200)
+    cam = sg.default_camera(480, 270)
+    g = render(stlib, s, cam, **kw)
+    assert g["max_overlap"] > 2000
+    sampled_parity(orc, s, cam, g, 300, seed=5)
+    assert g["counters"][7] == 0
