@@ -7,7 +7,7 @@
  *   1. st_build_tiles: a low-resolution A-buffer holding, for every screen
  *      tile, the primitives whose volume of interest is hit by at least one
  *      of the tile's pixel rays, with conservative entry / exit depths,
- *      sorted by entry depth (Sec. 3 "tiled acceleration structure", Sec. 6).
+ *      sorted by entry depth (the per-tile structure of Sec. 3 and Sec. 6).
  *   2. st_trace: synchronized sphere tracing of each tile's subfrustums over
  *      a blobtree pruned to the subfrustum's active primitives by the sparse
  *      bottom-up traversal (Sec. 7, Sec. 8 Algorithm 2 and 3, Sec. 9).
@@ -195,8 +195,8 @@ typedef struct {
 #define ST_NUM_COUNTERS 8
 
 /* ---- scenes --------------------------------------------------------------
- * st_scene_create: host preparation of a tree structure (Sec. 10 / Sec. 11
- * "preprocessing"): post-order linearisation, isLeft, ignoreMod, fast
+ * st_scene_create: host preparation of a tree structure (the preparation
+ * step of Sec. 10 / Sec. 11): post-order linearisation, isLeft, ignoreMod, fast
  * ancestor pointers (Sec. 7.2, cut at intersections and at right-operand ->
  * difference edges, Sec. 9), ranges of interest propagated from the root
  * (Sec. 5), then upload of the node arrays to the current device.  Fails with

@@ -18,7 +18,7 @@
  *     ancestor pointers by their recursive definition (Sec. 7.2, cut at
  *     intersections and right-child -> difference edges, Sec. 9)
  *   - the pruned field f_A of an active set A (Sec. 3 local equivalence,
- *     Sec. 5/9 "an infinite value can be returned safely") and the pruned
+ *     Sec. 5/9: an absent operand may be taken as +inf) and the pruned
  *     tree view by its plain definition (the tree induced by A, with the
  *     usage rewrite of Sec. 9)
  *   - primitive volumes of interest (Sec. 6.1) and brute-force per-tile

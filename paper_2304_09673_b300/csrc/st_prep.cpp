@@ -1,11 +1,11 @@
 // st_prep.cpp -- host preparation of a blobtree structure (runs once per tree
 // structure; primitive parameter edits never re-run it).
 //
-//   post-order linearisation .............. Sec. 4 ("postfix storage order")
+//   post-order linearisation .............. Sec. 4 (nodes stored after their children)
 //   isLeft / ignoreMod .................... Sec. 4 bitfield, Sec. 9
 //   fast ancestor pointers ................ Sec. 7.2, cuts of Sec. 9
 //   ranges of interest .................... Sec. 5 (root (-inf, 0], R_o U R_p)
-//   evaluation stack depth ................ Sec. 10 "memory allocation"
+//   evaluation stack depth ................ Sec. 10, register and stack budget
 #include <cmath>
 #include <cstring>
 #include <sstream>

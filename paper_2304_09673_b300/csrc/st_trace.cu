@@ -846,7 +846,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
   int ray[kR];
   float z[kR], d[kR][3], inv_ld[kR];
   uint32_t steps[kR];
-  // Relaxed stepping state (Sec. 10 "overrelaxed sphere tracing"): the
+  // Relaxed stepping state (Sec. 10, sphere tracing with over-relaxation): the
   // surface-free radius rp of the previous point, the last step length dzp
   // (0: no previous point in this subfrustum; a plain step has dzp = rp and
   // can never be rejected), the plain-step position zf = previous point + rp

@@ -201,7 +201,7 @@ def test_pruned_view_evaluates_to_f_A(orc, seed):
 
 def test_stack_depth_bounds_pruned_views(orc):
     # An induced (pruned) tree never needs a deeper evaluation stack than the
-    # full tree (Sec. 10 "memory allocation").
+    # full tree (Sec. 10, stack budget).
     rng = np.random.default_rng(9)
     s = sg.make_scene(100, 14, 42)
     st = orc.structure(s)
