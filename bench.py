@@ -671,7 +671,8 @@ def main():
     ap.add_argument("--batch-scenes", type=int, default=64, help="scenes of the batch64 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-pixels", type=int, default=256)
+    ap.add_argument("--ref-pixels", type=int, default=8192,
+                    help="oracle rays per step of the reference arm")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
