@@ -67,6 +67,18 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def workload_of(args):
+    """The single-scene workload of the command line, at --res if given (a
+    smaller frame of the same scene, for profiling captures of small cases)."""
+    scene, cam, cfg = workload(args.workload)
+    if getattr(args, "res", None):
+        from paper_2304_09673_b300 import scenegen as sg
+        w, h = (int(v) for v in args.res.lower().split("x"))
+        cam = sg.default_camera(w, h)
+        cfg = dict(cfg, resolution=f"{w}x{h}", workload=cfg["workload"] + f", rendered at {w}x{h}")
+    return scene, cam, cfg
+
+
 def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -198,7 +210,7 @@ def run_reference(args):
         return
     import numpy as np
     import oracle
-    scene, cam, cfg = workload(args.workload)
+    scene, cam, cfg = workload_of(args)
     oracle.build()
     rng = np.random.default_rng(11)
     n = args.ref_pixels
@@ -285,7 +297,7 @@ def run_ours(args):
     from paper_2304_09673_b300 import learn
     from paper_2304_09673_b300 import st
 
-    scene, cam, cfg = workload(args.workload)
+    scene, cam, cfg = workload_of(args)
     modes = [m.strip() for m in args.modes.split(",") if m.strip()]
     head = modes[0]
     stream = torch.cuda.current_stream()
@@ -669,6 +681,7 @@ def main():
                     help="step modes to time; the first one is the headline value")
     ap.add_argument("--max-new", type=int, default=32, help="new primitives per subfrustum")
     ap.add_argument("--batch-scenes", type=int, default=64, help="scenes of the batch64 workload")
+    ap.add_argument("--res", default=None, help="WxH: render the single-scene workload at another resolution")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-pixels", type=int, default=8192,
