@@ -178,6 +178,11 @@ typedef struct {
                                units [1/32000 of the largest extent of the
                                primitives' bounding box measured at
                                st_scene_create, Sec. 10]                   */
+    int32_t split_kcycles;  /* a tile still tracing this many thousand SM
+                               cycles after its CTA started it hands parts
+                               of its pending rays to other CTAs at its next
+                               subfrustum boundary (the output does not
+                               change); 0 = default [2000], < 0 = never   */
 } st_trace_opts;
 
 /* Optional per-call counters (device pointer to 8 uint64, accumulated with
@@ -186,7 +191,8 @@ typedef struct {
  *   [1] useful primitive evaluations (pruned-view primitives x live steps)
  *   [2] useful operator evaluations
  *   [3] algorithmic FP32 flops of those evaluations (fixed per-node counts)
- *   [4] subfrustums processed
+ *   [4] subfrustums processed (each part of a tile split across CTAs
+ *       counts those it marches)
  *   [5] rejected learned steps
  *   [6] finalisation field evaluations (Newton + normal)
  *   [7] device error flags (bit 0: view capacity, bit 1: stack overflow,

@@ -90,7 +90,7 @@ struct st_scene {
   DBuf<uint32_t> prim;
   DBuf<Job> job;
   // tracing
-  DBuf<uint32_t> g_work, item_counter, order;
+  DBuf<uint32_t> g_work, item_counter, order, split;
   // updates
   DBuf<float4> upd_words;
   DBuf<uint32_t> upd_index;
@@ -208,7 +208,7 @@ void st_scene_destroy(st_scene *s) {
   s->cand_count.release(); s->cand_off.release(); s->tile_count.release(); s->offsets.release();
   s->scan_sums.release(); s->small.release(); s->rects.release(); s->pairs.release(); s->keys.release();
   s->ztmp.release(); s->z_in.release(); s->z_out.release(); s->prim.release(); s->job.release();
-  s->g_work.release(); s->item_counter.release(); s->order.release(); s->upd_words.release();
+  s->g_work.release(); s->item_counter.release(); s->order.release(); s->split.release(); s->upd_words.release();
   s->upd_index.release(); s->prim_index.release();
   s->dx_count.release(); s->dx_offsets.release(); s->dx_prim.release(); s->dx_small.release();
   s->dx_keys.release(); s->dx_ztmp.release(); s->dx_zin.release(); s->dx_zout.release(); s->dx_act.release();
@@ -460,6 +460,14 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
   ST_CK(s->order.ensure(L.n_items));
   launch_tile_order(s->job.p, 1, L.n_items, s->order.p, st);
   L.order = s->order.p;
+  const long long split_cycles = trace_split_cycles(o.split_kcycles);
+  if (split_cycles >= 0 && tp.step_mode != ST_STEP_RECORD) {
+    L.split_cap = trace_split_cap(L.max_tile_rays, L.n_items);
+    ST_CK(s->split.ensure(trace_split_words(L.max_tile_rays, L.split_cap)));
+    L.split = s->split.p;
+    L.split_cycles = split_cycles;
+    ST_CK(cudaMemsetAsync(L.split, 0, trace_split_zero_bytes(L.split_cap), st));
+  }
   ST_CK(trace_launch(s->job.p, 1, L, s->n_sm, st));
   return ST_OK;
 }

@@ -222,7 +222,7 @@ struct st_batch {
   uint32_t n_prims = 0, n_tiles = 0;
   std::vector<Job> jobs;
   Buf<Job> d_jobs;
-  Buf<uint32_t> cand_count, cand_off, tile_count, offsets, scan_sums, small, item_counter, status, g_work, order;
+  Buf<uint32_t> cand_count, cand_off, tile_count, offsets, scan_sums, small, item_counter, status, g_work, order, split;
   Buf<int4> rects;
   Buf<Pair> pairs;
   Buf<uint64_t> keys, counters;
@@ -371,6 +371,13 @@ int plan(st_batch *b) {
     BK(b->g_work.ensure((size_t)b->n_sm * 64 * L.g_work_words));
     L.g_work = b->g_work.p;
   }
+  const long long split_cycles = trace_split_cycles(b->opts.split_kcycles);
+  if (split_cycles >= 0) {
+    L.split_cap = trace_split_cap(L.max_tile_rays, L.n_items);
+    BK(b->split.ensure(trace_split_words(L.max_tile_rays, L.split_cap)));
+    L.split = b->split.p;
+    L.split_cycles = split_cycles;
+  }
   BK(trace_plan(L, b->n_sm, &b->grid, &b->smem));
   BK(cudaStreamSynchronize(s));
 
@@ -383,6 +390,7 @@ int plan(st_batch *b) {
   cudaMemsetAsync(b->status.p, 0, 4, cs);
   cudaMemsetAsync(b->item_counter.p, 0, 4, cs);
   cudaMemsetAsync(b->counters.p, 0, ST_NUM_COUNTERS * sizeof(uint64_t), cs);
+  if (L.split) cudaMemsetAsync(L.split, 0, trace_split_zero_bytes(L.split_cap), cs);
   enqueue_culling(b, cs, b->pair_cap);
   launch_check_capacity(b->small.p + 1, b->pair_cap, b->small.p + 2, b->overlap_cap, b->status.p, cs);
   launch_scatter_sort(b->pairs.p, b->small.p + 1, b->pair_cap, b->offsets.p, b->n_tiles, b->overlap_cap, b->keys.p,
@@ -409,7 +417,7 @@ void destroy(st_batch *b) {
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   b->d_jobs.release(); b->cand_count.release(); b->cand_off.release(); b->tile_count.release();
   b->offsets.release(); b->scan_sums.release(); b->small.release(); b->item_counter.release();
-  b->status.release(); b->g_work.release(); b->order.release(); b->rects.release(); b->pairs.release(); b->keys.release();
+  b->status.release(); b->g_work.release(); b->order.release(); b->split.release(); b->rects.release(); b->pairs.release(); b->keys.release();
   b->counters.release(); b->ztmp.release(); b->z_in.release(); b->z_out.release(); b->prim.release();
   delete b;
 }

@@ -92,7 +92,31 @@ struct TraceLaunch {
                            // returns at once when the capacity bit is set
   const uint32_t *order;   // optional [n_items] global tile per work item
                            // (launch_tile_order: longest list first)
+  uint32_t *split;         // optional split area (tiles split across CTAs,
+                           // see st_trace.cu); its first 4 + 2 split_cap
+                           // words are zeroed before the launch
+  uint32_t split_cap;      // split records in the area
+  long long split_cycles;  // a tile still tracing after this many SM cycles
+                           // splits at its next subfrustum boundary
 };
+
+// Split area sizing: words per record (header, pending ray ids, depth and
+// steps by ray id), records of a launch (at most one per tile, about 16 MiB
+// in all), total words and the words to zero before each launch.
+__host__ __device__ inline size_t split_rec_words(int max_tile_rays) { return 4 + 3 * (size_t)max_tile_rays; }
+inline uint32_t trace_split_cap(int max_tile_rays, uint32_t n_items) {
+  const size_t by_size = (size_t(16) << 20) / (4 * split_rec_words(max_tile_rays));
+  return (uint32_t)(n_items < by_size ? n_items : by_size);
+}
+inline size_t trace_split_words(int max_tile_rays, uint32_t cap) {
+  return 4 + 2 * (size_t)cap + (size_t)cap * split_rec_words(max_tile_rays);
+}
+inline size_t trace_split_zero_bytes(uint32_t cap) { return 4 * (4 + 2 * (size_t)cap); }
+// st_trace_opts::split_kcycles -> SM cycles (-1: tiles never split).
+inline long long trace_split_cycles(int32_t split_kcycles) {
+  if (split_kcycles < 0) return -1;
+  return 1000ll * (split_kcycles > 0 ? split_kcycles : 2000);
+}
 
 constexpr int ST_STEP_RECORD = 15;  // plain stepping that records training data (internal)
 

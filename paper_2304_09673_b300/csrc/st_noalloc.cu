@@ -1,6 +1,7 @@
 // st_noalloc.cu -- st_trace_noalloc: the tracing call without any device
-// allocation.  Its scratch memory (work-queue counter, the job record and,
-// for long tile lists, the per-CTA work areas) lives in one file-scope
+// allocation.  Its scratch memory (work-queue counter, the job record, for
+// long tile lists the per-CTA work areas, then the records of tiles split
+// across CTAs, as many as fit) lives in one file-scope
 // device array of fixed size that every device loading the library keeps
 // until the process exits.
 #include <cstring>
@@ -156,13 +157,29 @@ extern "C" int st_trace_noalloc(st_scene *s, const st_camera *cam, const st_tile
     }
     L.g_work = reinterpret_cast<uint32_t *>(scratch + work_off);
   }
+  // Then the records of tiles split across CTAs, as many as fit.
+  const long long split_cycles = trace_split_cycles(o.split_kcycles);
+  const size_t split_off = (work_off + (L.work_in_smem ? 0 : (size_t)n_sm * trace_ctas_per_sm(L) * L.g_work_words * 4) +
+                            255) & ~size_t(255);
+  if (split_cycles >= 0 && split_off < kScratchBytes) {
+    uint32_t cap = trace_split_cap(L.max_tile_rays, L.n_items);
+    const size_t room = (kScratchBytes - split_off) / 4;
+    while (cap > 0 && trace_split_words(L.max_tile_rays, cap) > room) cap >>= 1;
+    if (cap > 0) {
+      L.split = reinterpret_cast<uint32_t *>(scratch + split_off);
+      L.split_cap = cap;
+      L.split_cycles = split_cycles;
+    }
+  }
   L.item_counter = reinterpret_cast<uint32_t *>(scratch + kCounterOff);
   Job *job_dev = reinterpret_cast<Job *>(scratch + kJobOff);
 
   cudaStream_t st = (cudaStream_t)stream;
-  // The scratch keeps the previous call's contents: the queue counter must
-  // start at zero; the job record and work areas are fully rewritten.
+  // The scratch keeps the previous call's contents: the queue counter and
+  // the split area's counters must start at zero; the job record, work
+  // areas and split records are fully rewritten before they are read.
   NA_CK(cudaMemsetAsync(L.item_counter, 0, sizeof(uint32_t), st));
+  if (L.split) NA_CK(cudaMemsetAsync(L.split, 0, trace_split_zero_bytes(L.split_cap), st));
   count_launch(), k_put_job<<<1, 32, 0, st>>>(job, job_dev);
   NA_CK(cudaGetLastError());
   NA_CK(trace_launch(job_dev, 1, L, n_sm, st));

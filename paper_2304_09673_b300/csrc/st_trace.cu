@@ -573,11 +573,12 @@ __device__ __forceinline__ int build_schedule(const uint32_t *view, int n_view, 
 // Tracking active primitives (Sec. 8): discard those with z_e <= z_end,
 // fetch new ones from the depth-sorted list while the four conditions hold,
 // keep the set sorted by node address; then Algorithm 1 (one lane) builds the
-// pruned view into `view`.  Warp-collective; lane 0 writes *out.
+// pruned view into `view` (not when !build: replaying a tile's segmentation).
+// Warp-collective; lane 0 writes *out.
 __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, const DevScene &sc, const TraceParams &tp,
                             const float *zin_l, const float *zout_l, const uint32_t *prim_l, uint32_t len,
                             int vb, int stack_slots, int dc_words, SubInfo *out, int *lvl_cur, ViewChunk *vch,
-                            unsigned long long *dbg) {
+                            unsigned long long *dbg, bool build = true) {
   uint32_t *view = pick(C.view, vb);
   const int lane = threadIdx.x & 31;
   long long tc = dbg ? clock64() : 0;
@@ -689,6 +690,8 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
     info.z_end = sg.z_end;
     __syncwarp();
     lap(1);
+  }
+  if (!info.done && build) {
     // ---- pruned view (the lowest-common-ancestor form of Algorithm 1) ----
     int n_lvl = 0;
     const ViewInfo vi = build_view_lca<false>(sc, pick(C.act, sg.cur), sg.n_act, view, *vch, pick(C.ops, vb), C.sort_tmp,
@@ -819,6 +822,83 @@ __device__ __forceinline__ int tq_pop(unsigned long long *tq, int *tail, int *he
   }
   err |= ST_STATUS_WAIT;
   return -1;
+}
+
+// ---- splitting a long-running tile across CTAs ----------------------------------
+// A handful of tiles (grazing rays near silhouettes: many steps over large
+// views) can take longer than the whole rest of the frame.  A CTA whose tile
+// is still tracing after L.split_cycles publishes, at a subfrustum boundary,
+// the state of the tile's pending rays (depth reached, steps) as a split
+// record of P parts: part p holds the pending rays i = p (mod P).  It keeps
+// part 0; CTAs looking for work claim the other parts before new tiles,
+// replay the tile's segmentation up to the resume subfrustum (it depends on
+// the A-buffer list only) and trace their rays from there.  A ray's
+// trajectory does not depend on the CTA that steps it, so the output is the
+// same.  Nothing waits on another CTA: a CTA that pushed a record claims its
+// unclaimed parts itself before it leaves, and an idle CTA only polls
+// (boundedly) while whole tiles are still being traced.
+//
+// Split area (words): [0] records taken, [1] no open part below this record,
+// [2] CTAs tracing a whole tile, [3] unused, [4, 4 + cap) parts P of record r
+// (0 until published), [4 + cap, 4 + 2 cap) parts of record r claimed by
+// other CTAs; then the records (split_rec_words each): [0] global tile,
+// [1] subfrustum to resume at, [2] pending rays n, [3] unused,
+// [4, 4 + rays) pending ray ids, then depth reached and steps | status by
+// ray id (rays = max_tile_rays).
+constexpr int kSplitMinRays = 16;   // pending rays per part at least
+constexpr int kSplitMaxParts = 8;
+constexpr uint32_t kSplitListBudget = 4096;   // parts x A-buffer list length at most
+constexpr uint32_t kSplitIdleSpins = 1u << 21;   // polls of an idle CTA (x ~1 us)
+
+__device__ __forceinline__ uint32_t *split_record(const TraceLaunch &L, uint32_t r) {
+  return L.split + 4 + 2 * (size_t)L.split_cap + (size_t)r * split_rec_words(L.max_tile_rays);
+}
+
+// Warp-collective: claims an unclaimed part of a published record.  Returns
+// the part (>= 1) and sets *rec, or returns 0.
+__device__ __forceinline__ int split_claim(const TraceLaunch &L, uint32_t *rec) {
+  const int lane = threadIdx.x & 31;
+  uint32_t *hdr = L.split;
+  uint32_t *parts = hdr + 4, *claimed = hdr + 4 + L.split_cap;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    const uint32_t n = min(*(volatile uint32_t *)&hdr[0], L.split_cap);
+    const uint32_t lo = *(volatile uint32_t *)&hdr[1];
+    bool raced = false;
+    for (uint32_t b = lo; b < n; b += 32) {
+      const uint32_t r = b + (uint32_t)lane;
+      uint32_t P = 0, c = 0;
+      if (r < n) {
+        P = *(volatile uint32_t *)&parts[r];
+        c = *(volatile uint32_t *)&claimed[r];
+      }
+      const bool open = P > 1 && c + 1 < P;
+      if (b == lo) {
+        // Records below the first one that is unpublished or still open
+        // need no more scans.
+        const uint32_t keep = __ballot_sync(0xFFFFFFFFu, r >= n || P == 0 || open);
+        const uint32_t first = keep ? b + (uint32_t)(__ffs(keep) - 1) : b + 32u;
+        if (lane == 0 && first > lo) atomicMax(&hdr[1], min(first, n));
+      }
+      const uint32_t om = __ballot_sync(0xFFFFFFFFu, open);
+      if (!om) continue;
+      const int l = __ffs(om) - 1;
+      int got = 0;
+      if (lane == l) {
+        const uint32_t cc = atomicAdd(&claimed[r], 1u);
+        if (cc + 1 < P) got = (int)cc + 1;
+      }
+      got = __shfl_sync(0xFFFFFFFFu, got, l);
+      if (got) {
+        *rec = __shfl_sync(0xFFFFFFFFu, r, l);
+        __threadfence();   // the record's contents were published before P
+        return got;
+      }
+      raced = true;
+      break;
+    }
+    if (!raced) return 0;
+  }
+  return 0;
 }
 
 // Returns the number of live ray-steps taken by this lane.  `wvals` is the
@@ -1006,15 +1086,19 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       n_need += __popc(need_m[s]);
     }
     if (n_need && !drained) {
+      // A warp takes at most its share of the subfrustum's rays at a time,
+      // so that short lists spread over the warps of the CTA.
+      const int take = min(n_need, (n_in + kWarps - 1) / kWarps);
       int base = 0;
-      if (lane == 0) base = atomicAdd(q_head, n_need);
+      if (lane == 0) base = atomicAdd(q_head, take);
       base = __shfl_sync(0xFFFFFFFFu, base, 0);
-      if (base + n_need >= n_in) drained = true;
+      if (base + take >= n_in) drained = true;
       int off = 0;
 #pragma unroll
       for (int s = 0; s < kR; ++s) {
-        const int rk = base + off + __popc(need_m[s] & lanemask_lt());
-        if (ray[s] < 0 && rk < n_in) {
+        const int idx = off + __popc(need_m[s] & lanemask_lt());
+        const int rk = base + idx;
+        if (ray[s] < 0 && idx < take && rk < n_in) {
           ray[s] = alive_in[rk];
           load_ray(M, C, ray[s], z_begin, z[s], steps[s], d[s], inv_ld[s]);
           dzp[s] = 0.f;
@@ -1321,7 +1405,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ uint32_t s_item;
+  __shared__ uint32_t s_item, s_rec;
+  __shared__ int s_part;
   __shared__ SubInfo s_info[2];
   __shared__ int s_lvl_cur[kMaxLevels + 1];   // level cursors of the view build (warp 0)
   __shared__ ViewChunk s_vchunk;               // view build staging (warp 0)
@@ -1349,11 +1434,62 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   if (L.status && (*(volatile const uint32_t *)L.status & ST_STATUS_CAPACITY)) return;
 
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(L.item_counter, 1u);
+    if (warp == 0) {
+      // ---- next work: a part of a split tile first, else the next tile ----
+      uint32_t gt = 0xFFFFFFFFu, rec = 0;
+      int part = 0;
+      for (uint32_t spins = 0;; ++spins) {
+        if (L.split) {
+          part = split_claim(L, &rec);
+          if (part) {
+            gt = __ldcg(split_record(L, rec));
+            break;
+          }
+        }
+        uint32_t it = 0xFFFFFFFFu;
+        if (lane == 0 && *(volatile uint32_t *)L.item_counter < L.n_items) {
+          if (L.split) {
+            atomicAdd(&L.split[2], 1u);
+            __threadfence();
+          }
+          it = atomicAdd(L.item_counter, 1u);
+          if (it >= L.n_items) {
+            it = 0xFFFFFFFFu;
+            if (L.split) atomicSub(&L.split[2], 1u);
+          }
+        }
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if (it != 0xFFFFFFFFu) {
+          gt = L.order ? L.order[it] : it;
+          break;
+        }
+        if (!L.split) break;
+        // Nothing to take now: poll while whole tiles are still being traced
+        // (they may split); a record published before the last of them ended
+        // is visible to the final claim.
+        int stop = 0;
+        if (lane == 0) stop = (*(volatile uint32_t *)&L.split[2] == 0u || spins >= kSplitIdleSpins) ? 1 : 0;
+        stop = __shfl_sync(0xFFFFFFFFu, stop, 0);
+        if (stop) {
+          __threadfence();
+          part = split_claim(L, &rec);
+          if (part) gt = __ldcg(split_record(L, rec));
+          break;
+        }
+        __nanosleep(1000);
+      }
+      if (lane == 0) {
+        s_item = gt;
+        s_rec = rec;
+        s_part = part;
+      }
+    }
     __syncthreads();
-    const uint32_t item = s_item;
-    if (item >= L.n_items) break;
-    const uint32_t gtile = L.order ? L.order[item] : item;
+    const uint32_t gtile = s_item;
+    if (gtile == 0xFFFFFFFFu) break;
+    const int part = s_part;
+    const uint32_t *prec = part ? split_record(L, s_rec) : nullptr;
+    bool split_done = false;   // this whole tile was split (its CTA keeps part 0)
     const int jb = find_job_tile(jobs, n_jobs, gtile);
     const Job &job = jobs[jb];
     const DevScene &sc = job.sc;
@@ -1375,6 +1511,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       // when a captured batch is replayed on edited scenes): report, no output.
       for (int r = threadIdx.x; r < nr; r += blockDim.x) write_miss(M, r, 0u, 0);
       c_err |= ST_STATUS_CAPACITY;
+      if (L.split && !part && threadIdx.x == 0) atomicSub(&L.split[2], 1u);
       __syncthreads();
       continue;
     }
@@ -1386,13 +1523,33 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     long long t_prep = 0, t_march = 0, t_fin = 0;
     uint32_t s_sub = 0, s_maxview = 0;
 
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-      C.ray_z[r] = kZNear;
-      C.ray_st[r] = 0u;
-      pick(C.alive, 0)[r] = (uint16_t)r;
+    // K: the first subfrustum this CTA marches (a part of a split tile
+    // resumes where the tile was split, after replaying its segmentation).
+    int K = 0, n_pending = nr;
+    if (!part) {
+      for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        C.ray_z[r] = kZNear;
+        C.ray_st[r] = 0u;
+        pick(C.alive, 0)[r] = (uint16_t)r;
+      }
+    } else {
+      // (defensive clamps: the record was written by this kernel)
+      K = min((int)__ldcg(prec + 1), 2 * (int)len + 2);
+      const int n = min((int)__ldcg(prec + 2), nr), P = max((int)__ldcg(prec + 3), 2);
+      const uint32_t *ids = prec + 4;
+      const float *rz = reinterpret_cast<const float *>(prec + 4 + L.max_tile_rays);
+      const uint32_t *rst = prec + 4 + 2 * L.max_tile_rays;
+      uint16_t *al = pick(C.alive, K & 1);
+      for (int j = threadIdx.x; part + j * P < n; j += blockDim.x) {
+        const int r = (int)__ldcg(ids + part + j * P);
+        C.ray_z[r] = __ldcg(rz + r);
+        C.ray_st[r] = __ldcg(rst + r);
+        al[j] = (uint16_t)r;
+      }
+      n_pending = part < n ? (n - part + P - 1) / P : 0;
     }
     if (threadIdx.x == 0) {
-      s_nctr[0] = nr; s_nctr[1] = 0; s_nctr[2] = 0;
+      s_nctr[0] = 0; s_nctr[1] = 0; s_nctr[2] = 0;
       s_qhead[0] = 0; s_qhead[1] = 0; s_qhead[2] = 0;
       for (int i = 0; i < 3; ++i) { s_tqt[i] = 0; s_tqh[i] = 0; s_ndone[i] = 0; s_nidle[i] = 0; }
       s_steps = 0u;
@@ -1400,12 +1557,12 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     }
     SegState sg;
     sg.next = 0; sg.n_act = 0; sg.cur = 0; sg.z_end = 0.f; sg.maxze = -INFINITY;
-    int n_pending = nr;
     int k = -1;
-    // k = -1 only prepares subfrustum 0; one call site for the preparation
-    // keeps the kernel's code (and instruction-fetch stalls) smaller.
+    // k < K only prepares subfrustum k + 1 (segmentation alone below K - 1);
+    // one call site for the preparation keeps the kernel's code (and
+    // instruction-fetch stalls) smaller.
     for (;; ++k) {
-      const bool run = k >= 0;
+      const bool run = k >= K;
       SubInfo inf{};
       if (run) {
         inf = s_info[k & 1];
@@ -1414,7 +1571,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
           break;
         }
       }
-      const int kk = run ? k : 0;
+      const int kk = run ? k : K;
       const int rd = kk % 3, wr = (kk + 1) % 3, rs = (kk + 2) % 3;
       const uint16_t *alive_in = pick(C.alive, kk & 1);
       uint16_t *alive_out = pick(C.alive, (kk + 1) & 1);
@@ -1428,7 +1585,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         // The next subfrustum's view is built while the other warps march.
         const long long t0 = clock64();
         prepare_sub(sg, C, sc, job.tp, zin_l, zout_l, prim_l, len, (k + 1) & 1, L.stack_slots, L.dc_words,
-                    &s_info[(k + 1) & 1], s_lvl_cur, &s_vchunk, L.tile_stats ? s_dbg : nullptr);
+                    &s_info[(k + 1) & 1], s_lvl_cur, &s_vchunk, L.tile_stats ? s_dbg : nullptr, k + 1 >= K);
         t_prep += clock64() - t0;
         if (run) {
           c_sub += 1;
@@ -1479,14 +1636,72 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       }
       __syncthreads();
       n_pending = s_nctr[wr];
+      if (MODE != ST_STEP_RECORD && L.split && !part && !split_done && n_pending >= 2 * kSplitMinRays) {
+        // ---- a tile still tracing after L.split_cycles: publish parts 1..P-1
+        // of its pending rays, keep part 0 ----
+        if (threadIdx.x == 0) {
+          int P = 0;
+          const SubInfo nx = s_info[(k + 1) & 1];
+          // Only once every tile has been handed out: before that, the other
+          // CTAs have whole tiles to trace, and a split only adds the parts'
+          // segmentation replays and view builds.
+          if (!nx.done && !nx.err && clock64() - t_tile0 > L.split_cycles &&
+              *(volatile uint32_t *)L.item_counter >= L.n_items) {
+            // Each part repeats the tile's segmentation and view builds, whose
+            // cost grows with the list: long lists split into fewer parts.
+            P = min(min(kSplitMaxParts, n_pending / kSplitMinRays), (int)(kSplitListBudget / max(len, 1u)));
+            if (P >= 2) {
+              const uint32_t r = atomicAdd(&L.split[0], 1u);
+              if (r < L.split_cap) s_rec = r; else P = 0;
+            }
+          }
+          s_part = P;
+        }
+        __syncthreads();
+        const int P = s_part;
+        if (P >= 2) {
+          const uint32_t rr = s_rec;
+          uint32_t *R = split_record(L, rr);
+          uint16_t *al = pick(C.alive, (k + 1) & 1);   // the next subfrustum's pending rays
+          float *rz = reinterpret_cast<float *>(R + 4 + L.max_tile_rays);
+          uint32_t *rst = R + 4 + 2 * L.max_tile_rays;
+          for (int i = threadIdx.x; i < n_pending; i += blockDim.x) {
+            const int r = al[i];
+            R[4 + i] = (uint32_t)r;
+            rz[r] = C.ray_z[r];
+            rst[r] = C.ray_st[r];
+          }
+          if (threadIdx.x == 0) {
+            R[0] = gtile;
+            R[1] = (uint32_t)(k + 1);
+            R[2] = (uint32_t)n_pending;
+            R[3] = (uint32_t)P;
+          }
+          __threadfence();
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            atomicExch(&L.split[4 + rr], (uint32_t)P);
+            atomicSub(&L.split[2], 1u);
+          }
+          uint16_t *tmp = pick(C.alive, k & 1);   // free: this subfrustum's list
+          const int m = (n_pending + P - 1) / P;
+          for (int j = threadIdx.x; j < m; j += blockDim.x) tmp[j] = al[j * P];
+          __syncthreads();
+          for (int j = threadIdx.x; j < m; j += blockDim.x) al[j] = tmp[j];
+          __syncthreads();
+          n_pending = m;
+          split_done = true;
+        }
+      }
     }
+    if (L.split && !part && !split_done && threadIdx.x == 0) atomicSub(&L.split[2], 1u);
     // ---- rays still pending when the list is exhausted: misses ----
     for (int i = threadIdx.x; i < n_pending; i += blockDim.x) {
       const int r = pick(C.alive, k & 1)[i];
       write_miss(M, r, C.ray_st[r] & 0xFFFFFFu, 0);
     }
     __syncthreads();
-    if (L.tile_stats && threadIdx.x == 0) {
+    if (L.tile_stats && threadIdx.x == 0 && !part) {
       uint32_t *ts = L.tile_stats + (size_t)gtile * 16;
       ts[8] = (uint32_t)(s_dbg[0] >> 4);
       ts[9] = (uint32_t)(s_dbg[1] >> 4);
