@@ -854,51 +854,40 @@ __device__ __forceinline__ uint32_t *split_record(const TraceLaunch &L, uint32_t
   return L.split + 4 + 2 * (size_t)L.split_cap + (size_t)r * split_rec_words(L.max_tile_rays);
 }
 
-// Warp-collective: claims an unclaimed part of a published record.  Returns
-// the part (>= 1) and sets *rec, or returns 0.
-__device__ __forceinline__ int split_claim(const TraceLaunch &L, uint32_t *rec) {
-  const int lane = threadIdx.x & 31;
+// One thread: claims an unclaimed part of a split record, polling while
+// whole tiles are still being traced (they may split; a record published
+// before the last of them ended is visible to one more scan).  Returns the
+// part's global tile with *part >= 1 and *rec, or 0xFFFFFFFF: no work left.
+__device__ __forceinline__ uint32_t next_part(const TraceLaunch &L, uint32_t *rec, int *part) {
   uint32_t *hdr = L.split;
   uint32_t *parts = hdr + 4, *claimed = hdr + 4 + L.split_cap;
-  for (int attempt = 0; attempt < 8; ++attempt) {
+  bool last = false;
+  for (uint32_t spins = 0;; ++spins) {
     const uint32_t n = min(*(volatile uint32_t *)&hdr[0], L.split_cap);
-    const uint32_t lo = *(volatile uint32_t *)&hdr[1];
-    bool raced = false;
-    for (uint32_t b = lo; b < n; b += 32) {
-      const uint32_t r = b + (uint32_t)lane;
-      uint32_t P = 0, c = 0;
-      if (r < n) {
-        P = *(volatile uint32_t *)&parts[r];
-        c = *(volatile uint32_t *)&claimed[r];
+    uint32_t r = *(volatile uint32_t *)&hdr[1];
+    bool prefix = true;   // records below r are published and fully claimed
+    for (; r < n; ++r) {
+      const uint32_t P = *(volatile uint32_t *)&parts[r];
+      if (P > 1 && *(volatile uint32_t *)&claimed[r] + 1 < P) {
+        const uint32_t c = atomicAdd(&claimed[r], 1u);
+        if (c + 1 < P) {
+          __threadfence();   // the record's contents were published before P
+          *rec = r;
+          *part = (int)c + 1;
+          return __ldcg(split_record(L, r));
+        }
       }
-      const bool open = P > 1 && c + 1 < P;
-      if (b == lo) {
-        // Records below the first one that is unpublished or still open
-        // need no more scans.
-        const uint32_t keep = __ballot_sync(0xFFFFFFFFu, r >= n || P == 0 || open);
-        const uint32_t first = keep ? b + (uint32_t)(__ffs(keep) - 1) : b + 32u;
-        if (lane == 0 && first > lo) atomicMax(&hdr[1], min(first, n));
-      }
-      const uint32_t om = __ballot_sync(0xFFFFFFFFu, open);
-      if (!om) continue;
-      const int l = __ffs(om) - 1;
-      int got = 0;
-      if (lane == l) {
-        const uint32_t cc = atomicAdd(&claimed[r], 1u);
-        if (cc + 1 < P) got = (int)cc + 1;
-      }
-      got = __shfl_sync(0xFFFFFFFFu, got, l);
-      if (got) {
-        *rec = __shfl_sync(0xFFFFFFFFu, r, l);
-        __threadfence();   // the record's contents were published before P
-        return got;
-      }
-      raced = true;
-      break;
+      if (P == 0 || *(volatile uint32_t *)&claimed[r] + 1 < P) prefix = false;
+      if (prefix) atomicMax(&hdr[1], r + 1);
     }
-    if (!raced) return 0;
+    if (last) return 0xFFFFFFFFu;
+    if (*(volatile uint32_t *)&hdr[2] == 0u || spins >= kSplitIdleSpins) {
+      __threadfence();
+      last = true;
+      continue;
+    }
+    __nanosleep(1000);
   }
-  return 0;
 }
 
 // Returns the number of live ray-steps taken by this lane.  `wvals` is the
@@ -1434,55 +1423,24 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   if (L.status && (*(volatile const uint32_t *)L.status & ST_STATUS_CAPACITY)) return;
 
   for (;;) {
-    if (warp == 0) {
-      // ---- next work: a part of a split tile first, else the next tile ----
+    if (threadIdx.x == 0) {
+      // ---- next work: the next whole tile; once all are handed out, a part
+      // of a split tile ----
       uint32_t gt = 0xFFFFFFFFu, rec = 0;
       int part = 0;
-      for (uint32_t spins = 0;; ++spins) {
+      if (*(volatile uint32_t *)L.item_counter < L.n_items) {
         if (L.split) {
-          part = split_claim(L, &rec);
-          if (part) {
-            gt = __ldcg(split_record(L, rec));
-            break;
-          }
-        }
-        uint32_t it = 0xFFFFFFFFu;
-        if (lane == 0 && *(volatile uint32_t *)L.item_counter < L.n_items) {
-          if (L.split) {
-            atomicAdd(&L.split[2], 1u);
-            __threadfence();
-          }
-          it = atomicAdd(L.item_counter, 1u);
-          if (it >= L.n_items) {
-            it = 0xFFFFFFFFu;
-            if (L.split) atomicSub(&L.split[2], 1u);
-          }
-        }
-        it = __shfl_sync(0xFFFFFFFFu, it, 0);
-        if (it != 0xFFFFFFFFu) {
-          gt = L.order ? L.order[it] : it;
-          break;
-        }
-        if (!L.split) break;
-        // Nothing to take now: poll while whole tiles are still being traced
-        // (they may split); a record published before the last of them ended
-        // is visible to the final claim.
-        int stop = 0;
-        if (lane == 0) stop = (*(volatile uint32_t *)&L.split[2] == 0u || spins >= kSplitIdleSpins) ? 1 : 0;
-        stop = __shfl_sync(0xFFFFFFFFu, stop, 0);
-        if (stop) {
+          atomicAdd(&L.split[2], 1u);
           __threadfence();
-          part = split_claim(L, &rec);
-          if (part) gt = __ldcg(split_record(L, rec));
-          break;
         }
-        __nanosleep(1000);
+        const uint32_t it = atomicAdd(L.item_counter, 1u);
+        if (it < L.n_items) gt = L.order ? L.order[it] : it;
+        else if (L.split) atomicSub(&L.split[2], 1u);
       }
-      if (lane == 0) {
-        s_item = gt;
-        s_rec = rec;
-        s_part = part;
-      }
+      if (gt == 0xFFFFFFFFu && L.split) gt = next_part(L, &rec, &part);
+      s_item = gt;
+      s_rec = rec;
+      s_part = part;
     }
     __syncthreads();
     const uint32_t gtile = s_item;
