@@ -845,8 +845,8 @@ __device__ __forceinline__ int tq_pop(unsigned long long *tq, int *tail, int *he
 // [1] subfrustum to resume at, [2] pending rays n, [3] unused,
 // [4, 4 + rays) pending ray ids, then depth reached and steps | status by
 // ray id (rays = max_tile_rays).
-constexpr int kSplitMinRays = 16;   // pending rays per part at least
-constexpr int kSplitMaxParts = 8;
+constexpr int kSplitMinRays = 8;    // pending rays per part at least
+constexpr int kSplitMaxParts = 16;
 constexpr uint32_t kSplitListBudget = 4096;   // parts x A-buffer list length at most
 constexpr uint32_t kSplitIdleSpins = 1u << 21;   // polls of an idle CTA (x ~1 us)
 
@@ -1613,7 +1613,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
               if (r < L.split_cap) s_rec = r; else P = 0;
             }
           }
-          s_part = P;
+          s_part = P;   // (s_part broadcasts P here; the tile's own part is in `part`)
         }
         __syncthreads();
         const int P = s_part;
