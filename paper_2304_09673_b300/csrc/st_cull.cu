@@ -170,7 +170,7 @@ __global__ void k_prim_bounds(const Job *jobs, int n_jobs, uint32_t n_prims_tota
 // their latency than the few spilled registers cost (measured on B300:
 // 1920x1080 culling 17-20 % faster than at 86 registers and three CTAs).
 constexpr int kCullWarps = 8;
-constexpr int kPairsPerWarp = 4;
+constexpr int kPairsPerWarp = 8;
 
 __global__ void __launch_bounds__(kCullWarps * 32, 4)
 k_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_prims_total,
@@ -184,17 +184,35 @@ k_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_p
   for (uint32_t base = blockIdx.x * per_round; base < total; base += gridDim.x * per_round) {
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
+    // A warp's consecutive candidates almost always share their primitive:
+    // its volume of interest and ray-independent terms are kept between them.
+    uint32_t g = 0xFFFFFFFFu;
+    int jb = 0;
+    Voi v;
+    VoiRay vq;
     for (int q = 0; q < kPairsPerWarp; ++q) {
       uint32_t p = base + warp * kPairsPerWarp + q;
       if (p >= total) break;
-      // candidate -> primitive (binary search on the candidate offsets)
-      uint32_t lo = 0, hi = n_prims_total - 1;
-      while (lo < hi) {
-        uint32_t mid = (lo + hi + 1) >> 1;
-        if (cand_off[mid] <= p) lo = mid; else hi = mid - 1;
+      // candidate -> primitive: the last g with cand_off[g] <= p (binary
+      // search for the warp's first candidate, then a forward scan)
+      uint32_t gn;
+      if (g == 0xFFFFFFFFu) {
+        uint32_t lo = 0, hi = n_prims_total - 1;
+        while (lo < hi) {
+          uint32_t mid = (lo + hi + 1) >> 1;
+          if (cand_off[mid] <= p) lo = mid; else hi = mid - 1;
+        }
+        gn = lo;
+      } else {
+        gn = g;
+        while (gn + 1 < n_prims_total && cand_off[gn + 1] <= p) ++gn;
       }
-      const uint32_t g = lo;
-      const int jb = find_job_prim(jobs, n_jobs, g);
+      if (gn != g) {
+        g = gn;
+        jb = find_job_prim(jobs, n_jobs, g);
+        load_voi(jobs[jb].sc, g - jobs[jb].prim_base, v);
+        voi_ray_setup(v, jobs[jb].cam, vq);
+      }
       const Job &job = jobs[jb];
       const uint32_t j = g - job.prim_base;
       const int4 rect = rects[g];
@@ -203,10 +221,6 @@ k_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_p
       const int tx = rect.x + (int)(k % rw), ty = rect.y + (int)(k / rw);
       const int T = job.tl.tile;
       const DevCamera &cam = job.cam;
-      Voi v;
-      load_voi(job.sc, j, v);
-      VoiRay vq;
-      voi_ray_setup(v, cam, vq);
       uint32_t zin_bits = 0xFFFFFFFFu, zout_bits = 0u;
       // Lane -> one pixel column (T <= 32 divides 32): its u and F + u R are
       // computed once; the rows' v come from the lanes that computed them.
