@@ -122,3 +122,28 @@ def test_forced_split_batch(stlib, cuda):
     finally:
         for h in handles:
             stlib.st_scene_destroy(h)
+
+
+@pytest.mark.parametrize("mode", ["learned", "plain"])
+def test_split_full_size_same_bytes(stlib, cuda, mode):
+    """The bench workload (1,024 primitives, 1920x1080, tile 16), where the
+    default budget splits the launch's last tiles and a 1k-cycle budget
+    splits every tile still tracing once the queue is empty: the same bytes
+    and per-ray counters as without splitting."""
+    import torch
+    kw = _mode_kw(stlib, mode)
+    s = sg.workload_1080p(100)
+    cam = sg.default_camera(1920, 1080)
+    h = stlib.st_scene_create(s)
+    try:
+        t = stlib.st_build_tiles(h, cam, 16)
+        base, c0 = _trace(stlib, torch, h, cam, t, stlib.make_opts(split_kcycles=-1, **kw))
+        assert c0[7] == 0 and not np.any(base[3] == 99)
+        for kc in (0, 1):
+            got, c1 = _trace(stlib, torch, h, cam, t, stlib.make_opts(split_kcycles=kc, **kw))
+            for k, name in enumerate(("depth", "normal", "evals", "flags")):
+                assert got[k].tobytes() == base[k].tobytes(), (kc, name, int(np.sum(got[k] != base[k])))
+            assert [c1[i] for i in SAME_COUNTERS] == [c0[i] for i in SAME_COUNTERS], (kc, c0, c1)
+        assert c1[4] > c0[4], "no tile was split"
+    finally:
+        stlib.st_scene_destroy(h)
