@@ -1447,7 +1447,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     if (gtile == 0xFFFFFFFFu) break;
     const int part = s_part;
     const uint32_t *prec = part ? split_record(L, s_rec) : nullptr;
-    bool split_done = false;   // this whole tile was split (its CTA keeps part 0)
+    bool split_done = false;   // this whole tile was split (its CTA keeps part 0) or cannot split
     const int jb = find_job_tile(jobs, n_jobs, gtile);
     const Job &job = jobs[jb];
     const DevScene &sc = job.sc;
@@ -1472,6 +1472,12 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       if (L.split && !part && threadIdx.x == 0) atomicSub(&L.split[2], 1u);
       __syncthreads();
       continue;
+    }
+    if (L.split && !part && (nr < 2 * kSplitMinRays || kSplitListBudget / max(len, 1u) < 2)) {
+      // Too few rays or too long a list to split: release this tile's count
+      // of whole tiles at once, so that CTAs out of work stop polling sooner.
+      if (threadIdx.x == 0) atomicSub(&L.split[2], 1u);
+      split_done = true;
     }
     LC.list_len = len;
     const float *zin_l = job.tl.z_in + lbeg;
