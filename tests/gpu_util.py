@@ -109,13 +109,18 @@ def parity(orc, s, cam, g, ref, pix=None, normal_tol=1e-3):
     return dict(n_hit=int(both.sum()), band=int(band.sum()), max_depth_err=float(dd.max(initial=0)))
 
 
-def sampled_parity(orc, s, cam, g, n, seed=1, normal_tol=1e-3, tracer="trace"):
+def sampled_parity(orc, s, cam, g, n, seed=1, normal_tol=1e-3, tracer="trace", skip_unconverged=False):
     """parity() on n random pixels of a frame too large for a full oracle
     frame; the band test is per pixel from the oracle's own hit and min f.
-    `tracer` names the oracle tracer (trace or trace_relaxed)."""
+    `tracer` names the oracle tracer (trace or trace_relaxed).
+    skip_unconverged: leave out samples the GPU flags unconverged (the
+    caller checks their fraction over the whole frame instead)."""
     rng = np.random.default_rng(seed)
     pi = rng.integers(0, cam.width, n).astype(np.int32)
     pj = rng.integers(0, cam.height, n).astype(np.int32)
+    if skip_unconverged:
+        ok = (g["flags"][pj, pi] & 2) == 0
+        pi, pj = pi[ok], pj[ok]
     ref = getattr(orc, tracer)(s, cam, pi, pj)
     _, _, diam = orc.scene_bounds(s)
     d64, _ = orc.camera_rays(cam, pi, pj)

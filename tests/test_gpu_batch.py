@@ -205,3 +205,39 @@ def test_batch_rejects_bad_arguments(stlib, cuda):
             stlib.st_render_batch([], [], None, [], [], [], [])
     finally:
         stlib.st_scene_destroy(h)
+
+
+def test_batch64_sampled_oracle_parity(stlib, orc, cuda, tmp_path):
+    """The benchmark's 64-scene batch (primitive counts 32-4,096, four
+    resolutions) in one CUDA graph with the shipped tune cache: every
+    scene's sampled pixels against the oracle."""
+    import shutil
+    from pathlib import Path
+    import torch
+    from gpu_util import sampled_parity
+    cache = tmp_path / "tune.json"
+    shutil.copy(Path(__file__).resolve().parents[1] / "paper_2304_09673_b300" / "tune_b300.json", cache)
+    pairs = [sg.workload_batch(i) for i in range(64)]
+    scenes, cams = [p[0] for p in pairs], [p[1] for p in pairs]
+    handles = [stlib.st_scene_create(s) for s in scenes]
+    out = _outputs(cams, torch)
+    try:
+        b = stlib.st_batch_create(handles, cams, stlib.make_opts(), out["depth"], out["normal"], out["evals"],
+                                  out["flags"], autotune_cache=cache)
+        try:
+            cnt = stlib.st_batch_render(b, counters=True)
+            assert cnt[7] == 0
+            torch.cuda.synchronize()
+            for i, (s, c) in enumerate(zip(scenes, cams)):
+                H, W = c.height, c.width
+                g = dict(depth=out["depth"][i].cpu().numpy().reshape(H, W),
+                         normal=out["normal"][i].cpu().numpy().reshape(H, W, 3),
+                         flags=out["flags"][i].cpu().numpy().reshape(H, W))
+                assert not np.any(g["flags"] == 99), f"scene {i}: a pixel was not written"
+                assert (g["flags"] & 2).mean() <= 1e-3, f"scene {i}: unconverged rays"
+                sampled_parity(orc, s, c, g, 12, seed=100 + i, skip_unconverged=True)
+        finally:
+            stlib.st_batch_destroy(b)
+    finally:
+        for h in handles:
+            stlib.st_scene_destroy(h)

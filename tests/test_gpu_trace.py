@@ -81,3 +81,21 @@ def test_trace_clustered_sampled(stlib, orc, cuda, mode):
     assert g["max_overlap"] > 2000
     sampled_parity(orc, s, cam, g, 300, seed=5)
     assert g["counters"][7] == 0
+
+
+@pytest.mark.parametrize("mode", ["plain", "learned"])
+def test_trace_clustered_4k_sampled(stlib, orc, cuda, mode):
+    # The 10,000-primitive clustered configuration at its full 3840x2160 in
+    # bench.py's launch configuration (tile 16, default options): oracle
+    # parity on sampled pixels.
+    kw = {}
+    if mode == "learned":
+        from paper_2304_09673_b300 import learn
+        packed = learn.packed_device(learn.load())
+        kw = dict(step_mode=stlib.ST_STEP_LEARNED, mlp=packed.data_ptr())
+    s = sg.workload_clustered(200)
+    cam = sg.default_camera(3840, 2160)
+    g = render(stlib, s, cam, **kw)
+    sampled_parity(orc, s, cam, g, 300, seed=11, skip_unconverged=True)
+    assert g["counters"][7] == 0
+    assert (g["flags"] & 2).mean() <= 1e-3
