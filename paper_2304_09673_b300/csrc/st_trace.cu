@@ -6,7 +6,9 @@
 // Execution model (own design for sm_103a):
 //   * persistent CTAs of kWarps warps, three per SM; a CTA traces one tile at
 //     a time, tiles handed out longest A-buffer list first from a global
-//     counter (one launch can cover the tiles of many scenes);
+//     counter (one launch can cover the tiles of many scenes); once every
+//     tile has been handed out, a tile still tracing after a cycle budget
+//     shares its pending rays with CTAs out of work (split records, below);
 //   * warp 0 walks the tile's depth-sorted A-buffer list, segmenting the tile
 //     frustum into subfrustums [z_begin, z_end] with a fixed active primitive
 //     set (Sec. 8 "tracking active primitives"; discard, fetch and sorted
