@@ -27,6 +27,7 @@ import json
 import math
 import os
 import statistics
+import re
 import subprocess
 import sys
 import tempfile
@@ -158,9 +159,15 @@ def measured_peaks() -> dict:
 
 
 def kernel_hash() -> str:
+    """Hash of the traced kernel's sources with comments and blank space
+    removed: a recorded ncu traffic figure stays valid across comment edits
+    and goes stale on any change to the code."""
     h = hashlib.sha256()
     for f in ("st_trace.cu", "st_field.cuh", "st_geom.cuh", "st_internal.h", "st_mlp.cuh", "st_kernels.h"):
-        h.update((ROOT / "paper_2304_09673_b300" / "csrc" / f).read_bytes())
+        src = (ROOT / "paper_2304_09673_b300" / "csrc" / f).read_text()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
