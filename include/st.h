@@ -170,7 +170,8 @@ typedef struct {
                                operator levels; [8] discard, [9] fetch,
                                [10] view build, [11] parameter cache fill
                                cycles / 16 (first warp); [15] marching
-                               cycles / 16 summed over warps
+                               cycles / 16 summed over warps; a tile split
+                               across CTAs reports its first part only
                                (NULL = off)                                */
     float omega;            /* relaxation factor of ST_STEP_OVERRELAX and
                                ST_STEP_CROSSING [1.7, Sec. 10]             */
