@@ -155,7 +155,8 @@ typedef struct {
     int32_t max_new_per_turn; /* new primitives fetched per subfrustum, at
                                  most 1024; a tile takes at least an eighth
                                  of its list per turn [32; Sec. 8 uses 6] */
-    int32_t newton_iters;   /* Newton refinements of a hit [4]             */
+    int32_t newton_iters;   /* Newton refinements of a hit, each ray
+                               stopping at its own convergence [2]      */
     float newton_clamp;     /* Newton step bound, distance units [64 eps]  */
     const void *mlp;        /* ST_STEP_LEARNED: device pointer (16-byte
                                aligned) to MLP weights packed by st_mlp_pack */

@@ -391,7 +391,7 @@ TraceParams make_trace_params(const st_trace_opts &o, double diameter, double ex
   const float frac = o.depth_slab_frac > 0.f ? o.depth_slab_frac : 0.05f;
   tp.depth_slab = std::max(frac * (float)diameter, 1e-6f);
   tp.max_new = o.max_new_per_turn > 0 ? std::min(o.max_new_per_turn, 1024) : 32;
-  tp.newton_iters = o.newton_iters > 0 ? o.newton_iters : (o.newton_iters < 0 ? 0 : 4);
+  tp.newton_iters = o.newton_iters > 0 ? o.newton_iters : (o.newton_iters < 0 ? 0 : 2);
   tp.newton_clamp = o.newton_clamp > 0.f ? o.newton_clamp : 64.f * tp.eps;
   tp.omega = o.omega > 1.f ? std::min(o.omega, 2.f) : 1.7f;
   tp.min_step = o.min_step > 0.f ? o.min_step : std::max((float)(extent / 32000.0), 1e-7f);

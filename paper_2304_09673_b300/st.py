@@ -162,7 +162,7 @@ def make_camera(cam) -> st_camera:
 
 
 def make_opts(eps=1e-4, lipschitz=1.45, max_steps=256, step_mode=ST_STEP_PLAIN, depth_slab_frac=0.05,
-              max_new_per_turn=32, newton_iters=4, newton_clamp=0.0, mlp=None, tile_stats=None,
+              max_new_per_turn=32, newton_iters=2, newton_clamp=0.0, mlp=None, tile_stats=None,
               omega=1.7, min_step=0.0, split_kcycles=0) -> st_trace_opts:
     o = st_trace_opts(eps, lipschitz, max_steps, step_mode, depth_slab_frac, max_new_per_turn,
                       newton_iters, newton_clamp, mlp, None, omega, min_step, split_kcycles)
