@@ -1391,7 +1391,7 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
 
 // ---- the tracing kernel ----------------------------------------------------------
 // Three CTAs per SM: up to 170 registers per thread (the learned step's MLP
-// fragments need 166) with ~57 KB of shared memory per CTA.
+// fragments take it to 168) with ~57 KB of shared memory per CTA.
 template <int MODE>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
