@@ -243,6 +243,58 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def ray_dirs(cam, torch):
+    """Unit view-ray directions of every pixel centre (float64, device), the
+    pinhole model of the library (d = F + u R + v U)."""
+    import numpy as np
+    eye = np.array(cam.eye, np.float64)
+    F = np.array(cam.target, np.float64) - eye
+    F /= np.linalg.norm(F)
+    R = np.cross(F, np.array(cam.up, np.float64))
+    R /= np.linalg.norm(R)
+    U = np.cross(R, F)
+    th = math.tan(math.radians(cam.vfov_deg) / 2)
+    R *= th * cam.width / cam.height
+    U *= th
+    dev = torch.device("cuda")
+    u = (2 * torch.arange(cam.width, device=dev, dtype=torch.float64) + 1) / cam.width - 1
+    v = 1 - (2 * torch.arange(cam.height, device=dev, dtype=torch.float64) + 1) / cam.height
+    d = (torch.tensor(F, device=dev)[None, None, :] + u[None, :, None] * torch.tensor(R, device=dev)[None, None, :]
+         + v[:, None, None] * torch.tensor(U, device=dev)[None, None, :])
+    return (d / d.norm(dim=-1, keepdim=True)).reshape(-1, 3)
+
+
+def agreement(cam, diam, ref, got, torch):
+    """Agreement of a mode with the plain tracer at the same eps.  The
+    silhouette band (plain mask differs from a 4-neighbour, or a grazing
+    plain hit with |n.d| < 0.05) is where the stopping rule f <= eps decides
+    hit or miss for rays that pass within eps of the surface; outside it the
+    modes must agree.  Depth in scene units (Euclidean)."""
+    fp, dp, npl = ref
+    fm, dm = got
+    H, W = cam.height, cam.width
+    hp, hm = (fp & 1).bool(), (fm & 1).bool()
+    m2 = hp.reshape(H, W)
+    edge = torch.zeros_like(m2)
+    edge[1:, :] |= m2[1:, :] != m2[:-1, :]
+    edge[:-1, :] |= m2[:-1, :] != m2[1:, :]
+    edge[:, 1:] |= m2[:, 1:] != m2[:, :-1]
+    edge[:, :-1] |= m2[:, :-1] != m2[:, 1:]
+    cosn = (npl.reshape(-1, 3).double() * ray_dirs(cam, torch)).sum(-1).abs()
+    band = edge.reshape(-1) | (hp & (cosn < 0.05))
+    both = hp & hm
+    dd = (dm - dp).abs()
+    far = both & (dd > 1e-4 * diam)
+    out = {"mask_mismatch_frac": float((hp != hm).float().mean().item()),
+           "depth_diff_p99": float(torch.quantile(dd[both][:1 << 24].float(), 0.99).item()) if both.any() else 0.0,
+           "depth_diff_max": float(dd[both].max().item()) if both.any() else 0.0,
+           "silhouette_band_frac": float(band.float().mean().item()),
+           "mask_mismatch_outside_band_frac": float(((hp != hm) & ~band).float().mean().item()),
+           "depth_beyond_tol_outside_band_frac": float((far & ~band).float().mean().item()),
+           "depth_tol": 1e-4 * diam}
+    return out
+
+
 def mode_opts(st, name: str, mlp, max_new: int):
     """Trace options of one step mode; eps, L, step cap and subfrustum sizes are identical across modes."""
     if name == "learned":
@@ -319,42 +371,48 @@ def run_ours(args):
     except Exception:
         gpu_id = None
 
-    results, images = {}, {}
-    clocks = None
-    for name in modes:
-        opts = mode_opts(st, name, mlp, args.max_new)
-        if world > 1:
-            dist.barrier()
-        sampler = ClockSampler(gpu_id) if (rank == 0 and name == head) else None
-        res = timed_loop(st, r, cam, opts, args.steps, args.warmup, flush, stream)
-        if sampler:
-            clocks = sampler.stop()
-        total_ms = max_over_ranks(sum(res["step_ms"]), world)
-        res["ms_per_step"] = total_ms / args.steps
-        results[name] = res
-        images[name] = (r.flags.clone(), r.depth.clone())
+    def measure(rr, cam_, steps):
+        """Every mode timed on one renderer; clocks sampled in the head mode's
+        timed region; agreement of each mode with the plain tracer."""
+        res_all, imgs, clk = {}, {}, None
+        for name in modes:
+            opts = mode_opts(st, name, mlp, args.max_new)
+            if world > 1:
+                dist.barrier()
+            sampler = ClockSampler(gpu_id) if (rank == 0 and name == head) else None
+            res = timed_loop(st, rr, cam_, opts, steps, args.warmup, flush, stream)
+            if sampler:
+                clk = sampler.stop()
+            res["ms_per_step"] = max_over_ranks(sum(res["step_ms"]), world) / steps
+            res_all[name] = res
+            imgs[name] = (rr.flags.clone(), rr.depth.clone(), rr.normal.clone())
+        agr = {}
+        if "plain" in imgs:
+            d = st.st_scene_info(rr.h)["diameter"]
+            for name, (f, dep, _) in imgs.items():
+                if name != "plain":
+                    agr[name] = agreement(cam_, d, imgs["plain"], (f, dep), torch)
+        return res_all, agr, clk
 
-    # Agreement of every mode with the plain tracer at the same eps: hit masks
-    # and planar hit depths (scene units) on the pixels both modes hit.
-    agreement = {}
-    if "plain" in images:
-        fp, dp = images["plain"]
-        for name, (f, d) in images.items():
-            if name == "plain":
-                continue
-            hp, hm = (fp & 1).bool(), (f & 1).bool()
-            both = hp & hm
-            dd = (d - dp).abs()[both]
-            agreement[name] = {
-                "mask_mismatch_frac": float((hp != hm).float().mean().item()),
-                "depth_diff_p99": float(torch.quantile(dd[:1 << 24].float(), 0.99).item()) if dd.numel() else 0.0,
-                "depth_diff_max": float(dd.max().item()) if dd.numel() else 0.0}
+    results, agreement_all, clocks = measure(r, cam, args.steps)
+
+    # The other end of the metric's primitive range: 10,000 clustered
+    # primitives at the same 1920x1080 (tile lists of thousands of entries),
+    # every mode, fewer timed steps (each takes tens of milliseconds).
+    secondary = None
+    if args.workload == "1080p" and not args.no_secondary:
+        s_scene, s_cam, s_cfg = workload("clustered1080p")
+        r2 = st.Renderer(s_scene, s_cam, tile=s_cfg["tile"], stream=stream)
+        s_steps = max(1, min(args.steps, 3))
+        s_res, s_agr, s_clk = measure(r2, s_cam, s_steps)
+        secondary = dict(cfg=s_cfg, cam=s_cam, res=s_res, agreement=s_agr, clocks=s_clk, steps=s_steps)
+        r2.close()
 
     # ---- end to end through the public API with host buffers (headline mode) ----
     opts = mode_opts(st, head, mlp, args.max_new)
     ids = np.flatnonzero(scene.kind < 16).astype(np.int32)
     params = np.ascontiguousarray(scene.params[ids])
-    words = {0: 1, 1: 4, 2: 3, 12: 2, 13: 4, 14: 5}   # record words per primitive kind
+    words = {0: 1, 1: 4, 2: 3, 11: 5, 12: 2, 13: 4, 14: 5, 15: 7}   # record words per primitive kind
     h2d = int(sum(words[int(k)] for k in scene.kind[ids]) * 20)
     host = dict(depth=torch.empty(H * W, dtype=torch.float32, pin_memory=True),
                 normal=torch.empty(H * W * 3, dtype=torch.float32, pin_memory=True),
@@ -427,7 +485,7 @@ def run_ours(args):
         sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
         peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
-        def summary(res):
+        def summary(res, W=W, H=H):
             cnt = res["cnt"]
             ms = res["ms_per_step"]
             trace_s = statistics.mean(res["trace_ms"]) / 1e3
@@ -467,8 +525,23 @@ def run_ours(args):
         if "plain" in per_mode and head != "plain":
             line["learned_vs_plain" if head == "learned" else f"{head}_vs_plain"] = (
                 hs["rays_per_s"] / per_mode["plain"]["rays_per_s"])
-        if agreement:
-            line["agreement_with_plain"] = agreement
+        if agreement_all:
+            line["agreement_with_plain"] = agreement_all
+        if secondary:
+            sw, sh = secondary["cam"].width, secondary["cam"].height
+            s_modes = {name: summary(res, sw, sh) for name, res in secondary["res"].items()}
+            sh_ = s_modes[head]
+            sec = {"workload": secondary["cfg"]["workload"], "prims": secondary["cfg"]["prims"],
+                   "resolution": secondary["cfg"]["resolution"], "steps": secondary["steps"],
+                   "value": sh_["rays_per_s"], "unit": "rays/s", "prim_evals_per_s": sh_["prim_evals_per_s"],
+                   "modes": s_modes,
+                   "roofline": {"bound": "alu", "kernel": f"k_trace<{head}>", "achieved": sh_["fp32_tflops"],
+                                "peak": peak_tflops, "unit": "TFLOP/s", "frac": sh_["fp32_tflops"] / peak_tflops,
+                                "traffic": recorded_traffic("clustered1080p", head)},
+                   "agreement_with_plain": secondary["agreement"], "clocks": secondary["clocks"]}
+            if "plain" in s_modes and head != "plain":
+                sec[f"{head}_vs_plain"] = sh_["rays_per_s"] / s_modes["plain"]["rays_per_s"]
+            line["secondary"] = sec
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(scene, cam, args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -730,6 +803,8 @@ def main():
     ap.add_argument("--batch-scenes", type=int, default=64, help="scenes of the batch64 workload")
     ap.add_argument("--res", default=None, help="WxH: render the single-scene workload at another resolution")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 10,000-primitive clustered 1920x1080 line of the default workload")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-pixels", type=int, default=8192,
                     help="oracle rays per step of the reference arm")

@@ -62,6 +62,28 @@ extern "C" {
                               rotation M as ST_PRIM_RBOX, rec[12:15] radii
                               > 0; field min(r) (|M (x - c) / r| - 1), a
                               Lipschitz-1 bound of the distance           */
+#define ST_PRIM_RTRI 15    /* rounded triangle: rec[0:3], rec[3:6], rec[6:9]
+                              vertices a, b, c (not collinear), rec[9]
+                              rounding r > 0; field = exact distance to the
+                              triangle minus r.  Its volume of interest is
+                              the sphere-triangle of Sec. 6.1 (points within
+                              r + d of the triangle)                      */
+#define ST_PRIM_QUADRIC 11 /* bounded quadric: the solid {q <= 0} inside an
+                              oriented box.  rec[0:3] centre, rec[3:7]
+                              rotation quaternion (w, x, y, z; any length >
+                              0; local = R^T (x - centre) for the rotation R
+                              it represents), rec[7:10] box half extents >
+                              0, rec[10:15] alpha, beta, gamma, delta,
+                              kappa of q(u) = alpha u0^2 + beta u1^2 +
+                              gamma u2^2 + delta u2 + kappa in local
+                              coordinates u (not all of alpha..delta zero).
+                              Field max(q(clamp(u)) / G, box distance) with
+                              G = |(2|alpha| e0, 2|beta| e1, 2|gamma| e2 +
+                              |delta|)| >= |grad q| on the box: Lipschitz 1,
+                              exact zero set.  Volume of interest: the
+                              oriented box of half extents e + d.
+                              (Kind 11 maps to view code 16; the other
+                              primitive kinds equal their view codes.)    */
 /* Operators (binary): compact smooth operators G_op of Sec. 5 (Eq.
  * "smooth_comp" with the smooth polynomial operators of Eq. 4-7 and the
  * transition b_r), rec[0] = blend range k > 0, rec[1] = operator range bound
@@ -160,7 +182,7 @@ typedef struct {
     float newton_clamp;     /* Newton step bound, distance units [64 eps]  */
     const void *mlp;        /* ST_STEP_LEARNED: device pointer (16-byte
                                aligned) to MLP weights packed by st_mlp_pack */
-    uint32_t *tile_stats;   /* optional device uint32[n_tiles][16] per-tile
+    uint32_t *tile_stats;   /* optional device uint32[n_tiles][24] per-tile
                                diagnostics: [0] total, [1] segmentation +
                                view build, [2] marching, [3] hit refinement
                                SM clock cycles / 16 (first warp); [4]
@@ -171,9 +193,14 @@ typedef struct {
                                operator levels; [8] discard, [9] fetch,
                                [10] view build, [11] parameter cache fill
                                cycles / 16 (first warp); [15] marching
-                               cycles / 16 summed over warps; a tile split
-                               across CTAs reports its first part only
-                               (NULL = off)                                */
+                               cycles / 16 summed over warps; [16]
+                               lockstep iterations and [17] live rays
+                               summed over them (lane use), [18] rays
+                               evaluated by the warp-wide tail mode, [19]
+                               hit refinement passes and [20] live lanes
+                               summed over them, all summed over warps;
+                               [21..23] 0; a tile split across CTAs
+                               reports its first part only (NULL = off) */
     float omega;            /* relaxation factor of ST_STEP_OVERRELAX and
                                ST_STEP_CROSSING [1.7, Sec. 10]             */
     float min_step;         /* ST_STEP_CROSSING: shortest step, distance
@@ -185,6 +212,30 @@ typedef struct {
                                of its pending rays to other CTAs at its next
                                subfrustum boundary (the output does not
                                change); 0 = default [2000], < 0 = never   */
+    int32_t heavy_split_len; /* > 0: a tile whose A-buffer list holds at
+                               least this many entries is split across CTAs
+                               before its first subfrustum (about one part
+                               per 512 list entries, at most 8; each part
+                               builds the tile's views itself), and CTAs
+                               take open parts before whole tiles (the
+                               output does not change); <= 0 = never
+                               [never: the repeated view builds cost more
+                               than the balance gains on the clustered
+                               workloads]                                 */
+    uint32_t wait_spin_limit; /* bound on the polls of a warp waiting for
+                               the other warps of its tile and of a CTA
+                               waiting for parts of split tiles; a warp
+                               wait that runs out sets error bit 3 and the
+                               kernel carries on without the waiting warp
+                               (results of that call are undefined) [0 =
+                               built-in bounds, 2^22 and 2^21 polls]      */
+    int32_t check_status;   /* 1: st_trace and st_trace_noalloc synchronise
+                               `stream` after the launch and return
+                               ST_ERR_TIMEOUT when a bounded device wait
+                               ran out, ST_ERR_CAPACITY or ST_ERR_INVALID
+                               for the other device error bits [0: the
+                               call stays asynchronous; the bits are in
+                               counters[7] when counters are given]      */
 } st_trace_opts;
 
 /* Optional per-call counters (device pointer to 8 uint64, accumulated with
@@ -225,6 +276,12 @@ int st_scene_update_prims(st_scene *scene, const int32_t *ids, const float *para
 
 /* Post-order address of every description node: host int32[n_nodes] out. */
 int st_scene_addresses(const st_scene *scene, int32_t *po_of_desc);
+
+/* Facts of the preparation, host double[4] out: [0] scene diameter (the
+ * diagonal of the axis-aligned box of all primitive bounds, measured at
+ * st_scene_create; it scales the subfrustum depth slab), [1] the largest
+ * edge of that box, [2] primitives, [3] post-order evaluation stack depth. */
+int st_scene_info(const st_scene *scene, double *out);
 
 void st_scene_destroy(st_scene *scene);
 
@@ -379,15 +436,23 @@ int st_mlp_infer(const void *packed, const float *x, int n, float *omega, void *
  * at draw time: render loops that run under a fixed memory budget or must
  * not stall on an allocation (cudaMalloc can synchronise the device), and
  * hosts whose device memory is owned by another allocator.  The paper has no
- * counterpart to this call.  Step modes ST_STEP_PLAIN, ST_STEP_OVERRELAX and
- * ST_STEP_CROSSING; ST_STEP_LEARNED returns ST_ERR_INVALID.
+ * counterpart to this call.  Every step mode of st_trace (ST_STEP_LEARNED
+ * reads the caller's packed weights, opts.mlp), and the same launch:
+ * parameter cache size, longest-list-first tile order, tiles split across
+ * CTAs, opts.check_status.
  *
- * Its scratch memory (the work-queue counter, the job record and, for long
- * tile lists, the per-CTA work areas) is one fixed 32 MiB device array
- * defined in the library; every device that loads the library holds it until
- * the process exits (st_trace_noalloc_scratch_bytes() returns the size).  A
- * launch whose work areas would not fit returns ST_ERR_CAPACITY with the
- * needed size in st_last_error(); st_trace has no such limit.
+ * Its scratch memory (the work-queue counter, the status word, the job
+ * record, the tile order, for long tile lists the per-CTA work areas, then
+ * as many split records as fit) is one fixed 32 MiB device array defined in
+ * the library; every device that loads the library holds it until the
+ * process exits (st_trace_noalloc_scratch_bytes() returns the size).  A
+ * launch whose tile order or work areas would not fit returns
+ * ST_ERR_CAPACITY with the needed size in st_last_error(), before anything
+ * is enqueued; st_trace has no such limit.
+ * st_trace_noalloc_last_layout(out[3]) reports the last call's layout:
+ * out[0] 1 when its per-CTA work areas were carved from the array (lists
+ * too long for shared memory), out[1] bytes of the array in use, out[2]
+ * split records.
  *
  * The first call on a device resolves the array's device address (with that
  * device current); make that first call before any stream capture.  Every
@@ -399,6 +464,7 @@ int st_trace_noalloc(st_scene *scene, const st_camera *cam, const st_tiles *tile
                      const st_trace_opts *opts, float *depth, float *normal, uint32_t *evals,
                      uint8_t *flags, uint64_t *counters, void *stream);
 size_t st_trace_noalloc_scratch_bytes(void);
+int st_trace_noalloc_last_layout(uint64_t *out);
 
 /* ---- the non-synchronized variants of Table 1 ---------------------------------
  * The paper measures its pipeline against per-pixel processing over a
@@ -456,11 +522,12 @@ int st_eval_sparse(const st_scene *scene, const uint32_t *act, int n, const floa
  * usage rewrite); same arguments and outputs.
  *   act        device uint32[n], post-order addresses of active primitives,
  *              strictly ascending, 1 <= n <= number of primitives
- *   view       device uint32[2n-1] out: bits 28..31 node code (0 sphere,
+ *   view       device uint32[2n-1] out: bits 27..31 node code (0 sphere,
  *              1 rounded box, 2 capsule, 3/4/5 compact union / intersection /
  *              difference, 6/7/8 sharp ones, 9 +inf, 10 right operand, 11 left
- *              operand), bit 27 set (record in the scene's global array),
- *              bits 0..26 record word offset
+ *              operand, 12 torus, 13 sphere-cone, 14 ellipsoid, 15 rounded
+ *              triangle, 16 bounded quadric), bit 26 set (record in the
+ *              scene's global array), bits 0..25 record word offset
  *   view_addr  device uint32[2n-1] out (optional): post-order address per entry
  *   info       device int32[4] out: view length, root usage bit, error (0 ok),
  *              number of primitives
@@ -493,6 +560,11 @@ int st_prep_tree(const st_scene_desc *desc, int32_t *po_of_desc, uint32_t *blob,
 
 /* Number of kernels this library has launched in this process so far. */
 uint64_t st_kernel_launches(void);
+
+/* Number of device allocations (cudaMalloc) this library has made in this
+ * process so far: scene arrays, tile and work buffers growing on demand,
+ * batch buffers.  st_trace_noalloc never adds to it. */
+uint64_t st_device_allocations(void);
 
 const char *st_last_error(void);
 const char *st_version(void);

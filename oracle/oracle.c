@@ -46,6 +46,8 @@
 #define K_TORUS 12
 #define K_SCONE 13
 #define K_ELLIPSOID 14
+#define K_RTRI 15
+#define K_QUADRIC 11
 #define K_UNION 16
 #define K_INTER 17
 #define K_DIFF 18
@@ -170,6 +172,91 @@ static double sdf_ellipsoid(const float *q, const double p[3]) {
     return rmin * (sqrt(s) - 1.0);
 }
 
+/* Rounded triangle (vertices a, b, c, rounding r): Euclidean distance to the
+ * triangle minus r.  The nearest point of the triangle is the orthogonal
+ * projection onto its plane when that projection falls inside (p on the
+ * inner side of all three edges, tested with the normal N = (b-a) x (c-a)),
+ * otherwise the nearest point of the nearest edge segment. */
+static double seg_dist(const double p[3], const double a[3], const double b[3]) {
+    double ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, ap[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+    double t = (ap[0] * ab[0] + ap[1] * ab[1] + ap[2] * ab[2]) / (ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
+    if (t < 0) t = 0;
+    if (t > 1) t = 1;
+    double x = ap[0] - t * ab[0], y = ap[1] - t * ab[1], z = ap[2] - t * ab[2];
+    return sqrt(x * x + y * y + z * z);
+}
+static void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double sdf_rtri(const float *q, const double p[3]) {
+    double v[3][3];
+    for (int i = 0; i < 3; ++i) for (int k = 0; k < 3; ++k) v[i][k] = q[3 * i + k];
+    double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+    double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+    double N[3];
+    cross3(e1, e2, N);
+    int inside = 1;
+    for (int i = 0; i < 3; ++i) {
+        const double *s = v[i], *t = v[(i + 1) % 3];
+        double ed[3] = {t[0] - s[0], t[1] - s[1], t[2] - s[2]}, sp[3] = {p[0] - s[0], p[1] - s[1], p[2] - s[2]};
+        double c[3];
+        cross3(ed, sp, c);   /* along +N when p is on the inner side of edge s -> t */
+        if (c[0] * N[0] + c[1] * N[1] + c[2] * N[2] < 0) inside = 0;
+    }
+    double dist;
+    if (inside) {
+        double nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+        dist = fabs((p[0] - v[0][0]) * N[0] + (p[1] - v[0][1]) * N[1] + (p[2] - v[0][2]) * N[2]) / nn;
+    } else {
+        dist = seg_dist(p, v[0], v[1]);
+        double d1 = seg_dist(p, v[1], v[2]), d2 = seg_dist(p, v[2], v[0]);
+        if (d1 < dist) dist = d1;
+        if (d2 < dist) dist = d2;
+    }
+    return dist - (double)q[9];
+}
+
+/* Bounded quadric: the solid {q(u) <= 0} of q(u) = alpha u0^2 + beta u1^2 +
+ * gamma u2^2 + delta u2 + kappa, clipped by the box |u_i| <= e_i, in the local
+ * frame u = R^T (p - c) of the unit quaternion's rotation R.  Its field:
+ * max(q(clamp(u)) / G, box distance), G = |(2|alpha| e0, 2|beta| e1,
+ * 2|gamma| e2 + |delta|)| bounding |grad q| on the box, so that q / G is
+ * 1-Lipschitz there and its clamped extension is 1-Lipschitz everywhere; the
+ * zero set is exactly the boundary of {q <= 0} inside the box. */
+static void quat_rot(const float *qq, double R[3][3]) {
+    double w = qq[0], x = qq[1], y = qq[2], z = qq[3];
+    double n = sqrt(w * w + x * x + y * y + z * z);
+    w /= n; x /= n; y /= n; z /= n;
+    R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - z * w);     R[0][2] = 2 * (x * z + y * w);
+    R[1][0] = 2 * (x * y + z * w);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - x * w);
+    R[2][0] = 2 * (x * z - y * w);     R[2][1] = 2 * (y * z + x * w);     R[2][2] = 1 - 2 * (x * x + y * y);
+}
+static double quadric_g(const float *q) {
+    double g0 = 2.0 * fabs((double)q[10]) * q[7], g1 = 2.0 * fabs((double)q[11]) * q[8];
+    double g2 = 2.0 * fabs((double)q[12]) * q[9] + fabs((double)q[13]);
+    return sqrt(g0 * g0 + g1 * g1 + g2 * g2);
+}
+static double sdf_quadric(const float *q, const double p[3]) {
+    double R[3][3];
+    quat_rot(q + 3, R);
+    double w[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]}, u[3], uc[3];
+    double out = 0.0, mx = -DBL_MAX;
+    for (int i = 0; i < 3; ++i) {
+        u[i] = R[0][i] * w[0] + R[1][i] * w[1] + R[2][i] * w[2];   /* (R^T w)_i */
+        double e = q[7 + i];
+        uc[i] = u[i] < -e ? -e : (u[i] > e ? e : u[i]);
+        double a = fabs(u[i]) - e;
+        if (a > 0) out += a * a;
+        if (a > mx) mx = a;
+    }
+    double box = sqrt(out) + (mx < 0 ? mx : 0.0);
+    double qv = q[10] * uc[0] * uc[0] + q[11] * uc[1] * uc[1] + q[12] * uc[2] * uc[2] + q[13] * uc[2] + q[14];
+    double f = qv / quadric_g(q);
+    return f > box ? f : box;
+}
+
 static double sdf_prim(int kind, const float *q, const double p[3]) {
     switch (kind) {
     case K_SPHERE: return sdf_sphere(q, p);
@@ -178,6 +265,8 @@ static double sdf_prim(int kind, const float *q, const double p[3]) {
     case K_TORUS: return sdf_torus(q, p);
     case K_SCONE: return sdf_scone(q, p);
     case K_ELLIPSOID: return sdf_ellipsoid(q, p);
+    case K_RTRI: return sdf_rtri(q, p);
+    case K_QUADRIC: return sdf_quadric(q, p);
     }
     return INFINITY;
 }
@@ -454,11 +543,40 @@ static void voi_rec(int kind, const float *q, double d, double *v) {
         for (int i = 0; i < 3; ++i) v[12 + i] = (double)q[12 + i] * (1.0 + d / rmin);
         break;
     }
+    case K_RTRI: v[9] = (double)q[9] + d; break;   /* vertices, radius r + d */
+    case K_QUADRIC: {   /* oriented box: centre, M = R^T rows, e + d */
+        double R[3][3];
+        quat_rot(q + 3, R);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) v[3 + 3 * i + j] = R[j][i];
+        for (int i = 0; i < 3; ++i) v[12 + i] = (double)q[7 + i] + d;
+        break;
+    }
     }
 }
 
 /* Axis-aligned bounds of a primitive's zero iso-volume. */
 static void prim_aabb(int kind, const float *q, double lo[3], double hi[3]) {
+    if (kind == K_RTRI) {   /* the vertices' box grown by the rounding */
+        for (int j = 0; j < 3; ++j) {
+            double a = q[j], b = q[3 + j], c = q[6 + j];
+            double mn = a < b ? a : b, mx = a > b ? a : b;
+            if (c < mn) mn = c;
+            if (c > mx) mx = c;
+            lo[j] = mn - q[9]; hi[j] = mx + q[9];
+        }
+        return;
+    }
+    if (kind == K_QUADRIC) {   /* inside its clipping box */
+        double R[3][3];
+        quat_rot(q + 3, R);
+        for (int j = 0; j < 3; ++j) {
+            double e = 0;
+            for (int i = 0; i < 3; ++i) e += fabs(R[j][i]) * q[7 + i];
+            lo[j] = q[j] - e; hi[j] = q[j] + e;
+        }
+        return;
+    }
     if (kind == K_SPHERE) {
         for (int j = 0; j < 3; ++j) { lo[j] = q[j] - (double)q[3]; hi[j] = q[j] + (double)q[3]; }
     } else if (kind == K_RBOX) {
@@ -670,9 +788,58 @@ static int ray_capsule64(const double o[3], const double d[3], const double *v, 
     return 1;
 }
 
+/* Ray against the sphere-triangle (points within r of the triangle a, b, c;
+ * v = a, b, c at [0:9], r at [9]): it is convex, the union of the prism
+ * {|n.(x - a)| <= r, x on the inner side of the three edge planes} and the
+ * three edge capsules, so its interval is the hull of the parts'. */
+static int ray_stri64(const double o[3], const double d[3], const double *v, double *t0, double *t1) {
+    const double *P[3] = {v, v + 3, v + 6};
+    double r = v[9];
+    double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+    double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+    double N[3];
+    cross3(e1, e2, N);
+    double nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    for (int k = 0; k < 3; ++k) N[k] /= nn;
+    double lo = INFINITY, hi = -INFINITY;
+    /* prism */
+    double a_lo = -INFINITY, a_hi = INFINITY;
+    int ok = 1;
+    double so = (o[0] - P[0][0]) * N[0] + (o[1] - P[0][1]) * N[1] + (o[2] - P[0][2]) * N[2];
+    double sd = d[0] * N[0] + d[1] * N[1] + d[2] * N[2];
+    if (sd == 0) { if (fabs(so) > r) ok = 0; }
+    else {
+        double ta = (-r - so) / sd, tb = (r - so) / sd;
+        a_lo = ta < tb ? ta : tb; a_hi = ta < tb ? tb : ta;
+    }
+    for (int i = 0; i < 3 && ok; ++i) {
+        const double *s = P[i], *t = P[(i + 1) % 3];
+        double ed[3] = {t[0] - s[0], t[1] - s[1], t[2] - s[2]}, m[3];
+        cross3(ed, N, m);   /* outward in-plane normal of edge s -> t */
+        double g = (o[0] - s[0]) * m[0] + (o[1] - s[1]) * m[1] + (o[2] - s[2]) * m[2];
+        double gd = d[0] * m[0] + d[1] * m[1] + d[2] * m[2];
+        if (gd == 0) { if (g > 0) ok = 0; }
+        else if (gd > 0) { double tl = -g / gd; if (tl < a_hi) a_hi = tl; }
+        else { double tl = -g / gd; if (tl > a_lo) a_lo = tl; }
+    }
+    if (ok && a_lo <= a_hi) { lo = a_lo; hi = a_hi; }
+    /* edges */
+    for (int i = 0; i < 3; ++i) {
+        double cap[7], s0, s1;
+        for (int k = 0; k < 3; ++k) { cap[k] = P[i][k]; cap[3 + k] = P[(i + 1) % 3][k]; }
+        cap[6] = r;
+        if (ray_capsule64(o, d, cap, &s0, &s1)) { lo = fmin(lo, s0); hi = fmax(hi, s1); }
+    }
+    if (lo > hi) return 0;
+    *t0 = lo; *t1 = hi;
+    return 1;
+}
+
 static int ray_voi64(int kind, const double *v, const double o[3], const double d[3],
                      double *t0, double *t1) {
     switch (kind) {
+    case K_RTRI: return ray_stri64(o, d, v, t0, t1);
+    case K_QUADRIC: return ray_obox64(o, d, v, t0, t1);
     case K_SPHERE: { double c[3] = {v[0], v[1], v[2]}; return ray_sphere64(o, d, c, v[3], t0, t1); }
     case K_RBOX: return ray_obox64(o, d, v, t0, t1);
     case K_CAPSULE: case K_SCONE: return ray_capsule64(o, d, v, t0, t1);
@@ -777,6 +944,100 @@ static int ray_capsule32(const float o[3], const float d[3], const float *q, flo
     return 1;
 }
 
+/* Sphere-triangle in FP32 (the same operations as the GPU culling kernel):
+ * the prism over the triangle, then the three edge capsules; the interval is
+ * the hull of the parts' (the volume is convex).  a, b, c: vertices as the
+ * kernel reconstructs them from the record words; n, m[0..2]: unit normal
+ * and in-plane edge normals of edges a-b, b-c, c-a; r: the radius. */
+static int ray_stri32(const float o[3], const float d[3], const float a[3], const float b[3], const float c[3],
+                      const float n[3], const float m[3][3], float r, float *t0, float *t1) {
+    float lo = INFINITY, hi = -INFINITY, s0, s1;
+    float oa[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
+    float ob[3] = {o[0] - b[0], o[1] - b[1], o[2] - b[2]};
+    float oc[3] = {o[0] - c[0], o[1] - c[1], o[2] - c[2]};
+    float so = (n[0] * oa[0] + n[1] * oa[1]) + n[2] * oa[2];
+    float g[3];
+    g[0] = (m[0][0] * oa[0] + m[0][1] * oa[1]) + m[0][2] * oa[2];
+    g[1] = (m[1][0] * ob[0] + m[1][1] * ob[1]) + m[1][2] * ob[2];
+    g[2] = (m[2][0] * oc[0] + m[2][1] * oc[1]) + m[2][2] * oc[2];
+    float a_lo = -INFINITY, a_hi = INFINITY;
+    int ok = 1;
+    float sd = (n[0] * d[0] + n[1] * d[1]) + n[2] * d[2];
+    if (sd == 0.0f) {
+        if (so < -r || so > r) ok = 0;
+    } else {
+        float ta = (-r - so) / sd, tb = (r - so) / sd;
+        a_lo = ta < tb ? ta : tb;
+        a_hi = ta < tb ? tb : ta;
+    }
+    for (int i = 0; i < 3; ++i) {
+        float gd = (m[i][0] * d[0] + m[i][1] * d[1]) + m[i][2] * d[2];
+        if (gd == 0.0f) {
+            if (g[i] > 0.0f) ok = 0;
+        } else {
+            float tl = (-g[i]) / gd;
+            if (gd > 0.0f) { if (tl < a_hi) a_hi = tl; }
+            else { if (tl > a_lo) a_lo = tl; }
+        }
+    }
+    if (ok && a_lo <= a_hi) { lo = a_lo; hi = a_hi; }
+    const float *P[3] = {a, b, c};
+    for (int i = 0; i < 3; ++i) {
+        float cap[6];
+        for (int k = 0; k < 3; ++k) { cap[k] = P[i][k]; cap[3 + k] = P[(i + 1) % 3][k]; }
+        if (ray_capsule32(o, d, cap, r, &s0, &s1)) { if (s0 < lo) lo = s0; if (s1 > hi) hi = s1; }
+    }
+    if (lo > hi) return 0;
+    *t0 = lo; *t1 = hi;
+    return 1;
+}
+
+/* Record words of a rounded triangle as the library's host preparation
+ * derives them in FP64 and rounds once to FP32 (edges e0 = b - a,
+ * e2 = a - c, unit normal n = e0 x (c - a) / |.|, edge normals m_i = e_i x n),
+ * and the vertices b = a + e0, c = a - e2 that the culling kernel rebuilds
+ * from them in FP32. */
+static void tri_words32(const float *q, float a[3], float b[3], float c[3], float n[3], float m[3][3]) {
+    double e[3][3];
+    for (int k = 0; k < 3; ++k) {
+        e[0][k] = (double)q[3 + k] - q[k];
+        e[1][k] = (double)q[6 + k] - q[3 + k];
+        e[2][k] = (double)q[k] - q[6 + k];
+    }
+    double ca[3] = {-e[2][0], -e[2][1], -e[2][2]};
+    double cr[3] = {e[0][1] * ca[2] - e[0][2] * ca[1], e[0][2] * ca[0] - e[0][0] * ca[2],
+                    e[0][0] * ca[1] - e[0][1] * ca[0]};
+    double len = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    double nd[3];
+    for (int k = 0; k < 3; ++k) nd[k] = len > 0.0 ? cr[k] / len : 0.0;
+    for (int i = 0; i < 3; ++i) {
+        m[i][0] = (float)(e[i][1] * nd[2] - e[i][2] * nd[1]);
+        m[i][1] = (float)(e[i][2] * nd[0] - e[i][0] * nd[2]);
+        m[i][2] = (float)(e[i][0] * nd[1] - e[i][1] * nd[0]);
+    }
+    for (int k = 0; k < 3; ++k) {
+        n[k] = (float)nd[k];
+        a[k] = q[k];
+        b[k] = a[k] + (float)e[0][k];
+        c[k] = a[k] - (float)e[2][k];
+    }
+}
+
+/* Rotation rows of a bounded quadric as the library's host preparation
+ * derives them (M = R^T of the normalised quaternion, FP64, rounded once);
+ * out: centre at [0:3], M at [3:12] (the oriented-box record layout). */
+static void quadric_box32(const float *q, float *box) {
+    double w = q[3], x = q[4], y = q[5], z = q[6];
+    double nq = sqrt(w * w + x * x + y * y + z * z);
+    if (nq > 0.0) { w /= nq; x /= nq; y /= nq; z /= nq; }
+    double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)},
+                      {2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)},
+                      {2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)}};
+    for (int k = 0; k < 3; ++k) box[k] = q[k];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) box[3 + 3 * i + j] = (float)R[j][i];
+}
+
 /* Record words that the library's host preparation derives in FP64 and
  * rounds once to FP32 (the unit axis of a torus). */
 static void unit3_f32(const float *a, float u[3]) {
@@ -834,7 +1095,15 @@ int or_cull(int n, int root, const int32_t *kind, const int32_t *left, const int
             /* FP32 VOI: extents ((size + d) + pad) in single precision. */
             float dp = (float)roi[i];
             float rr32 = 0, e32[3] = {0, 0, 0}, ca32[3] = {0, 0, 0}, cb32[3] = {0, 0, 0};
+            float ta32[3], tb32[3], tc32[3], tn32[3], tm32[3][3], qbox32[12];
             if (k == K_SPHERE) rr32 = (q[3] + dp) + pad;
+            else if (k == K_RTRI) {
+                tri_words32(q, ta32, tb32, tc32, tn32, tm32);
+                rr32 = (q[9] + dp) + pad;
+            } else if (k == K_QUADRIC) {
+                quadric_box32(q, qbox32);
+                for (int a = 0; a < 3; ++a) e32[a] = (q[7 + a] + dp) + pad;
+            }
             else if (k == K_CAPSULE) rr32 = (q[6] + dp) + pad;
             else if (k == K_SCONE) rr32 = ((q[6] > q[7] ? q[6] : q[7]) + dp) + pad;
             else if (k == K_TORUS) {
@@ -871,6 +1140,9 @@ int or_cull(int n, int root, const int32_t *kind, const int32_t *left, const int
                         cam_ray32(&c, px, py, d);
                         if (k == K_SPHERE) h = ray_sphere32(c.of, d, q, rr32, &t0, &t1);
                         else if (k == K_RBOX || k == K_ELLIPSOID) h = ray_obox32(c.of, d, q, e32, &t0, &t1);
+                        else if (k == K_QUADRIC) h = ray_obox32(c.of, d, qbox32, e32, &t0, &t1);
+                        else if (k == K_RTRI)
+                            h = ray_stri32(c.of, d, ta32, tb32, tc32, tn32, tm32, rr32, &t0, &t1);
                         else if (k == K_TORUS) h = ray_cylinder32(c.of, d, ca32, cb32, rr32, &t0, &t1);
                         else h = ray_capsule32(c.of, d, q, rr32, &t0, &t1);
                         if (!h) continue;

@@ -38,6 +38,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     build_dir.mkdir(exist_ok=True)
     common = ["-O3", "-std=c++17", "-lineinfo", "-I", str(ROOT / "include"), "-I", str(CSRC),
               "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr"]
+    cmds = []
     for src in SOURCES:
         obj = build_dir / (src + ".o")
         cmd = [nvcc(), *ARCH, *common, "-c", str(CSRC / src), "-o", str(obj)]
@@ -45,8 +46,17 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             cmd += ["-Xptxas", "-v"]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
-        subprocess.run(cmd, check=True)
+        cmds.append(cmd)
         objs.append(str(obj))
+    # the sources compile independently: in parallel (the tracer's kernel
+    # instances take most of the time)
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
+        for r in ex.map(lambda c: subprocess.run(c, capture_output=ptxas_info), cmds):
+            if ptxas_info:
+                sys.stderr.write(r.stderr.decode(errors="replace"))
+            if r.returncode != 0:
+                raise subprocess.CalledProcessError(r.returncode, r.args)
     tmp = LIB.with_suffix(".so.tmp%d" % os.getpid())
     cmd = [nvcc(), *ARCH, "-shared", "-o", str(tmp), *objs]
     subprocess.run(cmd, check=True)

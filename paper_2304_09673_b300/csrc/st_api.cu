@@ -14,6 +14,7 @@ namespace st {
 int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st_trace_opts &o, float *depth,
                  float *normal, uint32_t *evals, uint8_t *flags, uint64_t *counters, void *stream, float *records,
                  uint32_t rec_cap, uint32_t *rec_count, int rec_stride);
+int trace_status_code(const uint32_t *status, cudaStream_t st, const char *who);
 TraceParams make_trace_params(const st_trace_opts &o, double diameter, double extent);
 
 static thread_local std::string g_err;
@@ -24,6 +25,8 @@ int count_launch() {
   return 0;
 }
 void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static std::atomic<uint64_t> g_allocs{0};
+void count_device_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 #define ST_CK(call)                                                        \
@@ -46,6 +49,7 @@ struct DBuf {
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
+    count_device_alloc();
     cudaError_t e = cudaMalloc(&p, want * sizeof(T));
     if (e == cudaSuccess) cap = want;
     return e;
@@ -125,6 +129,9 @@ static DevScene dev_scene(const st_scene *s) {
   return d;
 }
 
+bool scene_has_stri(const st_scene *s) { return s->prep.has_stri; }
+bool scene_has_further(const st_scene *s) { return s->prep.has_further; }
+
 // Read-only facts of a scene for entry points defined in other files.
 void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, double *extent, int *n_sm) {
   *sc = dev_scene(s);
@@ -150,6 +157,7 @@ extern "C" {
 const char *st_last_error(void) { return st::g_err.c_str(); }
 const char *st_version(void) { return "st 0.1 (sm_103a)"; }
 uint64_t st_kernel_launches(void) { return g_launches.load(); }
+uint64_t st_device_allocations(void) { return g_allocs.load(); }
 
 int st_scene_create(const st_scene_desc *desc, st_scene **out, void *stream) {
   if (!desc || !out) { set_error("null argument"); return ST_ERR_INVALID; }
@@ -215,6 +223,15 @@ void st_scene_destroy(st_scene *s) {
   delete s;
 }
 
+int st_scene_info(const st_scene *s, double *out) {
+  if (!s || !out) { set_error("null argument"); return ST_ERR_INVALID; }
+  out[0] = s->prep.diameter;
+  out[1] = s->prep.extent;
+  out[2] = (double)s->n_prims;
+  out[3] = (double)s->prep.stack_depth;
+  return ST_OK;
+}
+
 int st_scene_addresses(const st_scene *s, int32_t *po_of_desc) {
   if (!s || !po_of_desc) { set_error("null argument"); return ST_ERR_INVALID; }
   std::memcpy(po_of_desc, s->prep.po_of_desc.data(), s->prep.po_of_desc.size() * sizeof(int32_t));
@@ -238,7 +255,7 @@ int st_scene_update_prims(st_scene *s, const int32_t *ids, const float *params, 
       set_error(std::string("st_scene_update_prims: ") + e);
       return ST_ERR_INVALID;
     }
-    float w[20];
+    float w[4 * kMaxRecWords];
     prim_words(kind, params + (size_t)i * ST_REC_FLOATS, w);
     for (int k = 0; k < rec_words(kind); ++k) {
       index.push_back(s->prep.rec_off[a] + k);
@@ -298,7 +315,7 @@ int st_build_tiles(st_scene *s, const st_camera *cam, int tile, st_tiles *out, v
     ST_CK(cudaMemsetAsync(s->tile_count.p, 0, (size_t)n_tiles * 4, st));
     ST_CK(cudaMemsetAsync(s->small.p + 1, 0, 3 * sizeof(uint32_t), st));
     launch_cull_pairs(s->job.p, 1, s->cand_off.p, np, cand_total, s->rects.p, s->tile_count.p, s->pairs.p,
-                      (uint32_t)s->pairs.cap, pair_counter, s->n_sm, st);
+                      (uint32_t)s->pairs.cap, pair_counter, s->n_sm, st, s->prep.has_stri);
     scan_u32(s->tile_count.p, s->offsets.p, n_tiles, s->scan_sums.p, tile_total, max_ov,
              s->offsets.p + n_tiles, st);
     ST_CK(cudaGetLastError());
@@ -309,17 +326,16 @@ int st_build_tiles(st_scene *s, const st_camera *cam, int tile, st_tiles *out, v
   }
   const uint32_t n_entries = host_small[1];
   const uint32_t max_overlap = host_small[2];
-  if (max_overlap > kSortLarge) {
-    set_error("a tile list exceeds the sort capacity (16384 entries)");
-    return ST_ERR_CAPACITY;
-  }
   ST_CK(s->keys.ensure(n_entries + 1));
   ST_CK(s->ztmp.ensure(n_entries + 1));
   ST_CK(s->z_in.ensure(n_entries + 1));
   ST_CK(s->z_out.ensure(n_entries + 1));
   ST_CK(s->prim.ensure(n_entries + 1));
+  // (tile_count is free after the scan: it lists the tiles of lists longer
+  // than the shared-memory sort, counted in small[5])
   launch_scatter_sort(s->pairs.p, pair_counter, (uint32_t)s->pairs.cap, s->offsets.p, n_tiles, max_overlap,
-                      s->keys.p, s->ztmp.p, s->z_in.p, s->z_out.p, s->prim.p, s->n_sm, st);
+                      s->keys.p, s->ztmp.p, s->z_in.p, s->z_out.p, s->prim.p, s->n_sm, st, nullptr,
+                      s->tile_count.p, s->small.p + 5);
   ST_CK(cudaGetLastError());
   out->tile = tile;
   out->tiles_x = tiles_x;
@@ -437,6 +453,7 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
   L.counters = counters;
   L.tile_stats = o.tile_stats;
   L.step_mode = tp.step_mode;
+  L.further = s->prep.has_further ? 1 : 0;
   L.mlp = tp.step_mode == ST_STEP_LEARNED ? o.mlp : nullptr;
   L.records = records;
   L.rec_cap = rec_cap;
@@ -447,9 +464,11 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
   L.work_in_smem = 1;
   if (trace_smem_per_warp(L) * 16 > 200 * 1024) L.work_in_smem = 0;
   if (!L.work_in_smem) {
-    const int warps_total = s->n_sm * 64;
+    // one work area per CTA of the persistent grid (indexed by blockIdx.x)
+    const int per_sm = trace_ctas_per_sm(L);
+    if (per_sm < 1) { set_error("st_trace: no valid launch configuration"); return ST_ERR_INVALID; }
     L.g_work_words = trace_work_words(L);
-    ST_CK(s->g_work.ensure((size_t)warps_total * L.g_work_words));
+    ST_CK(s->g_work.ensure((size_t)s->n_sm * per_sm * L.g_work_words));
     L.g_work = s->g_work.p;
   }
   ST_CK(s->item_counter.ensure(4));
@@ -466,9 +485,41 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
     ST_CK(s->split.ensure(trace_split_words(L.max_tile_rays, L.split_cap)));
     L.split = s->split.p;
     L.split_cycles = split_cycles;
+    L.heavy_len = trace_heavy_len(o.heavy_split_len);
     ST_CK(cudaMemsetAsync(L.split, 0, trace_split_zero_bytes(L.split_cap), st));
   }
+  L.idle_spins = o.wait_spin_limit;
+  L.split_spins = o.wait_spin_limit;
+  uint32_t *status = o.check_status ? s->small.p + 8 : nullptr;
+  if (status) {
+    ST_CK(cudaMemsetAsync(status, 0, sizeof(uint32_t), st));
+    L.status = status;
+  }
   ST_CK(trace_launch(s->job.p, 1, L, s->n_sm, st));
+  if (status) return trace_status_code(status, st, "st_trace");
+  return ST_OK;
+}
+
+// Reads a launch's device status word (synchronising the stream) and maps
+// its bits to a return code: a bounded wait that ran out -> ST_ERR_TIMEOUT;
+// a list beyond the launch's capacity -> ST_ERR_CAPACITY; a view or stack
+// overflow -> ST_ERR_INVALID.
+int trace_status_code(const uint32_t *status, cudaStream_t st, const char *who) {
+  uint32_t h = 0;
+  ST_CK(cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, st));
+  ST_CK(cudaStreamSynchronize(st));
+  if (h & ST_STATUS_WAIT) {
+    set_error(std::string(who) + ": a bounded wait between the warps of a tile ran out (device status bit 3)");
+    return ST_ERR_TIMEOUT;
+  }
+  if (h & ST_STATUS_CAPACITY) {
+    set_error(std::string(who) + ": a tile list is longer than the launch's capacity (device status bit 2)");
+    return ST_ERR_CAPACITY;
+  }
+  if (h & (ST_STATUS_VIEW | ST_STATUS_STACK)) {
+    set_error(std::string(who) + ": a pruned view or evaluation stack overflowed (device status bits 0-1)");
+    return ST_ERR_INVALID;
+  }
   return ST_OK;
 }
 

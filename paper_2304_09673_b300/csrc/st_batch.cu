@@ -23,6 +23,8 @@
 
 namespace st {
 void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, double *extent, int *n_sm);
+bool scene_has_stri(const st_scene *s);
+bool scene_has_further(const st_scene *s);
 TraceParams make_trace_params(const st_trace_opts &o, double diameter, double extent);
 }  // namespace st
 
@@ -190,6 +192,7 @@ struct Buf {   // device buffer owned by a batch or the autotuner
   cudaError_t ensure(size_t n) {
     if (n <= cap) return cudaSuccess;
     release();
+    count_device_alloc();
     cudaError_t e = cudaMalloc(&p, n * sizeof(T));
     if (e == cudaSuccess) cap = n; else p = nullptr;
     return e;
@@ -230,6 +233,8 @@ struct st_batch {
   Buf<uint32_t> prim;
   uint32_t pair_cap = 0, overlap_cap = 0;
   uint32_t longest_seen = 0, entries_seen = 0;   // sizing pass: longest list, entry total
+  bool has_stri = false;   // a scene holds rounded triangles (second culling launch)
+  bool has_further = false;   // a scene holds primitives beyond the three basic families
   TraceLaunch L;
   int grid = 0;
   size_t smem = 0;
@@ -255,7 +260,7 @@ void enqueue_culling(st_batch *b, cudaStream_t s, uint32_t pair_cap) {
   launch_prim_bounds(b->d_jobs.p, (int)b->jobs.size(), b->n_prims, b->cand_count.p, b->rects.p, s);
   scan_u32(b->cand_count.p, b->cand_off.p, b->n_prims, b->scan_sums.p, cand_total, nullptr, nullptr, s);
   launch_cull_pairs(b->d_jobs.p, (int)b->jobs.size(), b->cand_off.p, b->n_prims, cand_total, b->rects.p,
-                    b->tile_count.p, b->pairs.p, pair_cap, pair_counter, b->n_sm, s);
+                    b->tile_count.p, b->pairs.p, pair_cap, pair_counter, b->n_sm, s, b->has_stri);
   scan_u32(b->tile_count.p, b->offsets.p, b->n_tiles, b->scan_sums.p, tile_total, max_ov, b->offsets.p + b->n_tiles,
            s);
 }
@@ -265,6 +270,8 @@ int plan(st_batch *b) {
   b->drop_graph();
   const int n = (int)b->scenes.size();
   b->jobs.assign(n, Job{});
+  b->has_stri = false;
+  b->has_further = false;
   uint32_t prim_base = 0, tile_base = 0;
   int max_tile = 8, stack_slots = 2;
   for (int i = 0; i < n; ++i) {
@@ -273,6 +280,8 @@ int plan(st_batch *b) {
     int sd = 0, nsm = 1;
     double diam = 0, ext = 0;
     scene_facts(b->scenes[i], &j.sc, &sd, &diam, &ext, &nsm);
+    if (scene_has_stri(b->scenes[i])) b->has_stri = true;
+    if (scene_has_further(b->scenes[i])) b->has_further = true;
     b->n_sm = nsm;
     camera_basis(b->cams[i], j.cam);
     const int T = b->tune[i].tile;
@@ -325,15 +334,11 @@ int plan(st_batch *b) {
     cap = host_small[1];
   }
   if (host_small[1] > cap) { set_error("st_batch: culling did not converge"); return ST_ERR_CAPACITY; }
-  if (host_small[2] > kSortLarge) {
-    set_error("st_batch: a tile list exceeds the sort capacity (16384 entries)");
-    return ST_ERR_CAPACITY;
-  }
   b->longest_seen = host_small[2];
   b->entries_seen = host_small[3];
   // Headroom for edits between renders.
   b->pair_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, (uint64_t)host_small[1] * 3 / 2 + 4096);
-  b->overlap_cap = std::min<uint32_t>(kSortLarge, std::max<uint32_t>(host_small[2] + host_small[2] / 4 + 16, 64));
+  b->overlap_cap = std::max<uint32_t>(host_small[2] + host_small[2] / 4 + 16, 64);
   BK(b->pairs.ensure(b->pair_cap));
   BK(b->keys.ensure((size_t)b->pair_cap + 1));
   BK(b->ztmp.ensure((size_t)b->pair_cap + 1));
@@ -363,12 +368,16 @@ int plan(st_batch *b) {
   L.status = b->status.p;
   L.order = b->order.p;
   L.step_mode = b->opts.step_mode;
+  L.further = b->has_further ? 1 : 0;
   L.mlp = L.step_mode == ST_STEP_LEARNED ? b->opts.mlp : nullptr;
   if (L.step_mode == ST_STEP_LEARNED && L.stack_slots < 10) L.stack_slots = 10;
   L.work_in_smem = trace_smem_per_warp(L) * 16 > 200 * 1024 ? 0 : 1;
   if (!L.work_in_smem) {
+    // one work area per CTA of the persistent grid (indexed by blockIdx.x)
+    const int per_sm = trace_ctas_per_sm(L);
+    if (per_sm < 1) { set_error("st_batch: no valid launch configuration"); return ST_ERR_INVALID; }
     L.g_work_words = trace_work_words(L);
-    BK(b->g_work.ensure((size_t)b->n_sm * 64 * L.g_work_words));
+    BK(b->g_work.ensure((size_t)b->n_sm * per_sm * L.g_work_words));
     L.g_work = b->g_work.p;
   }
   const long long split_cycles = trace_split_cycles(b->opts.split_kcycles);
@@ -377,7 +386,10 @@ int plan(st_batch *b) {
     BK(b->split.ensure(trace_split_words(L.max_tile_rays, L.split_cap)));
     L.split = b->split.p;
     L.split_cycles = split_cycles;
+    L.heavy_len = trace_heavy_len(b->opts.heavy_split_len);
   }
+  L.idle_spins = b->opts.wait_spin_limit;
+  L.split_spins = b->opts.wait_spin_limit;
   BK(trace_plan(L, b->n_sm, &b->grid, &b->smem));
   BK(cudaStreamSynchronize(s));
 
@@ -394,7 +406,8 @@ int plan(st_batch *b) {
   enqueue_culling(b, cs, b->pair_cap);
   launch_check_capacity(b->small.p + 1, b->pair_cap, b->small.p + 2, b->overlap_cap, b->status.p, cs);
   launch_scatter_sort(b->pairs.p, b->small.p + 1, b->pair_cap, b->offsets.p, b->n_tiles, b->overlap_cap, b->keys.p,
-                      b->ztmp.p, b->z_in.p, b->z_out.p, b->prim.p, b->n_sm, cs, b->status.p);
+                      b->ztmp.p, b->z_in.p, b->z_out.p, b->prim.p, b->n_sm, cs, b->status.p, b->tile_count.p,
+                      b->small.p + 5);
   launch_tile_order(b->d_jobs.p, n, b->n_tiles, b->order.p, cs);
   cudaError_t le = trace_launch_planned(b->d_jobs.p, n, L, b->grid, b->smem, cs);
   cudaGraph_t g = nullptr;

@@ -17,6 +17,11 @@
 //   k_scatter      pair -> CSR slot (offset + rank)
 //   k_tile_sort    per-tile bitonic sort in shared memory by
 //                  (z_in, post-order address) (sorted lists, Sec. 6.2)
+//   lists longer than kSortLarge (no length cap): chunks of kSortLarge
+//                  entries sorted in shared memory (k_chunk_sort), then
+//                  pairwise merges of sorted runs in global memory
+//                  (k_merge_pass), each element placed by a binary search
+//                  in the partner run
 #include <cstdint>
 
 #include "st_geom.cuh"
@@ -121,6 +126,17 @@ __global__ void k_prim_bounds(const Job *jobs, int n_jobs, uint32_t n_prims_tota
   int st;
   if (v.fam == VOI_SPHERE) {
     st = sphere_pixel_rect(cam, v.c, v.r, px);
+  } else if (v.fam == VOI_STRI) {
+    // bounding sphere: the vertices' centroid, the farthest vertex + r
+    const float C[3] = {(v.c[0] + v.b[0] + v.e[0]) / 3.f, (v.c[1] + v.b[1] + v.e[1]) / 3.f,
+                        (v.c[2] + v.b[2] + v.e[2]) / 3.f};
+    float rho = 0.f;
+    for (int k = 0; k < 3; ++k) {
+      const float *p = k == 0 ? v.c : (k == 1 ? v.b : v.e);
+      const float dx = p[0] - C[0], dy = p[1] - C[1], dz = p[2] - C[2];
+      rho = fmaxf(rho, sqrtf(dx * dx + dy * dy + dz * dz));
+    }
+    st = sphere_pixel_rect(cam, C, rho * 1.0001f + v.r, px);
   } else if (v.fam == VOI_BOX) {
     st = box_pixel_rect(cam, v, px);
     if (st == 2) {
@@ -172,6 +188,42 @@ __global__ void k_prim_bounds(const Job *jobs, int n_jobs, uint32_t n_prims_tota
 constexpr int kCullWarps = 8;
 constexpr int kPairsPerWarp = 8;
 
+// The tile's pixel-centre rays against one volume of interest: this lane's
+// rays (one column, rows lane / T, lane / T + 32 / T, ...), with the same
+// per-ray arithmetic as pixel_ray.  Returns the lane's (min entry, max exit)
+// bits (0xFFFFFFFF, 0 when none hits).
+template <bool kStri>
+__device__ __forceinline__ uint2 cull_rays(const Voi &v, const VoiRay &vq, const DevCamera &cam, int T, int tx,
+                                           int ty, int lane) {
+  uint32_t zin_bits = 0xFFFFFFFFu, zout_bits = 0u;
+  // Lane -> one pixel column (T <= 32 divides 32): its u and F + u R are
+  // computed once; the rows' v come from the lanes that computed them.
+  const int px = tx * T + lane % T;
+  const float u = ieee_sub(ieee_div((float)(2 * px + 1), (float)cam.W), 1.0f);
+  const float fu[3] = {ieee_add(cam.F[0], ieee_mul(u, cam.R[0])), ieee_add(cam.F[1], ieee_mul(u, cam.R[1])),
+                       ieee_add(cam.F[2], ieee_mul(u, cam.R[2]))};
+  const float v_row = ieee_sub(1.0f, ieee_div((float)(2 * (ty * T + lane % T) + 1), (float)cam.H));
+  const int rows_per_pass = 32 / T;
+  for (int row = lane / T; row < T; row += rows_per_pass) {
+    const int py = ty * T + row;
+    const float vv = __shfl_sync(0xFFFFFFFFu, v_row, row);
+    if (px >= cam.W || py >= cam.H) continue;
+    float d[3], t0, t1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = ieee_add(fu[k], ieee_mul(vv, cam.U[k]));
+    if (!voi_ray_hit<kStri>(v, vq, d, t0, t1)) continue;
+    // t0, t1 >= 0: float order equals unsigned bit order.
+    uint32_t b0 = __float_as_uint(t0), b1 = __float_as_uint(t1);
+    zin_bits = b0 < zin_bits ? b0 : zin_bits;
+    zout_bits = b1 > zout_bits ? b1 : zout_bits;
+  }
+  return make_uint2(zin_bits, zout_bits);
+}
+
+// kStri: the launch for sphere-triangle volumes only (a second launch, made
+// only for scenes with rounded triangles); the first launch skips them.
+// Their long ray test would otherwise weigh on every family's registers.
+template <bool kStri>
 __global__ void __launch_bounds__(kCullWarps * 32, 4)
 k_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_prims_total,
              const uint32_t *cand_total, const int4 *rects, uint32_t *tile_count,
@@ -210,8 +262,8 @@ k_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_p
       if (gn != g) {
         g = gn;
         jb = find_job_prim(jobs, n_jobs, g);
-        load_voi(jobs[jb].sc, g - jobs[jb].prim_base, v);
-        voi_ray_setup(v, jobs[jb].cam, vq);
+        load_voi<kStri>(jobs[jb].sc, g - jobs[jb].prim_base, v, vq.cc.wa);
+        if ((v.fam == VOI_STRI) == kStri) voi_ray_setup<kStri>(v, jobs[jb].cam, vq);
       }
       const Job &job = jobs[jb];
       const uint32_t j = g - job.prim_base;
@@ -221,29 +273,9 @@ k_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_p
       const int tx = rect.x + (int)(k % rw), ty = rect.y + (int)(k / rw);
       const int T = job.tl.tile;
       const DevCamera &cam = job.cam;
-      uint32_t zin_bits = 0xFFFFFFFFu, zout_bits = 0u;
-      // Lane -> one pixel column (T <= 32 divides 32): its u and F + u R are
-      // computed once; the rows' v come from the lanes that computed them.
-      // Per ray this is pixel_ray's arithmetic, operation for operation.
-      const int px = tx * T + lane % T;
-      const float u = ieee_sub(ieee_div((float)(2 * px + 1), (float)cam.W), 1.0f);
-      const float fu[3] = {ieee_add(cam.F[0], ieee_mul(u, cam.R[0])), ieee_add(cam.F[1], ieee_mul(u, cam.R[1])),
-                           ieee_add(cam.F[2], ieee_mul(u, cam.R[2]))};
-      const float v_row = ieee_sub(1.0f, ieee_div((float)(2 * (ty * T + lane % T) + 1), (float)cam.H));
-      const int rows_per_pass = 32 / T;
-      for (int row = lane / T; row < T; row += rows_per_pass) {
-        const int py = ty * T + row;
-        const float vv = __shfl_sync(0xFFFFFFFFu, v_row, row);
-        if (px >= cam.W || py >= cam.H) continue;
-        float d[3], t0, t1;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) d[k] = ieee_add(fu[k], ieee_mul(vv, cam.U[k]));
-        if (!voi_ray_hit(v, vq, d, t0, t1)) continue;
-        // t0, t1 >= 0: float order equals unsigned bit order.
-        uint32_t b0 = __float_as_uint(t0), b1 = __float_as_uint(t1);
-        zin_bits = b0 < zin_bits ? b0 : zin_bits;
-        zout_bits = b1 > zout_bits ? b1 : zout_bits;
-      }
+      if ((v.fam == VOI_STRI) != kStri) continue;
+      const uint2 zb = cull_rays<kStri>(v, vq, cam, T, tx, ty, lane);
+      uint32_t zin_bits = zb.x, zout_bits = zb.y;
       zin_bits = __reduce_min_sync(0xFFFFFFFFu, zin_bits);
       zout_bits = __reduce_max_sync(0xFFFFFFFFu, zout_bits);
       if (lane == 0 && zin_bits != 0xFFFFFFFFu) {
@@ -340,6 +372,125 @@ __global__ void k_tile_sort(const uint32_t *offsets, uint32_t n_tiles, const uin
       z_out[beg + i] = sv[i];
     }
     __syncthreads();
+  }
+}
+
+// ---- lists longer than kSortLarge -----------------------------------------------
+// Keys are unique within a list (one entry per primitive and tile), so an
+// element's place in a merged run is its offset in its own run plus the
+// number of keys of the partner run below it.
+__global__ void k_long_lists(const uint32_t *offsets, uint32_t n_tiles, uint32_t *list, uint32_t *count,
+                             const uint32_t *abort) {
+  if (aborted(abort)) return;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
+    if (offsets[t + 1] - offsets[t] > kSortLarge) list[atomicAdd(count, 1u)] = t;
+}
+
+// One CTA per chunk of kSortLarge entries of a long list: bitonic sort in
+// shared memory, written back in place (sorted runs of kSortLarge).
+__global__ void k_chunk_sort(const uint32_t *offsets, const uint32_t *list, const uint32_t *count, uint64_t *keys,
+                             float *z_out_tmp, const uint32_t *abort) {
+  if (aborted(abort)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);
+  float *sv = reinterpret_cast<float *>(sk + kSortLarge);
+  const uint32_t n_long = *count;
+  for (uint32_t li = 0; li < n_long; ++li) {
+    const uint32_t t = list[li];
+    const uint32_t beg = offsets[t], len = offsets[t + 1] - beg;
+    const uint32_t n_chunks = (len + kSortLarge - 1) / kSortLarge;
+    for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+      const uint32_t c0 = beg + c * kSortLarge, cl = min(kSortLarge, len - c * kSortLarge);
+      for (uint32_t i = threadIdx.x; i < kSortLarge; i += blockDim.x) {
+        if (i < cl) { sk[i] = keys[c0 + i]; sv[i] = z_out_tmp[c0 + i]; }
+        else { sk[i] = ~0ull; sv[i] = 0.f; }
+      }
+      __syncthreads();
+      for (uint32_t k = 2; k <= kSortLarge; k <<= 1) {
+        for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+          for (uint32_t i = threadIdx.x; i < kSortLarge; i += blockDim.x) {
+            const uint32_t l = i ^ jj;
+            if (l > i) {
+              const bool up = (i & k) == 0;
+              const uint64_t a = sk[i], b = sk[l];
+              if ((a > b) == up) {
+                sk[i] = b; sk[l] = a;
+                const float x = sv[i]; sv[i] = sv[l]; sv[l] = x;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (uint32_t i = threadIdx.x; i < cl; i += blockDim.x) {
+        keys[c0 + i] = sk[i];
+        z_out_tmp[c0 + i] = sv[i];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Sorted runs of w entries (a list's last run may be shorter) merged in
+// pairs into runs of 2w.  The two buffers: A = (64-bit keys, z_out) as the
+// scatter wrote them, B = the output arrays (z_in bits = key >> 32, prim =
+// low word, z_out).  kFromA: read A, write B; else read B, write A.
+template <bool kFromA>
+__global__ void k_merge_pass(const uint32_t *offsets, const uint32_t *list, const uint32_t *count, uint32_t w,
+                             uint64_t *keys, float *z_out_tmp, float *z_in, uint32_t *prim, float *z_out,
+                             const uint32_t *abort) {
+  if (aborted(abort)) return;
+  auto key_at = [&](uint32_t i) -> uint64_t {
+    if (kFromA) return keys[i];
+    return ((uint64_t)__float_as_uint(z_in[i]) << 32) | (uint64_t)prim[i];
+  };
+  const uint32_t n_long = *count;
+  for (uint32_t li = 0; li < n_long; ++li) {
+    const uint32_t t = list[li];
+    const uint32_t beg = offsets[t], len = offsets[t + 1] - beg;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += gridDim.x * blockDim.x) {
+      const uint32_t r = e / w, base = (r & ~1u) * w;
+      const uint32_t lo = (r & 1u) ? base : base + w;          // partner run [lo, hi)
+      const uint32_t hi = (r & 1u) ? base + w : min(base + 2 * w, len);
+      const uint64_t key = key_at(beg + e);
+      const float zo = kFromA ? z_out_tmp[beg + e] : z_out[beg + e];
+      uint32_t below = 0;   // keys of the partner run below `key`
+      if (lo < hi) {
+        uint32_t a = lo, b = hi;
+        while (a < b) {
+          const uint32_t m = (a + b) >> 1;
+          if (key_at(beg + m) < key) a = m + 1; else b = m;
+        }
+        below = a - lo;
+      }
+      const uint32_t dst = beg + base + (e - r * w) + below;
+      if (kFromA) {
+        z_in[dst] = __uint_as_float((uint32_t)(key >> 32));
+        prim[dst] = (uint32_t)key;
+        z_out[dst] = zo;
+      } else {
+        keys[dst] = key;
+        z_out_tmp[dst] = zo;
+      }
+    }
+  }
+}
+
+// Final copy of long lists left in buffer A into the output arrays.
+__global__ void k_long_copy(const uint32_t *offsets, const uint32_t *list, const uint32_t *count,
+                            const uint64_t *keys, const float *z_out_tmp, float *z_in, uint32_t *prim, float *z_out,
+                            const uint32_t *abort) {
+  if (aborted(abort)) return;
+  const uint32_t n_long = *count;
+  for (uint32_t li = 0; li < n_long; ++li) {
+    const uint32_t t = list[li];
+    const uint32_t beg = offsets[t], len = offsets[t + 1] - beg;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += gridDim.x * blockDim.x) {
+      const uint64_t key = keys[beg + e];
+      z_in[beg + e] = __uint_as_float((uint32_t)(key >> 32));
+      prim[beg + e] = (uint32_t)key;
+      z_out[beg + e] = z_out_tmp[beg + e];
+    }
   }
 }
 
@@ -466,10 +617,15 @@ void launch_prim_bounds(const Job *jobs, int n_jobs, uint32_t n_prims, uint32_t 
 
 void launch_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_prims,
                        const uint32_t *cand_total, const int4 *rects, uint32_t *tile_count, Pair *pairs,
-                       uint32_t pair_cap, uint32_t *pair_counter, int n_sm, cudaStream_t s) {
+                       uint32_t pair_cap, uint32_t *pair_counter, int n_sm, cudaStream_t s, bool stri) {
   if (!n_prims) return;
-  count_launch(), k_cull_pairs<<<n_sm * 8, kCullWarps * 32, 0, s>>>(jobs, n_jobs, cand_off, n_prims, cand_total, rects,
-                                                    tile_count, pairs, pair_cap, pair_counter);
+  count_launch(), k_cull_pairs<false><<<n_sm * 8, kCullWarps * 32, 0, s>>>(jobs, n_jobs, cand_off, n_prims,
+                                                                           cand_total, rects, tile_count, pairs,
+                                                                           pair_cap, pair_counter);
+  if (stri)
+    count_launch(), k_cull_pairs<true><<<n_sm * 8, kCullWarps * 32, 0, s>>>(jobs, n_jobs, cand_off, n_prims,
+                                                                            cand_total, rects, tile_count, pairs,
+                                                                            pair_cap, pair_counter);
 }
 
 void launch_copy_short(const uint32_t *offsets, uint32_t n_segs, const uint64_t *keys, const float *z_out_tmp,
@@ -495,23 +651,51 @@ void launch_tile_sort_range(const uint32_t *offsets, uint32_t n_segs, uint32_t m
                                                                                abort);
   }
   if (max_len > small) {
+    const uint32_t cap = max_len < kSortLarge ? max_len : kSortLarge;   // longer lists: launch_long_sort
     uint32_t n2 = 1;
-    while (n2 < max_len) n2 <<= 1;
+    while (n2 < cap) n2 <<= 1;
     size_t sm = (size_t)n2 * 12;
     count_launch(), k_tile_sort<<<n_sm, 1024, sm, s>>>(offsets, n_segs, keys, z_out_tmp, z_in, z_out, prim,
                                                        min_len > small ? min_len : small, kSortLarge, abort);
   }
 }
 
+void launch_long_sort(const uint32_t *offsets, uint32_t n_tiles, uint32_t max_len, uint64_t *keys,
+                      float *z_out_tmp, float *z_in, float *z_out, uint32_t *prim, uint32_t *list,
+                      uint32_t *count, int n_sm, cudaStream_t s, const uint32_t *abort) {
+  if (max_len <= kSortLarge || !n_tiles) return;
+  cudaMemsetAsync(count, 0, sizeof(uint32_t), s);
+  count_launch(), k_long_lists<<<(n_tiles + 255) / 256, 256, 0, s>>>(offsets, n_tiles, list, count, abort);
+  count_launch(), k_chunk_sort<<<n_sm, 1024, (size_t)kSortLarge * 12, s>>>(offsets, list, count, keys, z_out_tmp,
+                                                                           abort);
+  bool in_a = true;
+  for (uint32_t w = kSortLarge; w < max_len; w <<= 1) {
+    if (in_a)
+      count_launch(), k_merge_pass<true><<<n_sm * 4, 256, 0, s>>>(offsets, list, count, w, keys, z_out_tmp, z_in,
+                                                                  prim, z_out, abort);
+    else
+      count_launch(), k_merge_pass<false><<<n_sm * 4, 256, 0, s>>>(offsets, list, count, w, keys, z_out_tmp, z_in,
+                                                                   prim, z_out, abort);
+    in_a = !in_a;
+  }
+  if (in_a)
+    count_launch(), k_long_copy<<<n_sm * 4, 256, 0, s>>>(offsets, list, count, keys, z_out_tmp, z_in, prim, z_out,
+                                                         abort);
+}
+
 void launch_scatter_sort(const Pair *pairs, const uint32_t *pair_counter, uint32_t pair_cap,
                          const uint32_t *offsets, uint32_t n_tiles, uint32_t max_overlap,
                          uint64_t *keys, float *z_out_tmp, float *z_in, float *z_out, uint32_t *prim,
-                         int n_sm, cudaStream_t s, const uint32_t *abort) {
+                         int n_sm, cudaStream_t s, const uint32_t *abort, uint32_t *long_list,
+                         uint32_t *long_count) {
   count_launch(), k_scatter<<<n_sm * 8, 256, 0, s>>>(pairs, pair_counter, pair_cap, offsets, keys, z_out_tmp, abort);
   if (!n_tiles) return;
   launch_copy_short(offsets, n_tiles, keys, z_out_tmp, z_in, z_out, prim, s, abort);
   if (max_overlap > 1)
     launch_tile_sort_range(offsets, n_tiles, max_overlap, 1, keys, z_out_tmp, z_in, z_out, prim, n_sm, s, abort);
+  if (max_overlap > kSortLarge && long_list && long_count)
+    launch_long_sort(offsets, n_tiles, max_overlap, keys, z_out_tmp, z_in, z_out, prim, long_list, long_count,
+                     n_sm, s, abort);
 }
 
 void launch_check_capacity(const uint32_t *pair_counter, uint32_t pair_cap, const uint32_t *max_overlap,
@@ -520,7 +704,10 @@ void launch_check_capacity(const uint32_t *pair_counter, uint32_t pair_cap, cons
 }
 
 cudaError_t cull_set_attributes() {
-  return cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((size_t)kSortLarge * 12));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)((size_t)kSortLarge * 12));
 }
 

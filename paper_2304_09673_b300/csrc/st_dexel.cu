@@ -37,8 +37,10 @@ namespace {
 
 constexpr int kDexelChunk = 64;   // tile-list entries staged per round
 
+// One thread per pixel of a tile: up to 32 x 32 = 1024 threads.
 template <bool kFill>
-__global__ void k_dexel_pass(Job job, uint32_t *count, const uint32_t *pix_off, uint64_t *keys, float *zo_tmp) {
+__global__ void __launch_bounds__(1024) k_dexel_pass(Job job, uint32_t *count, const uint32_t *pix_off, uint64_t *keys,
+                                                     float *zo_tmp) {
   __shared__ Voi s_v[kDexelChunk];
   __shared__ VoiRay s_q[kDexelChunk];
   const DevCamera &cam = job.cam;
@@ -59,7 +61,7 @@ __global__ void k_dexel_pass(Job job, uint32_t *count, const uint32_t *pix_off, 
       __syncthreads();
       if (threadIdx.x < m) {
         const uint32_t a = job.tl.prim[c + threadIdx.x];
-        load_voi(job.sc, job.sc.prim_index[a], s_v[threadIdx.x]);
+        load_voi(job.sc, job.sc.prim_index[a], s_v[threadIdx.x], s_q[threadIdx.x].cc.wa);
         voi_ray_setup(s_v[threadIdx.x], cam, s_q[threadIdx.x]);
       }
       __syncthreads();
@@ -127,7 +129,7 @@ __device__ __forceinline__ T prim_value(const DevScene &sc, uint32_t a, uint32_t
     case ST_PRIM_SPHERE: return sd_sphere<T>(q[0], p);
     case ST_PRIM_RBOX: return sd_rbox<T>(q[0], q[1], q[2], q[3], p);
     case ST_PRIM_CAPSULE: return sd_capsule<T>(q[0], q[2], p);
-    default: return sd_further<T>(kind, q, p[0], p[1], p[2]);
+    default: return sd_further<T>(prim_view_code(kind), q, p[0], p[1], p[2]);
   }
 }
 

@@ -204,6 +204,83 @@ __device__ __forceinline__ T sd_ellipsoid(const float4 a0, const float4 a1, cons
   return fma_(s, a0.w, -a0.w);
 }
 
+// Rounded triangle: distance to the triangle (a, b, c) minus r.  With w =
+// p - a, the point projects inside the triangle when it lies on the inner
+// side of the three edge planes m_i . (p - v_i) <= 0 (m_i = e_i x n, the
+// outward in-plane edge normals; tested on FP32 values, so the float and
+// dual-number evaluations take the same branch); the distance is then
+// |n . w|, else the least distance to the three edge segments.  Records [a, r] [e0, 1/|e0|^2]
+// [e1, 1/|e1|^2] [e2, 1/|e2|^2] [n, m2.x] [m0, m2.y] [m1, m2.z].
+template <class T>
+__device__ __forceinline__ T seg_dist2(const T &wx, const T &wy, const T &wz, const float4 e) {
+  T h = mul_(fma_(wx, e.x, fma_(wy, e.y, mul_(wz, e.z))), e.w);
+  h = min_(max_(h, 0.f), 1.f);
+  const T qx = fma_(h, -e.x, wx), qy = fma_(h, -e.y, wy), qz = fma_(h, -e.z, wz);
+  return fma_(qx, qx, fma_(qy, qy, mul_(qz, qz)));
+}
+template <class T>
+__device__ __forceinline__ T sd_rtri(const float4 *q, const T p[3]) {
+  // Few values live at a time (this body is part of the out-of-line
+  // sd_further, whose registers count for the tracing kernel): the inside
+  // tests first, then the plane distance or the three edge distances.
+  const float4 a0 = ldrec(q);
+  const T wx = sub_(p[0], a0.x), wy = sub_(p[1], a0.y), wz = sub_(p[2], a0.z);   // p - a
+  bool inside;
+  {
+    const float4 a5 = ldrec(q + 5);
+    inside = fma_(val(wx), a5.x, fma_(val(wy), a5.y, mul_(val(wz), a5.z))) <= 0.f;
+  }
+  {
+    const float4 a1 = ldrec(q + 1), a6 = ldrec(q + 6);
+    const float ux = sub_(val(wx), a1.x), uy = sub_(val(wy), a1.y), uz = sub_(val(wz), a1.z);   // p - b
+    inside = inside && fma_(ux, a6.x, fma_(uy, a6.y, mul_(uz, a6.z))) <= 0.f;
+  }
+  {
+    const float4 a3 = ldrec(q + 3);
+    const float m2x = ldrec(q + 4).w, m2y = ldrec(q + 5).w, m2z = ldrec(q + 6).w;
+    const float vx = add_(val(wx), a3.x), vy = add_(val(wy), a3.y), vz = add_(val(wz), a3.z);   // p - c
+    inside = inside && fma_(vx, m2x, fma_(vy, m2y, mul_(vz, m2z))) <= 0.f;
+  }
+  T d2;
+  if (inside) {
+    const float4 a4 = ldrec(q + 4);
+    const T pd = fma_(wx, a4.x, fma_(wy, a4.y, mul_(wz, a4.z)));
+    d2 = mul_(pd, pd);
+  } else {
+    const float4 a1 = ldrec(q + 1);
+    d2 = seg_dist2<T>(wx, wy, wz, a1);
+    d2 = min_(d2, seg_dist2<T>(sub_(wx, a1.x), sub_(wy, a1.y), sub_(wz, a1.z), ldrec(q + 2)));
+    const float4 a3 = ldrec(q + 3);
+    d2 = min_(d2, seg_dist2<T>(add_(wx, a3.x), add_(wy, a3.y), add_(wz, a3.z), a3));
+  }
+  return sub_(sqrt_(d2), a0.w);
+}
+
+// Bounded quadric: max(q'(clamp_e(u)), box distance(u)) in local
+// coordinates u = M (p - c), q' = q / G (coefficients pre-divided by the
+// gradient bound), accumulated axis by axis.  Records [c, kappa'] [M row i,
+// e_i] x 3 [alpha', beta', gamma', delta'].
+template <class T>
+__device__ __forceinline__ T sd_quadric(const float4 *q, const T p[3]) {
+  const float4 a0 = ldrec(q);
+  const T wx = sub_(p[0], a0.x), wy = sub_(p[1], a0.y), wz = sub_(p[2], a0.z);
+  const float4 cf = ldrec(q + 4);
+  T qv = T(a0.w), out2 = T(0.f), inner = T(-INFINITY);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float4 m = ldrec(q + 1 + i);
+    const T u = fma_(wx, m.x, fma_(wy, m.y, mul_(wz, m.z)));
+    const T c = min_(max_(u, -m.w), m.w);
+    qv = i == 2 ? fma_(c, fma_(c, cf.z, cf.w), qv) : fma_(mul_(c, c), i == 0 ? cf.x : cf.y, qv);
+    const T b = sub_(abs_(u), m.w);
+    const T bp = max_(b, 0.f);
+    out2 = fma_(bp, bp, out2);
+    inner = max_(inner, b);
+  }
+  const T box = add_(sqrt_(out2), min_(inner, 0.f));
+  return max_(qv, box);
+}
+
 // The further families out of line: one copy per value type instead of one
 // per interpreter instantiation and call site, so scenes without them keep
 // the interpreter's code (and instruction-fetch footprint) of the three
@@ -213,6 +290,8 @@ __device__ __noinline__ T sd_further(uint32_t code, const float4 *q, T px, T py,
   const T p[3] = {px, py, pz};
   if (code == V_TORUS) return sd_torus<T>(ldrec(q), ldrec(q + 1), p);
   if (code == V_SCONE) return sd_scone<T>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p);
+  if (code == V_RTRI) return sd_rtri<T>(q, p);
+  if (code == V_QUADRIC) return sd_quadric<T>(q, p);
   return sd_ellipsoid<T>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), ldrec(q + 4), p);
 }
 
@@ -271,6 +350,8 @@ __device__ __forceinline__ uint32_t node_flops(uint32_t code) {
     case V_TORUS: return kFlopsTorus;
     case V_SCONE: return kFlopsScone;
     case V_ELLIPSOID: return kFlopsEllipsoid;
+    case V_RTRI: return kFlopsRtri;
+    case V_QUADRIC: return kFlopsQuadric;
     case V_UNION: case V_INTER: case V_DIFF: return kFlopsCompactOp;
     case V_SUNION: case V_SINTER: case V_SDIFF: return kFlopsSharpOp;
     default: return 0;
@@ -282,7 +363,11 @@ __device__ __forceinline__ uint32_t node_flops(uint32_t code) {
 // acc[r]; deeper entries in `stk` (one slot holds the R values).  The first
 // primitive pushes an unused value, so `stk` needs one slot more than the
 // live depth.  T is float (tracing) or a dual number (refinement).
-template <int R, class T, class Stk>
+// kFurther = false: a lean instance for views of spheres, rounded boxes and
+// capsules only (the further families are never evaluated; a view holding
+// one gets +inf there -- the host picks the lean instance only for scenes
+// without them).
+template <int R, class T, class Stk, bool kFurther = true>
 __device__ __forceinline__ void eval_view_r(const uint32_t *view, int n_view, const RecSrc &src,
                                             const T (&p)[R][3], T (&acc)[R], Stk &stk) {
 #pragma unroll
@@ -315,12 +400,6 @@ __device__ __forceinline__ void eval_view_r(const uint32_t *view, int n_view, co
         for (int r = 0; r < R; ++r) acc[r] = sd_capsule<T>(a0, a2, p[r]);
         break;
       }
-      case V_TORUS: case V_SCONE: case V_ELLIPSOID: {
-        stk.push(sp++, acc);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = sd_further<T>(code, q, p[r][0], p[r][1], p[r][2]);
-        break;
-      }
       case V_UNION: case V_INTER: case V_DIFF: {
         const float4 c = ldrec(q);
         T l[R];
@@ -343,8 +422,14 @@ __device__ __forceinline__ void eval_view_r(const uint32_t *view, int n_view, co
         break;
       }
       case V_RIGHT: --sp; break;
-      default: {  // V_LEFT
+      case V_LEFT: {
         stk.pop(--sp, acc);
+        break;
+      }
+      default: {   // the further primitive families (codes 12..16)
+        stk.push(sp++, acc);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = kFurther ? sd_further<T>(code, q, p[r][0], p[r][1], p[r][2]) : T(INFINITY);
         break;
       }
     }

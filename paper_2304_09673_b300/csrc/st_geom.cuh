@@ -140,20 +140,33 @@ __device__ __forceinline__ bool ray_capsule32(const CapsuleConst &k, const float
 // Volume of interest of primitive j (Sec. 6.1: the primitive's bound offset by
 // its range-of-interest bound d_prim), extents in FP32: ((size + d) + pad).
 // Families: sphere (sphere); oriented box (rounded box; ellipsoid, the box
-// around {f <= d}, half extents r (1 + d / min r)); capsule (capsule;
-// sphere-cone with radius max(r_a, r_b) + d); capped cylinder (torus: radius
-// (R + r) + d around the axis, half-height r + d).
-enum VoiFamily : int { VOI_SPHERE = 0, VOI_BOX = 1, VOI_CAPSULE = 2, VOI_CYLINDER = 3 };
+// around {f <= d}, half extents r (1 + d / min r); bounded quadric, its
+// clipping box grown by d); capsule (capsule; sphere-cone with radius
+// max(r_a, r_b) + d); capped cylinder (torus: radius (R + r) + d around the
+// axis, half-height r + d); sphere-triangle (rounded triangle: the points
+// within (r + d) of the triangle).
+enum VoiFamily : int { VOI_SPHERE = 0, VOI_BOX = 1, VOI_CAPSULE = 2, VOI_CYLINDER = 3, VOI_STRI = 4 };
 struct Voi {
   int fam;
-  float c[3];      // centre (sphere, box) or end a (capsule, cylinder)
-  float M[9];      // box rotation rows
-  float e[3];      // box half extents
-  float b[3];      // capsule / cylinder end b
-  float r;         // sphere / capsule / cylinder radius
+  float c[3];      // centre (sphere, box), end a (capsule, cylinder), vertex a (triangle)
+  float M[9];      // box rotation rows; triangle: unit normal n, edge normals m0, m1
+  float e[3];      // box half extents; triangle: vertex c
+  float b[3];      // capsule / cylinder end b; triangle: vertex b
+  float r;         // sphere / capsule / cylinder / sphere-triangle radius
 };
 
-__device__ __forceinline__ void load_voi(const DevScene &sc, uint32_t j, Voi &v) {
+// Ray-independent quantities of a volume of interest seen from the eye.
+// Sphere-triangle: w = o, lo3 = (g0, g1, g2), cc.r = so, cc.wa = m2.
+struct VoiRay {
+  float w[3], lo3[3];
+  CapsuleConst cc;
+};
+
+// tri_m2: the triangle's third edge normal goes there (the volume of
+// interest's ray constants); null when not needed.  kStri = false: a rounded
+// triangle only gets its family (no parameters).
+template <bool kStri = true>
+__device__ __forceinline__ void load_voi(const DevScene &sc, uint32_t j, Voi &v, float *tri_m2 = nullptr) {
   uint32_t a = sc.prim_addr[j];
   uint32_t kind = blob_kind(sc.blob[a]);
   const float4 *w = sc.rec + sc.rec_off[a];
@@ -181,6 +194,31 @@ __device__ __forceinline__ void load_voi(const DevScene &sc, uint32_t j, Voi &v)
       v.M[3 * i] = m.x; v.M[3 * i + 1] = m.y; v.M[3 * i + 2] = m.z;
       v.e[i] = ieee_add(ieee_mul(m.w, grow), pad);
     }
+  } else if (kind == ST_PRIM_QUADRIC) {
+    v.fam = VOI_BOX;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float4 m = w[1 + i];
+      v.M[3 * i] = m.x; v.M[3 * i + 1] = m.y; v.M[3 * i + 2] = m.z;
+      v.e[i] = ieee_add(ieee_add(m.w, dp), pad);
+    }
+  } else if (kind == ST_PRIM_RTRI) {
+    v.fam = VOI_STRI;
+    if (!kStri) return;
+    const float4 e0 = w[1], e2 = w[3], w4 = w[4], w5 = w[5], w6 = w[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float a = k == 0 ? w0.x : (k == 1 ? w0.y : w0.z);
+      const float ek0 = k == 0 ? e0.x : (k == 1 ? e0.y : e0.z);
+      const float ek2 = k == 0 ? e2.x : (k == 1 ? e2.y : e2.z);
+      v.b[k] = ieee_add(a, ek0);    // b = a + e0
+      v.e[k] = ieee_sub(a, ek2);    // c = a - e2
+    }
+    v.M[0] = w4.x; v.M[1] = w4.y; v.M[2] = w4.z;
+    v.M[3] = w5.x; v.M[4] = w5.y; v.M[5] = w5.z;
+    v.M[6] = w6.x; v.M[7] = w6.y; v.M[8] = w6.z;
+    if (tri_m2) { tri_m2[0] = w4.w; tri_m2[1] = w5.w; tri_m2[2] = w6.w; }
+    v.r = ieee_add(ieee_add(w0.w, dp), pad);
   } else if (kind == ST_PRIM_TORUS) {
     v.fam = VOI_CYLINDER;
     const float4 w1 = w[1];   // unit axis, R
@@ -202,14 +240,98 @@ __device__ __forceinline__ void load_voi(const DevScene &sc, uint32_t j, Voi &v)
   }
 }
 
-// Ray-independent quantities of a volume of interest seen from the eye.
-struct VoiRay {
-  float w[3], lo3[3];
-  CapsuleConst cc;
-};
+// Capsule constants of the segment [p0, p1] with radius r seen from o.
+__device__ __forceinline__ void capsule_setup(const float p0[3], const float p1[3], float r, const float o[3],
+                                              CapsuleConst &cc) {
+  float w[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cc.wa[i] = ieee_sub(p0[i], o[i]);
+    cc.wb[i] = ieee_sub(p1[i], o[i]);
+    cc.ba[i] = ieee_sub(p1[i], p0[i]);
+    w[i] = ieee_sub(o[i], p0[i]);
+  }
+  cc.bb = ieee_dot3(cc.ba[0], cc.ba[1], cc.ba[2], cc.ba[0], cc.ba[1], cc.ba[2]);
+  cc.r = r;
+  cc.wbv = 0.0f;
+  cc.p[0] = cc.p[1] = cc.p[2] = 0.0f;
+  if (cc.bb > 0.0f) {
+    cc.wbv = ieee_dot3(w[0], w[1], w[2], cc.ba[0], cc.ba[1], cc.ba[2]);
+    float fw = ieee_div(cc.wbv, cc.bb);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) cc.p[i] = ieee_sub(w[i], ieee_mul(fw, cc.ba[i]));
+  }
+}
 
+// Sphere-triangle (points within r of the triangle a, b, c): the union of the
+// prism over the triangle (|n.(x - a)| <= r and inside the three edge planes
+// m_i.(x - v_i) <= 0) and the three edge capsules; being convex, the ray
+// meets it in one interval, [least entry, greatest exit] of the pieces.
+// Ray-independent inputs: so = n.(o - a), g_i = m_i.(o - v_i), m2.
+__device__ __forceinline__ bool ray_stri32(const Voi &v, const float o[3], const float so, const float g[3],
+                                           const float m2[3], const float d[3], float &t0, float &t1) {
+  float lo = INFINITY, hi = -INFINITY, s0, s1;
+  // prism: slab of the plane, then the three edge half-spaces
+  {
+    float a_lo = -INFINITY, a_hi = INFINITY;
+    bool ok = true;
+    const float sd = ieee_dot3(v.M[0], v.M[1], v.M[2], d[0], d[1], d[2]);
+    if (sd == 0.0f) {
+      if (so < -v.r || so > v.r) ok = false;
+    } else {
+      const float ta = ieee_div(ieee_sub(-v.r, so), sd);
+      const float tb = ieee_div(ieee_sub(v.r, so), sd);
+      a_lo = ta < tb ? ta : tb;
+      a_hi = ta < tb ? tb : ta;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float *m = i == 0 ? v.M + 3 : (i == 1 ? v.M + 6 : m2);
+      const float gd = ieee_dot3(m[0], m[1], m[2], d[0], d[1], d[2]);
+      if (gd == 0.0f) {
+        if (g[i] > 0.0f) ok = false;
+      } else {
+        const float tl = ieee_div(-g[i], gd);
+        if (gd > 0.0f) { if (tl < a_hi) a_hi = tl; }
+        else { if (tl > a_lo) a_lo = tl; }
+      }
+    }
+    if (ok && a_lo <= a_hi) { lo = a_lo; hi = a_hi; }
+  }
+  // edge capsules a-b, b-c, c-a
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float *p0 = i == 0 ? v.c : (i == 1 ? v.b : v.e);
+    const float *p1 = i == 0 ? v.b : (i == 1 ? v.e : v.c);
+    CapsuleConst cc;
+    capsule_setup(p0, p1, v.r, o, cc);
+    if (ray_capsule32(cc, d, s0, s1)) { if (s0 < lo) lo = s0; if (s1 > hi) hi = s1; }
+  }
+  if (lo > hi) return false;
+  t0 = lo;
+  t1 = hi;
+  return true;
+}
+
+// q.cc.wa must already hold the triangle's m2 (load_voi's tri_m2) for the
+// sphere-triangle family (kStri = false: that family is not set up).
+template <bool kStri = true>
 __device__ __forceinline__ void voi_ray_setup(const Voi &v, const DevCamera &cam, VoiRay &q) {
-  if (v.fam == VOI_SPHERE) {
+  if (kStri && v.fam == VOI_STRI) {
+    // w = o (for the per-ray edge capsules), lo3 = (g0, g1, g2), cc.r = so
+    float oa[3], ob[3], oc[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      q.w[i] = cam.o[i];
+      oa[i] = ieee_sub(cam.o[i], v.c[i]);
+      ob[i] = ieee_sub(cam.o[i], v.b[i]);
+      oc[i] = ieee_sub(cam.o[i], v.e[i]);
+    }
+    q.cc.r = ieee_dot3(v.M[0], v.M[1], v.M[2], oa[0], oa[1], oa[2]);
+    q.lo3[0] = ieee_dot3(v.M[3], v.M[4], v.M[5], oa[0], oa[1], oa[2]);
+    q.lo3[1] = ieee_dot3(v.M[6], v.M[7], v.M[8], ob[0], ob[1], ob[2]);
+    q.lo3[2] = ieee_dot3(q.cc.wa[0], q.cc.wa[1], q.cc.wa[2], oc[0], oc[1], oc[2]);
+  } else if (v.fam == VOI_SPHERE) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) q.w[i] = ieee_sub(v.c[i], cam.o[i]);
   } else if (v.fam == VOI_BOX) {
@@ -239,12 +361,16 @@ __device__ __forceinline__ void voi_ray_setup(const Voi &v, const DevCamera &cam
 
 // Entry and exit of the ray o + t d in the volume of interest, the entry
 // clamped to t >= 0 (the eye may be inside); false when the ray misses it.
+// kStri = false leaves the sphere-triangle family out (callers that test it
+// on a separate path, keeping its registers off the other families' path).
+template <bool kStri = true>
 __device__ __forceinline__ bool voi_ray_hit(const Voi &v, const VoiRay &q, const float d[3], float &t0,
                                             float &t1) {
   bool h;
   if (v.fam == VOI_SPHERE) h = ray_sphere32(q.w, d, v.r, t0, t1);
   else if (v.fam == VOI_BOX) h = ray_obox32(q.lo3, v.M, v.e, d, t0, t1);
   else if (v.fam == VOI_CAPSULE) h = ray_capsule32(q.cc, d, t0, t1);
+  else if (kStri && v.fam == VOI_STRI) h = ray_stri32(v, q.w, q.cc.r, q.lo3, q.cc.wa, d, t0, t1);
   else h = ray_cylinder32(q.cc, d, t0, t1);
   if (!h) return false;
   t0 = t0 > 0.0f ? t0 : 0.0f;

@@ -25,22 +25,27 @@ __host__ __device__ inline uint32_t make_blob(uint32_t isprim, uint32_t kind, ui
 }
 
 // ---- pruned-view node codes --------------------------------------------------
-// A view entry is uint32: bits 28..31 code, bit 27 set when the record is
+// A view entry is uint32: bits 27..31 code, bit 26 set when the record is
 // read from the scene's global record array (else from the view's shared
-// parameter cache), bits 0..26 record word offset.
+// parameter cache), bits 0..25 record word offset.
 enum ViewCode : uint32_t {
   V_SPHERE = 0, V_RBOX = 1, V_CAPSULE = 2,            // primitives (< V_FIRST_OP)
   V_UNION = 3, V_INTER = 4, V_DIFF = 5,               // compact smooth G_op
   V_SUNION = 6, V_SINTER = 7, V_SDIFF = 8,            // sharp CSG
   V_INF = 9, V_RIGHT = 10, V_LEFT = 11,               // usage rewrites (Sec. 9)
   V_TORUS = 12, V_SCONE = 13, V_ELLIPSOID = 14,       // further primitives
+  V_RTRI = 15, V_QUADRIC = 16,
 };
 constexpr uint32_t V_FIRST_OP = 3;
-// Primitive view codes (equal to the primitive kinds): 0..2 and 12..14.
+// Primitive view codes: 0..2 and 12..16 (equal to the primitive kinds but
+// for the bounded quadric, kind 11 -> code 16).
 __host__ __device__ inline bool is_prim_code(uint32_t code) { return code < V_FIRST_OP || code >= V_TORUS; }
-constexpr uint32_t kViewCodeShift = 28;
-constexpr uint32_t kViewGlobal = 1u << 27;
-constexpr uint32_t kViewOffMask = (1u << 27) - 1u;
+__host__ __device__ inline uint32_t prim_view_code(uint32_t kind) {
+  return kind == (uint32_t)ST_PRIM_QUADRIC ? (uint32_t)V_QUADRIC : kind;
+}
+constexpr uint32_t kViewCodeShift = 27;
+constexpr uint32_t kViewGlobal = 1u << 26;
+constexpr uint32_t kViewOffMask = (1u << 26) - 1u;
 
 // Record words (float4) per node kind.
 //   sphere : [c, r]
@@ -52,8 +57,16 @@ constexpr uint32_t kViewOffMask = (1u << 27) - 1u;
 //                outward normal in the axial plane is (cos, sin))
 //   ellipsoid: [c, min r] [M row0, r0] [M row1, r1] [M row2, r2]
 //              [1/r0, 1/r1, 1/r2, 0]
+//   rounded triangle: [a, r] [e0 = b - a, 1/|e0|^2] [e1 = c - b, 1/|e1|^2]
+//              [e2 = a - c, 1/|e2|^2] [unit normal n, m2.x] [m0, m2.y]
+//              [m1, m2.z] with m_i = e_i x n (outward edge normals in the
+//              plane)
+//   bounded quadric: [c, kappa'] [M row0, e0] [M row1, e1] [M row2, e2]
+//              [alpha', beta', gamma', delta'] (M world->local rotation,
+//              coefficients divided by the gradient bound G)
 //   compact operator: [k, d_o, 6 / (6 d_o - k), 1 / k]
 //   sharp operator  : [0, 0, 0, 0]
+constexpr int kMaxRecWords = 8;   // record words of any node kind, at most
 __host__ __device__ inline int rec_words(int kind) {
   switch (kind) {
     case ST_PRIM_RBOX: return 4;
@@ -61,6 +74,8 @@ __host__ __device__ inline int rec_words(int kind) {
     case ST_PRIM_TORUS: return 2;
     case ST_PRIM_SCONE: return 4;
     case ST_PRIM_ELLIPSOID: return 5;
+    case ST_PRIM_RTRI: return 7;
+    case ST_PRIM_QUADRIC: return 5;
     default: return 1;
   }
 }
@@ -74,6 +89,8 @@ constexpr uint32_t kFlopsCapsule = 25;
 constexpr uint32_t kFlopsTorus = 20;
 constexpr uint32_t kFlopsScone = 27;
 constexpr uint32_t kFlopsEllipsoid = 28;
+constexpr uint32_t kFlopsRtri = 80;
+constexpr uint32_t kFlopsQuadric = 55;
 constexpr uint32_t kFlopsCompactOp = 30;
 constexpr uint32_t kFlopsSharpOp = 2;
 constexpr uint32_t kFlopsStep = 6;
@@ -151,6 +168,8 @@ struct Prep {
   int stack_depth = 0;
   double diameter = 0;   // diagonal of the primitives' bounding box
   double extent = 0;     // its largest edge
+  bool has_stri = false; // a rounded triangle (sphere-triangle volume) is present
+  bool has_further = false;  // a primitive beyond sphere, rounded box and capsule
 };
 
 // Returns ST_OK or ST_ERR_INVALID with `err` set.
@@ -169,5 +188,7 @@ void set_error(const std::string &msg);
 int count_launch();
 void count_launches(uint64_t n);
 uint64_t launches_so_far();
+// Host-side count of device allocations (cudaMalloc) made by the library.
+void count_device_alloc();
 
 }  // namespace st

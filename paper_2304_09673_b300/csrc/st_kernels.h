@@ -23,11 +23,18 @@ void launch_prim_bounds(const Job *jobs, int n_jobs, uint32_t n_prims, uint32_t 
                         cudaStream_t s);
 void launch_cull_pairs(const Job *jobs, int n_jobs, const uint32_t *cand_off, uint32_t n_prims,
                        const uint32_t *cand_total, const int4 *rects, uint32_t *tile_count, Pair *pairs,
-                       uint32_t pair_cap, uint32_t *pair_counter, int n_sm, cudaStream_t s);
+                       uint32_t pair_cap, uint32_t *pair_counter, int n_sm, cudaStream_t s,
+                       bool stri);   // stri: some scene holds rounded triangles (second launch)
 void launch_scatter_sort(const Pair *pairs, const uint32_t *pair_counter, uint32_t pair_cap,
                          const uint32_t *offsets, uint32_t n_tiles, uint32_t max_overlap, uint64_t *keys,
                          float *z_out_tmp, float *z_in, float *z_out, uint32_t *prim, int n_sm, cudaStream_t s,
-                         const uint32_t *abort = nullptr);
+                         const uint32_t *abort = nullptr, uint32_t *long_list = nullptr,
+                         uint32_t *long_count = nullptr);
+// Lists longer than kSortLarge (launch_scatter_sort calls it when it is given
+// a tile-sized list buffer and a counter): sorted chunks, then merge passes.
+void launch_long_sort(const uint32_t *offsets, uint32_t n_tiles, uint32_t max_len, uint64_t *keys,
+                      float *z_out_tmp, float *z_in, float *z_out, uint32_t *prim, uint32_t *list,
+                      uint32_t *count, int n_sm, cudaStream_t s, const uint32_t *abort = nullptr);
 void launch_check_capacity(const uint32_t *pair_counter, uint32_t pair_cap, const uint32_t *max_overlap,
                            uint32_t overlap_cap, uint32_t *status, cudaStream_t s);
 cudaError_t cull_set_attributes();
@@ -68,7 +75,8 @@ constexpr uint32_t ST_STATUS_STACK = 2u;      // evaluation stack overflow
 constexpr uint32_t ST_STATUS_CAPACITY = 4u;   // entries / list length beyond the planned buffers
 constexpr uint32_t ST_STATUS_WAIT = 8u;       // a bounded wait inside a CTA expired
 
-// Tracing: per-warp working set layout is computed by trace_layout().
+// Tracing launch: shared memory per CTA, and the per-CTA work areas (active
+// sets, views, level schedules) in shared or global memory; see st_trace.cu.
 struct TraceLaunch {
   int32_t max_tile_rays;   // tile * tile of the largest tile in the launch
   int32_t act_cap;         // active-set capacity (>= longest tile list)
@@ -76,8 +84,10 @@ struct TraceLaunch {
   int32_t stack_slots;     // evaluation stack slots per lane
   int32_t work_in_smem;    // 1: active set + view in shared memory
   int32_t dc_words;        // shared parameter cache per view buffer (float4 words)
-  uint32_t *g_work;        // global per-warp working sets (when not in smem)
-  uint32_t g_work_words;   // words per warp in g_work
+  uint32_t *g_work;        // global per-CTA work areas (when not in shared
+                           // memory), one per CTA of the persistent grid,
+                           // indexed by blockIdx.x
+  uint32_t g_work_words;   // words per CTA in g_work
   uint32_t n_items;        // total (job, tile) work items
   uint32_t *item_counter;  // zeroed before launch
   uint64_t *counters;      // optional ST_NUM_COUNTERS
@@ -98,6 +108,16 @@ struct TraceLaunch {
   uint32_t split_cap;      // split records in the area
   long long split_cycles;  // a tile still tracing after this many SM cycles
                            // splits at its next subfrustum boundary
+  uint32_t heavy_len;      // a tile whose list holds at least this many
+                           // entries splits before its first subfrustum,
+                           // and CTAs claim open parts before whole tiles
+                           // (0: no early splits)
+  uint32_t idle_spins;     // polls of a warp waiting for rays of its tile
+                           // (0: built-in bound)
+  uint32_t split_spins;    // polls of a CTA waiting for split parts
+                           // (0: built-in bound)
+  int32_t further;         // 1: some scene holds primitives beyond spheres,
+                           // rounded boxes and capsules (kernel instance)
 };
 
 // Split area sizing: words per record (header, pending ray ids, depth and
@@ -117,6 +137,15 @@ inline long long trace_split_cycles(int32_t split_kcycles) {
   if (split_kcycles < 0) return -1;
   return 1000ll * (split_kcycles > 0 ? split_kcycles : 2000);
 }
+
+// st_trace_opts::heavy_split_len -> TraceLaunch::heavy_len (0: off).
+// Early splits are off by default: each part of a split tile repeats the
+// tile's view builds, and on the 10k clustered scene, where hundreds of tiles
+// hold 2,000-4,000 entries and view preparation is most of a tile's time,
+// splitting the longest lists early was slower (measured on B300 at
+// 1920x1080: learned trace 109 ms without, 191-194 ms with thresholds
+// 1500-3000; at 960x540 132 vs 135-143 ms; at 3840x2160 145 vs 325 ms).
+inline uint32_t trace_heavy_len(int32_t opt) { return opt > 0 ? (uint32_t)opt : 0u; }
 
 constexpr int ST_STEP_RECORD = 15;  // plain stepping that records training data (internal)
 

@@ -131,10 +131,11 @@ __device__ __forceinline__ float omega_of(float v) {
   return 1.5f + 0.5f * th;
 }
 
-// Warp-collective: evaluates the MLP on the rows of live slots (row
-// s * 32 + lane holds feature vector x[s] of this lane, s = 0, 1; slot s of
-// the lane is live when bit s of `live` is set) and returns omega per slot
-// (1 for dead slots).  16-row tiles without a live row are skipped.
+// Warp-collective: evaluates the MLP on the feature vectors of live slots
+// (slot s of a lane is live when bit s of `live` is set) and returns omega
+// per slot (1 for dead slots).  Live slots are packed into consecutive rows
+// (slot 0 of the lanes in order, then slot 1), so only ceil(live / 16)
+// 16-row tiles run; a row's result does not depend on its position.
 // xs: per-warp shared scratch of 64 rows x 4 words (1 KB; words 0..2 hold
 // the six BF16 features), os: 64 floats.
 __device__ __forceinline__ void mlp_omega_warp(const MlpSmem &W, const float (&x)[2][6], float (&omega)[2],
@@ -142,40 +143,37 @@ __device__ __forceinline__ void mlp_omega_warp(const MlpSmem &W, const float (&x
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   uint32_t *xu = reinterpret_cast<uint32_t *>(xs);
-  uint32_t tiles = 0;   // bit mt: tile mt (rows 16 mt .. 16 mt + 15) has a live row
+  uint32_t lt;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+  const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, live & 1u);
+  const uint32_t m1 = __ballot_sync(0xFFFFFFFFu, (live >> 1) & 1u);
+  const int row[2] = {__popc(m0 & lt), __popc(m0) + __popc(m1 & lt)};
+  const int n_rows = __popc(m0) + __popc(m1);
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, (live >> s) & 1u);
-    tiles |= ((m & 0xFFFFu) ? 1u : 0u) << (2 * s);
-    tiles |= ((m >> 16) ? 1u : 0u) << (2 * s + 1);
     if ((live >> s) & 1u) {
-      uint32_t *row = xu + (s * 32 + lane) * 4;
-      row[0] = pack_bf16(x[s][0], x[s][1]);
-      row[1] = pack_bf16(x[s][2], x[s][3]);
-      row[2] = pack_bf16(x[s][4], x[s][5]);
+      uint32_t *r = xu + row[s] * 4;
+      r[0] = pack_bf16(x[s][0], x[s][1]);
+      r[1] = pack_bf16(x[s][2], x[s][3]);
+      r[2] = pack_bf16(x[s][4], x[s][5]);
     }
   }
   __syncwarp();
 #pragma unroll 1
-  for (int mt = 0; mt < 4; ++mt) {
-    if (!((tiles >> mt) & 1u)) continue;
-    const int m0 = 16 * mt;
-    // Rows of dead slots hold stale words; their outputs are never used.
-    const uint32_t a0 = t < 3 ? xu[(m0 + g) * 4 + t] : 0u;
-    const uint32_t a1 = t < 3 ? xu[(m0 + g + 8) * 4 + t] : 0u;
+  for (int m0r = 0; m0r < n_rows; m0r += 16) {
+    // Rows past n_rows hold stale words; their outputs are never used.
+    const uint32_t a0 = t < 3 ? xu[(m0r + g) * 4 + t] : 0u;
+    const uint32_t a1 = t < 3 ? xu[(m0r + g + 8) * 4 + t] : 0u;
     float lo, hi;
     mlp_tile(W, a0, a1, g, t, lo, hi);
     if (t == 0) {
-      os[m0 + g] = lo;
-      os[m0 + g + 8] = hi;
+      os[m0r + g] = lo;
+      os[m0r + g + 8] = hi;
     }
   }
   __syncwarp();
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const float v = os[s * 32 + lane];
-    omega[s] = ((live >> s) & 1u) ? omega_of(v) : 1.f;
-  }
+  for (int s = 0; s < 2; ++s) omega[s] = ((live >> s) & 1u) ? omega_of(os[row[s]]) : 1.f;
   __syncwarp();
 }
 

@@ -16,7 +16,45 @@ namespace st {
 
 bool is_prim_kind(int k) {
   return k == ST_PRIM_SPHERE || k == ST_PRIM_RBOX || k == ST_PRIM_CAPSULE || k == ST_PRIM_TORUS ||
-         k == ST_PRIM_SCONE || k == ST_PRIM_ELLIPSOID;
+         k == ST_PRIM_SCONE || k == ST_PRIM_ELLIPSOID || k == ST_PRIM_RTRI || k == ST_PRIM_QUADRIC;
+}
+
+// Triangle frame in FP64 from a description record: edges e0 = b - a,
+// e1 = c - b, e2 = a - c, unit normal n = e0 x (c - a) / |.|, and the
+// in-plane outward edge normals m_i = e_i x n.  Returns |e0 x (c - a)|.
+static double tri_frame(const float *q, double e[3][3], double n[3], double m[3][3]) {
+  for (int k = 0; k < 3; ++k) {
+    e[0][k] = (double)q[3 + k] - q[k];
+    e[1][k] = (double)q[6 + k] - q[3 + k];
+    e[2][k] = (double)q[k] - q[6 + k];
+  }
+  const double ca[3] = {-e[2][0], -e[2][1], -e[2][2]};
+  double c[3] = {e[0][1] * ca[2] - e[0][2] * ca[1], e[0][2] * ca[0] - e[0][0] * ca[2],
+                 e[0][0] * ca[1] - e[0][1] * ca[0]};
+  const double len = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+  for (int k = 0; k < 3; ++k) n[k] = len > 0.0 ? c[k] / len : 0.0;
+  for (int i = 0; i < 3; ++i) {
+    m[i][0] = e[i][1] * n[2] - e[i][2] * n[1];
+    m[i][1] = e[i][2] * n[0] - e[i][0] * n[2];
+    m[i][2] = e[i][0] * n[1] - e[i][1] * n[0];
+  }
+  return len;
+}
+
+// Bounded quadric in FP64: rotation rows M (world -> local, the transpose of
+// the unit quaternion's rotation) and the gradient bound G of q over the box.
+static double quadric_frame(const float *q, double M[3][3]) {
+  double w = q[3], x = q[4], y = q[5], z = q[6];
+  const double nq = std::sqrt(w * w + x * x + y * y + z * z);
+  if (nq > 0.0) { w /= nq; x /= nq; y /= nq; z /= nq; }
+  const double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)},
+                          {2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)},
+                          {2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) M[i][j] = R[j][i];
+  const double g0 = 2.0 * std::fabs((double)q[10]) * q[7], g1 = 2.0 * std::fabs((double)q[11]) * q[8];
+  const double g2 = 2.0 * std::fabs((double)q[12]) * q[9] + std::fabs((double)q[13]);
+  return std::sqrt(g0 * g0 + g1 * g1 + g2 * g2);
 }
 
 const char *prim_record_error(int kind, const float *q) {
@@ -37,6 +75,19 @@ const char *prim_record_error(int kind, const float *q) {
     case ST_PRIM_ELLIPSOID:
       if (!(q[12] > 0.f) || !(q[13] > 0.f) || !(q[14] > 0.f)) return "ellipsoid: radii must be > 0";
       return nullptr;
+    case ST_PRIM_RTRI: {
+      double e[3][3], n[3], m[3][3];
+      if (!(q[9] > 0.f)) return "rounded triangle: rounding must be > 0";
+      if (!(tri_frame(q, e, n, m) > 0.0)) return "rounded triangle: collinear vertices";
+      return nullptr;
+    }
+    case ST_PRIM_QUADRIC: {
+      double M[3][3];
+      if (!(norm3(q + 3) > 0.0 || q[6] != 0.f)) return "bounded quadric: zero quaternion";
+      if (!(q[7] > 0.f) || !(q[8] > 0.f) || !(q[9] > 0.f)) return "bounded quadric: box half extents must be > 0";
+      if (!(quadric_frame(q, M) > 0.0)) return "bounded quadric: alpha, beta, gamma and delta all zero";
+      return nullptr;
+    }
     default:
       return nullptr;
   }
@@ -87,6 +138,30 @@ void prim_words(int kind, const float *q, float *w) {
     for (int k = 0; k < 3; ++k) w[8 + k] = (float)(ba[k] / h);
     w[11] = (float)h;
     w[12] = (float)sn; w[13] = (float)cs; w[14] = (float)(cs * h); w[15] = 0.f;
+  } else if (kind == ST_PRIM_RTRI) {
+    double e[3][3], n[3], m[3][3];
+    tri_frame(q, e, n, m);
+    w[0] = q[0]; w[1] = q[1]; w[2] = q[2]; w[3] = q[9];
+    for (int i = 0; i < 3; ++i) {
+      const double ee = e[i][0] * e[i][0] + e[i][1] * e[i][1] + e[i][2] * e[i][2];
+      for (int k = 0; k < 3; ++k) w[4 + 4 * i + k] = (float)e[i][k];
+      w[4 + 4 * i + 3] = (float)(1.0 / ee);
+    }
+    for (int k = 0; k < 3; ++k) {
+      w[16 + k] = (float)n[k];
+      w[20 + k] = (float)m[0][k];
+      w[24 + k] = (float)m[1][k];
+    }
+    w[19] = (float)m[2][0]; w[23] = (float)m[2][1]; w[27] = (float)m[2][2];
+  } else if (kind == ST_PRIM_QUADRIC) {
+    double M[3][3];
+    const double G = quadric_frame(q, M);
+    w[0] = q[0]; w[1] = q[1]; w[2] = q[2]; w[3] = (float)((double)q[14] / G);
+    for (int i = 0; i < 3; ++i) {
+      for (int k = 0; k < 3; ++k) w[4 + 4 * i + k] = (float)M[i][k];
+      w[4 + 4 * i + 3] = q[7 + i];
+    }
+    for (int k = 0; k < 4; ++k) w[16 + k] = (float)((double)q[10 + k] / G);
   } else {   // ellipsoid
     const float rmin = std::fmin(q[12], std::fmin(q[13], q[14]));
     w[0] = q[0]; w[1] = q[1]; w[2] = q[2]; w[3] = rmin;
@@ -127,6 +202,19 @@ static void prim_bounds(int kind, const float *q, double lo[3], double hi[3]) {
       lo[j] = std::fmin((double)q[j] - q[6], (double)q[3 + j] - q[7]);
       hi[j] = std::fmax((double)q[j] + q[6], (double)q[3 + j] + q[7]);
     }
+  } else if (kind == ST_PRIM_RTRI) {
+    for (int j = 0; j < 3; ++j) {
+      lo[j] = std::fmin((double)q[j], std::fmin((double)q[3 + j], (double)q[6 + j])) - q[9];
+      hi[j] = std::fmax((double)q[j], std::fmax((double)q[3 + j], (double)q[6 + j])) + q[9];
+    }
+  } else if (kind == ST_PRIM_QUADRIC) {   // inside its clipping box
+    double M[3][3];
+    quadric_frame(q, M);
+    for (int j = 0; j < 3; ++j) {
+      double e = 0;
+      for (int i = 0; i < 3; ++i) e += std::fabs(M[i][j]) * q[7 + i];
+      lo[j] = q[j] - e; hi[j] = q[j] + e;
+    }
   } else {   // ellipsoid: inside its oriented box of half extents r
     for (int j = 0; j < 3; ++j) {
       double e = 0;
@@ -153,6 +241,8 @@ int prepare(const st_scene_desc &d, Prep &p, std::string &err) {
         return fail(s.str());
       }
       ++n_prims;
+      if (k == ST_PRIM_RTRI) p.has_stri = true;
+      if (k != ST_PRIM_SPHERE && k != ST_PRIM_RBOX && k != ST_PRIM_CAPSULE) p.has_further = true;
       continue;
     }
     if (!is_op_kind(k)) {
@@ -305,7 +395,7 @@ int prepare(const st_scene_desc &d, Prep &p, std::string &err) {
     const float *q = d.params + (size_t)i * ST_REC_FLOATS;
     p.rec_off[a] = (uint32_t)(p.rec.size() / 4);
     if (is_prim_kind(k)) {
-      float w[20];
+      float w[4 * kMaxRecWords];
       prim_words(k, q, w);
       p.rec.insert(p.rec.end(), w, w + 4 * rec_words(k));
       p.prim_index[a] = (uint32_t)p.prim_addr.size();

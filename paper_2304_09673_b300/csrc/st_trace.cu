@@ -29,6 +29,7 @@
 //   * hits are refined with Newton steps on the ray (dual numbers) and get
 //     the normalised forward-mode gradient of f_A as normal.
 #include <cstdint>
+#include <type_traits>
 
 #include "st_field.cuh"
 #include "st_geom.cuh"
@@ -38,6 +39,8 @@
 namespace st {
 
 constexpr int kWarps = 4;   // warps per CTA; a CTA traces one tile at a time
+constexpr int kFurtherBit = 64;   // instance bit: the interpreter evaluates the further families
+constexpr int kTileStatWords = 24;   // words per tile of the optional diagnostics
 constexpr int kR = 2;       // rays per lane (shared node decode, two evaluation chains)
 
 int trace_warps_per_cta() { return kWarps; }
@@ -173,6 +176,22 @@ __device__ __forceinline__ int kth_set_bit(uint32_t m, int k) {
   return pos;
 }
 
+// Number of lanes l < n whose value v (sorted ascending over lanes 0..n-1)
+// is below q; q may differ per lane.  Five shuffles.
+__device__ __forceinline__ int lanes_below(uint32_t v, int n, uint32_t q) {
+  int c = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const int probe = c + step - 1;
+    const uint32_t x = __shfl_sync(0xFFFFFFFFu, v, probe & 31);
+    if (probe < n && x < q) c += step;
+  }
+  // the steps reach 31 at most: all 32 below q
+  const uint32_t last = __shfl_sync(0xFFFFFFFFu, v, 31);
+  if (c == 31 && n == 32 && last < q) c = 32;
+  return c;
+}
+
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
@@ -203,7 +222,7 @@ __device__ __forceinline__ ViewInfo build_view(const DevScene &sc, const uint32_
     uint32_t u = 1;
     uint32_t isl = blob_isleft(nb);
     {
-      const uint32_t code = blob_kind(nb);  // primitive kinds equal their view codes
+      const uint32_t code = prim_view_code(blob_kind(nb));
       if (vaddr) vaddr[nv] = P;
       view[nv++] = (code << kViewCodeShift) | kViewGlobal | __ldg(sc.rec_off + P);
       vi.flops += node_flops(code);
@@ -334,7 +353,7 @@ __device__ __forceinline__ ViewInfo build_view_lca(const DevScene &sc, const uin
       const int i = c0 + q * 32 + lane;
       if (i < n) {
         const uint32_t ab = __ldg(sc.blob + a[q]);
-        const uint32_t leaf = (blob_kind(ab) << kViewCodeShift) | kViewGlobal | __ldg(sc.rec_off + a[q]);
+        const uint32_t leaf = (prim_view_code(blob_kind(ab)) << kViewCodeShift) | kViewGlobal | __ldg(sc.rec_off + a[q]);
         const uint32_t lb = __ldg(sc.blk + a[q]);
         uint32_t X = kNone, xw = 0u, xblk = kNoAnc, xrec = 0u;
         if (nxt[q]) {
@@ -348,7 +367,7 @@ __device__ __forceinline__ ViewInfo build_view_lca(const DevScene &sc, const uin
         }
         ch.a[q * 32 + lane] = make_uint4(X, min(xblk, kNoAnc), min(lb, kNoAnc), xw);
         ch.b[q * 32 + lane] = make_uint2(leaf, kViewGlobal | xrec);
-        leaf_flops += node_flops(blob_kind(ab));
+        leaf_flops += node_flops(prim_view_code(blob_kind(ab)));
       }
     }
     __syncwarp();
@@ -474,6 +493,8 @@ __device__ __forceinline__ int code_words(uint32_t code) {
     case V_TORUS: return 2;
     case V_SCONE: return 4;
     case V_ELLIPSOID: return 5;
+    case V_RTRI: return 7;
+    case V_QUADRIC: return 5;
     case V_UNION: case V_INTER: case V_DIFF: return 1;
     default: return 0;
   }
@@ -654,31 +675,45 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
       const int take = fail ? __ffs(fail) - 1 : 32;
       const bool taken = lane < take;
       sg.maxze = warp_max(taken ? fmaxf(ze, sg.maxze) : sg.maxze);
-      // sorted merge by node address
-      int rank_new = 0;
-      for (int j = 0; j < take; ++j) rank_new += (__shfl_sync(0xFFFFFFFFu, pa, j) < pa) ? 1 : 0;
+      // sorted merge by node address: the taken candidates are sorted
+      // across the lanes (bitonic network), then one pass over the active
+      // set places every old entry after the new ones below it and counts,
+      // for every new entry, the old ones below it (binary searches over
+      // sorted lanes, five shuffles each).
+      uint32_t key = taken ? pa : 0xFFFFFFFFu;
+      float kze = ze;
+#pragma unroll
+      for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+          const uint32_t ok = __shfl_xor_sync(0xFFFFFFFFu, key, jj);
+          const float oz = __shfl_xor_sync(0xFFFFFFFFu, kze, jj);
+          const bool keep_min = ((lane & jj) == 0) == ((lane & kk) == 0);
+          if (keep_min ? ok < key : ok > key) {
+            key = ok;
+            kze = oz;
+          }
+        }
+      }
       const uint32_t *A = pick(C.act, sg.cur);
       const float *AZ = pick(C.act_ze, sg.cur);
       uint32_t *B = pick(C.act, sg.cur ^ 1);
       float *BZ = pick(C.act_ze, sg.cur ^ 1);
-      if (taken) {
-        int lo = 0, hi = sg.n_act;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (A[mid] < pa) lo = mid + 1; else hi = mid;
-        }
-        B[rank_new + lo] = pa;
-        BZ[rank_new + lo] = ze;
-      }
+      int below_new = 0;   // old entries below this lane's new key
       for (int b = 0; b < sg.n_act; b += 32) {
         const int i = b + lane;
         const uint32_t ad = i < sg.n_act ? A[i] : 0xFFFFFFFFu;
-        int before = 0;
-        for (int j = 0; j < take; ++j) before += (__shfl_sync(0xFFFFFFFFu, pa, j) < ad) ? 1 : 0;
+        const int m = min(32, sg.n_act - b);
+        const int before = lanes_below(key, take, ad);
+        below_new += lanes_below(ad, m, key);
         if (i < sg.n_act) {
           B[i + before] = ad;
           BZ[i + before] = AZ[i];
         }
+      }
+      if (lane < take) {
+        B[lane + below_new] = key;
+        BZ[lane + below_new] = kze;
       }
       sg.n_act += take;
       sg.cur ^= 1;
@@ -717,6 +752,7 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
 // All lanes hold the same point p.  Primitives are evaluated in parallel,
 // then operators level by level (operands always sit on lower levels).
 // `vals` is per-warp shared memory of at least n_view floats.
+template <bool kFurther>
 __device__ __forceinline__ float tail_eval(const uint32_t *view, int n_view, const uint2 *ops, const int *lvl_off, int n_lvl,
                            const RecSrc &src, const float p[3], float *vals) {
   const int lane = threadIdx.x & 31;
@@ -730,7 +766,7 @@ __device__ __forceinline__ float tail_eval(const uint32_t *view, int n_view, con
       case V_SPHERE: v = sd_sphere<float>(ldrec(q), p); break;
       case V_RBOX: v = sd_rbox<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p); break;
       case V_CAPSULE: v = sd_capsule<float>(ldrec(q), ldrec(q + 2), p); break;
-      default: v = sd_further<float>(code, q, p[0], p[1], p[2]); break;
+      default: v = kFurther ? sd_further<float>(code, q, p[0], p[1], p[2]) : INFINITY; break;
     }
     vals[i] = v;
   }
@@ -849,11 +885,38 @@ __device__ __forceinline__ int tq_pop(unsigned long long *tq, int *tail, int *he
 // ray id (rays = max_tile_rays).
 constexpr int kSplitMinRays = 8;    // pending rays per part at least
 constexpr int kSplitMaxParts = 16;
+constexpr int kHeavyParts = 8;      // parts of a tile split before its first subfrustum
 constexpr uint32_t kSplitListBudget = 4096;   // parts x A-buffer list length at most
 constexpr uint32_t kSplitIdleSpins = 1u << 21;   // polls of an idle CTA (x ~1 us)
 
 __device__ __forceinline__ uint32_t *split_record(const TraceLaunch &L, uint32_t r) {
   return L.split + 4 + 2 * (size_t)L.split_cap + (size_t)r * split_rec_words(L.max_tile_rays);
+}
+
+// One thread, no waiting: claims an unclaimed part of a published split
+// record (tiles split before their first subfrustum are open while whole
+// tiles remain; CTAs take their parts first).  Returns the part's global
+// tile with *part >= 1 and *rec, or 0xFFFFFFFF when no part is open now.
+__device__ __forceinline__ uint32_t try_part(const TraceLaunch &L, uint32_t *rec, int *part) {
+  uint32_t *hdr = L.split;
+  uint32_t *parts = hdr + 4, *claimed = hdr + 4 + L.split_cap;
+  const uint32_t n = min(*(volatile uint32_t *)&hdr[0], L.split_cap);
+  bool prefix = true;   // records below r are published and fully claimed
+  for (uint32_t r = *(volatile uint32_t *)&hdr[1]; r < n; ++r) {
+    const uint32_t P = *(volatile uint32_t *)&parts[r];
+    if (P > 1 && *(volatile uint32_t *)&claimed[r] + 1 < P) {
+      const uint32_t c = atomicAdd(&claimed[r], 1u);
+      if (c + 1 < P) {
+        __threadfence();   // the record's contents were published before P
+        *rec = r;
+        *part = (int)c + 1;
+        return __ldcg(split_record(L, r));
+      }
+    }
+    if (P == 0 || *(volatile uint32_t *)&claimed[r] + 1 < P) prefix = false;
+    if (prefix) atomicMax(&hdr[1], r + 1);
+  }
+  return 0xFFFFFFFFu;
 }
 
 // One thread: claims an unclaimed part of a split record, polling while
@@ -883,7 +946,7 @@ __device__ __forceinline__ uint32_t next_part(const TraceLaunch &L, uint32_t *re
       if (prefix) atomicMax(&hdr[1], r + 1);
     }
     if (last) return 0xFFFFFFFFu;
-    if (*(volatile uint32_t *)&hdr[2] == 0u || spins >= kSplitIdleSpins) {
+    if (*(volatile uint32_t *)&hdr[2] == 0u || spins >= (L.split_spins ? L.split_spins : kSplitIdleSpins)) {
       __threadfence();
       last = true;
       continue;
@@ -898,9 +961,12 @@ struct LearnCtx {      // learned step / recording context of a subfrustum
   MlpSmem W;
   uint32_t list_len;
   const TraceLaunch *L;
+  unsigned long long *diag;   // tile diagnostics (shared, null when off): lockstep
+                              // iterations, live slots over them, tail evaluations,
+                              // refinement passes, live lanes over them
 };
 
-template <int MODE>
+template <int MODE, bool kFurther>
 __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &C, const RecSrc &src, const SubInfo &inf,
                               const uint32_t *view, const uint2 *ops, const int *lvl_off, const uint16_t *alive_in,
                               int n_in, int *q_head, uint16_t *alive_out, int *n_out, uint16_t *hits, int &n_hits,
@@ -909,6 +975,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
                               uint32_t tag, uint32_t &c_err) {
   constexpr bool kShare = MODE != ST_STEP_RECORD;
   uint32_t idle_spins = 0;
+  const uint32_t idle_limit = LC.L->idle_spins ? LC.L->idle_spins : kIdleSpinLimit;
   bool idle = false;   // this warp is registered in *n_idle (waiting for handed-over rays)
   uint32_t rejected = 0;
   const int lane = threadIdx.x & 31;
@@ -1129,8 +1196,8 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
     if (n_live == 0) {
       if (!kShare) break;
       // Every ray of the subfrustum finished?  Else wait for handed-over rays.
-      if (*(volatile int *)n_done >= n_in || ++idle_spins > kIdleSpinLimit) {
-        if (idle_spins > kIdleSpinLimit) c_err |= ST_STATUS_WAIT;
+      if (*(volatile int *)n_done >= n_in || ++idle_spins > idle_limit) {
+        if (idle_spins > idle_limit) c_err |= ST_STATUS_WAIT;
         if (idle && lane == 0) atomicSub(n_idle, 1);
         break;
       }
@@ -1139,7 +1206,16 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
     }
 
     float f[kR];
-    if (drained && tail_ok && n_live * tail_cost < inf.n_view) {
+    const bool tail_now = drained && tail_ok && n_live * tail_cost < inf.n_view;
+    if (LC.diag && lane == 0) {
+      if (tail_now) {
+        atomicAdd(&LC.diag[2], (unsigned long long)n_live);
+      } else {
+        atomicAdd(&LC.diag[0], 1ull);
+        atomicAdd(&LC.diag[1], (unsigned long long)n_live);
+      }
+    }
+    if (tail_now) {
       int n_give = 0;
       if (kShare && n_live > 1) n_give = min(n_live - 1, *(volatile int *)n_idle);
       n_give = __shfl_sync(0xFFFFFFFFu, n_give, 0);
@@ -1188,7 +1264,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
           const float pt[3] = {fma_(zz, __shfl_sync(0xFFFFFFFFu, d[s][0], owner), M.cam->o[0]),
                                fma_(zz, __shfl_sync(0xFFFFFFFFu, d[s][1], owner), M.cam->o[1]),
                                fma_(zz, __shfl_sync(0xFFFFFFFFu, d[s][2], owner), M.cam->o[2])};
-          const float fv = tail_eval(view, inf.n_view, ops, lvl_off, inf.n_lvl, src, pt, wvals);
+          const float fv = tail_eval<kFurther>(view, inf.n_view, ops, lvl_off, inf.n_lvl, src, pt, wvals);
           if (lane == owner) f[s] = fv;
         }
       }
@@ -1250,7 +1326,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
                            fma_(z[0], d[0][2], M.cam->o[2])}};
         float f1[1];
         SmemStack1 stk1{stk.base};
-        eval_view_r<1, float>(view, inf.n_view, src, p1, f1, stk1);
+        eval_view_r<1, float, SmemStack1, kFurther>(view, inf.n_view, src, p1, f1, stk1);
         f[0] = f1[0];
         f[1] = 0.f;
       } else {
@@ -1261,7 +1337,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
           p[s][1] = fma_(z[s], d[s][1], M.cam->o[1]);
           p[s][2] = fma_(z[s], d[s][2], M.cam->o[2]);
         }
-        eval_view_r<kR, float>(view, inf.n_view, src, p, f, stk);
+        eval_view_r<kR, float, SmemStack2, kFurther>(view, inf.n_view, src, p, f, stk);
       }
     }
     float om[kR];
@@ -1306,14 +1382,19 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
 // Hit refinement: Newton steps along the ray on f_A (value + derivative along
 // d), then the gradient of f_A from three directional derivatives; a
 // crossing that lies past z_end is handed to the next subfrustum.
+template <bool kFurther>
 __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &C, const RecSrc &src, const SubInfo &inf,
                               const uint32_t *view, const uint16_t *hits, int n_hits, uint16_t *alive_out,
-                              int *n_out, float2 *stk_lane, uint64_t &c_fin) {
+                              int *n_out, float2 *stk_lane, uint64_t &c_fin, unsigned long long *diag) {
   const int lane = threadIdx.x & 31;
   SmemStackD1 stk{stk_lane};
   const DevCamera &cam = *M.cam;
   for (int b = 0; b < n_hits; b += 32) {
     const int idx = b + lane;
+    if (diag && lane == 0) {
+      atomicAdd(&diag[3], 1ull);
+      atomicAdd(&diag[4], (unsigned long long)min(32, n_hits - b));
+    }
     const bool v = idx < n_hits;
     const int r = v ? hits[idx] : 0;
     float zz = v ? C.ray_z[r] : inf.z_begin;
@@ -1343,7 +1424,7 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
         pd[0][j].v = cam.o[j] + zz * d[j];
         pd[0][j].g[0] = newton ? d[j] : (j == k ? 1.f : 0.f);
       }
-      eval_view_r<1, Dual<1>>(view, inf.n_view, src, pd, fd, stk);
+      eval_view_r<1, Dual<1>, SmemStackD1, kFurther>(view, inf.n_view, src, pd, fd, stk);
       if (newton) {
         // a first sample inside the solid at the near plane: clipped hit
         if (it == 0 && zz <= kZNear && fd[0].v < -M.tp->eps) done = true;
@@ -1392,9 +1473,11 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
 // ---- the tracing kernel ----------------------------------------------------------
 // Three CTAs per SM: up to 170 registers per thread (the learned step's MLP
 // fragments take it to 168) with ~57 KB of shared memory per CTA.
-template <int MODE>
+template <int INST>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
+  constexpr int MODE = INST & ~kFurtherBit;
+  constexpr bool kFurther = (INST & kFurtherBit) != 0;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_item, s_rec;
   __shared__ int s_part;
@@ -1405,6 +1488,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   __shared__ int s_tqt[3], s_tqh[3], s_ndone[3], s_nidle[3];   // tail sharing per subfrustum slot
   __shared__ uint32_t s_steps;
   __shared__ unsigned long long s_dbg[8];
+  __shared__ unsigned long long s_diag[5];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const CtaWork C = carve(smem, L, L.g_work ? L.g_work + (size_t)blockIdx.x * L.g_work_words : nullptr);
@@ -1413,6 +1497,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   LearnCtx LC;
   LC.L = &L;
   LC.list_len = 0;
+  LC.diag = L.tile_stats ? s_diag : nullptr;
   if (MODE == ST_STEP_LEARNED) LC.W = load_mlp(L.mlp, C.mlp);
   uint16_t *my_hits = C.hits + (size_t)warp * L.max_tile_rays;
 
@@ -1430,7 +1515,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       // of a split tile ----
       uint32_t gt = 0xFFFFFFFFu, rec = 0;
       int part = 0;
-      if (*(volatile uint32_t *)L.item_counter < L.n_items) {
+      if (L.split && L.heavy_len) gt = try_part(L, &rec, &part);
+      if (gt == 0xFFFFFFFFu && *(volatile uint32_t *)L.item_counter < L.n_items) {
         if (L.split) {
           atomicAdd(&L.split[2], 1u);
           __threadfence();
@@ -1475,7 +1561,14 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       __syncthreads();
       continue;
     }
-    if (L.split && !part && (nr < 2 * kSplitMinRays || kSplitListBudget / max(len, 1u) < 2)) {
+    // A heavy tile (long list) splits before its first subfrustum into about
+    // one part per 512 entries (at most kHeavyParts): each part builds the
+    // tile's views itself (no replay), and CTAs claim open parts before
+    // whole tiles, so the tile's rays are traced by several CTAs from the
+    // start instead of one CTA outlasting the frame.
+    const bool heavy = MODE != ST_STEP_RECORD && L.split && L.heavy_len && !part && len >= L.heavy_len &&
+                       nr >= 2 * kSplitMinRays;
+    if (L.split && !part && !heavy && (nr < 2 * kSplitMinRays || kSplitListBudget / max(len, 1u) < 2)) {
       // Too few rays or too long a list to split: release this tile's count
       // of whole tiles at once, so that CTAs out of work stop polling sooner.
       if (threadIdx.x == 0) atomicSub(&L.split[2], 1u);
@@ -1520,7 +1613,50 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       for (int i = 0; i < 3; ++i) { s_tqt[i] = 0; s_tqh[i] = 0; s_ndone[i] = 0; s_nidle[i] = 0; }
       s_steps = 0u;
       for (int i = 0; i < 8; ++i) s_dbg[i] = 0ull;
+      for (int i = 0; i < 5; ++i) s_diag[i] = 0ull;
     }
+    // Split records (thread 0 reserves; all threads publish).  A record
+    // resumes at subfrustum kn with the pending rays of alive[kn & 1]; part p
+    // holds pending rays i = p (mod P); this CTA keeps part 0.
+    auto reserve_split = [&](int P) -> int {
+      if (P >= 2) {
+        const uint32_t r = atomicAdd(&L.split[0], 1u);
+        if (r < L.split_cap) s_rec = r; else P = 0;
+      }
+      return P >= 2 ? P : 0;
+    };
+    auto publish_split = [&](int kn, int P) {
+      const uint32_t rr = s_rec;
+      uint32_t *R = split_record(L, rr);
+      uint16_t *al = pick(C.alive, kn & 1);   // the resume subfrustum's pending rays
+      float *rz = reinterpret_cast<float *>(R + 4 + L.max_tile_rays);
+      uint32_t *rst = R + 4 + 2 * L.max_tile_rays;
+      for (int i = threadIdx.x; i < n_pending; i += blockDim.x) {
+        const int r = al[i];
+        R[4 + i] = (uint32_t)r;
+        rz[r] = C.ray_z[r];
+        rst[r] = C.ray_st[r];
+      }
+      if (threadIdx.x == 0) {
+        R[0] = gtile;
+        R[1] = (uint32_t)kn;
+        R[2] = (uint32_t)n_pending;
+        R[3] = (uint32_t)P;
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        atomicExch(&L.split[4 + rr], (uint32_t)P);
+        atomicSub(&L.split[2], 1u);
+      }
+      uint16_t *tmp = pick(C.alive, (kn + 1) & 1);   // free: written by subfrustum kn's march
+      const int m = (n_pending + P - 1) / P;
+      for (int j = threadIdx.x; j < m; j += blockDim.x) tmp[j] = al[j * P];
+      __syncthreads();
+      for (int j = threadIdx.x; j < m; j += blockDim.x) al[j] = tmp[j];
+      __syncthreads();
+      n_pending = m;
+    };
     SegState sg;
     sg.next = 0; sg.n_act = 0; sg.cur = 0; sg.z_end = 0.f; sg.maxze = -INFINITY;
     int k = -1;
@@ -1561,13 +1697,33 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       }
       if (!run) {
         __syncthreads();
+        if (heavy && k == -1) {
+          if (threadIdx.x == 0) {
+            const SubInfo nx = s_info[0];
+            // about one part per 512 list entries (each part repeats the views)
+            const int P = (!nx.done && !nx.err)
+                              ? min(min(kHeavyParts, nr / kSplitMinRays), max(2, (int)(len / 512u)))
+                              : 0;
+            s_part = reserve_split(P);
+          }
+          __syncthreads();
+          const int P = s_part;
+          if (P >= 2) {
+            publish_split(0, P);
+            split_done = true;
+          } else if (kSplitListBudget / max(len, 1u) < 2) {
+            // not split (no record left): as a tile that cannot split
+            if (threadIdx.x == 0) atomicSub(&L.split[2], 1u);
+            split_done = true;
+          }
+        }
         continue;
       }
       if (inf.root_used) {
         const long long t0 = clock64();
         int n_hits = 0;
         const RecSrc src{sc.rec, pick(C.dc, k & 1)};
-        const uint32_t ls = march_sub<MODE>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
+        const uint32_t ls = march_sub<MODE, kFurther>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
                                       n_pending, &s_qhead[rd], alive_out, &s_nctr[wr], my_hits, n_hits, stk_lane,
                                       wvals, 2 * L.stack_slots * 32, c_rej, LC, &s_tqt[rd], &s_tqh[rd], &s_ndone[rd],
                                       &s_nidle[rd], g_sub, c_err);
@@ -1576,7 +1732,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         c_prim += (uint64_t)ls * inf.n_prim;
         c_op += (uint64_t)ls * inf.n_op;
         c_flops += (uint64_t)ls * (inf.flops + kFlopsStep);
-        finalize_hits(M, C, src, inf, pick(C.view, k & 1), my_hits, n_hits, alive_out, &s_nctr[wr], stk_lane, c_fin);
+        finalize_hits<kFurther>(M, C, src, inf, pick(C.view, k & 1), my_hits, n_hits, alive_out, &s_nctr[wr],
+                                stk_lane, c_fin, LC.diag);
         if (L.tile_stats && lane == 0) {
           atomicAdd(&s_dbg[4], (unsigned long long)(clock64() - t1));
           atomicAdd(&s_dbg[7], (unsigned long long)(t1 - t0));
@@ -1616,46 +1773,13 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
             // Each part repeats the tile's segmentation and view builds, whose
             // cost grows with the list: long lists split into fewer parts.
             P = min(min(kSplitMaxParts, n_pending / kSplitMinRays), (int)(kSplitListBudget / max(len, 1u)));
-            if (P >= 2) {
-              const uint32_t r = atomicAdd(&L.split[0], 1u);
-              if (r < L.split_cap) s_rec = r; else P = 0;
-            }
           }
-          s_part = P;   // (s_part broadcasts P here; the tile's own part is in `part`)
+          s_part = reserve_split(P);   // (s_part broadcasts P here; the tile's own part is in `part`)
         }
         __syncthreads();
         const int P = s_part;
         if (P >= 2) {
-          const uint32_t rr = s_rec;
-          uint32_t *R = split_record(L, rr);
-          uint16_t *al = pick(C.alive, (k + 1) & 1);   // the next subfrustum's pending rays
-          float *rz = reinterpret_cast<float *>(R + 4 + L.max_tile_rays);
-          uint32_t *rst = R + 4 + 2 * L.max_tile_rays;
-          for (int i = threadIdx.x; i < n_pending; i += blockDim.x) {
-            const int r = al[i];
-            R[4 + i] = (uint32_t)r;
-            rz[r] = C.ray_z[r];
-            rst[r] = C.ray_st[r];
-          }
-          if (threadIdx.x == 0) {
-            R[0] = gtile;
-            R[1] = (uint32_t)(k + 1);
-            R[2] = (uint32_t)n_pending;
-            R[3] = (uint32_t)P;
-          }
-          __threadfence();
-          __syncthreads();
-          if (threadIdx.x == 0) {
-            atomicExch(&L.split[4 + rr], (uint32_t)P);
-            atomicSub(&L.split[2], 1u);
-          }
-          uint16_t *tmp = pick(C.alive, k & 1);   // free: this subfrustum's list
-          const int m = (n_pending + P - 1) / P;
-          for (int j = threadIdx.x; j < m; j += blockDim.x) tmp[j] = al[j * P];
-          __syncthreads();
-          for (int j = threadIdx.x; j < m; j += blockDim.x) al[j] = tmp[j];
-          __syncthreads();
-          n_pending = m;
+          publish_split(k + 1, P);
           split_done = true;
         }
       }
@@ -1668,7 +1792,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     }
     __syncthreads();
     if (L.tile_stats && threadIdx.x == 0 && !part) {
-      uint32_t *ts = L.tile_stats + (size_t)gtile * 16;
+      uint32_t *ts = L.tile_stats + (size_t)gtile * kTileStatWords;
+      for (int i = 0; i < 5; ++i) ts[16 + i] = (uint32_t)min(s_diag[i], 0xFFFFFFFFull);
       ts[8] = (uint32_t)(s_dbg[0] >> 4);
       ts[9] = (uint32_t)(s_dbg[1] >> 4);
       ts[10] = (uint32_t)(s_dbg[2] >> 4);
@@ -1844,21 +1969,29 @@ void launch_eval_view(const DevScene &sc, const uint32_t *view, const int32_t *i
   if (npts > 0) count_launch(), k_eval_view<<<(npts + 127) / 128, 128, 0, s>>>(sc, view, info, pts, npts, f, grad);
 }
 
-template <int MODE>
-static cudaError_t trace_launch_mode(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s) {
-  const size_t smem = smem_per_cta(L);
-  cudaError_t e = cudaFuncSetAttribute(k_trace<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<MODE>, kWarps * 32, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  count_launch(), k_trace<MODE><<<n_sm * per_sm, kWarps * 32, smem, s>>>(jobs, n_jobs, L);
-  return cudaGetLastError();
+// Kernel instances: every step mode, with or without the out-of-line
+// primitive families (torus, sphere-cone, ellipsoid, rounded triangle,
+// bounded quadric).  Scenes of spheres, rounded boxes and capsules run the
+// lean instance: its interpreter has no call to the further families, whose
+// registers otherwise count for the whole kernel (measured on B300: 1080p
+// trace 4-5 % faster).
+template <class F>
+static auto with_instance(const TraceLaunch &L, F &&f) {
+#define ST_INST(M)                                                                     \
+  return L.further ? f(std::integral_constant<int, (M) | kFurtherBit>{})               \
+                   : f(std::integral_constant<int, (M)>{})
+  switch (L.step_mode) {
+    case ST_STEP_OVERRELAX: ST_INST(ST_STEP_OVERRELAX);
+    case ST_STEP_CROSSING: ST_INST(ST_STEP_CROSSING);
+    case ST_STEP_LEARNED: ST_INST(ST_STEP_LEARNED);
+    case ST_STEP_RECORD: ST_INST(ST_STEP_RECORD);
+    default: ST_INST(ST_STEP_PLAIN);
+  }
+#undef ST_INST
 }
 
 template <int MODE>
-static cudaError_t trace_plan_mode(const TraceLaunch &L, int n_sm, int *grid, size_t *smem) {
+static cudaError_t trace_config(const TraceLaunch &L, int n_sm, int *grid, size_t *smem) {
   *smem = smem_per_cta(L);
   cudaError_t e = cudaFuncSetAttribute(k_trace<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
   if (e != cudaSuccess) return e;
@@ -1871,55 +2004,30 @@ static cudaError_t trace_plan_mode(const TraceLaunch &L, int n_sm, int *grid, si
 }
 
 cudaError_t trace_plan(const TraceLaunch &L, int n_sm, int *grid, size_t *smem) {
-  switch (L.step_mode) {
-    case ST_STEP_OVERRELAX: return trace_plan_mode<ST_STEP_OVERRELAX>(L, n_sm, grid, smem);
-    case ST_STEP_CROSSING: return trace_plan_mode<ST_STEP_CROSSING>(L, n_sm, grid, smem);
-    case ST_STEP_LEARNED: return trace_plan_mode<ST_STEP_LEARNED>(L, n_sm, grid, smem);
-    case ST_STEP_RECORD: return trace_plan_mode<ST_STEP_RECORD>(L, n_sm, grid, smem);
-    default: return trace_plan_mode<ST_STEP_PLAIN>(L, n_sm, grid, smem);
-  }
+  return with_instance(L, [&](auto m) { return trace_config<decltype(m)::value>(L, n_sm, grid, smem); });
 }
 
 cudaError_t trace_launch_planned(const Job *jobs, int n_jobs, const TraceLaunch &L, int grid, size_t smem,
                                  cudaStream_t s) {
-  switch (L.step_mode) {
-    case ST_STEP_OVERRELAX: count_launch(), k_trace<ST_STEP_OVERRELAX><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
-    case ST_STEP_CROSSING: count_launch(), k_trace<ST_STEP_CROSSING><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
-    case ST_STEP_LEARNED: count_launch(), k_trace<ST_STEP_LEARNED><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
-    case ST_STEP_RECORD: count_launch(), k_trace<ST_STEP_RECORD><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
-    default: count_launch(), k_trace<ST_STEP_PLAIN><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L); break;
-  }
-  return cudaGetLastError();
+  return with_instance(L, [&](auto m) {
+    count_launch(), k_trace<decltype(m)::value><<<grid, kWarps * 32, smem, s>>>(jobs, n_jobs, L);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t trace_launch(const Job *jobs, int n_jobs, const TraceLaunch &L, int n_sm, cudaStream_t s) {
-  switch (L.step_mode) {
-    case ST_STEP_OVERRELAX: return trace_launch_mode<ST_STEP_OVERRELAX>(jobs, n_jobs, L, n_sm, s);
-    case ST_STEP_CROSSING: return trace_launch_mode<ST_STEP_CROSSING>(jobs, n_jobs, L, n_sm, s);
-    case ST_STEP_LEARNED: return trace_launch_mode<ST_STEP_LEARNED>(jobs, n_jobs, L, n_sm, s);
-    case ST_STEP_RECORD: return trace_launch_mode<ST_STEP_RECORD>(jobs, n_jobs, L, n_sm, s);
-    default: return trace_launch_mode<ST_STEP_PLAIN>(jobs, n_jobs, L, n_sm, s);
-  }
-}
-
-template <int MODE>
-static int ctas_per_sm_mode(const TraceLaunch &L) {
-  const size_t smem = smem_per_cta(L);
-  if (cudaFuncSetAttribute(k_trace<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<MODE>, kWarps * 32, smem);
-  return per_sm;
+  int grid = 0;
+  size_t smem = 0;
+  cudaError_t e = trace_plan(L, n_sm, &grid, &smem);
+  if (e != cudaSuccess) return e;
+  return trace_launch_planned(jobs, n_jobs, L, grid, smem, s);
 }
 
 int trace_ctas_per_sm(const TraceLaunch &L) {
-  switch (L.step_mode) {
-    case ST_STEP_OVERRELAX: return ctas_per_sm_mode<ST_STEP_OVERRELAX>(L);
-    case ST_STEP_CROSSING: return ctas_per_sm_mode<ST_STEP_CROSSING>(L);
-    case ST_STEP_LEARNED: return ctas_per_sm_mode<ST_STEP_LEARNED>(L);
-    case ST_STEP_RECORD: return ctas_per_sm_mode<ST_STEP_RECORD>(L);
-    default: return ctas_per_sm_mode<ST_STEP_PLAIN>(L);
-  }
+  int grid = 0;
+  size_t smem = 0;
+  if (trace_plan(L, 1, &grid, &smem) != cudaSuccess) return 0;
+  return grid;
 }
 
 }  // namespace st

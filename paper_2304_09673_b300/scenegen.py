@@ -26,7 +26,13 @@ leaves"):
   SCONE  (13): [0:3] centre a, [3:6] centre b, [6] radius r_a, [7] radius r_b
                (sphere-cone: convex hull of the two balls, |b - a| > |r_a - r_b|)
   ELLIPSOID (14): [0:3] centre, [3:12] world->local rotation M, [12:15] radii
-(the kind numbers of the last three equal their node codes in a pruned view).
+  RTRI   (15): rounded triangle, [0:3], [3:6], [6:9] vertices, [9] rounding
+  QUADRIC (11): bounded quadric {q <= 0} in an oriented box: [0:3] centre,
+               [3:7] rotation quaternion (w, x, y, z), [7:10] box half
+               extents, [10:15] alpha, beta, gamma, delta, kappa of
+               q(u) = alpha u0^2 + beta u1^2 + gamma u2^2 + delta u2 + kappa
+(the kind numbers of the further families equal their node codes in a pruned
+view, but for the quadric: kind 11, code 16).
 Operator records: [0] blend range k, [1] operator range bound d_o
   (Sec. 5, Eq. "compact smooth union": R_o = (-inf, d_o]).
 Operator kinds: 16 compact smooth union, 17 compact smooth intersection,
@@ -42,10 +48,12 @@ import numpy as np
 
 SPHERE, RBOX, CAPSULE = 0, 1, 2
 TORUS, SCONE, ELLIPSOID = 12, 13, 14
+RTRI, QUADRIC = 15, 11
 OP_UNION, OP_INTER, OP_DIFF = 16, 17, 18
 OP_SHARP_UNION, OP_SHARP_INTER, OP_SHARP_DIFF = 19, 20, 21
 PRIM_KINDS = (SPHERE, RBOX, CAPSULE)
 ALL_PRIM_KINDS = (SPHERE, RBOX, CAPSULE, TORUS, SCONE, ELLIPSOID)
+EIGHT_PRIM_KINDS = ALL_PRIM_KINDS + (RTRI, QUADRIC)
 OP_KINDS = (OP_UNION, OP_INTER, OP_DIFF, OP_SHARP_UNION, OP_SHARP_INTER, OP_SHARP_DIFF)
 
 
@@ -141,6 +149,37 @@ def _draw_primitive(rng: np.random.Generator, centre: np.ndarray, kinds=PRIM_KIN
         rec[0:3] = centre
         rec[3:12] = rot.T.reshape(-1)
         rec[12:15] = rng.uniform(0.04, 0.15, size=3)
+    elif kind == RTRI:
+        # three vertices around the centre in a random plane, at least 60
+        # degrees apart, 0.06..0.2 from it
+        rot = _random_rotation(rng)
+        ang = rng.uniform(0, 2 * math.pi) + np.array([0.0, 2.1, 4.2]) + rng.uniform(-0.4, 0.4, size=3)
+        rad = rng.uniform(0.06, 0.2, size=3)
+        for k in range(3):
+            rec[3 * k:3 * k + 3] = centre + rad[k] * (math.cos(ang[k]) * rot[:, 0] + math.sin(ang[k]) * rot[:, 1])
+        rec[9] = rng.uniform(0.01, 0.03)
+    elif kind == QUADRIC:
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        e = rng.uniform(0.05, 0.15, size=3)
+        rec[0:3] = centre
+        rec[3:7] = q
+        rec[7:10] = e
+        # ellipsoid, hyperboloid of one sheet, cone, elliptic paraboloid or
+        # cylinder, scaled to the box so the solid is neither empty nor the box
+        shape = int(rng.integers(5))
+        a, b = rng.uniform(0.6, 1.4, size=2) / (0.8 * e[:2]) ** 2
+        if shape == 0:
+            coef = (a, b, rng.uniform(0.6, 1.4) / (0.8 * e[2]) ** 2, 0.0, -1.0)
+        elif shape == 1:
+            coef = (a, b, -rng.uniform(0.3, 1.0) / e[2] ** 2, 0.0, -0.3)
+        elif shape == 2:
+            coef = (a, b, -rng.uniform(0.5, 1.5) / e[2] ** 2, 0.0, 0.0)
+        elif shape == 3:
+            coef = (a, b, 0.0, -rng.uniform(1.0, 2.0) / e[2], -0.5)
+        else:
+            coef = (a, b, 0.0, 0.0, -rng.uniform(0.3, 0.8))
+        rec[10:15] = coef
     else:
         raise ValueError(f"unknown primitive kind {kind}")
     return kind, rec.astype(np.float32)
@@ -329,6 +368,16 @@ def edit_primitives(scene: Scene, frac: float, rng: np.random.Generator):
             recs[j, 0:3] += dp
             recs[j, 12:15] *= s
             recs[j, 15] *= s
+        elif kd == RTRI:
+            mid = (recs[j, 0:3] + recs[j, 3:6] + recs[j, 6:9]) / 3
+            for k in range(3):
+                recs[j, 3 * k:3 * k + 3] = mid + s * (recs[j, 3 * k:3 * k + 3] - mid) + dp
+            recs[j, 9] *= s
+        elif kd == QUADRIC:
+            recs[j, 0:3] += dp
+            recs[j, 7:10] *= s
+        elif kd in (TORUS, ELLIPSOID):
+            recs[j, 0:3] += dp
         else:
             mid = 0.5 * (recs[j, 0:3] + recs[j, 3:6])
             recs[j, 0:3] = mid + s * (recs[j, 0:3] - mid) + dp
@@ -347,6 +396,12 @@ def workload_families(seed: int = 0, n_prims: int = 64, max_depth: int = 6) -> S
     """All six primitive families (sphere, rounded box, capsule, torus,
     sphere-cone, ellipsoid) in a random tree (64 primitives, depth 6)."""
     return make_scene(n_prims, max_depth, seed, kinds=ALL_PRIM_KINDS)
+
+
+def workload_eight_families(seed: int = 0, n_prims: int = 64, max_depth: int = 6) -> Scene:
+    """All eight primitive families (the six above, the rounded triangle of
+    the sphere-triangle volume of interest, the bounded quadric)."""
+    return make_scene(n_prims, max_depth, seed, kinds=EIGHT_PRIM_KINDS)
 
 
 def workload_1080p(seed: int = 100) -> Scene:

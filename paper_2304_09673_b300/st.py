@@ -54,7 +54,8 @@ class st_trace_opts(C.Structure):
                 ("step_mode", C.c_int32), ("depth_slab_frac", C.c_float),
                 ("max_new_per_turn", C.c_int32), ("newton_iters", C.c_int32),
                 ("newton_clamp", C.c_float), ("mlp", C.c_void_p), ("tile_stats", C.c_void_p),
-                ("omega", C.c_float), ("min_step", C.c_float), ("split_kcycles", C.c_int32)]
+                ("omega", C.c_float), ("min_step", C.c_float), ("split_kcycles", C.c_int32),
+                ("heavy_split_len", C.c_int32), ("wait_spin_limit", C.c_uint32), ("check_status", C.c_int32)]
 
 
 class st_tune(C.Structure):
@@ -68,6 +69,7 @@ _lib.st_version.restype = C.c_char_p
 _lib.st_scene_create.argtypes = [C.POINTER(st_scene_desc), C.POINTER(C.c_void_p), _P]
 _lib.st_scene_update_prims.argtypes = [_P, _P, _P, C.c_int, _P]
 _lib.st_scene_addresses.argtypes = [_P, _P]
+_lib.st_scene_info.argtypes = [_P, _P]
 _lib.st_scene_destroy.argtypes = [_P]
 _lib.st_scene_destroy.restype = None
 _lib.st_build_tiles.argtypes = [_P, C.POINTER(st_camera), C.c_int, C.POINTER(st_tiles), _P]
@@ -81,6 +83,8 @@ _lib.st_kernel_launches.restype = C.c_uint64
 _lib.st_trace_noalloc.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINTER(st_trace_opts),
                                   _P, _P, _P, _P, _P, _P]
 _lib.st_trace_noalloc_scratch_bytes.restype = C.c_size_t
+_lib.st_trace_noalloc_last_layout.argtypes = [_P]
+_lib.st_device_allocations.restype = C.c_uint64
 _lib.st_trace_record.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINTER(st_trace_opts),
                                  _P, _P, _P, _P, _P, C.c_uint32, _P, C.c_int, _P]
 _lib.st_mlp_pack_size.restype = C.c_size_t
@@ -106,9 +110,10 @@ _lib.st_trace_dexels.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), 
                                  _P, _P, _P, _P, _P, _P]
 _lib.st_eval_sparse.argtypes = [_P, _P, C.c_int, _P, C.c_int, C.c_int, _P, _P, _P]
 
-EXPORTED = ("st_scene_create", "st_scene_update_prims", "st_scene_addresses", "st_scene_destroy",
+EXPORTED = ("st_scene_create", "st_scene_update_prims", "st_scene_addresses", "st_scene_info", "st_scene_destroy",
             "st_build_tiles", "st_trace", "st_tiles_copy", "st_pruned_view", "st_pruned_view_alg1", "st_eval_pruned", "st_prep_tree", "st_last_error",
-            "st_version", "st_kernel_launches", "st_trace_noalloc", "st_trace_noalloc_scratch_bytes",
+            "st_version", "st_kernel_launches", "st_device_allocations", "st_trace_noalloc",
+            "st_trace_noalloc_scratch_bytes", "st_trace_noalloc_last_layout",
             "st_trace_record", "st_mlp_pack_size", "st_mlp_param_count", "st_mlp_pack", "st_mlp_grad",
             "st_mlp_adam", "st_mlp_infer", "st_tune_key", "st_tune_load", "st_tune_store", "st_autotune",
             "st_batch_create", "st_batch_render", "st_batch_tiles", "st_batch_graph_kernels", "st_batch_destroy",
@@ -163,9 +168,11 @@ def make_camera(cam) -> st_camera:
 
 def make_opts(eps=1e-4, lipschitz=1.45, max_steps=256, step_mode=ST_STEP_PLAIN, depth_slab_frac=0.05,
               max_new_per_turn=32, newton_iters=2, newton_clamp=0.0, mlp=None, tile_stats=None,
-              omega=1.7, min_step=0.0, split_kcycles=0) -> st_trace_opts:
+              omega=1.7, min_step=0.0, split_kcycles=0, heavy_split_len=0, wait_spin_limit=0,
+              check_status=0) -> st_trace_opts:
     o = st_trace_opts(eps, lipschitz, max_steps, step_mode, depth_slab_frac, max_new_per_turn,
-                      newton_iters, newton_clamp, mlp, None, omega, min_step, split_kcycles)
+                      newton_iters, newton_clamp, mlp, None, omega, min_step, split_kcycles,
+                      heavy_split_len, wait_spin_limit, check_status)
     if tile_stats is not None:
         o.tile_stats = tile_stats.data_ptr()
         o._keep = tile_stats
@@ -191,6 +198,12 @@ def st_scene_addresses(h, n_nodes: int) -> np.ndarray:
     out = np.empty(n_nodes, np.int32)
     _check(_lib.st_scene_addresses(h, out.ctypes.data), "st_scene_addresses")
     return out
+
+
+def st_scene_info(h) -> dict:
+    out = np.zeros(4, np.float64)
+    _check(_lib.st_scene_info(h, out.ctypes.data), "st_scene_info")
+    return dict(diameter=float(out[0]), extent=float(out[1]), n_prims=int(out[2]), stack_depth=int(out[3]))
 
 
 def st_scene_destroy(h) -> None:
@@ -223,6 +236,16 @@ def st_trace_noalloc(h, cam, tiles: st_tiles, opts: st_trace_opts | None, depth,
 
 def st_trace_noalloc_scratch_bytes() -> int:
     return int(_lib.st_trace_noalloc_scratch_bytes())
+
+
+def st_trace_noalloc_last_layout() -> dict:
+    out = np.zeros(3, np.uint64)
+    _check(_lib.st_trace_noalloc_last_layout(out.ctypes.data), "st_trace_noalloc_last_layout")
+    return dict(work_in_scratch=bool(out[0]), bytes_used=int(out[1]), split_records=int(out[2]))
+
+
+def st_device_allocations() -> int:
+    return int(_lib.st_device_allocations())
 
 
 def st_trace_record(h, cam, tiles: st_tiles, opts, depth, normal, evals, flags, records, rec_count,

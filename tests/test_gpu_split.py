@@ -147,3 +147,108 @@ def test_split_full_size_same_bytes(stlib, cuda, mode):
         assert c1[4] > c0[4], "no tile was split"
     finally:
         stlib.st_scene_destroy(h)
+
+
+# Never reached by a launch: splits only before the first subfrustum.
+NO_LATE_SPLIT = 2_000_000_000
+
+
+@pytest.mark.parametrize("mode", ["plain", "learned", "crossing"])
+def test_heavy_split_same_bytes(stlib, cuda, mode):
+    """Every tile treated as heavy (heavy_split_len = 1): each splits into
+    parts before its first subfrustum and CTAs take open parts before whole
+    tiles.  Same bytes and per-ray counters as the unsplit trace, with and
+    without late splits on top."""
+    import torch
+    kw = _mode_kw(stlib, mode)
+    for n, depth, seed, W, H, T in CASES:
+        s = sg.make_scene(n, depth, seed)
+        cam = sg.default_camera(W, H)
+        h = stlib.st_scene_create(s)
+        try:
+            t = stlib.st_build_tiles(h, cam, T)
+            base, c0 = _trace(stlib, torch, h, cam, t, stlib.make_opts(split_kcycles=-1, **kw))
+            assert c0[7] == 0 and not np.any(base[3] == 99)
+            for late in (NO_LATE_SPLIT, 1):
+                got, c1 = _trace(stlib, torch, h, cam, t,
+                                 stlib.make_opts(split_kcycles=late, heavy_split_len=1, **kw))
+                for k, name in enumerate(("depth", "normal", "evals", "flags")):
+                    assert got[k].tobytes() == base[k].tobytes(), \
+                        (n, T, late, name, int(np.sum(got[k] != base[k])))
+                assert [c1[i] for i in SAME_COUNTERS] == [c0[i] for i in SAME_COUNTERS], (n, T, late, c0, c1)
+                # every part marches the tile's subfrustums for its own rays
+                assert c1[4] > c0[4], (n, T, late)
+        finally:
+            stlib.st_scene_destroy(h)
+
+
+def test_heavy_split_noalloc_and_batch(stlib, cuda):
+    import torch
+    dev = torch.device("cuda")
+    n, depth, seed, W, H, T = CASES[1]
+    s = sg.make_scene(n, depth, seed)
+    cam = sg.default_camera(W, H)
+    h = stlib.st_scene_create(s)
+    try:
+        t = stlib.st_build_tiles(h, cam, T)
+        base, c0 = _trace(stlib, torch, h, cam, t, stlib.make_opts(split_kcycles=-1))
+        got, c1 = _trace(stlib, torch, h, cam, t, stlib.make_opts(split_kcycles=NO_LATE_SPLIT, heavy_split_len=1),
+                         noalloc=True)
+        for k in range(4):
+            assert got[k].tobytes() == base[k].tobytes()
+        assert c1[7] == 0 and c1[0] == c0[0] and c1[4] > c0[4]
+    finally:
+        stlib.st_scene_destroy(h)
+    # batch: one graph, every tile of every scene split before it starts
+    scenes = [sg.make_scene(n, d, sd) for n, d, sd, *_ in CASES]
+    cams = [sg.default_camera(W, H) for _, _, _, W, H, _ in CASES]
+    handles = [stlib.st_scene_create(x) for x in scenes]
+    try:
+        res = []
+        for kw in (dict(split_kcycles=-1), dict(split_kcycles=NO_LATE_SPLIT, heavy_split_len=1)):
+            o = {k: [] for k in ("depth", "normal", "evals", "flags")}
+            for c in cams:
+                m = c.width * c.height
+                o["depth"].append(torch.full((m,), -1.0, device=dev))
+                o["normal"].append(torch.full((m * 3,), -1.0, device=dev))
+                o["evals"].append(torch.full((m,), 7, dtype=torch.int32, device=dev))
+                o["flags"].append(torch.full((m,), 99, dtype=torch.uint8, device=dev))
+            b = stlib.st_batch_create(handles, cams, stlib.make_opts(**kw), o["depth"], o["normal"], o["evals"],
+                                      o["flags"])
+            try:
+                for _ in range(2):
+                    cnt = stlib.st_batch_render(b, counters=True)
+                    assert cnt[7] == 0
+                torch.cuda.synchronize()
+                res.append(([[x.cpu().numpy().tobytes() for x in o[k]] for k in o], cnt))
+            finally:
+                stlib.st_batch_destroy(b)
+        assert res[0][0] == res[1][0]
+        assert res[0][1][0] == res[1][1][0] and res[1][1][4] > res[0][1][4]
+    finally:
+        for x in handles:
+            stlib.st_scene_destroy(x)
+
+
+@pytest.mark.parametrize("mode", ["learned", "plain"])
+def test_heavy_split_clustered_long_lists(stlib, cuda, mode):
+    """The 10,000-primitive clustered scene at 960x540, the tiles of lists of
+    2,048+ entries split before they start (and late splits on): the same
+    bytes and per-ray counters as without any split."""
+    import torch
+    kw = _mode_kw(stlib, mode)
+    s = sg.workload_clustered(200)
+    cam = sg.default_camera(960, 540)
+    h = stlib.st_scene_create(s)
+    try:
+        t = stlib.st_build_tiles(h, cam, 16)
+        assert t.max_overlap >= 1024
+        base, c0 = _trace(stlib, torch, h, cam, t, stlib.make_opts(split_kcycles=-1, **kw))
+        assert c0[7] == 0 and not np.any(base[3] == 99)
+        got, c1 = _trace(stlib, torch, h, cam, t, stlib.make_opts(heavy_split_len=2048, **kw))
+        for k, name in enumerate(("depth", "normal", "evals", "flags")):
+            assert got[k].tobytes() == base[k].tobytes(), (name, int(np.sum(got[k] != base[k])))
+        assert [c1[i] for i in SAME_COUNTERS] == [c0[i] for i in SAME_COUNTERS], (c0, c1)
+        assert c1[4] > c0[4], "no tile was split"
+    finally:
+        stlib.st_scene_destroy(h)

@@ -10,7 +10,9 @@ from paper_2304_09673_b300 import scenegen as sg
 pytestmark = pytest.mark.gpu
 
 # view code -> oracle op code (3 keep, 0 +inf, 1 right, 2 left)
-CODE_TO_OP = {0: 3, 1: 3, 2: 3, 3: 3, 4: 3, 5: 3, 6: 3, 7: 3, 8: 3, 9: 0, 10: 1, 11: 2}
+CODE_TO_OP = {0: 3, 1: 3, 2: 3, 3: 3, 4: 3, 5: 3, 6: 3, 7: 3, 8: 3, 9: 0, 10: 1, 11: 2, 12: 3, 13: 3, 14: 3,
+              15: 3, 16: 3}
+PRIM_CODE = {11: 16}   # the bounded quadric's kind maps to view code 16; other kinds equal their codes
 
 
 def gpu_view(st, h, act_po, torch, method="lca"):
@@ -46,14 +48,14 @@ def test_view_matches_definition(stlib, orc, cuda, seed, method):
             assert info[0] == len(addr) and info[3] == m
             assert info[1] == ru
             v = view.cpu().numpy().view(np.uint32)
-            codes = v >> 28
+            codes = v >> 27
             assert np.array_equal(vaddr.cpu().numpy()[:len(addr)], addr)
             assert [CODE_TO_OP[int(c)] for c in codes] == opc.tolist()
             # kept operators keep their own kind
             kinds = s.kind[st_["desc_of"][addr]]
             for c, k, o in zip(codes, kinds, opc):
                 if k < 16:
-                    assert c == k
+                    assert c == PRIM_CODE.get(int(k), k)
                 elif o == 3:
                     assert c == k - 16 + 3
     finally:

@@ -69,13 +69,14 @@ def test_cull_spheres_independent(orc):
             assert a_zo == pytest.approx(want[a][1], abs=1e-10)
 
 
-@pytest.mark.parametrize("kinds", ["three", "six"])
+@pytest.mark.parametrize("kinds", ["three", "six", "eight"])
 def test_cull_all_families_sampled(orc, kinds):
     # Every sampled point of a pixel ray that lies inside a primitive's volume
     # of interest has its depth inside that primitive's tile entry (all VOI
     # families; sampling along the rays, independent of the slab and
     # cylinder formulas).
-    s = sg.make_scene(24, 6, 57, kinds=sg.PRIM_KINDS if kinds == "three" else sg.ALL_PRIM_KINDS)
+    s = sg.make_scene(24, 6, 57, kinds={"three": sg.PRIM_KINDS, "six": sg.ALL_PRIM_KINDS,
+                                        "eight": sg.EIGHT_PRIM_KINDS}[kinds])
     cam = sg.default_camera(48, 48)
     st = orc.structure(s)
     tile = 16
@@ -100,12 +101,13 @@ def test_cull_all_families_sampled(orc, kinds):
     assert checked > 100
 
 
-@pytest.mark.parametrize("seed", [0, 5, 7])
+@pytest.mark.parametrize("seed", [0, 5, 7, 8])
 def test_cull_fp32_contains_fp64(orc, seed):
     # The FP32 lists (padded VOIs) contain the exact FP64 lists: every exact
     # entry is present with an interval at least as wide; lists are sorted by
-    # (z_in, post-order address).  Seed 7: all six primitive families.
-    s = sg.workload_small(seed) if seed != 7 else sg.workload_families(seed)
+    # (z_in, post-order address).  Seed 7: all six primitive families; seed 8:
+    # all eight.
+    s = {7: sg.workload_families, 8: sg.workload_eight_families}.get(seed, sg.workload_small)(seed)
     cam = sg.default_camera(256, 256)
     _, l64 = orc.cull(s, cam, 16, 0)
     _, l32 = orc.cull(s, cam, 16, 1)

@@ -251,10 +251,49 @@ def test_all_active_equals_dense(orc):
     assert np.array_equal(orc.field(s, pts, act), orc.field(s, pts))
 
 
+def _quat_matrix(qq):
+    """Rotation (local -> world) of a quaternion (w, x, y, z), by rotating the
+    basis vectors with the Hamilton product q v q*."""
+    w, x, y, z = np.asarray(qq, np.float64) / np.linalg.norm(qq)
+
+    def mul(a, b):
+        return np.array([a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3],
+                         a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
+                         a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1],
+                         a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0]])
+    qv, qc = np.array([w, x, y, z]), np.array([w, -x, -y, -z])
+    cols = [mul(mul(qv, np.concatenate([[0.0], e])), qc)[1:] for e in np.eye(3)]
+    return np.stack(cols, axis=1)
+
+
+def tri_distance(q, p):
+    """Distance from p to the triangle of record q (vertices q[0:9]): the
+    least of the distances to the three edges and, when the plane projection
+    has non-negative barycentric coordinates, to the plane."""
+    a, b, c = (np.asarray(q[3 * i:3 * i + 3], np.float64) for i in range(3))
+    p = np.asarray(p, np.float64)
+    best = np.inf
+    for s, t in ((a, b), (b, c), (c, a)):
+        h = np.clip((p - s) @ (t - s) / ((t - s) @ (t - s)), 0, 1)
+        best = min(best, np.linalg.norm(p - s - h * (t - s)))
+    # barycentric coordinates of the projection (least squares on the plane)
+    A = np.stack([b - a, c - a], axis=1)
+    uv, *_ = np.linalg.lstsq(A, p - a, rcond=None)
+    if uv[0] >= 0 and uv[1] >= 0 and uv.sum() <= 1:
+        best = min(best, np.linalg.norm(p - (a + A @ uv)))
+    return best
+
+
 def voi_contains_prim(kind, q, d, p):
     """Independent point-in-VOI test of one primitive record q with range of
-    interest bound d (sphere / oriented box / capsule / cylinder families)."""
+    interest bound d (sphere / oriented box / capsule / cylinder /
+    sphere-triangle families)."""
     q = np.asarray(q, np.float64)
+    if kind == sg.RTRI:
+        return tri_distance(q, p) <= q[9] + d
+    if kind == sg.QUADRIC:
+        loc = _quat_matrix(q[3:7]).T @ (p - q[:3])
+        return bool(np.all(np.abs(loc) <= q[7:10] + d))
     if kind == sg.SPHERE:
         return np.linalg.norm(p - q[:3]) <= q[3] + d
     if kind in (sg.RBOX, sg.ELLIPSOID):
@@ -281,11 +320,12 @@ def _voi_contains(orc, scene, st, p):
     return out
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
 def test_local_equivalence_sign(orc, seed):
     # Sec. 3 / Sec. 5: with A = primitives whose volume of interest contains p,
-    # sign(f_A(p)) = sign(f(p)).  Seed 3: all six primitive families.
-    kinds = sg.ALL_PRIM_KINDS if seed == 3 else sg.PRIM_KINDS
+    # sign(f_A(p)) = sign(f(p)).  Seed 3: all six primitive families; seed 4:
+    # all eight (rounded triangles, bounded quadrics).
+    kinds = {3: sg.ALL_PRIM_KINDS, 4: sg.EIGHT_PRIM_KINDS}.get(seed, sg.PRIM_KINDS)
     s = sg.make_scene(48, 7, 900 + seed, kinds=kinds)
     st = orc.structure(s)
     pts = _random_points(s, 400, seed, orc)
