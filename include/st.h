@@ -222,6 +222,14 @@ typedef struct {
                                [never: the repeated view builds cost more
                                than the balance gains on the clustered
                                workloads]                                 */
+    int32_t heavy_split_rank; /* > 0: the tiles of the heavy_split_rank
+                               longest lists (each at least 1024 entries
+                               and four times the mean list) split as
+                               heavy_split_len describes; the threshold is
+                               taken on the device from the launch's own
+                               lists; 0 = default [see st_trace_opts
+                               defaults below], < 0 = never; a positive
+                               heavy_split_len takes precedence           */
     uint32_t wait_spin_limit; /* bound on the polls of a warp waiting for
                                the other warps of its tile and of a CTA
                                waiting for parts of split tiles; a warp

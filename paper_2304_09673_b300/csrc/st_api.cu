@@ -477,9 +477,14 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
   ST_CK(cudaMemcpyAsync(s->job.p, &job, sizeof(Job), cudaMemcpyHostToDevice, st));
   ST_CK(cudaMemsetAsync(s->item_counter.p, 0, 4, st));
   ST_CK(s->order.ensure(L.n_items));
-  launch_tile_order(s->job.p, 1, L.n_items, s->order.p, st);
-  L.order = s->order.p;
   const long long split_cycles = trace_split_cycles(o.split_kcycles);
+  const uint32_t heavy_rank = split_cycles >= 0 && tp.step_mode != ST_STEP_RECORD
+                                  ? trace_heavy_rank(o.heavy_split_len, o.heavy_split_rank) : 0u;
+  uint32_t *heavy_thr = heavy_rank ? s->small.p + 9 : nullptr;
+  launch_tile_order(s->job.p, 1, L.n_items, s->order.p, st, heavy_rank, trace_heavy_min(tl->n_entries, L.n_items),
+                    heavy_thr);
+  L.order = s->order.p;
+  L.heavy_thr = heavy_thr;
   if (split_cycles >= 0 && tp.step_mode != ST_STEP_RECORD) {
     L.split_cap = trace_split_cap(L.max_tile_rays, L.n_items);
     ST_CK(s->split.ensure(trace_split_words(L.max_tile_rays, L.split_cap)));

@@ -387,6 +387,7 @@ int plan(st_batch *b) {
     L.split = b->split.p;
     L.split_cycles = split_cycles;
     L.heavy_len = trace_heavy_len(b->opts.heavy_split_len);
+    if (trace_heavy_rank(b->opts.heavy_split_len, b->opts.heavy_split_rank)) L.heavy_thr = b->small.p + 6;
   }
   L.idle_spins = b->opts.wait_spin_limit;
   L.split_spins = b->opts.wait_spin_limit;
@@ -408,7 +409,12 @@ int plan(st_batch *b) {
   launch_scatter_sort(b->pairs.p, b->small.p + 1, b->pair_cap, b->offsets.p, b->n_tiles, b->overlap_cap, b->keys.p,
                       b->ztmp.p, b->z_in.p, b->z_out.p, b->prim.p, b->n_sm, cs, b->status.p, b->tile_count.p,
                       b->small.p + 5);
-  launch_tile_order(b->d_jobs.p, n, b->n_tiles, b->order.p, cs);
+  {
+    const uint32_t heavy_rank = L.split ? trace_heavy_rank(b->opts.heavy_split_len, b->opts.heavy_split_rank) : 0u;
+    uint32_t *heavy_thr = heavy_rank ? const_cast<uint32_t *>(L.heavy_thr) : nullptr;
+    launch_tile_order(b->d_jobs.p, n, b->n_tiles, b->order.p, cs, heavy_rank,
+                      trace_heavy_min(b->entries_seen, b->n_tiles), heavy_thr);
+  }
   cudaError_t le = trace_launch_planned(b->d_jobs.p, n, L, b->grid, b->smem, cs);
   cudaGraph_t g = nullptr;
   cudaError_t ce = cudaStreamEndCapture(cs, &g);

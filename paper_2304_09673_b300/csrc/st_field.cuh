@@ -116,6 +116,58 @@ template <class A, class B, class C> __device__ __forceinline__ auto fma_(const 
   return a * b + c;
 }
 
+// ---- paired FP32 (Blackwell FFMA2 / FADD2 / FMUL2) -------------------------------
+// Two evaluation points per thread as one float2: every arithmetic step is one
+// paired instruction whose components round exactly as the scalar __fmaf_rn /
+// __fadd_rn / __fmul_rn (so a ray's values do not depend on whether it is
+// evaluated alone or in a pair); min / max / abs, the MUFU square root and
+// reciprocal and the branches are taken per component.
+struct F2 {
+  float2 v;
+  __device__ F2() {}
+  __device__ explicit F2(float s) : v(make_float2(s, s)) {}
+  __device__ F2(float2 x) : v(x) {}
+};
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ F2 add_(const F2 &a, const F2 &b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 add_(const F2 &a, float b) { return F2(__fadd2_rn(a.v, bc2(b))); }
+__device__ __forceinline__ F2 add_(float a, const F2 &b) { return F2(__fadd2_rn(bc2(a), b.v)); }
+// a - b as a + (-1) b: the product is exact, so the fused form rounds once,
+// as __fsub_rn does
+__device__ __forceinline__ F2 sub_(const F2 &a, const F2 &b) { return F2(__ffma2_rn(b.v, bc2(-1.f), a.v)); }
+__device__ __forceinline__ F2 sub_(const F2 &a, float b) { return F2(__fadd2_rn(a.v, bc2(-b))); }
+__device__ __forceinline__ F2 sub_(float a, const F2 &b) { return F2(__ffma2_rn(b.v, bc2(-1.f), bc2(a))); }
+__device__ __forceinline__ F2 mul_(const F2 &a, const F2 &b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 mul_(const F2 &a, float b) { return F2(__fmul2_rn(a.v, bc2(b))); }
+__device__ __forceinline__ F2 fma_(const F2 &a, const F2 &b, const F2 &c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ F2 fma_(const F2 &a, float b, const F2 &c) { return F2(__ffma2_rn(a.v, bc2(b), c.v)); }
+__device__ __forceinline__ F2 fma_(const F2 &a, const F2 &b, float c) { return F2(__ffma2_rn(a.v, b.v, bc2(c))); }
+__device__ __forceinline__ F2 fma_(const F2 &a, float b, float c) { return F2(__ffma2_rn(a.v, bc2(b), bc2(c))); }
+__device__ __forceinline__ F2 operator-(const F2 &a) { return F2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ F2 min_(const F2 &a, const F2 &b) { return F2(make_float2(fminf(a.v.x, b.v.x), fminf(a.v.y, b.v.y))); }
+__device__ __forceinline__ F2 max_(const F2 &a, const F2 &b) { return F2(make_float2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y))); }
+__device__ __forceinline__ F2 min_(const F2 &a, float b) { return F2(make_float2(fminf(a.v.x, b), fminf(a.v.y, b))); }
+__device__ __forceinline__ F2 max_(const F2 &a, float b) { return F2(make_float2(fmaxf(a.v.x, b), fmaxf(a.v.y, b))); }
+__device__ __forceinline__ F2 abs_(const F2 &a) { return F2(make_float2(fabsf(a.v.x), fabsf(a.v.y))); }
+__device__ __forceinline__ F2 sqrt_(const F2 &a) { return F2(make_float2(fsqrt(a.v.x), fsqrt(a.v.y))); }
+__device__ __forceinline__ F2 rcp_(const F2 &a) { return F2(make_float2(frcp(a.v.x), frcp(a.v.y))); }
+
+// Comparisons and selects: a bool for one point (float, dual number), a pair
+// of bools for F2.
+struct M2 { bool x, y; };
+__device__ __forceinline__ bool le_(float a, float b) { return a <= b; }
+__device__ __forceinline__ bool gt_(float a, float b) { return a > b; }
+template <int N> __device__ __forceinline__ bool le_(const Dual<N> &a, float b) { return a.v <= b; }
+template <int N> __device__ __forceinline__ bool gt_(const Dual<N> &a, float b) { return a.v > b; }
+__device__ __forceinline__ M2 le_(const F2 &a, float b) { return M2{a.v.x <= b, a.v.y <= b}; }
+__device__ __forceinline__ M2 gt_(const F2 &a, float b) { return M2{a.v.x > b, a.v.y > b}; }
+__device__ __forceinline__ bool and_(bool a, bool b) { return a && b; }
+__device__ __forceinline__ M2 and_(M2 a, M2 b) { return M2{a.x && b.x, a.y && b.y}; }
+template <class T> __device__ __forceinline__ T sel_(bool m, const T &a, const T &b) { return m ? a : b; }
+__device__ __forceinline__ F2 sel_(M2 m, const F2 &a, const F2 &b) {
+  return F2(make_float2(m.x ? a.v.x : b.v.x, m.y ? a.v.y : b.v.y));
+}
+
 // Record word k of a view node: from the view's shared parameter cache or,
 // for nodes that did not fit, from the scene's global record array.
 struct RecSrc {
@@ -295,6 +347,21 @@ __device__ __noinline__ T sd_further(uint32_t code, const float4 *q, T px, T py,
   return sd_ellipsoid<T>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), ldrec(q + 4), p);
 }
 
+// The further families for a pair of points: the scalar function per
+// component (out of line, as for one point).
+__device__ __forceinline__ F2 further_pair(uint32_t code, const float4 *q, const F2 p[3]) {
+  return F2(make_float2(sd_further<float>(code, q, p[0].v.x, p[1].v.x, p[2].v.x),
+                        sd_further<float>(code, q, p[0].v.y, p[1].v.y, p[2].v.y)));
+}
+template <class T>
+__device__ __forceinline__ T further_eval(uint32_t code, const float4 *q, const T p[3]) {
+  return sd_further<T>(code, q, p[0], p[1], p[2]);
+}
+template <>
+__device__ __forceinline__ F2 further_eval<F2>(uint32_t code, const float4 *q, const F2 p[3]) {
+  return further_pair(code, q, p);
+}
+
 // ---- compact smooth operators G_op (Sec. 5) -------------------------------------
 // Record [k, d_o, c1 = 6 / (6 d_o - k), 1/k].  Smooth displacement of Eq. 5:
 // d(f0, f1, k) = k/6 max(1 - a/k, 0)^3 with a = |f0 - f1|; transition
@@ -306,9 +373,9 @@ __device__ __forceinline__ T cube_(const T &x) { return mul_(x, mul_(x, x)); }
 // fused m -/+ (kr/6) x^3; a non-positive range gives no displacement.
 template <class T>
 __device__ __forceinline__ void disp_terms(const T &kr, const T &a, T &kr6, T &x3) {
-  const bool pos = val(kr) > 1e-30f;
-  const T x = mul_(max_(sub_(kr, a), 0.f), rcp_(pos ? kr : T(1.f)));
-  kr6 = pos ? mul_(kr, 1.f / 6.f) : T(0.f);
+  const auto pos = gt_(kr, 1e-30f);
+  const T x = mul_(max_(sub_(kr, a), 0.f), rcp_(sel_(pos, kr, T(1.f))));
+  kr6 = sel_(pos, mul_(kr, 1.f / 6.f), T(0.f));
   x3 = cube_(x);
 }
 
@@ -321,7 +388,7 @@ __device__ __forceinline__ void disp_terms(const T &kr, const T &a, T &kr6, T &x
 template <class T>
 __device__ __forceinline__ T op_compact_any(uint32_t code, float4 c, const T &f0, const T &f1) {
   const bool uni = code == V_UNION, dif = code == V_DIFF;
-  const bool inside = val(f0) <= c.y && val(f1) <= c.y;
+  const auto inside = and_(le_(f0, c.y), le_(f1, c.y));
   const float k6 = mul_(c.x, 1.f / 6.f);
   const T g1 = dif ? -f1 : f1;
   const T m = uni ? min_(f0, g1) : max_(f0, g1);
@@ -333,7 +400,7 @@ __device__ __forceinline__ T op_compact_any(uint32_t code, float4 c, const T &f0
   T kr6, x3;
   disp_terms(kr, a, kr6, x3);
   const T res = fma_(uni ? -kr6 : kr6, x3, m);
-  return inside ? res : m;
+  return sel_(inside, res, m);
 }
 
 template <class T>
@@ -429,7 +496,7 @@ __device__ __forceinline__ void eval_view_r(const uint32_t *view, int n_view, co
       default: {   // the further primitive families (codes 12..16)
         stk.push(sp++, acc);
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = kFurther ? sd_further<T>(code, q, p[r][0], p[r][1], p[r][2]) : T(INFINITY);
+        for (int r = 0; r < R; ++r) acc[r] = kFurther ? further_eval<T>(code, q, p[r]) : T(INFINITY);
         break;
       }
     }
@@ -456,6 +523,11 @@ struct SmemStack2 {   // R = 2 float points
     a[0] = v.x;
     a[1] = v.y;
   }
+};
+struct SmemStackF2 {  // R = 1 pair of float points (F2), the same slots as SmemStack2
+  float2 *base;
+  __device__ __forceinline__ void push(int s, const F2 (&a)[1]) { base[s * 32] = a[0].v; }
+  __device__ __forceinline__ void pop(int s, F2 (&a)[1]) const { a[0] = F2(base[s * 32]); }
 };
 struct SmemStack1 {   // R = 1 float point (the .x half of SmemStack2's slots)
   float2 *base;

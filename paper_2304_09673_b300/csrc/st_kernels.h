@@ -118,6 +118,9 @@ struct TraceLaunch {
                            // (0: built-in bound)
   int32_t further;         // 1: some scene holds primitives beyond spheres,
                            // rounded boxes and capsules (kernel instance)
+  const uint32_t *heavy_thr;  // optional device word: early-split threshold
+                              // (written by launch_tile_order); overrides
+                              // heavy_len
 };
 
 // Split area sizing: words per record (header, pending ray ids, depth and
@@ -146,6 +149,17 @@ inline long long trace_split_cycles(int32_t split_kcycles) {
 // 1920x1080: learned trace 109 ms without, 191-194 ms with thresholds
 // 1500-3000; at 960x540 132 vs 135-143 ms; at 3840x2160 145 vs 325 ms).
 inline uint32_t trace_heavy_len(int32_t opt) { return opt > 0 ? (uint32_t)opt : 0u; }
+// st_trace_opts::heavy_split_rank -> rank of the list-length threshold taken
+// on the device (0: no rank rule), and the least list length it splits.
+constexpr int32_t kHeavyRankDefault = 0;
+inline uint32_t trace_heavy_rank(int32_t len_opt, int32_t rank_opt) {
+  if (len_opt > 0 || rank_opt < 0) return 0u;
+  return (uint32_t)(rank_opt > 0 ? rank_opt : kHeavyRankDefault);
+}
+inline uint32_t trace_heavy_min(uint64_t n_entries, uint32_t n_tiles) {
+  const double m = n_tiles ? 4.0 * (double)n_entries / (double)n_tiles : 0.0;
+  return (uint32_t)(m > 1024.0 ? (m < 4.0e9 ? m : 4.0e9) : 1024.0);
+}
 
 constexpr int ST_STEP_RECORD = 15;  // plain stepping that records training data (internal)
 
@@ -166,7 +180,11 @@ int trace_warps_per_cta();
 // Work order of a trace launch: the jobs' n_tiles global tiles sorted by
 // A-buffer list length, longest first (counting sort; equal lengths in any
 // order -- results do not depend on the order tiles are traced in).
-void launch_tile_order(const Job *jobs, int n_jobs, uint32_t n_tiles, uint32_t *order, cudaStream_t s);
+// heavy_thr (optional): receives the early-split threshold, the list length
+// of the heavy_rank-th longest tile but at least heavy_min (0xFFFFFFFF when
+// heavy_rank is 0).
+void launch_tile_order(const Job *jobs, int n_jobs, uint32_t n_tiles, uint32_t *order, cudaStream_t s,
+                       uint32_t heavy_rank = 0, uint32_t heavy_min = 0, uint32_t *heavy_thr = nullptr);
 int trace_ctas_per_sm(const TraceLaunch &L);
 void launch_pruned_view(const DevScene &sc, const uint32_t *act, int n, uint32_t *view, uint32_t *vaddr,
                         int32_t *info, uint32_t *scratch, int stack_cap, int method, cudaStream_t s);

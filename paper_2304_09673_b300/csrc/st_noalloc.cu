@@ -2,7 +2,7 @@
 // allocation.  Its scratch memory lives in one file-scope device array of
 // fixed size that every device loading the library keeps until the process
 // exits.  Layout (byte offsets): [0] work-queue counter, [4] status word,
-// [256] the job record, then the tile order (one word per tile), then for
+// [8] early-split threshold, [256] the job record, then the tile order (one word per tile), then for
 // long tile lists the per-CTA work areas, then as many records of tiles split
 // across CTAs as fit.
 #include <atomic>
@@ -24,6 +24,7 @@ namespace {
 constexpr size_t kScratchBytes = size_t(32) << 20;   // 32 MiB
 constexpr size_t kCounterOff = 0;                     // uint32 work-queue counter
 constexpr size_t kStatusOff = 4;                      // uint32 device status word
+constexpr size_t kHeavyOff = 8;                       // uint32 early-split threshold
 constexpr size_t kJobOff = 256;                       // st::Job record
 constexpr int kMaxDevices = 64;
 
@@ -222,9 +223,13 @@ extern "C" int st_trace_noalloc(st_scene *s, const st_camera *cam, const st_tile
   if (L.split) NA_CK(cudaMemsetAsync(L.split, 0, trace_split_zero_bytes(L.split_cap), st));
   count_launch(), k_put_job<<<1, 32, 0, st>>>(job, job_dev);
   NA_CK(cudaGetLastError());
-  launch_tile_order(job_dev, 1, L.n_items, order, st);
+  const uint32_t heavy_rank = L.split ? trace_heavy_rank(o.heavy_split_len, o.heavy_split_rank) : 0u;
+  uint32_t *heavy_thr = heavy_rank ? reinterpret_cast<uint32_t *>(scratch + kHeavyOff) : nullptr;
+  launch_tile_order(job_dev, 1, L.n_items, order, st, heavy_rank, trace_heavy_min(tl->n_entries, L.n_items),
+                    heavy_thr);
   NA_CK(cudaGetLastError());
   L.order = order;
+  L.heavy_thr = heavy_thr;
   NA_CK(trace_launch(job_dev, 1, L, n_sm, st));
   if (L.status) return trace_status_code(status, st, "st_trace_noalloc");
   return ST_OK;

@@ -1330,14 +1330,16 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         f[0] = f1[0];
         f[1] = 0.f;
       } else {
-        float p[kR][3];
+        // the two slots' points as one pair: paired FP32 instructions
+        const F2 zz = F2(make_float2(z[0], z[1]));
+        F2 p2[1][3];
 #pragma unroll
-        for (int s = 0; s < kR; ++s) {
-          p[s][0] = fma_(z[s], d[s][0], M.cam->o[0]);
-          p[s][1] = fma_(z[s], d[s][1], M.cam->o[1]);
-          p[s][2] = fma_(z[s], d[s][2], M.cam->o[2]);
-        }
-        eval_view_r<kR, float, SmemStack2, kFurther>(view, inf.n_view, src, p, f, stk);
+        for (int k = 0; k < 3; ++k) p2[0][k] = fma_(zz, F2(make_float2(d[0][k], d[1][k])), M.cam->o[k]);
+        F2 f2[1];
+        SmemStackF2 stk2{stk.base};
+        eval_view_r<1, F2, SmemStackF2, kFurther>(view, inf.n_view, src, p2, f2, stk2);
+        f[0] = f2[0].v.x;
+        f[1] = f2[0].v.y;
       }
     }
     float om[kR];
@@ -1359,7 +1361,9 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         x[s][3] = mul_((float)(steps[s] + 1), 1.f / 64.f);
         x[s][4] = feat_prim;
         x[s][5] = feat_len;
-        live |= (ray[s] >= 0 ? 1u : 0u) << s;
+        // a slot whose relaxation is off (after a rejected step) steps with
+        // omega = 1 whatever the network says: no row for it
+        live |= ((ray[s] >= 0 && !((relax_off >> s) & 1u)) ? 1u : 0u) << s;
       }
       __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(wvals);
       mlp_omega_warp(LC.W, x, om, xs, wvals + 64 * 4, live);
@@ -1515,7 +1519,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       // of a split tile ----
       uint32_t gt = 0xFFFFFFFFu, rec = 0;
       int part = 0;
-      if (L.split && L.heavy_len) gt = try_part(L, &rec, &part);
+      if (L.split && (L.heavy_len || L.heavy_thr)) gt = try_part(L, &rec, &part);
       if (gt == 0xFFFFFFFFu && *(volatile uint32_t *)L.item_counter < L.n_items) {
         if (L.split) {
           atomicAdd(&L.split[2], 1u);
@@ -1566,8 +1570,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     // tile's views itself (no replay), and CTAs claim open parts before
     // whole tiles, so the tile's rays are traced by several CTAs from the
     // start instead of one CTA outlasting the frame.
-    const bool heavy = MODE != ST_STEP_RECORD && L.split && L.heavy_len && !part && len >= L.heavy_len &&
-                       nr >= 2 * kSplitMinRays;
+    const uint32_t heavy_at = L.heavy_thr ? *L.heavy_thr : (L.heavy_len ? L.heavy_len : 0xFFFFFFFFu);
+    const bool heavy = MODE != ST_STEP_RECORD && L.split && !part && len >= heavy_at && nr >= 2 * kSplitMinRays;
     if (L.split && !part && !heavy && (nr < 2 * kSplitMinRays || kSplitListBudget / max(len, 1u) < 2)) {
       // Too few rays or too long a list to split: release this tile's count
       // of whole tiles at once, so that CTAs out of work stop polling sooner.
@@ -1842,7 +1846,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
 // One CTA: histogram of list lengths (4096 bins, longer lists share the
 // last), bins scanned from the longest down, tiles scattered.  Heavy tiles
 // then start while every SM is free instead of finishing last.
-__global__ void __launch_bounds__(1024) k_tile_order(const Job *jobs, int n_jobs, uint32_t n_tiles, uint32_t *order) {
+__global__ void __launch_bounds__(1024) k_tile_order(const Job *jobs, int n_jobs, uint32_t n_tiles, uint32_t *order,
+                                                     uint32_t heavy_rank, uint32_t heavy_min, uint32_t *heavy_thr) {
   constexpr int kBins = 4096;
   __shared__ uint32_t cnt[kBins];
   __shared__ uint32_t s_warp[32];
@@ -1890,10 +1895,30 @@ __global__ void __launch_bounds__(1024) k_tile_order(const Job *jobs, int n_jobs
   }
   __syncthreads();
   for (uint32_t g = threadIdx.x; g < n_tiles; g += blockDim.x) order[atomicAdd(&cnt[tile_bin(g)], 1u)] = g;
+  if (heavy_thr) {
+    // Early-split threshold: the list length of the heavy_rank-th longest
+    // tile, at least heavy_min (lists of 4095+ entries share the top bin, in
+    // any order; ties are all heavy).
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t thr = 0xFFFFFFFFu;
+      if (heavy_rank > 0 && n_tiles > 0) {
+        const uint32_t g = order[min(heavy_rank, n_tiles) - 1];
+        const Job &job = jobs[find_job_tile(jobs, n_jobs, g)];
+        const uint32_t t = g - job.tile_base;
+        thr = max(job.tl.offsets[t + 1] - job.tl.offsets[t], heavy_min);
+      }
+      *heavy_thr = thr;
+    }
+  }
 }
 
-void launch_tile_order(const Job *jobs, int n_jobs, uint32_t n_tiles, uint32_t *order, cudaStream_t s) {
-  if (n_tiles) count_launch(), k_tile_order<<<1, 1024, 0, s>>>(jobs, n_jobs, n_tiles, order);
+void launch_tile_order(const Job *jobs, int n_jobs, uint32_t n_tiles, uint32_t *order, cudaStream_t s,
+                       uint32_t heavy_rank, uint32_t heavy_min, uint32_t *heavy_thr) {
+  if (n_tiles)
+    count_launch(), k_tile_order<<<1, 1024, 0, s>>>(jobs, n_jobs, n_tiles, order, heavy_rank, heavy_min, heavy_thr);
+  else if (heavy_thr)
+    cudaMemsetAsync(heavy_thr, 0xFF, sizeof(uint32_t), s);
 }
 
 // ---- inspection kernels: the same view build and evaluator as k_trace ----------

@@ -252,3 +252,30 @@ def test_heavy_split_clustered_long_lists(stlib, cuda, mode):
         assert c1[4] > c0[4], "no tile was split"
     finally:
         stlib.st_scene_destroy(h)
+
+
+@pytest.mark.parametrize("mode", ["plain", "learned"])
+def test_heavy_split_by_rank_same_bytes(stlib, cuda, mode):
+    """The rank rule: the tiles of the few longest lists (threshold taken on
+    the device from the launch's own lists) split before they start; same
+    bytes and per-ray counters as the unsplit trace, and st_trace_noalloc
+    agrees."""
+    import torch
+    kw = _mode_kw(stlib, mode)
+    s = sg.make_scene(3000, 16, 7, clusters=10)
+    cam = sg.default_camera(480, 270)
+    h = stlib.st_scene_create(s)
+    try:
+        t = stlib.st_build_tiles(h, cam, 16)
+        assert t.max_overlap >= 1024
+        base, c0 = _trace(stlib, torch, h, cam, t, stlib.make_opts(split_kcycles=-1, **kw))
+        for fn_noalloc in (False, True):
+            got, c1 = _trace(stlib, torch, h, cam, t,
+                             stlib.make_opts(split_kcycles=NO_LATE_SPLIT, heavy_split_rank=6, **kw),
+                             noalloc=fn_noalloc)
+            for k, name in enumerate(("depth", "normal", "evals", "flags")):
+                assert got[k].tobytes() == base[k].tobytes(), (fn_noalloc, name)
+            assert [c1[i] for i in SAME_COUNTERS] == [c0[i] for i in SAME_COUNTERS], (c0, c1)
+            assert c1[4] > c0[4], "no tile was split"
+    finally:
+        stlib.st_scene_destroy(h)
