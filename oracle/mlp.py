@@ -108,6 +108,47 @@ def forward_bf16(p, X):
     return 1.0 + _sigmoid(o)
 
 
+def grad_bf16(p, X, y, rnd=bf16):
+    """Gradient of ``loss`` as a BF16 tensor-core training step computes it
+    (FP64 here, so only the rounding points differ from ``grad``).  Forward as
+    ``forward_bf16``: inputs, weights and post-ReLU activations rounded by
+    ``rnd``, biases unrounded.  Backward: every signal that enters a matrix
+    product is rounded as well, the layer-2 signal d2 = dout w3 (masked by
+    a2 > 0) before it meets W2 and h1, the layer-1 signal d1 before it meets
+    x; the bias gradients sum each signal before its own rounding (d1 is
+    computed from the rounded d2) and w3's gradient is h2^T dout with the
+    rounded h2.  With ``rnd`` the identity this is
+    ``grad``."""
+    W1, b1, W2, b2, w3, b3 = unpack(p)
+    X = rnd(np.asarray(X, np.float32).reshape(-1, IN))
+    y = np.asarray(y, np.float64)
+    W1, W2, w3 = rnd(W1), rnd(W2), rnd(w3)
+    a1 = X @ W1.T + b1
+    h1 = rnd(np.maximum(a1, 0))
+    a2 = h1 @ W2.T + b2
+    h2 = rnd(np.maximum(a2, 0))
+    o = h2 @ w3 + b3
+    s = _sigmoid(o)
+    err = 1.0 + s - y
+    w = np.where(err > 0, 4.0, 1.0)
+    dout = 2 * w * err * s * (1 - s)
+    gw3 = h2.T @ dout
+    gb3 = dout.sum()
+    d2 = np.outer(dout, w3) * (a2 > 0)
+    d2r = rnd(d2)
+    gW2 = d2r.T @ h1
+    gb2 = d2.sum(0)
+    d1 = (d2r @ W2) * (a1 > 0)
+    gW1 = rnd(d1).T @ X
+    gb1 = d1.sum(0)
+    return np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gw3, [gb3]])
+
+
+def no_rounding(a):
+    """The identity as a rounding function (``grad_bf16`` without rounding)."""
+    return np.asarray(a, np.float64)
+
+
 # Step features and training label, restated from their definitions.
 def step_features(f, f_prev, dz_prev_dist, have_prev, steps, n_prim, list_len, lipschitz=1.45):
     """Features of one sphere-tracing step: 8 f / L, 8 f_prev / L (f when no

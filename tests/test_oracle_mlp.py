@@ -61,3 +61,63 @@ def test_features_definition():
     assert np.allclose(x, [1.6, 3.2, 0.8, 0.5, 0.5, 1.0])
     x = mlp.step_features(0.29, 0.58, 0.1, False, 32, 15, 255)
     assert x[1] == x[0] and x[2] == 0.0
+
+
+def test_mixed_precision_gradient_without_rounding_is_backprop():
+    # grad_bf16 with the identity as rounding must be the backpropagation
+    # gradient, itself pinned by finite differences above
+    rng = np.random.default_rng(3)
+    p = mlp.init_params(2).astype(np.float64) + rng.normal(scale=0.05, size=mlp.N_PARAMS)
+    X = rng.normal(size=(64, 6)).astype(np.float32)
+    y = rng.uniform(1, 2, size=64)
+    g = mlp.grad(p, X, y)
+    gr = mlp.grad_bf16(p, X, y, rnd=mlp.no_rounding)
+    assert np.abs(gr - g).max() <= 1e-12 * np.abs(g).max()
+
+
+def test_mixed_precision_gradient_one_path_network():
+    # One path through the network: W1[0][0] = W2[0][0] = w3[0] = 1, all else
+    # zero.  With x = (x0, 0, ...), x0 > 0: h1 = h2 = o = bf16(x0) and, with
+    # dout = d loss / d o at that o, the rounded signals are d2 = d1 = bf16(dout):
+    #   dW1[0][0] = bf16(dout) bf16(x0), dW2[0][0] = bf16(dout) bf16(x0),
+    #   dw3[0] = dout bf16(x0), db2[0] = db3 = dout, db1[0] = bf16(dout)
+    # (d1 comes from the rounded d2), every other entry zero.
+    W1 = np.zeros((32, 6)); W1[0, 0] = 1.0
+    W2 = np.zeros((32, 32)); W2[0, 0] = 1.0
+    w3 = np.zeros(32); w3[0] = 1.0
+    p = np.concatenate([W1.ravel(), np.zeros(32), W2.ravel(), np.zeros(32), w3, [0.0]])
+    x0, y0 = 1.2345, 1.1
+    X = np.array([[x0, 0, 0, 0, 0, 0]], np.float32)
+    xb = float(mlp.bf16(np.array([x0], np.float32))[0])
+    s = 1 / (1 + np.exp(-xb))
+    err = 1 + s - y0
+    dout = 2 * (4.0 if err > 0 else 1.0) * err * s * (1 - s)
+    db = float(mlp.bf16(np.array([dout], np.float32))[0])
+    assert db != dout    # the case exercises the rounding of the signals
+    g = mlp.grad_bf16(p, X, [y0])
+    want = np.zeros(mlp.N_PARAMS)
+    want[0] = db * xb                  # W1[0][0]
+    want[192] = db                     # b1[0]
+    want[224] = db * xb                # W2[0][0]
+    want[1248] = dout                  # b2[0]
+    want[1280] = dout * xb             # w3[0]
+    want[1312] = dout                  # b3
+    assert np.allclose(g, want, rtol=1e-12, atol=0)
+    # the FP64 gradient of the same network takes x0 and dout unrounded
+    g64 = mlp.grad(p, X, [y0])
+    assert g64[0] != pytest.approx(want[0], rel=1e-6)
+
+
+def test_mixed_precision_gradient_within_bf16_error():
+    # Rounding to 8 significant bits moves each product by at most ~2^-8
+    # relative: the mixed-precision gradient stays within a few percent of the
+    # largest entry, and it does differ (the rounding is applied)
+    rng = np.random.default_rng(4)
+    p = mlp.init_params(5)
+    X = np.stack([rng.uniform(0, 3, 500), rng.uniform(0, 3, 500), rng.uniform(0, 2, 500),
+                  rng.uniform(0, 2, 500), rng.uniform(0, 1, 500), rng.uniform(0, 1.2, 500)], 1).astype(np.float32)
+    y = rng.uniform(1, 2, 500)
+    g = mlp.grad(p, X, y)
+    gb = mlp.grad_bf16(p, X, y)
+    d = np.abs(gb - g).max() / np.abs(g).max()
+    assert 1e-5 < d < 3e-2
