@@ -418,6 +418,12 @@ int st_render_batch(st_scene *const *scenes, const st_camera *cams, int n, const
  * loss_sum (device float[1]) the value, of sum_i w_i (omega_i - y_i)^2 over
  * records i (x: device float[n][6], y: device float[n]), w_i = 4 when
  * omega_i > y_i else 1.  FP32.
+ * st_mlp_grad_bf16: the same sums with the products on BF16 tensor cores
+ * (FP32 accumulation; params stay FP32): inputs, weights and post-ReLU
+ * activations rounded to BF16 as in the tracer's inference, and the
+ * backpropagated signals rounded to BF16 where they enter a product (the
+ * layer-2 signal dout x w3 before it meets W2 and h1, the layer-1 signal
+ * before it meets x); bias gradients sum the signals before that rounding.
  * st_mlp_adam: one Adam step on params with grad x grad_scale (bias
  * corrected for step >= 1); m, v: device float[1313] moments.
  * st_mlp_pack: host float[1313] -> host buffer of st_mlp_pack_size() bytes
@@ -433,6 +439,8 @@ int st_mlp_param_count(void);
 int st_mlp_pack(const float *params, void *packed);
 int st_mlp_grad(const float *params, const float *x, const float *y, int n, float *grad,
                 float *loss_sum, void *stream);
+int st_mlp_grad_bf16(const float *params, const float *x, const float *y, int n, float *grad,
+                     float *loss_sum, void *stream);
 int st_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr,
                 float beta1, float beta2, float eps, float grad_scale, void *stream);
 int st_mlp_infer(const void *packed, const float *x, int n, float *omega, void *stream);

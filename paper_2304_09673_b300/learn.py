@@ -69,8 +69,11 @@ def record(scenes, cam, opts, ray_stride: int = 331, cap_per_scene: int = 200000
 
 
 def train(records: np.ndarray, epochs: int = 12, batch: int = 65536, lr: float = 3e-3, seed: int = 0,
-          val_frac: float = 0.05, log=print):
-    """Adam on the asymmetric squared error; returns (params, history)."""
+          val_frac: float = 0.05, log=print, tensor_cores: bool = True):
+    """Adam on the asymmetric squared error; returns (params, history).
+    Gradients from the BF16 tensor-core kernel (st_mlp_grad_bf16) unless
+    tensor_cores is False (the FP32 kernel, st_mlp_grad)."""
+    grad_fn = st.st_mlp_grad_bf16 if tensor_cores else st.st_mlp_grad
     import torch
     dev = torch.device("cuda")
     rng = np.random.default_rng(seed)
@@ -100,14 +103,14 @@ def train(records: np.ndarray, epochs: int = 12, batch: int = 65536, lr: float =
             yb = yt[idx].contiguous()
             grad.zero_()
             loss.zero_()
-            st.st_mlp_grad(params, xb, yb, grad, loss)
+            grad_fn(params, xb, yb, grad, loss)
             step += 1
             cur_lr = lr * 0.5 * (1 + math.cos(math.pi * step / total_steps))
             st.st_mlp_adam(params, grad, m, v, step, cur_lr, grad_scale=1.0 / len(idx))
             tl += float(loss.item()) / len(idx)
         grad.zero_()
         loss.zero_()
-        st.st_mlp_grad(params, Xv, yv, grad, loss)
+        grad_fn(params, Xv, yv, grad, loss)
         vl = float(loss.item()) / Xv.shape[0]
         hist.append(dict(epoch=ep, train_loss=tl / n_batches, val_loss=vl))
         log(f"epoch {ep}: train {tl / n_batches:.5f} val {vl:.5f}")

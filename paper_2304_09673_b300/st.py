@@ -91,6 +91,7 @@ _lib.st_trace_record.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), 
 _lib.st_mlp_pack_size.restype = C.c_size_t
 _lib.st_mlp_pack.argtypes = [_P, _P]
 _lib.st_mlp_grad.argtypes = [_P, _P, _P, C.c_int, _P, _P, _P]
+_lib.st_mlp_grad_bf16.argtypes = [_P, _P, _P, C.c_int, _P, _P, _P]
 _lib.st_mlp_adam.argtypes = [_P, _P, _P, _P, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, _P]
 _lib.st_mlp_infer.argtypes = [_P, _P, C.c_int, _P, _P]
 _lib.st_prep_tree.argtypes = [C.POINTER(st_scene_desc), _P, _P, _P, _P]
@@ -112,11 +113,11 @@ _lib.st_trace_dexels.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), 
 _lib.st_eval_sparse.argtypes = [_P, _P, C.c_int, _P, C.c_int, C.c_int, _P, _P, _P]
 
 EXPORTED = ("st_scene_create", "st_scene_update_prims", "st_scene_addresses", "st_scene_info", "st_scene_destroy",
-            "st_build_tiles", "st_trace", "st_tiles_copy", "st_pruned_view", "st_pruned_view_alg1", "st_eval_pruned", "st_prep_tree", "st_last_error",
-            "st_version", "st_kernel_launches", "st_device_allocations", "st_trace_noalloc",
-            "st_trace_noalloc_scratch_bytes", "st_trace_noalloc_last_layout",
+            "st_build_tiles", "st_trace", "st_tiles_copy", "st_pruned_view", "st_pruned_view_alg1", "st_eval_pruned",
+            "st_prep_tree", "st_last_error", "st_version", "st_kernel_launches", "st_device_allocations",
+            "st_trace_noalloc", "st_trace_noalloc_scratch_bytes", "st_trace_noalloc_last_layout",
             "st_trace_record", "st_mlp_pack_size", "st_mlp_param_count", "st_mlp_pack", "st_mlp_grad",
-            "st_mlp_adam", "st_mlp_infer", "st_tune_key", "st_tune_load", "st_tune_store", "st_autotune",
+            "st_mlp_grad_bf16", "st_mlp_adam", "st_mlp_infer", "st_tune_key", "st_tune_load", "st_tune_store", "st_autotune",
             "st_batch_create", "st_batch_render", "st_batch_tiles", "st_batch_graph_kernels", "st_batch_destroy",
             "st_render_batch", "st_build_dexels", "st_trace_dexels", "st_eval_sparse")
 
@@ -283,6 +284,11 @@ def st_mlp_pack(params) -> np.ndarray:
 def st_mlp_grad(params, x, y, grad, loss_sum, stream=None) -> None:
     _check(_lib.st_mlp_grad(_ptr(params), _ptr(x), _ptr(y), int(y.numel()), _ptr(grad), _ptr(loss_sum),
                             _stream(stream)), "st_mlp_grad")
+
+
+def st_mlp_grad_bf16(params, x, y, grad, loss_sum, stream=None) -> None:
+    _check(_lib.st_mlp_grad_bf16(_ptr(params), _ptr(x), _ptr(y), int(y.numel()), _ptr(grad), _ptr(loss_sum),
+                                 _stream(stream)), "st_mlp_grad_bf16")
 
 
 def st_mlp_adam(params, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0,

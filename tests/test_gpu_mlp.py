@@ -38,6 +38,68 @@ def test_grad_matches_fp64(stlib, cuda):
     assert np.abs(got - ref_g).max() <= 1e-3 * scale
 
 
+@pytest.mark.parametrize("n", [1, 17, 3000, 70001])
+def test_tensor_core_grad_matches_mixed_precision_reference(stlib, cuda, n):
+    """st_mlp_grad_bf16 against the FP64 gradient taken at the same BF16
+    rounding points (tight), and against the unrounded FP64 gradient (the
+    BF16 error); ragged record counts leave partial 16-record tiles."""
+    import torch
+    rng = np.random.default_rng(n)
+    p = omlp.init_params(3) + rng.normal(scale=0.05, size=stlib.MLP_PARAMS).astype(np.float32)
+    X, y = _records(rng, n)
+    g = torch.zeros(stlib.MLP_PARAMS, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    stlib.st_mlp_grad_bf16(torch.tensor(p, device="cuda"), torch.tensor(X, device="cuda"),
+                           torch.tensor(y, device="cuda"), g, loss)
+    torch.cuda.synchronize()
+    got = g.cpu().numpy().astype(np.float64)
+    ref = omlp.grad_bf16(p, X, y)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-3 * scale, np.abs(got - ref).max() / scale
+    ref64 = omlp.grad(p, X, y)
+    assert np.abs(got - ref64).max() <= 3e-2 * np.abs(ref64).max()
+    # the loss is the BF16 network's
+    om = omlp.forward_bf16(p, X)
+    err = om - y.astype(np.float64)
+    assert float(loss.item()) == pytest.approx(np.sum(np.where(err > 0, 4, 1) * err * err), rel=1e-4)
+
+
+def test_tensor_core_grad_empty_and_accumulates(stlib, cuda):
+    import torch
+    rng = np.random.default_rng(9)
+    p = torch.tensor(omlp.init_params(1), device="cuda")
+    g = torch.ones(stlib.MLP_PARAMS, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    empty = torch.zeros(0, device="cuda")
+    stlib.st_mlp_grad_bf16(p, empty, empty, g, loss)
+    torch.cuda.synchronize()
+    assert torch.all(g == 1) and float(loss.item()) == 0.0
+    X, y = _records(rng, 500)
+    g.zero_()
+    Xd, yd = torch.tensor(X, device="cuda"), torch.tensor(y, device="cuda")
+    stlib.st_mlp_grad_bf16(p, Xd, yd, g, loss)
+    once = g.clone()
+    stlib.st_mlp_grad_bf16(p, Xd, yd, g, loss)   # adds to grad
+    torch.cuda.synchronize()
+    assert torch.allclose(g, 2 * once, rtol=1e-5, atol=1e-6)
+
+
+def test_tensor_core_training_lowers_loss(stlib, cuda):
+    """A few Adam steps on tensor-core gradients reduce the loss on labels
+    drawn from a fixed smooth function of the features."""
+    import torch
+    from paper_2304_09673_b300 import learn
+    rng = np.random.default_rng(12)
+    X, _ = _records(rng, 40000)
+    y = (1.0 + 1.0 / (1.0 + np.exp(-(X[:, 0] - X[:, 1])))).astype(np.float32)
+    rec = np.zeros((len(X), 8), np.float32)
+    rec[:, :6] = X
+    rec[:, 6] = y
+    params, hist = learn.train(rec, epochs=8, batch=2048, lr=3e-3, log=lambda *a: None)
+    assert hist[-1]["val_loss"] < 0.7 * hist[0]["val_loss"], hist
+    assert np.all(np.isfinite(params))
+
+
 def test_adam_step(stlib, cuda):
     import torch
     p0 = omlp.init_params(4)
