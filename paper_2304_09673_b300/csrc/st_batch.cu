@@ -372,6 +372,7 @@ int plan(st_batch *b) {
   L.mlp = L.step_mode == ST_STEP_LEARNED ? b->opts.mlp : nullptr;
   if (L.step_mode == ST_STEP_LEARNED && L.stack_slots < 10) L.stack_slots = 10;
   L.work_in_smem = trace_smem_per_warp(L) * 16 > 200 * 1024 ? 0 : 1;
+  L.staged = trace_staged(L);
   if (!L.work_in_smem) {
     // one work area per CTA of the persistent grid (indexed by blockIdx.x)
     const int per_sm = trace_ctas_per_sm(L);

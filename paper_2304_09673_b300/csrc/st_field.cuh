@@ -425,6 +425,69 @@ __device__ __forceinline__ uint32_t node_flops(uint32_t code) {
   }
 }
 
+// One node of Algorithm 3 for R points: a primitive pushes the running value
+// and evaluates itself, an operator pops its left operand and combines; q is
+// the node's record (unused by nodes without one).
+template <int R, class T, class Stk, bool kFurther>
+__device__ __forceinline__ void eval_node(uint32_t code, const float4 *q, const T (&p)[R][3], T (&acc)[R], Stk &stk,
+                                          int &sp) {
+  switch (code) {
+    case V_SPHERE: {
+      const float4 a = ldrec(q);
+      stk.push(sp++, acc);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = sd_sphere<T>(a, p[r]);
+      break;
+    }
+    case V_RBOX: {
+      const float4 a0 = ldrec(q), a1 = ldrec(q + 1), a2 = ldrec(q + 2), a3 = ldrec(q + 3);
+      stk.push(sp++, acc);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = sd_rbox<T>(a0, a1, a2, a3, p[r]);
+      break;
+    }
+    case V_CAPSULE: {
+      const float4 a0 = ldrec(q), a2 = ldrec(q + 2);
+      stk.push(sp++, acc);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = sd_capsule<T>(a0, a2, p[r]);
+      break;
+    }
+    case V_UNION: case V_INTER: case V_DIFF: {
+      const float4 c = ldrec(q);
+      T l[R];
+      stk.pop(--sp, l);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = op_compact_any<T>(code, c, l[r], acc[r]);
+      break;
+    }
+    case V_SUNION: case V_SINTER: case V_SDIFF: {
+      T l[R];
+      stk.pop(--sp, l);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = op_sharp_any<T>(code, l[r], acc[r]);
+      break;
+    }
+    case V_INF: {
+      --sp;
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = T(INFINITY);
+      break;
+    }
+    case V_RIGHT: --sp; break;
+    case V_LEFT: {
+      stk.pop(--sp, acc);
+      break;
+    }
+    default: {   // the further primitive families (codes 12..16)
+      stk.push(sp++, acc);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = kFurther ? further_eval<T>(code, q, p[r]) : T(INFINITY);
+      break;
+    }
+  }
+}
+
 // Algorithm 3 for R independent evaluation points per thread, sharing one
 // decode and one record load per node.  The top of each stack lives in
 // acc[r]; deeper entries in `stk` (one slot holds the R values).  The first
@@ -445,61 +508,7 @@ __device__ __forceinline__ void eval_view_r(const uint32_t *view, int n_view, co
     const uint32_t code = w >> kViewCodeShift;
     const float4 *q = rec_ptr(src, w);
     if (i + 1 < n_view) w = view[i + 1];
-    switch (code) {
-      case V_SPHERE: {
-        const float4 a = ldrec(q);
-        stk.push(sp++, acc);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = sd_sphere<T>(a, p[r]);
-        break;
-      }
-      case V_RBOX: {
-        const float4 a0 = ldrec(q), a1 = ldrec(q + 1), a2 = ldrec(q + 2), a3 = ldrec(q + 3);
-        stk.push(sp++, acc);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = sd_rbox<T>(a0, a1, a2, a3, p[r]);
-        break;
-      }
-      case V_CAPSULE: {
-        const float4 a0 = ldrec(q), a2 = ldrec(q + 2);
-        stk.push(sp++, acc);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = sd_capsule<T>(a0, a2, p[r]);
-        break;
-      }
-      case V_UNION: case V_INTER: case V_DIFF: {
-        const float4 c = ldrec(q);
-        T l[R];
-        stk.pop(--sp, l);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = op_compact_any<T>(code, c, l[r], acc[r]);
-        break;
-      }
-      case V_SUNION: case V_SINTER: case V_SDIFF: {
-        T l[R];
-        stk.pop(--sp, l);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = op_sharp_any<T>(code, l[r], acc[r]);
-        break;
-      }
-      case V_INF: {
-        --sp;
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = T(INFINITY);
-        break;
-      }
-      case V_RIGHT: --sp; break;
-      case V_LEFT: {
-        stk.pop(--sp, acc);
-        break;
-      }
-      default: {   // the further primitive families (codes 12..16)
-        stk.push(sp++, acc);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = kFurther ? further_eval<T>(code, q, p[r]) : T(INFINITY);
-        break;
-      }
-    }
+    eval_node<R, T, Stk, kFurther>(code, q, p, acc, stk, sp);
   }
 }
 

@@ -83,6 +83,7 @@ struct TraceLaunch {
   int32_t view_cap;        // 2 * act_cap - 1
   int32_t stack_slots;     // evaluation stack slots per lane
   int32_t work_in_smem;    // 1: active set + view in shared memory
+  int32_t staged;          // 1: views evaluated in staged chunks (trace_staged)
   int32_t dc_words;        // shared parameter cache per view buffer (float4 words)
   uint32_t *g_work;        // global per-CTA work areas (when not in shared
                            // memory), one per CTA of the persistent grid,
@@ -148,6 +149,13 @@ inline long long trace_split_cycles(int32_t split_kcycles) {
 // splitting the longest lists early was slower (measured on B300 at
 // 1920x1080: learned trace 109 ms without, 191-194 ms with thresholds
 // 1500-3000; at 960x540 132 vs 135-143 ms; at 3840x2160 145 vs 325 ms).
+// Views evaluated in staged chunks (shared-memory stages filled by
+// asynchronous copies): launches whose views live in global memory and can
+// outgrow the shared parameter cache.  Short views stay on the plain
+// interpreter, for which the view words' loads hit L1 (measured on B300:
+// staging costs 4-12 % on 1,024 primitives at 1920x1080 and saves ~20 % on
+// 10k clustered primitives).
+inline int32_t trace_staged(const TraceLaunch &L) { return !L.work_in_smem && L.view_cap > 2048 ? 1 : 0; }
 inline uint32_t trace_heavy_len(int32_t opt) { return opt > 0 ? (uint32_t)opt : 0u; }
 // st_trace_opts::heavy_split_rank -> rank of the list-length threshold taken
 // on the device (0: no rank rule), and the least list length it splits.

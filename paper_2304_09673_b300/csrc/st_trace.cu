@@ -40,6 +40,8 @@ namespace st {
 
 constexpr int kWarps = 4;   // warps per CTA; a CTA traces one tile at a time
 constexpr int kFurtherBit = 64;   // instance bit: the interpreter evaluates the further families
+constexpr int kStagedBit = 128;   // instance bit: views in global memory, evaluated in staged chunks
+constexpr int kStageWords = 64;   // float4 record words of a warp's stage buffer (staged instances)
 constexpr int kTileStatWords = 24;   // words per tile of the optional diagnostics
 constexpr int kR = 2;       // rays per lane (shared node decode, two evaluation chains)
 
@@ -63,7 +65,8 @@ __host__ __device__ inline size_t smem_fixed_bytes(const TraceLaunch &L) {
   return align16(r * 4) + align16(r * 4) + 2 * align16(r * 2) + (size_t)kWarps * align16(r * 2) +
          align16(r * 16) + align16(r * 8) + align16(r * 8) +
          (size_t)kWarps * align16((size_t)L.stack_slots * 32 * 8) + align16(bstk_words(L) * 4) +
-         2 * (size_t)L.dc_words * 16 + (L.mlp ? kMlpPackBytes : 0);
+         2 * (size_t)L.dc_words * 16 + (L.mlp ? kMlpPackBytes : 0) +
+         (L.staged ? (size_t)kWarps * kStageWords * 16 : 0);
 }
 constexpr int kMaxLevels = 64;   // operator levels of a view usable by the tail mode
 
@@ -107,6 +110,7 @@ struct CtaWork {
   uint32_t *view[2];
   float4 *dc[2];       // shared parameter cache of each view (the paper's D_cache)
   unsigned char *mlp;  // packed MLP weights (learned step) or null
+  float4 *stage;       // [kWarps][kStageWords] record stages (views in global memory) or null
   uint2 *ops[2];       // operators of each view sorted by level: (self | left << 16, right)
   int *lvl_off[2];     // [kMaxLevels + 1] level offsets into ops
   uint2 *sort_tmp;     // view build: level-sort scratch [act_cap]
@@ -129,6 +133,8 @@ __device__ CtaWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork
   w.dc[1] = (float4 *)p; p += (size_t)L.dc_words * 16;
   w.mlp = nullptr;
   if (L.mlp) { w.mlp = p; p += kMlpPackBytes; }
+  w.stage = nullptr;
+  if (L.staged) { w.stage = (float4 *)p; p += (size_t)kWarps * kStageWords * 16; }
   unsigned char *q = L.work_in_smem ? p : (unsigned char *)gwork;
   const size_t a = align16((size_t)L.act_cap * 4);
   w.act[0] = (uint32_t *)q; q += a;
@@ -497,6 +503,61 @@ __device__ __forceinline__ int code_words(uint32_t code) {
     case V_QUADRIC: return 5;
     case V_UNION: case V_INTER: case V_DIFF: return 1;
     default: return 0;
+  }
+}
+
+// ---- staged evaluation of views held in global memory ------------------------------
+// When a launch's views do not fit in shared memory, reading a view word and
+// then its node's record from L2 costs two dependent memory latencies per
+// node, which the interpreter's one-node-ahead load of the next word cannot
+// hide.  The staged form has the warp fetch the next chunk of up to 32 nodes
+// at once: one coalesced load of their view words (one per lane), then
+// asynchronous copies (cp.async, 16 bytes each, all lanes at once) of the
+// record words of the nodes whose records are not in the shared parameter
+// cache, into the warp's shared stage buffer; the chunk is then evaluated from
+// shared memory.  One round of latency per chunk instead of one per node.
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int R, class T, class Stk, bool kFurther>
+__device__ __forceinline__ void eval_view_staged(const uint32_t *view, int n_view, const RecSrc &src,
+                                                 const T (&p)[R][3], T (&acc)[R], Stk &stk, float4 *stage) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = T(0.f);
+  int sp = 0;
+  // staged records are read through the "global" side of the record source
+  const RecSrc ss{stage, src.dc};
+  for (int i0 = 0; i0 < n_view;) {
+    const int i = i0 + lane;
+    uint32_t w = i < n_view ? view[i] : 0u;
+    const int nw = (w & kViewGlobal) ? code_words(w >> kViewCodeShift) : 0;
+    int x = nw;   // inclusive prefix sum of the words to stage
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    const bool fits = x <= kStageWords;   // a prefix of the lanes (x never decreases)
+    const int nb = min(n_view - i0, __popc(__ballot_sync(0xFFFFFFFFu, fits)));
+    if (fits && nw > 0) {
+      const int off = x - nw;
+      const float4 *g = src.rec + (w & kViewOffMask);
+      for (int k = 0; k < nw; ++k) cp_async16(stage + off + k, g + k);
+      w = (w & ~kViewOffMask) | (uint32_t)off;
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    for (int j = 0; j < nb; ++j) {
+      const uint32_t wj = __shfl_sync(0xFFFFFFFFu, w, j);
+      eval_node<R, T, Stk, kFurther>(wj >> kViewCodeShift, rec_ptr(ss, wj), p, acc, stk, sp);
+    }
+    __syncwarp();   // the next chunk overwrites the stage
+    i0 += nb;
   }
 }
 
@@ -964,9 +1025,10 @@ struct LearnCtx {      // learned step / recording context of a subfrustum
   unsigned long long *diag;   // tile diagnostics (shared, null when off): lockstep
                               // iterations, live slots over them, tail evaluations,
                               // refinement passes, live lanes over them
+  float4 *stage;              // this warp's record stage (staged instances)
 };
 
-template <int MODE, bool kFurther>
+template <int MODE, bool kFurther, bool kStaged>
 __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &C, const RecSrc &src, const SubInfo &inf,
                               const uint32_t *view, const uint2 *ops, const int *lvl_off, const uint16_t *alive_in,
                               int n_in, int *q_head, uint16_t *alive_out, int *n_out, uint16_t *hits, int &n_hits,
@@ -1326,7 +1388,10 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
                            fma_(z[0], d[0][2], M.cam->o[2])}};
         float f1[1];
         SmemStack1 stk1{stk.base};
-        eval_view_r<1, float, SmemStack1, kFurther>(view, inf.n_view, src, p1, f1, stk1);
+        if (kStaged)
+          eval_view_staged<1, float, SmemStack1, kFurther>(view, inf.n_view, src, p1, f1, stk1, LC.stage);
+        else
+          eval_view_r<1, float, SmemStack1, kFurther>(view, inf.n_view, src, p1, f1, stk1);
         f[0] = f1[0];
         f[1] = 0.f;
       } else {
@@ -1337,7 +1402,10 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         for (int k = 0; k < 3; ++k) p2[0][k] = fma_(zz, F2(make_float2(d[0][k], d[1][k])), M.cam->o[k]);
         F2 f2[1];
         SmemStackF2 stk2{stk.base};
-        eval_view_r<1, F2, SmemStackF2, kFurther>(view, inf.n_view, src, p2, f2, stk2);
+        if (kStaged)
+          eval_view_staged<1, F2, SmemStackF2, kFurther>(view, inf.n_view, src, p2, f2, stk2, LC.stage);
+        else
+          eval_view_r<1, F2, SmemStackF2, kFurther>(view, inf.n_view, src, p2, f2, stk2);
         f[0] = f2[0].v.x;
         f[1] = f2[0].v.y;
       }
@@ -1480,8 +1548,9 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
 template <int INST>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
-  constexpr int MODE = INST & ~kFurtherBit;
+  constexpr int MODE = INST & ~(kFurtherBit | kStagedBit);
   constexpr bool kFurther = (INST & kFurtherBit) != 0;
+  constexpr bool kStaged = (INST & kStagedBit) != 0;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_item, s_rec;
   __shared__ int s_part;
@@ -1503,6 +1572,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   LC.list_len = 0;
   LC.diag = L.tile_stats ? s_diag : nullptr;
   if (MODE == ST_STEP_LEARNED) LC.W = load_mlp(L.mlp, C.mlp);
+  LC.stage = C.stage ? C.stage + (size_t)warp * kStageWords : nullptr;
   uint16_t *my_hits = C.hits + (size_t)warp * L.max_tile_rays;
 
   uint64_t c_steps = 0, c_prim = 0, c_op = 0, c_flops = 0, c_sub = 0, c_fin = 0, c_rej = 0;
@@ -1727,7 +1797,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         const long long t0 = clock64();
         int n_hits = 0;
         const RecSrc src{sc.rec, pick(C.dc, k & 1)};
-        const uint32_t ls = march_sub<MODE, kFurther>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
+        const uint32_t ls = march_sub<MODE, kFurther, kStaged>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
                                       n_pending, &s_qhead[rd], alive_out, &s_nctr[wr], my_hits, n_hits, stk_lane,
                                       wvals, 2 * L.stack_slots * 32, c_rej, LC, &s_tqt[rd], &s_tqh[rd], &s_ndone[rd],
                                       &s_nidle[rd], g_sub, c_err);
@@ -2002,9 +2072,12 @@ void launch_eval_view(const DevScene &sc, const uint32_t *view, const int32_t *i
 // trace 4-5 % faster).
 template <class F>
 static auto with_instance(const TraceLaunch &L, F &&f) {
-#define ST_INST(M)                                                                     \
+#define ST_INST1(M)                                                                    \
   return L.further ? f(std::integral_constant<int, (M) | kFurtherBit>{})               \
                    : f(std::integral_constant<int, (M)>{})
+#define ST_INST(M)                          \
+  if (!L.staged) { ST_INST1(M); }          \
+  ST_INST1((M) | kStagedBit)
   switch (L.step_mode) {
     case ST_STEP_OVERRELAX: ST_INST(ST_STEP_OVERRELAX);
     case ST_STEP_CROSSING: ST_INST(ST_STEP_CROSSING);
@@ -2013,6 +2086,7 @@ static auto with_instance(const TraceLaunch &L, F &&f) {
     default: ST_INST(ST_STEP_PLAIN);
   }
 #undef ST_INST
+#undef ST_INST1
 }
 
 template <int MODE>
