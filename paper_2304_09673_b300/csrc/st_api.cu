@@ -130,7 +130,7 @@ static DevScene dev_scene(const st_scene *s) {
 }
 
 bool scene_has_stri(const st_scene *s) { return s->prep.has_stri; }
-bool scene_has_further(const st_scene *s) { return s->prep.has_further; }
+int scene_further_level(const st_scene *s) { return s->prep.further_level(); }
 
 // Read-only facts of a scene for entry points defined in other files.
 void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, double *extent, int *n_sm) {
@@ -453,7 +453,7 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
   L.counters = counters;
   L.tile_stats = o.tile_stats;
   L.step_mode = tp.step_mode;
-  L.further = s->prep.has_further ? 1 : 0;
+  L.further = s->prep.further_level();
   L.mlp = tp.step_mode == ST_STEP_LEARNED ? o.mlp : nullptr;
   L.records = records;
   L.rec_cap = rec_cap;

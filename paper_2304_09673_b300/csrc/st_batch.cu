@@ -24,7 +24,7 @@
 namespace st {
 void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, double *extent, int *n_sm);
 bool scene_has_stri(const st_scene *s);
-bool scene_has_further(const st_scene *s);
+int scene_further_level(const st_scene *s);
 TraceParams make_trace_params(const st_trace_opts &o, double diameter, double extent);
 }  // namespace st
 
@@ -234,7 +234,7 @@ struct st_batch {
   uint32_t pair_cap = 0, overlap_cap = 0;
   uint32_t longest_seen = 0, entries_seen = 0;   // sizing pass: longest list, entry total
   bool has_stri = false;   // a scene holds rounded triangles (second culling launch)
-  bool has_further = false;   // a scene holds primitives beyond the three basic families
+  int further = 0;   // kernel instance tier: the largest scene_further_level of the scenes
   TraceLaunch L;
   int grid = 0;
   size_t smem = 0;
@@ -271,7 +271,7 @@ int plan(st_batch *b) {
   const int n = (int)b->scenes.size();
   b->jobs.assign(n, Job{});
   b->has_stri = false;
-  b->has_further = false;
+  b->further = 0;
   uint32_t prim_base = 0, tile_base = 0;
   int max_tile = 8, stack_slots = 2;
   for (int i = 0; i < n; ++i) {
@@ -281,7 +281,7 @@ int plan(st_batch *b) {
     double diam = 0, ext = 0;
     scene_facts(b->scenes[i], &j.sc, &sd, &diam, &ext, &nsm);
     if (scene_has_stri(b->scenes[i])) b->has_stri = true;
-    if (scene_has_further(b->scenes[i])) b->has_further = true;
+    b->further = std::max(b->further, scene_further_level(b->scenes[i]));
     b->n_sm = nsm;
     camera_basis(b->cams[i], j.cam);
     const int T = b->tune[i].tile;
@@ -368,7 +368,7 @@ int plan(st_batch *b) {
   L.status = b->status.p;
   L.order = b->order.p;
   L.step_mode = b->opts.step_mode;
-  L.further = b->has_further ? 1 : 0;
+  L.further = b->further;
   L.mlp = L.step_mode == ST_STEP_LEARNED ? b->opts.mlp : nullptr;
   if (L.step_mode == ST_STEP_LEARNED && L.stack_slots < 10) L.stack_slots = 10;
   L.work_in_smem = trace_smem_per_warp(L) * 16 > 200 * 1024 ? 0 : 1;

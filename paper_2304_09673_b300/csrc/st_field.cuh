@@ -7,6 +7,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "st_internal.h"
 
 namespace st {
@@ -336,30 +338,35 @@ __device__ __forceinline__ T sd_quadric(const float4 *q, const T p[3]) {
 // The further families out of line: one copy per value type instead of one
 // per interpreter instantiation and call site, so scenes without them keep
 // the interpreter's code (and instruction-fetch footprint) of the three
-// basic families.
-template <class T>
+// basic families.  kAll = false: the copy without the rounded triangle and
+// the bounded quadric, for scenes whose further primitives are tori,
+// sphere-cones and ellipsoids only (the larger body costs such scenes ~10 %
+// of tracing time through the calling kernel's registers).
+template <class T, bool kAll = true>
 __device__ __noinline__ T sd_further(uint32_t code, const float4 *q, T px, T py, T pz) {
   const T p[3] = {px, py, pz};
   if (code == V_TORUS) return sd_torus<T>(ldrec(q), ldrec(q + 1), p);
   if (code == V_SCONE) return sd_scone<T>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p);
-  if (code == V_RTRI) return sd_rtri<T>(q, p);
-  if (code == V_QUADRIC) return sd_quadric<T>(q, p);
+  if (kAll) {
+    if (code == V_RTRI) return sd_rtri<T>(q, p);
+    if (code == V_QUADRIC) return sd_quadric<T>(q, p);
+  }
   return sd_ellipsoid<T>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), ldrec(q + 4), p);
 }
 
 // The further families for a pair of points: the scalar function per
 // component (out of line, as for one point).
+template <bool kAll>
 __device__ __forceinline__ F2 further_pair(uint32_t code, const float4 *q, const F2 p[3]) {
-  return F2(make_float2(sd_further<float>(code, q, p[0].v.x, p[1].v.x, p[2].v.x),
-                        sd_further<float>(code, q, p[0].v.y, p[1].v.y, p[2].v.y)));
+  return F2(make_float2(sd_further<float, kAll>(code, q, p[0].v.x, p[1].v.x, p[2].v.x),
+                        sd_further<float, kAll>(code, q, p[0].v.y, p[1].v.y, p[2].v.y)));
 }
-template <class T>
+template <class T, bool kAll>
 __device__ __forceinline__ T further_eval(uint32_t code, const float4 *q, const T p[3]) {
-  return sd_further<T>(code, q, p[0], p[1], p[2]);
-}
-template <>
-__device__ __forceinline__ F2 further_eval<F2>(uint32_t code, const float4 *q, const F2 p[3]) {
-  return further_pair(code, q, p);
+  if constexpr (std::is_same<T, F2>::value)
+    return further_pair<kAll>(code, q, p);
+  else
+    return sd_further<T, kAll>(code, q, p[0], p[1], p[2]);
 }
 
 // ---- compact smooth operators G_op (Sec. 5) -------------------------------------
@@ -428,7 +435,7 @@ __device__ __forceinline__ uint32_t node_flops(uint32_t code) {
 // One node of Algorithm 3 for R points: a primitive pushes the running value
 // and evaluates itself, an operator pops its left operand and combines; q is
 // the node's record (unused by nodes without one).
-template <int R, class T, class Stk, bool kFurther>
+template <int R, class T, class Stk, int kFam>
 __device__ __forceinline__ void eval_node(uint32_t code, const float4 *q, const T (&p)[R][3], T (&acc)[R], Stk &stk,
                                           int &sp) {
   switch (code) {
@@ -482,7 +489,7 @@ __device__ __forceinline__ void eval_node(uint32_t code, const float4 *q, const 
     default: {   // the further primitive families (codes 12..16)
       stk.push(sp++, acc);
 #pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = kFurther ? further_eval<T>(code, q, p[r]) : T(INFINITY);
+      for (int r = 0; r < R; ++r) acc[r] = kFam ? further_eval<T, kFam == 2>(code, q, p[r]) : T(INFINITY);
       break;
     }
   }
@@ -493,11 +500,12 @@ __device__ __forceinline__ void eval_node(uint32_t code, const float4 *q, const 
 // acc[r]; deeper entries in `stk` (one slot holds the R values).  The first
 // primitive pushes an unused value, so `stk` needs one slot more than the
 // live depth.  T is float (tracing) or a dual number (refinement).
-// kFurther = false: a lean instance for views of spheres, rounded boxes and
-// capsules only (the further families are never evaluated; a view holding
-// one gets +inf there -- the host picks the lean instance only for scenes
-// without them).
-template <int R, class T, class Stk, bool kFurther = true>
+// kFam, the primitive families the instance evaluates: 0 a lean instance for
+// views of spheres, rounded boxes and capsules only (the further families are
+// never evaluated; a view holding one gets +inf there -- the host picks the
+// lean instance only for scenes without them), 1 also tori, sphere-cones and
+// ellipsoids, 2 all eight families.
+template <int R, class T, class Stk, int kFam = 2>
 __device__ __forceinline__ void eval_view_r(const uint32_t *view, int n_view, const RecSrc &src,
                                             const T (&p)[R][3], T (&acc)[R], Stk &stk) {
 #pragma unroll
@@ -508,7 +516,7 @@ __device__ __forceinline__ void eval_view_r(const uint32_t *view, int n_view, co
     const uint32_t code = w >> kViewCodeShift;
     const float4 *q = rec_ptr(src, w);
     if (i + 1 < n_view) w = view[i + 1];
-    eval_node<R, T, Stk, kFurther>(code, q, p, acc, stk, sp);
+    eval_node<R, T, Stk, kFam>(code, q, p, acc, stk, sp);
   }
 }
 

@@ -170,6 +170,9 @@ struct Prep {
   double extent = 0;     // its largest edge
   bool has_stri = false; // a rounded triangle (sphere-triangle volume) is present
   bool has_further = false;  // a primitive beyond sphere, rounded box and capsule
+  bool has_rtri_quadric = false;  // a rounded triangle or a bounded quadric
+  // kernel instance tier of the scene (TraceLaunch::further)
+  int further_level() const { return has_rtri_quadric ? 2 : has_further ? 1 : 0; }
 };
 
 // Returns ST_OK or ST_ERR_INVALID with `err` set.

@@ -117,8 +117,9 @@ struct TraceLaunch {
                            // (0: built-in bound)
   uint32_t split_spins;    // polls of a CTA waiting for split parts
                            // (0: built-in bound)
-  int32_t further;         // 1: some scene holds primitives beyond spheres,
-                           // rounded boxes and capsules (kernel instance)
+  int32_t further;         // kernel instance by the scenes' primitive families:
+                           // 0 spheres, rounded boxes and capsules only; 1 also
+                           // tori, sphere-cones, ellipsoids; 2 any family
   const uint32_t *heavy_thr;  // optional device word: early-split threshold
                               // (written by launch_tile_order); overrides
                               // heavy_len

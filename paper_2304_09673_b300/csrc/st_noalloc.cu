@@ -16,7 +16,7 @@ namespace st {
 void scene_facts(const st_scene *s, DevScene *sc, int *stack_depth, double *diameter, double *extent, int *n_sm);
 TraceParams make_trace_params(const st_trace_opts &o, double diameter, double extent);
 int trace_status_code(const uint32_t *status, cudaStream_t st, const char *who);
-bool scene_has_further(const st_scene *s);
+int scene_further_level(const st_scene *s);
 }
 
 namespace {
@@ -154,7 +154,7 @@ extern "C" int st_trace_noalloc(st_scene *s, const st_camera *cam, const st_tile
   L.counters = counters;
   L.tile_stats = o.tile_stats;
   L.step_mode = job.tp.step_mode;
-  L.further = scene_has_further(s) ? 1 : 0;
+  L.further = scene_further_level(s);
   L.mlp = job.tp.step_mode == ST_STEP_LEARNED ? o.mlp : nullptr;
   if (job.tp.step_mode == ST_STEP_LEARNED && L.stack_slots < 10) L.stack_slots = 10;
   L.work_in_smem = 1;

@@ -243,6 +243,7 @@ int prepare(const st_scene_desc &d, Prep &p, std::string &err) {
       ++n_prims;
       if (k == ST_PRIM_RTRI) p.has_stri = true;
       if (k != ST_PRIM_SPHERE && k != ST_PRIM_RBOX && k != ST_PRIM_CAPSULE) p.has_further = true;
+      if (k == ST_PRIM_RTRI || k == ST_PRIM_QUADRIC) p.has_rtri_quadric = true;
       continue;
     }
     if (!is_op_kind(k)) {

@@ -40,6 +40,7 @@ namespace st {
 
 constexpr int kWarps = 4;   // warps per CTA; a CTA traces one tile at a time
 constexpr int kFurtherBit = 64;   // instance bit: the interpreter evaluates the further families
+constexpr int kAllFamBit = 256;   // instance bit (with kFurtherBit): ... including the rounded triangle and quadric
 constexpr int kStagedBit = 128;   // instance bit: views in global memory, evaluated in staged chunks
 constexpr int kStageWords = 64;   // float4 record words of a warp's stage buffer (staged instances)
 constexpr int kTileStatWords = 24;   // words per tile of the optional diagnostics
@@ -523,7 +524,7 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-template <int R, class T, class Stk, bool kFurther>
+template <int R, class T, class Stk, int kFam>
 __device__ __forceinline__ void eval_view_staged(const uint32_t *view, int n_view, const RecSrc &src,
                                                  const T (&p)[R][3], T (&acc)[R], Stk &stk, float4 *stage) {
   const int lane = threadIdx.x & 31;
@@ -554,7 +555,7 @@ __device__ __forceinline__ void eval_view_staged(const uint32_t *view, int n_vie
     __syncwarp();
     for (int j = 0; j < nb; ++j) {
       const uint32_t wj = __shfl_sync(0xFFFFFFFFu, w, j);
-      eval_node<R, T, Stk, kFurther>(wj >> kViewCodeShift, rec_ptr(ss, wj), p, acc, stk, sp);
+      eval_node<R, T, Stk, kFam>(wj >> kViewCodeShift, rec_ptr(ss, wj), p, acc, stk, sp);
     }
     __syncwarp();   // the next chunk overwrites the stage
     i0 += nb;
@@ -813,7 +814,7 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
 // All lanes hold the same point p.  Primitives are evaluated in parallel,
 // then operators level by level (operands always sit on lower levels).
 // `vals` is per-warp shared memory of at least n_view floats.
-template <bool kFurther>
+template <int kFam>
 __device__ __forceinline__ float tail_eval(const uint32_t *view, int n_view, const uint2 *ops, const int *lvl_off, int n_lvl,
                            const RecSrc &src, const float p[3], float *vals) {
   const int lane = threadIdx.x & 31;
@@ -827,7 +828,7 @@ __device__ __forceinline__ float tail_eval(const uint32_t *view, int n_view, con
       case V_SPHERE: v = sd_sphere<float>(ldrec(q), p); break;
       case V_RBOX: v = sd_rbox<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p); break;
       case V_CAPSULE: v = sd_capsule<float>(ldrec(q), ldrec(q + 2), p); break;
-      default: v = kFurther ? sd_further<float>(code, q, p[0], p[1], p[2]) : INFINITY; break;
+      default: v = kFam ? sd_further<float, kFam == 2>(code, q, p[0], p[1], p[2]) : INFINITY; break;
     }
     vals[i] = v;
   }
@@ -1028,7 +1029,7 @@ struct LearnCtx {      // learned step / recording context of a subfrustum
   float4 *stage;              // this warp's record stage (staged instances)
 };
 
-template <int MODE, bool kFurther, bool kStaged>
+template <int MODE, int kFam, bool kStaged>
 __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &C, const RecSrc &src, const SubInfo &inf,
                               const uint32_t *view, const uint2 *ops, const int *lvl_off, const uint16_t *alive_in,
                               int n_in, int *q_head, uint16_t *alive_out, int *n_out, uint16_t *hits, int &n_hits,
@@ -1326,7 +1327,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
           const float pt[3] = {fma_(zz, __shfl_sync(0xFFFFFFFFu, d[s][0], owner), M.cam->o[0]),
                                fma_(zz, __shfl_sync(0xFFFFFFFFu, d[s][1], owner), M.cam->o[1]),
                                fma_(zz, __shfl_sync(0xFFFFFFFFu, d[s][2], owner), M.cam->o[2])};
-          const float fv = tail_eval<kFurther>(view, inf.n_view, ops, lvl_off, inf.n_lvl, src, pt, wvals);
+          const float fv = tail_eval<kFam>(view, inf.n_view, ops, lvl_off, inf.n_lvl, src, pt, wvals);
           if (lane == owner) f[s] = fv;
         }
       }
@@ -1389,9 +1390,9 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         float f1[1];
         SmemStack1 stk1{stk.base};
         if (kStaged)
-          eval_view_staged<1, float, SmemStack1, kFurther>(view, inf.n_view, src, p1, f1, stk1, LC.stage);
+          eval_view_staged<1, float, SmemStack1, kFam>(view, inf.n_view, src, p1, f1, stk1, LC.stage);
         else
-          eval_view_r<1, float, SmemStack1, kFurther>(view, inf.n_view, src, p1, f1, stk1);
+          eval_view_r<1, float, SmemStack1, kFam>(view, inf.n_view, src, p1, f1, stk1);
         f[0] = f1[0];
         f[1] = 0.f;
       } else {
@@ -1403,9 +1404,9 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         F2 f2[1];
         SmemStackF2 stk2{stk.base};
         if (kStaged)
-          eval_view_staged<1, F2, SmemStackF2, kFurther>(view, inf.n_view, src, p2, f2, stk2, LC.stage);
+          eval_view_staged<1, F2, SmemStackF2, kFam>(view, inf.n_view, src, p2, f2, stk2, LC.stage);
         else
-          eval_view_r<1, F2, SmemStackF2, kFurther>(view, inf.n_view, src, p2, f2, stk2);
+          eval_view_r<1, F2, SmemStackF2, kFam>(view, inf.n_view, src, p2, f2, stk2);
         f[0] = f2[0].v.x;
         f[1] = f2[0].v.y;
       }
@@ -1454,7 +1455,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
 // Hit refinement: Newton steps along the ray on f_A (value + derivative along
 // d), then the gradient of f_A from three directional derivatives; a
 // crossing that lies past z_end is handed to the next subfrustum.
-template <bool kFurther>
+template <int kFam>
 __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &C, const RecSrc &src, const SubInfo &inf,
                               const uint32_t *view, const uint16_t *hits, int n_hits, uint16_t *alive_out,
                               int *n_out, float2 *stk_lane, uint64_t &c_fin, unsigned long long *diag) {
@@ -1496,7 +1497,7 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
         pd[0][j].v = cam.o[j] + zz * d[j];
         pd[0][j].g[0] = newton ? d[j] : (j == k ? 1.f : 0.f);
       }
-      eval_view_r<1, Dual<1>, SmemStackD1, kFurther>(view, inf.n_view, src, pd, fd, stk);
+      eval_view_r<1, Dual<1>, SmemStackD1, kFam>(view, inf.n_view, src, pd, fd, stk);
       if (newton) {
         // a first sample inside the solid at the near plane: clipped hit
         if (it == 0 && zz <= kZNear && fd[0].v < -M.tp->eps) done = true;
@@ -1548,8 +1549,8 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
 template <int INST>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
-  constexpr int MODE = INST & ~(kFurtherBit | kStagedBit);
-  constexpr bool kFurther = (INST & kFurtherBit) != 0;
+  constexpr int MODE = INST & ~(kFurtherBit | kStagedBit | kAllFamBit);
+  constexpr int kFam = (INST & kFurtherBit) ? ((INST & kAllFamBit) ? 2 : 1) : 0;
   constexpr bool kStaged = (INST & kStagedBit) != 0;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_item, s_rec;
@@ -1797,7 +1798,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         const long long t0 = clock64();
         int n_hits = 0;
         const RecSrc src{sc.rec, pick(C.dc, k & 1)};
-        const uint32_t ls = march_sub<MODE, kFurther, kStaged>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
+        const uint32_t ls = march_sub<MODE, kFam, kStaged>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
                                       n_pending, &s_qhead[rd], alive_out, &s_nctr[wr], my_hits, n_hits, stk_lane,
                                       wvals, 2 * L.stack_slots * 32, c_rej, LC, &s_tqt[rd], &s_tqh[rd], &s_ndone[rd],
                                       &s_nidle[rd], g_sub, c_err);
@@ -1806,7 +1807,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         c_prim += (uint64_t)ls * inf.n_prim;
         c_op += (uint64_t)ls * inf.n_op;
         c_flops += (uint64_t)ls * (inf.flops + kFlopsStep);
-        finalize_hits<kFurther>(M, C, src, inf, pick(C.view, k & 1), my_hits, n_hits, alive_out, &s_nctr[wr],
+        finalize_hits<kFam>(M, C, src, inf, pick(C.view, k & 1), my_hits, n_hits, alive_out, &s_nctr[wr],
                                 stk_lane, c_fin, LC.diag);
         if (L.tile_stats && lane == 0) {
           atomicAdd(&s_dbg[4], (unsigned long long)(clock64() - t1));
@@ -2073,8 +2074,9 @@ void launch_eval_view(const DevScene &sc, const uint32_t *view, const int32_t *i
 template <class F>
 static auto with_instance(const TraceLaunch &L, F &&f) {
 #define ST_INST1(M)                                                                    \
-  return L.further ? f(std::integral_constant<int, (M) | kFurtherBit>{})               \
-                   : f(std::integral_constant<int, (M)>{})
+  return L.further == 2 ? f(std::integral_constant<int, (M) | kFurtherBit | kAllFamBit>{}) \
+         : L.further    ? f(std::integral_constant<int, (M) | kFurtherBit>{})               \
+                        : f(std::integral_constant<int, (M)>{})
 #define ST_INST(M)                          \
   if (!L.staged) { ST_INST1(M); }          \
   ST_INST1((M) | kStagedBit)
