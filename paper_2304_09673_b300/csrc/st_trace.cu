@@ -824,12 +824,10 @@ __device__ __forceinline__ float tail_eval(const uint32_t *view, int n_view, con
     if (!is_prim_code(code)) continue;
     const float4 *q = rec_ptr(src, w);
     float v;
-    switch (code) {
-      case V_SPHERE: v = sd_sphere<float>(ldrec(q), p); break;
-      case V_RBOX: v = sd_rbox<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p); break;
-      case V_CAPSULE: v = sd_capsule<float>(ldrec(q), ldrec(q + 2), p); break;
-      default: v = kFam ? sd_further<float, kFam == 2>(code, q, p[0], p[1], p[2]) : INFINITY; break;
-    }
+    if (code == V_SPHERE) v = sd_sphere<float>(ldrec(q), p);
+    else if (code == V_RBOX) v = sd_rbox<float>(ldrec(q), ldrec(q + 1), ldrec(q + 2), ldrec(q + 3), p);
+    else if (code == V_CAPSULE) v = sd_capsule<float>(ldrec(q), ldrec(q + 2), p);
+    else v = kFam ? sd_further<float, kFam == 2>(code, q, p[0], p[1], p[2]) : INFINITY;
     vals[i] = v;
   }
   __syncwarp();
@@ -843,13 +841,11 @@ __device__ __forceinline__ float tail_eval(const uint32_t *view, int n_view, con
       const float4 *q = rec_ptr(src, w);
       float v;
       const uint32_t code = w >> kViewCodeShift;
-      switch (code) {
-        case V_UNION: case V_INTER: case V_DIFF: v = op_compact_any<float>(code, ldrec(q), f0, f1); break;
-        case V_SUNION: case V_SINTER: case V_SDIFF: v = op_sharp_any<float>(code, f0, f1); break;
-        case V_INF: v = INFINITY; break;
-        case V_RIGHT: v = f1; break;
-        default: v = f0; break;
-      }
+      if (code <= V_DIFF) v = op_compact_any<float>(code, ldrec(q), f0, f1);
+      else if (code <= V_SDIFF) v = op_sharp_any<float>(code, f0, f1);
+      else if (code == V_INF) v = INFINITY;
+      else if (code == V_RIGHT) v = f1;
+      else v = f0;
       vals[self] = v;
     }
     __syncwarp();
