@@ -493,18 +493,10 @@ __device__ __forceinline__ ViewInfo build_view_lca(const DevScene &sc, const uin
 // in view order until the cache is full; the remaining nodes keep reading
 // the scene's global records.  Record words needed per node code.
 __device__ __forceinline__ int code_words(uint32_t code) {
-  switch (code) {
-    case V_SPHERE: return 1;
-    case V_RBOX: return 4;
-    case V_CAPSULE: return 3;
-    case V_TORUS: return 2;
-    case V_SCONE: return 4;
-    case V_ELLIPSOID: return 5;
-    case V_RTRI: return 7;
-    case V_QUADRIC: return 5;
-    case V_UNION: case V_INTER: case V_DIFF: return 1;
-    default: return 0;
-  }
+  // record words of codes 0..15 as 4-bit fields (1 4 3 1 1 1 0 0 0 0 0 0 2 4 5 7),
+  // code 16 (bounded quadric) 5: no indexed jump per staged node
+  constexpr unsigned long long kWords = 0x7542000000111341ull;
+  return code < 16 ? (int)((kWords >> (4 * code)) & 15u) : (code == V_QUADRIC ? 5 : 0);
 }
 
 // ---- staged evaluation of views held in global memory ------------------------------
