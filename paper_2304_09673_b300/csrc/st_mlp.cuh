@@ -49,12 +49,18 @@ __host__ __device__ inline float step_label(float f_i, float f_next) {
   return fminf(fmaxf(w, 1.f), 2.f);
 }
 
-struct MlpSmem {   // packed weights staged in shared memory (16-byte aligned)
-  const uint32_t *w1;   // bf16 pairs, [32][8]
-  const uint32_t *w2;   // [32][16]
-  const uint32_t *w3;   // [8][16]
-  const float *b1, *b2;
-  float b3;
+// Packed weights staged in shared memory (16-byte aligned), held as one base
+// pointer with the parts at their fixed offsets: the tracer keeps this across
+// its whole loop, and one pointer instead of six values leaves registers to
+// the marching state (learned step, B300: 1080p -2 %, 10k clustered -12 %).
+struct MlpSmem {
+  const unsigned char *base;
+  __device__ __forceinline__ const uint32_t *w1() const { return reinterpret_cast<const uint32_t *>(base + kMlpW1Off); }
+  __device__ __forceinline__ const uint32_t *w2() const { return reinterpret_cast<const uint32_t *>(base + kMlpW2Off); }
+  __device__ __forceinline__ const uint32_t *w3() const { return reinterpret_cast<const uint32_t *>(base + kMlpW3Off); }
+  __device__ __forceinline__ const float *b1() const { return reinterpret_cast<const float *>(base + kMlpB1Off); }
+  __device__ __forceinline__ const float *b2() const { return reinterpret_cast<const float *>(base + kMlpB2Off); }
+  __device__ __forceinline__ float b3() const { return *reinterpret_cast<const float *>(base + kMlpB3Off); }
 };
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -83,14 +89,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // (valid in lanes with t == 0).
 __device__ __forceinline__ void mlp_tile(const MlpSmem &W, uint32_t a0, uint32_t a1, int g, int t, float &o_lo,
                                          float &o_hi) {
-  const float2 *b1 = reinterpret_cast<const float2 *>(W.b1);
-  const float2 *b2 = reinterpret_cast<const float2 *>(W.b2);
+  const float2 *b1 = reinterpret_cast<const float2 *>(W.b1());
+  const float2 *b2 = reinterpret_cast<const float2 *>(W.b2());
   float h1[4][4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const float2 b = b1[4 * q + t];
     h1[q][0] = b.x; h1[q][1] = b.y; h1[q][2] = b.x; h1[q][3] = b.y;
-    mma_bf16_k8(h1[q], a0, a1, W.w1[(8 * q + g) * 8 + t]);
+    mma_bf16_k8(h1[q], a0, a1, W.w1()[(8 * q + g) * 8 + t]);
   }
   uint32_t a2[2][4];
 #pragma unroll
@@ -107,7 +113,7 @@ __device__ __forceinline__ void mlp_tile(const MlpSmem &W, uint32_t a0, uint32_t
     h2[q][0] = b.x; h2[q][1] = b.y; h2[q][2] = b.x; h2[q][3] = b.y;
 #pragma unroll
     for (int kt = 0; kt < 2; ++kt)
-      mma_bf16(h2[q], a2[kt], W.w2[(8 * q + g) * 16 + 8 * kt + t], W.w2[(8 * q + g) * 16 + 8 * kt + t + 4]);
+      mma_bf16(h2[q], a2[kt], W.w2()[(8 * q + g) * 16 + 8 * kt + t], W.w2()[(8 * q + g) * 16 + 8 * kt + t + 4]);
   }
   uint32_t a3[2][4];
 #pragma unroll
@@ -119,9 +125,10 @@ __device__ __forceinline__ void mlp_tile(const MlpSmem &W, uint32_t a0, uint32_t
   }
   float o[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int kt = 0; kt < 2; ++kt) mma_bf16(o, a3[kt], W.w3[g * 16 + 8 * kt + t], W.w3[g * 16 + 8 * kt + t + 4]);
-  o_lo = o[0] + W.b3;
-  o_hi = o[2] + W.b3;
+  for (int kt = 0; kt < 2; ++kt) mma_bf16(o, a3[kt], W.w3()[g * 16 + 8 * kt + t], W.w3()[g * 16 + 8 * kt + t + 4]);
+  const float b3 = W.b3();
+  o_lo = o[0] + b3;
+  o_hi = o[2] + b3;
 }
 
 // 1 + sigmoid(v) = 1.5 + tanh(v / 2) / 2 (one MUFU tanh).
@@ -184,12 +191,7 @@ __device__ __forceinline__ MlpSmem load_mlp(const void *packed, unsigned char *s
   for (int i = threadIdx.x; i < (int)(kMlpPackBytes / 16); i += blockDim.x) dst[i] = src[i];
   __syncthreads();
   MlpSmem w;
-  w.w1 = reinterpret_cast<const uint32_t *>(sm + kMlpW1Off);
-  w.w2 = reinterpret_cast<const uint32_t *>(sm + kMlpW2Off);
-  w.w3 = reinterpret_cast<const uint32_t *>(sm + kMlpW3Off);
-  w.b1 = reinterpret_cast<const float *>(sm + kMlpB1Off);
-  w.b2 = reinterpret_cast<const float *>(sm + kMlpB2Off);
-  w.b3 = *reinterpret_cast<const float *>(sm + kMlpB3Off);
+  w.base = sm;
   return w;
 }
 
