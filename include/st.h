@@ -561,6 +561,23 @@ int st_pruned_view_alg1(const st_scene *scene, const uint32_t *act, int n, uint3
 int st_eval_pruned(const st_scene *scene, const uint32_t *view, const int32_t *info, const float *pts,
                    int npts, float *f, float *grad, void *stream);
 
+/* st_eval_pruned_levels: f_A (Sec. 3) at points over the pruned view of an
+ * active set, evaluated as st_trace's tail mode does for the last rays of a
+ * subfrustum: the view is built as by st_pruned_view, its operators are
+ * grouped by height in the view (operands always sit lower), and one warp
+ * evaluates a point: the primitives in parallel, then the operators level by
+ * level, one per lane (the same node values as Algorithm 3 over the view, in
+ * another order).
+ *   act, n     as st_pruned_view;   view  device uint32[2n-1] out
+ *   info       device int32[4] out: view length, root usage bit, error (0 ok),
+ *              operator levels (0: the view has no level schedule -- a single
+ *              primitive, more than 64 levels or an unused root -- and f is NaN)
+ *   pts        device float[npts][3];   f  device float[npts] out
+ * Uses the library-owned scratch of st_pruned_view (stream ordered on one
+ * scene).  ST_ERR_INVALID on bad arguments. */
+int st_eval_pruned_levels(const st_scene *scene, const uint32_t *act, int n, uint32_t *view, int32_t *info,
+                          const float *pts, int npts, float *f, void *stream);
+
 /* ---- host-only preparation (no GPU needed) ----------------------------------
  * The preparation step of st_scene_create on its own, for inspection: every
  * output is a host array indexed by post-order address (n_nodes entries):

@@ -563,6 +563,20 @@ int st_eval_pruned(const st_scene *s, const uint32_t *view, const int32_t *info,
   return ST_OK;
 }
 
+int st_eval_pruned_levels(const st_scene *s, const uint32_t *act, int n, uint32_t *view, int32_t *info,
+                          const float *pts, int npts, float *f, void *stream) {
+  if (!s || !act || n < 1 || n > s->n_prims || !view || !info || npts < 0 || (npts > 0 && (!pts || !f))) {
+    set_error("invalid arguments");
+    return ST_ERR_INVALID;
+  }
+  st_scene *m = const_cast<st_scene *>(s);
+  const int cap = ST_MAX_STACK + 2;
+  ST_CK(m->g_work.ensure(eval_levels_scratch_words(n, cap)));
+  launch_eval_levels(dev_scene(s), act, n, view, info, m->g_work.p, cap, pts, npts, f, (cudaStream_t)stream);
+  ST_CK(cudaGetLastError());
+  return ST_OK;
+}
+
 int st_build_dexels(st_scene *s, const st_camera *cam, const st_tiles *tl, st_tiles *out, void *stream) {
   if (!s || !tl || !out) { set_error("null argument"); return ST_ERR_INVALID; }
   int rc = check_camera(cam);

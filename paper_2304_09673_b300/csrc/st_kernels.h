@@ -198,6 +198,9 @@ int trace_ctas_per_sm(const TraceLaunch &L);
 void launch_pruned_view(const DevScene &sc, const uint32_t *act, int n, uint32_t *view, uint32_t *vaddr,
                         int32_t *info, uint32_t *scratch, int stack_cap, int method, cudaStream_t s);
 size_t pruned_view_scratch_words(int n, int stack_cap);
+size_t eval_levels_scratch_words(int n, int stack_cap);
+void launch_eval_levels(const DevScene &sc, const uint32_t *act, int n, uint32_t *view, int32_t *info,
+                        uint32_t *scratch, int stack_cap, const float *pts, int npts, float *f, cudaStream_t s);
 void launch_eval_view(const DevScene &sc, const uint32_t *view, const int32_t *info, const float *pts, int npts,
                       float *f, float *grad, cudaStream_t s);
 

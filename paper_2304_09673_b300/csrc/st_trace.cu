@@ -2043,6 +2043,49 @@ __global__ void k_eval_view(DevScene sc, const uint32_t *view, const int32_t *in
   }
 }
 
+// The tracer's view build followed by the warp-wide level evaluation of the
+// tail mode, one point after another (one warp).  info: view length, root
+// usage bit, error, operator levels of the schedule (0: no schedule; f is
+// then NaN).  `scratch` as for k_pruned_view plus 2n floats of node values.
+__global__ void k_eval_levels(DevScene sc, const uint32_t *act, int n, uint32_t *view, int32_t *info,
+                              uint32_t *scratch, int stack_cap, const float *pts, int npts, float *f) {
+  if (blockIdx.x != 0) return;
+  __shared__ ViewChunk vch;
+  uint32_t *stk = scratch;
+  uint2 *ops = reinterpret_cast<uint2 *>(scratch + align16((size_t)6 * (stack_cap + 2) * 4) / 4);
+  uint2 *sort_tmp = ops + n;
+  int *lvl_off = reinterpret_cast<int *>(sort_tmp + n);
+  int *lvl_cur = lvl_off + kMaxLevels + 1;
+  float *vals = reinterpret_cast<float *>(lvl_cur + kMaxLevels + 1);
+  int n_lvl = 0;
+  const ViewInfo vi = build_view_lca<false>(sc, act, n, view, vch, ops, sort_tmp, lvl_off, lvl_cur, stk, stack_cap,
+                                            nullptr, &n_lvl);
+  const bool ok = !vi.err && vi.root_used && n_lvl > 0;
+  if (threadIdx.x == 0) {
+    info[0] = vi.n_view;
+    info[1] = vi.root_used;
+    info[2] = vi.err;
+    info[3] = ok ? n_lvl : 0;
+  }
+  __syncwarp();
+  const RecSrc src{sc.rec, nullptr};
+  for (int i = 0; i < npts; ++i) {
+    float v = NAN;
+    if (ok) {
+      const float p[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+      v = tail_eval<2>(view, vi.n_view, ops, lvl_off, n_lvl, src, p, vals);
+    }
+    if (threadIdx.x == 0) f[i] = v;
+  }
+}
+
+size_t eval_levels_scratch_words(int n, int stack_cap) { return pruned_view_scratch_words(n, stack_cap) + 2 * (size_t)n; }
+
+void launch_eval_levels(const DevScene &sc, const uint32_t *act, int n, uint32_t *view, int32_t *info,
+                        uint32_t *scratch, int stack_cap, const float *pts, int npts, float *f, cudaStream_t s) {
+  count_launch(), k_eval_levels<<<1, 32, 0, s>>>(sc, act, n, view, info, scratch, stack_cap, pts, npts, f);
+}
+
 void launch_pruned_view(const DevScene &sc, const uint32_t *act, int n, uint32_t *view, uint32_t *vaddr,
                         int32_t *info, uint32_t *scratch, int stack_cap, int method, cudaStream_t s) {
   count_launch(), k_pruned_view<<<1, 32, 0, s>>>(sc, act, n, view, vaddr, info, scratch, stack_cap, method);

@@ -80,6 +80,7 @@ _lib.st_tiles_copy.argtypes = [C.POINTER(st_tiles), _P, _P, _P, _P, _P]
 _lib.st_pruned_view.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
 _lib.st_pruned_view_alg1.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
 _lib.st_eval_pruned.argtypes = [_P, _P, _P, _P, C.c_int, _P, _P, _P]
+_lib.st_eval_pruned_levels.argtypes = [_P, _P, C.c_int, _P, _P, _P, C.c_int, _P, _P]
 _lib.st_kernel_launches.restype = C.c_uint64
 _lib.st_trace_noalloc.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINTER(st_trace_opts),
                                   _P, _P, _P, _P, _P, _P]
@@ -114,6 +115,7 @@ _lib.st_eval_sparse.argtypes = [_P, _P, C.c_int, _P, C.c_int, C.c_int, _P, _P, _
 
 EXPORTED = ("st_scene_create", "st_scene_update_prims", "st_scene_addresses", "st_scene_info", "st_scene_destroy",
             "st_build_tiles", "st_trace", "st_tiles_copy", "st_pruned_view", "st_pruned_view_alg1", "st_eval_pruned",
+            "st_eval_pruned_levels",
             "st_prep_tree", "st_last_error", "st_version", "st_kernel_launches", "st_device_allocations",
             "st_trace_noalloc", "st_trace_noalloc_scratch_bytes", "st_trace_noalloc_last_layout",
             "st_trace_record", "st_mlp_pack_size", "st_mlp_param_count", "st_mlp_pack", "st_mlp_grad",
@@ -315,6 +317,11 @@ def st_pruned_view_alg1(h, act, view, view_addr, info, stream=None) -> None:
 def st_eval_pruned(h, view, info, pts, f, grad=None, stream=None) -> None:
     _check(_lib.st_eval_pruned(h, _ptr(view), _ptr(info), _ptr(pts), int(pts.numel() // 3), _ptr(f), _ptr(grad),
                                _stream(stream)), "st_eval_pruned")
+
+
+def st_eval_pruned_levels(h, act, view, info, pts, f, stream=None) -> None:
+    _check(_lib.st_eval_pruned_levels(h, _ptr(act), int(act.numel()), _ptr(view), _ptr(info), _ptr(pts),
+                                      int(pts.numel() // 3), _ptr(f), _stream(stream)), "st_eval_pruned_levels")
 
 
 def st_build_dexels(h, cam, tiles: st_tiles, stream=None) -> st_tiles:
