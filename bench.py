@@ -295,18 +295,23 @@ def agreement(cam, diam, ref, got, torch):
     return out
 
 
+# Launch options shared by every mode (set from the command line).
+TRACE_EXTRA: dict = {}
+
+
 def mode_opts(st, name: str, mlp, max_new: int):
     """Trace options of one step mode; eps, L, step cap and subfrustum sizes are identical across modes."""
+    x = TRACE_EXTRA
     if name == "learned":
-        return st.make_opts(step_mode=st.ST_STEP_LEARNED, mlp=mlp.data_ptr(), max_new_per_turn=max_new)
+        return st.make_opts(step_mode=st.ST_STEP_LEARNED, mlp=mlp.data_ptr(), max_new_per_turn=max_new, **x)
     if name == "overrelax":
-        return st.make_opts(step_mode=st.ST_STEP_OVERRELAX, omega=1.7, max_new_per_turn=max_new)
+        return st.make_opts(step_mode=st.ST_STEP_OVERRELAX, omega=1.7, max_new_per_turn=max_new, **x)
     if name == "plain":
-        return st.make_opts(step_mode=st.ST_STEP_PLAIN, max_new_per_turn=max_new)
+        return st.make_opts(step_mode=st.ST_STEP_PLAIN, max_new_per_turn=max_new, **x)
     if name == "crossing":
         # Sec. 10's own ray processing: omega = 1.7 with sphere reuse, minimum
         # step instead of eps and step cap (hits are crossings, f <= 0)
-        return st.make_opts(step_mode=st.ST_STEP_CROSSING, omega=1.7, max_new_per_turn=max_new)
+        return st.make_opts(step_mode=st.ST_STEP_CROSSING, omega=1.7, max_new_per_turn=max_new, **x)
     raise SystemExit(f"unknown step mode {name}")
 
 
@@ -800,6 +805,8 @@ def main():
     ap.add_argument("--modes", default="learned,plain,overrelax,crossing",
                     help="step modes to time; the first one is the headline value")
     ap.add_argument("--max-new", type=int, default=32, help="new primitives per subfrustum")
+    ap.add_argument("--cta-min-view", type=int, default=0,
+                    help="st_trace_opts.cta_eval_min_view (0: library default, < 0: no CTA-split evaluation)")
     ap.add_argument("--batch-scenes", type=int, default=64, help="scenes of the batch64 workload")
     ap.add_argument("--res", default=None, help="WxH: render the single-scene workload at another resolution")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -809,6 +816,8 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=8192,
                     help="oracle rays per step of the reference arm")
     args = ap.parse_args()
+    if args.cta_min_view:
+        TRACE_EXTRA["cta_eval_min_view"] = args.cta_min_view
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -199,7 +199,9 @@ typedef struct {
                                evaluated by the warp-wide tail mode, [19]
                                hit refinement passes and [20] live lanes
                                summed over them, all summed over warps;
-                               [21..23] 0; a tile split across CTAs
+                               [21] CTA-split passes (see
+                               cta_eval_min_view) and [22] live rays
+                               summed over them; [23] 0; a tile split across CTAs
                                reports its first part only (NULL = off) */
     float omega;            /* relaxation factor of ST_STEP_OVERRELAX and
                                ST_STEP_CROSSING [1.7, Sec. 10]             */
@@ -244,6 +246,16 @@ typedef struct {
                                for the other device error bits [0: the
                                call stays asynchronous; the bits are in
                                counters[7] when counters are given]      */
+    int32_t cta_eval_min_view; /* launches whose views live in global
+                               memory (tile lists over 1024 entries): a
+                               subfrustum whose pruned view has at least
+                               this many nodes is, once at most 64 of its
+                               rays are unfinished, stepped by one warp
+                               while all four warps of the CTA evaluate a
+                               quarter of the view each (Algorithm 3 cut
+                               at subtree boundaries; the same values bit
+                               for bit); 0 = default [1024], < 0 = never;
+                               st_trace_noalloc never splits            */
 } st_trace_opts;
 
 /* Optional per-call counters (device pointer to 8 uint64, accumulated with

@@ -432,6 +432,10 @@ __device__ __forceinline__ uint32_t node_flops(uint32_t code) {
   }
 }
 
+// Stacks that carry the output slots of the CTA-split evaluation.
+template <class S, class = void> struct StkCta { static constexpr bool value = false; };
+template <class S> struct StkCta<S, std::void_t<decltype(S::kCta)>> { static constexpr bool value = S::kCta; };
+
 // One node of Algorithm 3 for R points: a primitive pushes the running value
 // and evaluates itself, an operator pops its left operand and combines; q is
 // the node's record (unused by nodes without one).
@@ -478,6 +482,21 @@ __device__ __forceinline__ void eval_node(uint32_t code, const float4 *q, const 
     --sp;
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = T(INFINITY);
+  } else if (StkCta<Stk>::value && code >= V_STORE) {
+    // CTA-split evaluation (pairs of points only; see st_trace.cu): STORE
+    // writes the running value to the stack's next output slot and pops,
+    // LOAD pushes and takes the lane's value from the node's staged record.
+    if constexpr (StkCta<Stk>::value) {
+      const int lane = threadIdx.x & 31;
+      if (code == V_STORE) {
+        __stcg(stk.xout + (size_t)stk.xn * 32 + lane, acc[0].v);
+        ++stk.xn;
+        stk.pop(--sp, acc);
+      } else {
+        stk.push(sp++, acc);
+        acc[0] = F2(reinterpret_cast<const float2 *>(q)[lane]);
+      }
+    }
   } else {   // the further primitive families (codes 12..16)
     stk.push(sp++, acc);
 #pragma unroll
@@ -533,6 +552,16 @@ struct SmemStack2 {   // R = 2 float points
 };
 struct SmemStackF2 {  // R = 1 pair of float points (F2), the same slots as SmemStack2
   float2 *base;
+  __device__ __forceinline__ void push(int s, const F2 (&a)[1]) { base[s * 32] = a[0].v; }
+  __device__ __forceinline__ void pop(int s, F2 (&a)[1]) const { a[0] = F2(base[s * 32]); }
+};
+// The same with the output slots of the CTA-split evaluation (the only stack
+// whose interpreter instance handles its STORE and LOAD codes).
+struct SmemStackF2Cta {
+  float2 *base;
+  float2 *xout;   // the warp's output slots (slot s of lane l at xout[s * 32 + l])
+  int xn;         // ... and the next slot to write
+  static constexpr bool kCta = true;
   __device__ __forceinline__ void push(int s, const F2 (&a)[1]) { base[s * 32] = a[0].v; }
   __device__ __forceinline__ void pop(int s, F2 (&a)[1]) const { a[0] = F2(base[s * 32]); }
 };

@@ -35,6 +35,10 @@ enum ViewCode : uint32_t {
   V_INF = 9, V_RIGHT = 10, V_LEFT = 11,               // usage rewrites (Sec. 9)
   V_TORUS = 12, V_SCONE = 13, V_ELLIPSOID = 14,       // further primitives
   V_RTRI = 15, V_QUADRIC = 16,
+  // CTA-split evaluation of a view (st_trace.cu): a segment stream stores
+  // the running value into the next output slot and pops; the top program
+  // pushes and loads a stored value (one float2 per lane).  Never in a view.
+  V_STORE = 17, V_LOAD = 18,
 };
 constexpr uint32_t V_FIRST_OP = 3;
 // Primitive view codes: 0..2 and 12..16 (equal to the primitive kinds but

@@ -123,6 +123,10 @@ struct TraceLaunch {
   const uint32_t *heavy_thr;  // optional device word: early-split threshold
                               // (written by launch_tile_order); overrides
                               // heavy_len
+  int32_t cta_min_view;    // staged launches: views of at least this many
+                           // nodes are prepared for the CTA-split evaluation
+                           // of a subfrustum's last rays (0: never; the work
+                           // areas then hold no split arrays)
 };
 
 // Split area sizing: words per record (header, pending ray ids, depth and
@@ -157,6 +161,12 @@ inline long long trace_split_cycles(int32_t split_kcycles) {
 // staging costs 4-12 % on 1,024 primitives at 1920x1080 and saves ~20 % on
 // 10k clustered primitives).
 inline int32_t trace_staged(const TraceLaunch &L) { return !L.work_in_smem && L.view_cap > 2048 ? 1 : 0; }
+// st_trace_opts::cta_eval_min_view -> TraceLaunch::cta_min_view (staged launches only).
+constexpr int32_t kCtaMinViewDefault = 1024;
+inline int32_t trace_cta_min_view(const TraceLaunch &L, int32_t opt) {
+  if (!L.staged || opt < 0) return 0;
+  return opt > 0 ? (opt < 64 ? 64 : opt) : kCtaMinViewDefault;
+}
 inline uint32_t trace_heavy_len(int32_t opt) { return opt > 0 ? (uint32_t)opt : 0u; }
 // st_trace_opts::heavy_split_rank -> rank of the list-length threshold taken
 // on the device (0: no rank rule), and the least list length it splits.

@@ -45,6 +45,19 @@ constexpr int kStagedBit = 128;   // instance bit: views in global memory, evalu
 constexpr int kStageWords = 64;   // float4 record words of a warp's stage buffer (staged instances)
 constexpr int kTileStatWords = 24;   // words per tile of the optional diagnostics
 constexpr int kR = 2;       // rays per lane (shared node decode, two evaluation chains)
+// CTA-split evaluation (staged instances): once a subfrustum with a large view
+// is down to kCtaMaxRays rays, one warp holds them all and each warp evaluates
+// a quarter of the view for them (see build_cta_split and march_sub).
+constexpr int kCtaMaxRays = 64;     // rays of the owner warp (two per lane)
+constexpr int kCtaTopMax = 256;     // words of a view's top program
+constexpr int kCtaOutMax = 128;     // output slots of the segments (one float2 per lane each)
+constexpr int kCtaDone = 2;         // owner -> helpers: the subfrustum is finished
+constexpr int kMaxTileRaysCta = 1024 / kWarps;   // owner's share of a 32x32 tile's hits at most
+// Tail queue entries: every ray once through tail sharing, and on launches
+// with the CTA split the rays that helpers hand to the owner.
+__host__ __device__ inline int tq_cap(const TraceLaunch &L) {
+  return L.max_tile_rays + (L.cta_min_view > 0 ? kCtaMaxRays : 0);
+}
 
 int trace_warps_per_cta() { return kWarps; }
 
@@ -64,17 +77,28 @@ __host__ __device__ inline size_t bstk_words(const TraceLaunch &L) { return 6 * 
 __host__ __device__ inline size_t smem_fixed_bytes(const TraceLaunch &L) {
   const size_t r = (size_t)L.max_tile_rays;
   return align16(r * 4) + align16(r * 4) + 2 * align16(r * 2) + (size_t)kWarps * align16(r * 2) +
-         align16(r * 16) + align16(r * 8) + align16(r * 8) +
+         align16(r * 16) + align16(r * 8) + align16((size_t)tq_cap(L) * 8) +
          (size_t)kWarps * align16((size_t)L.stack_slots * 32 * 8) + align16(bstk_words(L) * 4) +
          2 * (size_t)L.dc_words * 16 + (L.mlp ? kMlpPackBytes : 0) +
          (L.staged ? (size_t)kWarps * kStageWords * 16 : 0);
 }
 constexpr int kMaxLevels = 64;   // operator levels of a view usable by the tail mode
 
+// CTA-split areas of a work area: two segment streams, two top programs, the
+// top programs' operator records, the segments' output slots and the owner's
+// points (global memory: shared memory has no room left on these launches),
+// and the split's build scratch (parent, left child, flags, slot per node).
+constexpr int kCtaPtsWords = 3 * 32 / 2;   // float4 words of the owner's points (x, y, z pairs per lane)
+__host__ __device__ inline size_t cta_bytes(const TraceLaunch &L) {
+  if (L.cta_min_view <= 0) return 0;
+  const size_t v = (size_t)L.view_cap;
+  return 2 * align16((v + kCtaOutMax) * 4) + 2 * align16((size_t)kCtaTopMax * 4) +
+         (size_t)(2 * kCtaTopMax + 16 * kCtaOutMax + kCtaPtsWords) * 16 + 4 * align16(v * 4);
+}
 __host__ __device__ inline size_t work_bytes(const TraceLaunch &L) {
   return align16((size_t)L.act_cap * 4) * 4 + 2 * align16((size_t)L.view_cap * 4) +
          2 * align16((size_t)L.act_cap * 8) + 2 * align16((size_t)(kMaxLevels + 1) * 4) +
-         align16((size_t)L.act_cap * 8);
+         align16((size_t)L.act_cap * 8) + cta_bytes(L);
 }
 __host__ __device__ inline size_t smem_per_cta(const TraceLaunch &L) {
   return smem_fixed_bytes(L) + (L.work_in_smem ? work_bytes(L) : 0);
@@ -82,8 +106,10 @@ __host__ __device__ inline size_t smem_per_cta(const TraceLaunch &L) {
 size_t trace_smem_per_warp(const TraceLaunch &L) { return smem_per_cta(L) / kWarps; }
 uint32_t trace_work_words(const TraceLaunch &L) { return (uint32_t)(work_bytes(L) / 4); }
 
-// The larger cache (2048 float4 words, twice) holds the parameters of views
-// of ~600 primitives but leaves room for two CTAs per SM instead of three.
+// The larger cache (2032 float4 words, twice) holds the parameters of views
+// of ~600 primitives but leaves room for two CTAs per SM instead of three
+// (2032 rather than 2048: two CTAs with the CTA split's tail-queue entries
+// and shared protocol words still fit the SM's 228 KB).
 // That pays when the launch is bound by its heaviest tiles, whose long lists
 // make large views and many subfrustums (their warps then get a larger share
 // of the SM), not when the work is spread over many more tiles than CTAs:
@@ -93,7 +119,7 @@ uint32_t trace_work_words(const TraceLaunch &L) { return (uint32_t)(work_bytes(L
 int trace_dcache_words(int view_cap, uint32_t max_overlap, uint64_t n_entries, int n_sm) {
   if (view_cap <= 2048) return 640;
   const double per_cta = (double)n_entries / (3.0 * std::max(n_sm, 1));
-  return (double)max_overlap > 0.3 * per_cta ? 2048 : 640;
+  return (double)max_overlap > 0.3 * per_cta ? 2032 : 640;
 }
 
 struct CtaWork {
@@ -115,6 +141,12 @@ struct CtaWork {
   uint2 *ops[2];       // operators of each view sorted by level: (self | left << 16, right)
   int *lvl_off[2];     // [kMaxLevels + 1] level offsets into ops
   uint2 *sort_tmp;     // view build: level-sort scratch [act_cap]
+  uint32_t *cseg[2];   // CTA split of each view: the four segment streams
+  uint32_t *ctop[2];   // ... the top program
+  float4 *crec;        // [2 kCtaTopMax] top programs' operator records, then
+                       // [kCtaOutMax][32] float2 output slots of the segments,
+                       // then [3][32] float2 points of the owner's pass
+  uint32_t *cscr;      // [4][view_cap] split build scratch
 };
 
 __device__ CtaWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork) {
@@ -127,7 +159,7 @@ __device__ CtaWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork
   w.hits = (uint16_t *)p; p += (size_t)kWarps * align16(r * 2);
   w.rs4 = (float4 *)p; p += align16(r * 16);
   w.rs2 = (float2 *)p; p += align16(r * 8);
-  w.tq = (unsigned long long *)p; p += align16(r * 8);
+  w.tq = (unsigned long long *)p; p += align16((size_t)tq_cap(L) * 8);
   w.stk = (float2 *)p; p += (size_t)kWarps * align16((size_t)L.stack_slots * 32 * 8);
   w.bstk = (uint32_t *)p; p += align16(bstk_words(L) * 4);
   w.dc[0] = (float4 *)p; p += (size_t)L.dc_words * 16;
@@ -148,7 +180,18 @@ __device__ CtaWork carve(unsigned char *p, const TraceLaunch &L, uint32_t *gwork
   w.ops[1] = (uint2 *)q; q += align16((size_t)L.act_cap * 8);
   w.lvl_off[0] = (int *)q; q += align16((size_t)(kMaxLevels + 1) * 4);
   w.lvl_off[1] = (int *)q; q += align16((size_t)(kMaxLevels + 1) * 4);
-  w.sort_tmp = (uint2 *)q;
+  w.sort_tmp = (uint2 *)q; q += align16((size_t)L.act_cap * 8);
+  w.cseg[0] = w.cseg[1] = w.ctop[0] = w.ctop[1] = w.cscr = nullptr;
+  w.crec = nullptr;
+  if (L.cta_min_view > 0) {
+    const size_t v = (size_t)L.view_cap;
+    w.cseg[0] = (uint32_t *)q; q += align16((v + kCtaOutMax) * 4);
+    w.cseg[1] = (uint32_t *)q; q += align16((v + kCtaOutMax) * 4);
+    w.ctop[0] = (uint32_t *)q; q += align16((size_t)kCtaTopMax * 4);
+    w.ctop[1] = (uint32_t *)q; q += align16((size_t)kCtaTopMax * 4);
+    w.crec = (float4 *)q; q += (size_t)(2 * kCtaTopMax + 16 * kCtaOutMax + kCtaPtsWords) * 16;
+    w.cscr = (uint32_t *)q;
+  }
   return w;
 }
 
@@ -173,6 +216,11 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 // Position of the k-th (0-based) set bit of m (k < popc(m)).
+// Named barrier over all warps of the CTA (ids 1 and 2; 0 is __syncthreads).
+__device__ __forceinline__ void cta_bar(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kWarps * 32) : "memory");
+}
+
 __device__ __forceinline__ int kth_set_bit(uint32_t m, int k) {
   int pos = 0;
 #pragma unroll
@@ -495,8 +543,9 @@ __device__ __forceinline__ ViewInfo build_view_lca(const DevScene &sc, const uin
 __device__ __forceinline__ int code_words(uint32_t code) {
   // record words of codes 0..15 as 4-bit fields (1 4 3 1 1 1 0 0 0 0 0 0 2 4 5 7),
   // code 16 (bounded quadric) 5: no indexed jump per staged node
+  // (a CTA-split LOAD stages the 32 lanes' float2 values: 16 words)
   constexpr unsigned long long kWords = 0x7542000000111341ull;
-  return code < 16 ? (int)((kWords >> (4 * code)) & 15u) : (code == V_QUADRIC ? 5 : 0);
+  return code < 16 ? (int)((kWords >> (4 * code)) & 15u) : (code == V_QUADRIC ? 5 : (code == V_LOAD ? 16 : 0));
 }
 
 // ---- staged evaluation of views held in global memory ------------------------------
@@ -647,6 +696,181 @@ __device__ __forceinline__ int build_schedule(const uint32_t *view, int n_view, 
 }
 
 
+// ---- CTA-split evaluation of a large view -------------------------------------------
+// Algorithm 3 over a view in post-order, cut into kWarps contiguous segments
+// (node count split evenly): warp w evaluates segment w for the owner warp's
+// points while the other warps evaluate theirs, and the owner then combines
+// the pieces.  A node whose subtree crosses a segment boundary (a proper
+// ancestor of the node just before a boundary) is a top node; the other
+// children of top nodes are forest roots, each the root of a complete subtree
+// inside one segment.  Segment w's stream is its nodes in order with the top
+// nodes replaced by a STORE for each of their children that is a forest root
+// of the same segment (right child first: it is the running value, the left
+// one lies just below it), followed by a STORE for every forest root still on
+// the stack at the segment's end (topmost first): its stack never holds more
+// than the full evaluation's, and the values leave it in a known order.  The
+// top program is the top nodes and forest roots in view order, the roots as
+// LOADs of their output slots: the post-order of the tree above the segments.
+// Every node computes the same operations on the same operands as in the full
+// evaluation, so the value is bit for bit the same.
+struct CtaInfo {   // CTA split of one view buffer (shared memory)
+  int n_top;       // top program words (0: no split for this view)
+  int off[kWarps], len[kWarps], slot[kWarps];   // segment streams and their first output slots
+  int stt[kWarps], ntr[kWarps];   // build: STOREs at top nodes, trailing STOREs per segment
+};
+struct CtaSync {   // CTA-split protocol of one subfrustum (shared memory)
+  int flag;        // 0 none, 1 requested (owner waits for the helpers), 2 running, 3 abandoned
+  int join;        // helpers that handed their rays over
+  int cmd;         // owner -> helpers at each pass: 1 evaluate, kCtaDone finished
+  int w0in;        // warp 0 (the view builder) is marching this subfrustum
+  int own, nh;     // at the end: the owner warp and its hit count
+  int vb;          // the subfrustum's view buffer
+};
+// CTA-split state of a CTA, at namespace scope so that march_sub reaches it
+// without carrying pointers through the lockstep loop (registers).
+struct CtaShared {
+  CtaInfo info[2];   // per view buffer
+  CtaSync sync[3];   // per subfrustum slot
+  const uint32_t *cseg[2], *ctop[2];
+  float4 *crec;
+};
+__shared__ CtaShared s_ctash;
+
+// Warp-collective (warp 0, after the parameter cache fill, so that segment
+// words are the view's own); node scratch and outputs in the work area.
+__device__ __forceinline__ void build_cta_split(const uint32_t *view, int n, const uint2 *ops, int nop, const float4 *rec,
+                                             const float4 *dc, int vb, const CtaWork &C, int view_cap, CtaInfo *out) {
+  constexpr uint32_t kNone = 0xFFFFFFFFu, kTop = 1u, kRoot = 2u, kTrail = 0x80000000u;
+  const int lane = threadIdx.x & 31;
+  uint32_t *par = C.cscr, *lft = C.cscr + view_cap, *flg = C.cscr + 2 * (size_t)view_cap,
+           *slt = C.cscr + 3 * (size_t)view_cap;
+  uint32_t *seg = pick(C.cseg, vb), *top = pick(C.ctop, vb);
+  const int seg_cap = view_cap + kCtaOutMax;
+  // (no local arrays: the per-segment values go to *out in shared memory)
+  auto bnd = [n](int w) { return (int)(((long long)n * w) / kWarps); };
+  if (lane == 0) out->n_top = 0;
+  // parents and left children from the operators' operand indices (the right
+  // child of an operator at i is i - 1)
+  for (int i = lane; i < n; i += 32) { par[i] = kNone; flg[i] = 0u; }
+  __syncwarp();
+  for (int k = lane; k < nop; k += 32) {
+    const uint2 o = ops[k];
+    const uint32_t t = o.x & 0xFFFFu, l = o.x >> 16, r = o.y & 0xFFFFu;
+    if (t < (uint32_t)n && l < t && r < t) {
+      par[l] = t;
+      par[r] = t;
+      lft[t] = l;
+    }
+  }
+  __syncwarp();
+  if (lane >= 1 && lane < kWarps) {   // top nodes: ancestors of the node before each boundary
+    uint32_t t = par[bnd(lane) - 1];
+    for (int it = 0; t != kNone && it < n; ++it) {
+      flg[t] = kTop;
+      t = par[t];
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    const uint32_t p = par[i];
+    if (!(flg[i] & kTop) && p != kNone && (flg[p] & kTop)) flg[i] = kRoot;
+  }
+  __syncwarp();
+  int off = 0, slot = 0;
+  bool ok = true;
+#pragma unroll 1
+  for (int w = 0; w < kWarps; ++w) {
+    const int lo = bnd(w), hi = bnd(w + 1);
+    int pos = 0, sst = 0, ntr = 0;
+    for (int c0 = lo; c0 < hi; c0 += 32) {
+      const int i = c0 + lane;
+      const bool v = i < hi;
+      const uint32_t f = v ? flg[i] : 0u;
+      int nw = 0, ns = 0;
+      bool sr = false, sl = false, trailing = false;
+      uint32_t l = 0u;
+      if (v) {
+        if (f & kTop) {
+          l = lft[i];
+          sr = i - 1 >= lo && (flg[i - 1] & kRoot);
+          sl = (int)l >= lo && (flg[l] & kRoot);
+          ns = nw = (int)sr + (int)sl;
+        } else {
+          nw = 1;
+          trailing = (f & kRoot) && par[i] >= (uint32_t)hi;
+        }
+      }
+      int xw = nw, xs = ns;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int yw = __shfl_up_sync(0xFFFFFFFFu, xw, o), ys = __shfl_up_sync(0xFFFFFFFFu, xs, o);
+        if (lane >= o) { xw += yw; xs += ys; }
+      }
+      const int pw = off + pos + xw - nw, ps = slot + sst + xs - ns;
+      if (v && pw + nw <= seg_cap) {
+        if (f & kTop) {
+          if (sr) { seg[pw] = (uint32_t)V_STORE << kViewCodeShift; slt[i - 1] = (uint32_t)ps; }
+          if (sl) { seg[pw + (int)sr] = (uint32_t)V_STORE << kViewCodeShift; slt[l] = (uint32_t)(ps + (int)sr); }
+        } else {
+          seg[pw] = view[i];
+        }
+      }
+      const uint32_t tm = __ballot_sync(0xFFFFFFFFu, trailing);
+      if (trailing) slt[i] = kTrail | (uint32_t)(ntr + __popc(tm & lanemask_lt()));
+      ntr += __popc(tm);
+      pos += __shfl_sync(0xFFFFFFFFu, xw, 31);
+      sst += __shfl_sync(0xFFFFFFFFu, xs, 31);
+    }
+    for (int j = lane; j < ntr; j += 32)
+      if (off + pos + j < seg_cap) seg[off + pos + j] = (uint32_t)V_STORE << kViewCodeShift;
+    pos += ntr;
+    if (lane == 0) {
+      out->off[w] = off;
+      out->len[w] = pos;
+      out->slot[w] = slot;
+      out->stt[w] = sst;
+      out->ntr[w] = ntr;
+    }
+    off += pos;
+    slot += sst + ntr;
+  }
+  if (off > seg_cap || slot > kCtaOutMax) ok = false;
+  __syncwarp();
+  // top program: top nodes (operators, records copied next to the program)
+  // and forest roots (LOADs of their slots) in view order
+  int ntop = 0;
+  for (int c0 = 0; c0 < n && ok; c0 += 32) {
+    const int i = c0 + lane;
+    const uint32_t f = i < n ? flg[i] : 0u;
+    const uint32_t mm = __ballot_sync(0xFFFFFFFFu, f != 0u);
+    const int p = ntop + __popc(mm & lanemask_lt());
+    if (f != 0u && p < kCtaTopMax) {
+      uint32_t word;
+      if (f & kTop) {
+        const uint32_t vw = view[i], code = vw >> kViewCodeShift;
+        if (code_words(code) > 0) {   // a compact operator: one record word
+          const int ri = vb * kCtaTopMax + p;
+          C.crec[ri] = *rec_ptr(RecSrc{rec, dc}, vw);
+          word = (code << kViewCodeShift) | kViewGlobal | (uint32_t)ri;
+        } else {
+          word = code << kViewCodeShift;
+        }
+      } else {
+        const int w = (i >= bnd(1)) + (i >= bnd(2)) + (i >= bnd(3));
+        uint32_t sl = slt[i];
+        if (sl & kTrail) sl = (uint32_t)(out->slot[w] + out->stt[w] + out->ntr[w] - 1 - (int)(sl & ~kTrail));
+        word = ((uint32_t)V_LOAD << kViewCodeShift) | kViewGlobal | (uint32_t)(2 * kCtaTopMax + 16 * (int)sl);
+      }
+      top[p] = word;
+    }
+    ntop += __popc(mm);
+  }
+  if (ntop > kCtaTopMax) ok = false;
+  __syncwarp();
+  if (lane == 0) out->n_top = ok ? ntop : 0;
+  __syncwarp();
+}
+
 // Tracking active primitives (Sec. 8): discard those with z_e <= z_end,
 // fetch new ones from the depth-sorted list while the four conditions hold,
 // keep the set sorted by node address; then Algorithm 1 (one lane) builds the
@@ -655,7 +879,7 @@ __device__ __forceinline__ int build_schedule(const uint32_t *view, int n_view, 
 __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, const DevScene &sc, const TraceParams &tp,
                             const float *zin_l, const float *zout_l, const uint32_t *prim_l, uint32_t len,
                             int vb, int stack_slots, int dc_words, SubInfo *out, int *lvl_cur, ViewChunk *vch,
-                            unsigned long long *dbg, bool build = true) {
+                            unsigned long long *dbg, bool build, int cta_min, int view_cap, CtaInfo *cta_out) {
   uint32_t *view = pick(C.view, vb);
   const int lane = threadIdx.x & 31;
   long long tc = dbg ? clock64() : 0;
@@ -797,6 +1021,14 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
     lap(2);
     if (!vi.err && vi.root_used) fill_dcache(view, vi.n_view, sc.rec, pick(C.dc, vb), dc_words);
     lap(3);
+    if (cta_min > 0) {
+      if (!vi.err && vi.root_used && vi.n_view >= cta_min && vi.n_view <= 65535)
+        build_cta_split(view, vi.n_view, pick(C.ops, vb), vi.n_op, sc.rec, pick(C.dc, vb), vb, C, view_cap,
+                        cta_out + vb);
+      else if (lane == 0)
+        cta_out[vb].n_top = 0;
+      __syncwarp();
+    }
   }
   if (lane == 0) *out = info;
   __syncwarp();
@@ -1023,8 +1255,24 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
                               int n_in, int *q_head, uint16_t *alive_out, int *n_out, uint16_t *hits, int &n_hits,
                               float2 *stk_lane, float *wvals, int vals_cap, uint64_t &c_rej,
                               const LearnCtx &LC, int *tq_tail, int *tq_head, int *n_done, int *n_idle,
-                              uint32_t tag, uint32_t &c_err) {
+                              uint32_t tag, uint32_t &c_err, int cta_slot) {
   constexpr bool kShare = MODE != ST_STEP_RECORD;
+  // CTA-split evaluation (staged instances; see build_cta_split): once the
+  // subfrustum's pending list is drained and at most kCtaMaxRays of its rays
+  // are unfinished, the first warp to notice (holding rays itself) becomes
+  // the owner: the others hand it their rays through the tail queue and
+  // help.  Each pass the owner publishes its points, every warp evaluates its
+  // segment of the view for them (named barrier 1 before, 2 after), and the
+  // owner evaluates the top program and steps the rays.  A warp can only
+  // leave the subfrustum when all of its rays are finished, which cannot
+  // happen before the owner's request is visible, so every warp joins; the
+  // joins and the go are still bounded waits, and a request that runs out is
+  // abandoned (CAS on the flag) before any barrier is taken.
+  constexpr bool kCtaOk = kStaged && kShare;
+  int cta = 0;   // 0 normal, 1 owner, 2 helper
+  CtaSync *const cs = &s_ctash.sync[cta_slot];
+  const bool cta_ok = kCtaOk && s_ctash.info[cs->vb].n_top > 0;
+  if (kCtaOk && threadIdx.x == 0) atomicExch(&cs->w0in, 1);
   uint32_t idle_spins = 0;
   const uint32_t idle_limit = LC.L->idle_spins ? LC.L->idle_spins : kIdleSpinLimit;
   bool idle = false;   // this warp is registered in *n_idle (waiting for handed-over rays)
@@ -1185,7 +1433,109 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
     if (hit || exit) ray[s] = -1;
   };
 
+  // Hands every live ray of this warp to the tail queue (state saved by ray).
+  auto give_all = [&]() {
+#pragma unroll
+    for (int s = 0; s < kR; ++s) {
+      const bool give = ray[s] >= 0;
+      const uint32_t gm = __ballot_sync(0xFFFFFFFFu, give);
+      if (!gm) continue;
+      if (give) {
+        const int r = ray[s];
+        C.ray_z[r] = z[s];
+        C.ray_st[r] = steps[s];
+        C.rs4[r] = make_float4(rp[s], dzp[s], zf[s], zs[s]);
+        C.rs2[r] = make_float2(rs[s], fpv[s]);
+      }
+      __threadfence_block();
+      int base = 0;
+      if (lane == __ffs(gm) - 1) base = atomicAdd(tq_tail, __popc(gm));
+      base = __shfl_sync(0xFFFFFFFFu, base, __ffs(gm) - 1);
+      const int idx = base + __popc(gm & lanemask_lt());
+      if (give && idx < tq_cap(*LC.L)) {
+        *(volatile unsigned long long *)(C.tq + idx) = ((unsigned long long)tag << 32) | (uint32_t)ray[s];
+        ray[s] = -1;
+      }
+    }
+  };
+
   for (;;) {
+    int n_live = 0;
+    if (kCtaOk && cta == 2) {
+      // ---- CTA-split helper: wait for the owner's points or its end ----
+      cta_bar(1);
+      if (*(volatile int *)&cs->cmd == kCtaDone) break;
+    } else {
+    if (kCtaOk && cta_ok && cta == 0) {
+      // ---- CTA-split request and joins ----
+      int st = 0;
+      if (lane == 0) st = *(volatile int *)&cs->flag;
+      st = __shfl_sync(0xFFFFFFFFu, st, 0);
+      if (st == 0 && drained && *(volatile int *)&cs->w0in &&
+          __any_sync(0xFFFFFFFFu, ray[0] >= 0 || ray[1] >= 0)) {
+        int won = 0;
+        if (lane == 0) {
+          if (n_in - *(volatile int *)n_done <= kCtaMaxRays) won = atomicCAS(&cs->flag, 0, 1) == 0;
+          st = *(volatile int *)&cs->flag;
+        }
+        won = __shfl_sync(0xFFFFFFFFu, won, 0);
+        st = __shfl_sync(0xFFFFFFFFu, st, 0);
+        if (won) cta = 1;
+      }
+      if (cta == 0 && st == 1) {
+        // join: hand every ray to the owner, then wait for its go
+        give_all();
+        if (idle && lane == 0) atomicSub(n_idle, 1);
+        idle = false;
+        __threadfence_block();
+        int g = 0;
+        if (lane == 0) {
+          atomicAdd(&cs->join, 1);
+          for (uint32_t it = 0;; ++it) {
+            g = *(volatile int *)&cs->flag;
+            if (g != 1) break;
+            if (it >= idle_limit) {
+              g = atomicCAS(&cs->flag, 1, 3);
+              if (g == 1) { g = 3; c_err |= ST_STATUS_WAIT; }
+              break;
+            }
+            __nanosleep(64);
+          }
+        }
+        g = __shfl_sync(0xFFFFFFFFu, g, 0);
+        if (g == 2) {
+          cta = 2;
+          continue;
+        }
+        // abandoned: this warp carries on without rays (tail sharing as usual)
+      }
+      if (cta == 1) {
+        // owner: wait until every other warp has handed its rays over
+        int g = 0;
+        if (lane == 0) {
+          for (uint32_t it = 0;; ++it) {
+            if (*(volatile int *)&cs->join >= kWarps - 1) {
+              g = atomicCAS(&cs->flag, 1, 2);
+              break;
+            }
+            if (*(volatile int *)&cs->flag != 1) {   // a helper's bound ran out
+              g = 3;
+              break;
+            }
+            if (it >= idle_limit) {
+              atomicCAS(&cs->flag, 1, 3);   // abandoned either way (3 already, or now)
+              g = 3;
+              c_err |= ST_STATUS_WAIT;
+              break;
+            }
+            __nanosleep(64);
+          }
+        }
+        g = __shfl_sync(0xFFFFFFFFu, g, 0);
+        if (g != 1) cta = 0;   // abandoned (by a helper's or this warp's bound)
+        __threadfence_block();
+      }
+    }
     // ---- refill empty slots from the tile's pending-ray list ----
     uint32_t need_m[kR];
     int n_need = 0;
@@ -1194,7 +1544,46 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       need_m[s] = __ballot_sync(0xFFFFFFFFu, ray[s] < 0);
       n_need += __popc(need_m[s]);
     }
-    if (n_need && !drained) {
+    if (kCtaOk && cta == 1 && n_need) {
+      // owner: the handed-over rays, as many as there are free slots
+#pragma unroll
+      for (int s = 0; s < kR; ++s) {
+        if (!need_m[s]) continue;
+        int h = 0, t = 0;
+        if (lane == 0) { h = *(volatile int *)tq_head; t = *(volatile int *)tq_tail; }
+        h = __shfl_sync(0xFFFFFFFFu, h, 0);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
+        const int take = min(__popc(need_m[s]), min(t, tq_cap(*LC.L)) - h);
+        if (take <= 0) continue;
+        if (lane == 0) atomicAdd(tq_head, take);
+        const int rank = __popc(need_m[s] & lanemask_lt());
+        if (ray[s] < 0 && rank < take) {
+          int got = -1;
+          for (uint32_t it = 0; it < kEntrySpinLimit; ++it) {
+            const unsigned long long e = *(volatile unsigned long long *)(C.tq + h + rank);
+            if ((uint32_t)(e >> 32) == tag) {
+              got = (int)(uint32_t)(e & 0xFFFFFFFFull);
+              break;
+            }
+            __nanosleep(20);
+          }
+          if (got < 0) {
+            c_err |= ST_STATUS_WAIT;
+          } else {
+            __threadfence_block();
+            ray[s] = got;
+            load_ray(M, C, got, z_begin, z[s], steps[s], d[s], inv_ld[s]);
+            const float4 a = C.rs4[got];
+            const float2 b = C.rs2[got];
+            rp[s] = a.x; dzp[s] = a.y; zf[s] = a.z; zs[s] = a.w;
+            rs[s] = b.x; fpv[s] = b.y;
+            relax_off = rs[s] >= 0.f ? (relax_off | (1u << s)) : (relax_off & ~(1u << s));
+            hv[s] = 0;
+          }
+        }
+      }
+    }
+    if (cta == 0 && n_need && !drained) {
       // A warp takes at most its share of the subfrustum's rays at a time,
       // so that short lists spread over the warps of the CTA.
       const int take = min(n_need, (n_in + kWarps - 1) / kWarps);
@@ -1219,12 +1608,12 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         off += __popc(need_m[s]);
       }
     }
-    if (kShare && drained && !__any_sync(0xFFFFFFFFu, ray[0] >= 0 || ray[1] >= 0)) {
+    if (kShare && cta == 0 && drained && !__any_sync(0xFFFFFFFFu, ray[0] >= 0 || ray[1] >= 0)) {
       // Out of rays: take one handed over by another warp.
       if (!idle && lane == 0) atomicAdd(n_idle, 1);
       idle = true;
       int got = -1;
-      if (lane == 0) got = tq_pop(C.tq, tq_tail, tq_head, tag, LC.L->max_tile_rays, c_err);
+      if (lane == 0) got = tq_pop(C.tq, tq_tail, tq_head, tag, tq_cap(*LC.L), c_err);
       got = __shfl_sync(0xFFFFFFFFu, got, 0);
       if (got >= 0) {
         if (lane == 0) atomicSub(n_idle, 1);
@@ -1241,11 +1630,21 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         hv[0] = 0;
       }
     }
-    int n_live = 0;
 #pragma unroll
     for (int s = 0; s < kR; ++s) n_live += __popc(__ballot_sync(0xFFFFFFFFu, ray[s] >= 0));
     if (n_live == 0) {
       if (!kShare) break;
+      if (kCtaOk && cta == 1) {
+        // owner: every ray is finished; release the helpers
+        if (lane == 0) {
+          *(volatile int *)&cs->own = threadIdx.x >> 5;
+          *(volatile int *)&cs->nh = n_hits;
+          *(volatile int *)&cs->cmd = kCtaDone;
+        }
+        __threadfence_block();
+        cta_bar(1);
+        break;
+      }
       // Every ray of the subfrustum finished?  Else wait for handed-over rays.
       if (*(volatile int *)n_done >= n_in || ++idle_spins > idle_limit) {
         if (idle_spins > idle_limit) c_err |= ST_STATUS_WAIT;
@@ -1255,11 +1654,15 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       __nanosleep(64);
       continue;
     }
+    }
 
     float f[kR];
-    const bool tail_now = drained && tail_ok && n_live * tail_cost < inf.n_view;
-    if (LC.diag && lane == 0) {
-      if (tail_now) {
+    const bool tail_now = cta == 0 && drained && tail_ok && n_live * tail_cost < inf.n_view;
+    if (LC.diag && lane == 0 && cta != 2) {
+      if (cta == 1) {
+        atomicAdd(&LC.diag[5], 1ull);
+        atomicAdd(&LC.diag[6], (unsigned long long)n_live);
+      } else if (tail_now) {
         atomicAdd(&LC.diag[2], (unsigned long long)n_live);
       } else {
         atomicAdd(&LC.diag[0], 1ull);
@@ -1296,7 +1699,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
           if (lane == __ffs(gm) - 1) base = atomicAdd(tq_tail, __popc(gm));
           base = __shfl_sync(0xFFFFFFFFu, base, __ffs(gm) - 1);
           const int idx = base + __popc(gm & lanemask_lt());
-          if (give && idx < LC.L->max_tile_rays) {
+          if (give && idx < tq_cap(*LC.L)) {
             *(volatile unsigned long long *)(C.tq + idx) = ((unsigned long long)tag << 32) | (uint32_t)ray[s];
             ray[s] = -1;
           }
@@ -1323,8 +1726,9 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       // ---- one lockstep field evaluation per slot (Algorithm 3 over the view) ----
       // At most 32 rays left but some lane holds two: lanes with two rays hand
       // their second ray to lanes with none (warp shuffles), so that one
-      // evaluation chain per lane suffices.
-      {
+      // evaluation chain per lane suffices.  (Not in a CTA-split pass: its
+      // helpers evaluate pairs.)
+      if (cta == 0) {
         const uint32_t two = __ballot_sync(0xFFFFFFFFu, ray[0] >= 0 && ray[1] >= 0);
         const uint32_t none = __ballot_sync(0xFFFFFFFFu, ray[0] < 0 && ray[1] < 0);
         if (two && n_live <= 32) {
@@ -1363,7 +1767,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       }
       // A lane whose first slot is empty takes its second slot's ray; when no
       // lane has a second ray left, one evaluation chain per lane suffices.
-      const bool mv = ray[0] < 0 && ray[1] >= 0;
+      const bool mv = cta == 0 && ray[0] < 0 && ray[1] >= 0;
       if (mv) {
         ray[0] = ray[1]; z[0] = z[1]; inv_ld[0] = inv_ld[1]; steps[0] = steps[1];
         d[0][0] = d[1][0]; d[0][1] = d[1][1]; d[0][2] = d[1][2];
@@ -1372,7 +1776,10 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         relax_off = (relax_off & ~3u) | ((relax_off >> 1) & 1u);
         ray[1] = -1;
       }
-      if (!__any_sync(0xFFFFFFFFu, ray[1] >= 0)) {
+      // (Instances with the CTA split evaluate pairs only: one interpreter
+      // instance less keeps their code within the instruction cache; a pair
+      // with one live ray issues the same instructions as the single chain.)
+      if (!kCtaOk && !__any_sync(0xFFFFFFFFu, ray[1] >= 0)) {
         float p1[1][3] = {{fma_(z[0], d[0][0], M.cam->o[0]), fma_(z[0], d[0][1], M.cam->o[1]),
                            fma_(z[0], d[0][2], M.cam->o[2])}};
         float f1[1];
@@ -1385,20 +1792,61 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
         f[1] = 0.f;
       } else {
         // the two slots' points as one pair: paired FP32 instructions
-        const F2 zz = F2(make_float2(z[0], z[1]));
         F2 p2[1][3];
+        if (cta != 2) {
+          const F2 zz = F2(make_float2(z[0], z[1]));
 #pragma unroll
-        for (int k = 0; k < 3; ++k) p2[0][k] = fma_(zz, F2(make_float2(d[0][k], d[1][k])), M.cam->o[k]);
+          for (int k = 0; k < 3; ++k) p2[0][k] = fma_(zz, F2(make_float2(d[0][k], d[1][k])), M.cam->o[k]);
+        }
         F2 f2[1];
-        SmemStackF2 stk2{stk.base};
-        if (kStaged)
-          eval_view_staged<1, F2, SmemStackF2, kFam>(view, inf.n_view, src, p2, f2, stk2, LC.stage);
-        else
-          eval_view_r<1, F2, SmemStackF2, kFam>(view, inf.n_view, src, p2, f2, stk2);
+        using Stk2 = std::conditional_t<kCtaOk, SmemStackF2Cta, SmemStackF2>;
+        Stk2 stk2{stk.base};
+        const uint32_t *ev_view = view;
+        int ev_n = inf.n_view;
+        RecSrc ev_src = src;
+        if (kCtaOk && cta != 0) {
+          // CTA-split pass: the owner publishes its points; every warp
+          // evaluates its segment, storing its forest roots' values
+          const int warp_id = threadIdx.x >> 5;
+          const CtaInfo *ci = &s_ctash.info[cs->vb];
+          float4 *crec = s_ctash.crec;
+          float2 *cpts = reinterpret_cast<float2 *>(crec + 2 * kCtaTopMax + 16 * kCtaOutMax);
+          if (cta == 1) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) __stcg(cpts + k * 32 + lane, p2[0][k].v);
+            if (lane == 0) *(volatile int *)&cs->cmd = 1;
+            __threadfence_block();
+            cta_bar(1);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) p2[0][k] = F2(__ldcg(cpts + k * 32 + lane));
+          }
+          ev_view = s_ctash.cseg[cs->vb] + ci->off[warp_id];
+          ev_n = ci->len[warp_id];
+          if constexpr (kCtaOk) {
+            stk2.xout = reinterpret_cast<float2 *>(crec + 2 * kCtaTopMax) + (size_t)ci->slot[warp_id] * 32;
+            stk2.xn = 0;
+          }
+        }
+        for (int ph = 0;; ++ph) {
+          if (kStaged)
+            eval_view_staged<1, F2, Stk2, kFam>(ev_view, ev_n, ev_src, p2, f2, stk2, LC.stage);
+          else
+            eval_view_r<1, F2, Stk2, kFam>(view, inf.n_view, src, p2, f2, stk2);
+          if (!kCtaOk || cta == 0 || ph > 0) break;
+          // every segment's values are stored: the owner combines them
+          __threadfence_block();
+          cta_bar(2);
+          if (cta == 2) break;
+          ev_view = s_ctash.ctop[cs->vb];
+          ev_n = s_ctash.info[cs->vb].n_top;
+          ev_src = RecSrc{s_ctash.crec, src.dc};
+        }
         f[0] = f2[0].v.x;
         f[1] = f2[0].v.y;
       }
     }
+    if (kCtaOk && cta == 2) continue;   // helpers: the owner steps the rays
     float om[kR];
 #pragma unroll
     for (int s = 0; s < kR; ++s) om[s] = omega_c;
@@ -1435,6 +1883,37 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
       retire(s, hit, exit);
     }
     if (kShare && n_fin && lane == 0) atomicAdd(n_done, n_fin);
+  }
+  if (kCtaOk && cta != 0) {
+    // After a CTA split every ray of its passes that hit is on the owner's
+    // hit list: spread the list over the warps for refinement (warp w takes
+    // the entries i = w mod kWarps; a ray's refinement does not depend on the
+    // warp that runs it).
+    const int warp_id = threadIdx.x >> 5;
+    const int own = *(volatile int *)&cs->own, nh = *(volatile int *)&cs->nh;
+    const uint16_t *oh = C.hits + (size_t)own * LC.L->max_tile_rays;
+    const int mine = nh > warp_id ? (nh - warp_id + kWarps - 1) / kWarps : 0;
+    if (cta == 2) {
+      for (int j = lane; j < mine; j += 32) hits[n_hits + j] = oh[warp_id + kWarps * j];
+      n_hits += mine;
+      __syncwarp();
+      cta_bar(1);
+    } else {
+      uint16_t keep[(kMaxTileRaysCta + 31) / 32];
+#pragma unroll
+      for (int q = 0; q < (kMaxTileRaysCta + 31) / 32; ++q) {
+        const int j = lane + 32 * q;
+        keep[q] = j < mine ? oh[warp_id + kWarps * j] : (uint16_t)0;
+      }
+      cta_bar(1);   // every helper has read its share
+#pragma unroll
+      for (int q = 0; q < (kMaxTileRaysCta + 31) / 32; ++q) {
+        const int j = lane + 32 * q;
+        if (j < mine) hits[j] = keep[q];
+      }
+      n_hits = mine;
+      __syncwarp();
+    }
   }
   c_rej += rejected;
   return live_steps;
@@ -1550,7 +2029,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   __shared__ int s_tqt[3], s_tqh[3], s_ndone[3], s_nidle[3];   // tail sharing per subfrustum slot
   __shared__ uint32_t s_steps;
   __shared__ unsigned long long s_dbg[8];
-  __shared__ unsigned long long s_diag[5];
+  __shared__ unsigned long long s_diag[7];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const CtaWork C = carve(smem, L, L.g_work ? L.g_work + (size_t)blockIdx.x * L.g_work_words : nullptr);
@@ -1569,7 +2048,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   uint32_t g_sub = 0;   // subfrustums this CTA has started (tail-queue tag)
   // Shared memory is not cleared at launch: zero the tail queue so that no
   // stale entry can carry a tag of this launch (tags start at 1).
-  for (int i = threadIdx.x; i < L.max_tile_rays; i += blockDim.x) C.tq[i] = 0ull;
+  for (int i = threadIdx.x; i < tq_cap(L); i += blockDim.x) C.tq[i] = 0ull;
   if (L.status && (*(volatile const uint32_t *)L.status & ST_STATUS_CAPACITY)) return;
 
   for (;;) {
@@ -1674,9 +2153,20 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       s_nctr[0] = 0; s_nctr[1] = 0; s_nctr[2] = 0;
       s_qhead[0] = 0; s_qhead[1] = 0; s_qhead[2] = 0;
       for (int i = 0; i < 3; ++i) { s_tqt[i] = 0; s_tqh[i] = 0; s_ndone[i] = 0; s_nidle[i] = 0; }
+      if (kStaged) {
+        // slot i is first used by subfrustum K + ((i - K) mod 3): its view buffer
+        for (int i = 0; i < 3; ++i) s_ctash.sync[i] = CtaSync{0, 0, 0, 0, 0, 0, (K + (i - K % 3 + 3) % 3) & 1};
+        s_ctash.info[0].n_top = 0;
+        s_ctash.info[1].n_top = 0;
+        s_ctash.cseg[0] = C.cseg[0];
+        s_ctash.cseg[1] = C.cseg[1];
+        s_ctash.ctop[0] = C.ctop[0];
+        s_ctash.ctop[1] = C.ctop[1];
+        s_ctash.crec = C.crec;
+      }
       s_steps = 0u;
       for (int i = 0; i < 8; ++i) s_dbg[i] = 0ull;
-      for (int i = 0; i < 5; ++i) s_diag[i] = 0ull;
+      for (int i = 0; i < 7; ++i) s_diag[i] = 0ull;
     }
     // Split records (thread 0 reserves; all threads publish).  A record
     // resumes at subfrustum kn with the pending rays of alive[kn & 1]; part p
@@ -1743,6 +2233,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       if (run) {
         if (threadIdx.x == 0) {
           s_nctr[rs] = 0; s_qhead[rs] = 0; s_tqt[rs] = 0; s_tqh[rs] = 0; s_ndone[rs] = 0; s_nidle[rs] = 0;
+          if (kStaged) s_ctash.sync[rs] = CtaSync{0, 0, 0, 0, 0, 0, k & 1};
         }
         ++g_sub;
       }
@@ -1750,7 +2241,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         // The next subfrustum's view is built while the other warps march.
         const long long t0 = clock64();
         prepare_sub(sg, C, sc, job.tp, zin_l, zout_l, prim_l, len, (k + 1) & 1, L.stack_slots, L.dc_words,
-                    &s_info[(k + 1) & 1], s_lvl_cur, &s_vchunk, L.tile_stats ? s_dbg : nullptr, k + 1 >= K);
+                    &s_info[(k + 1) & 1], s_lvl_cur, &s_vchunk, L.tile_stats ? s_dbg : nullptr, k + 1 >= K,
+                    kStaged ? L.cta_min_view : 0, L.view_cap, s_ctash.info);
         t_prep += clock64() - t0;
         if (run) {
           c_sub += 1;
@@ -1789,7 +2281,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         const uint32_t ls = march_sub<MODE, kFam, kStaged>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
                                       n_pending, &s_qhead[rd], alive_out, &s_nctr[wr], my_hits, n_hits, stk_lane,
                                       wvals, 2 * L.stack_slots * 32, c_rej, LC, &s_tqt[rd], &s_tqh[rd], &s_ndone[rd],
-                                      &s_nidle[rd], g_sub, c_err);
+                                      &s_nidle[rd], g_sub, c_err, rd);
         const long long t1 = clock64();
         c_steps += ls;
         c_prim += (uint64_t)ls * inf.n_prim;
@@ -1856,7 +2348,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
     __syncthreads();
     if (L.tile_stats && threadIdx.x == 0 && !part) {
       uint32_t *ts = L.tile_stats + (size_t)gtile * kTileStatWords;
-      for (int i = 0; i < 5; ++i) ts[16 + i] = (uint32_t)min(s_diag[i], 0xFFFFFFFFull);
+      for (int i = 0; i < 7; ++i) ts[16 + i] = (uint32_t)min(s_diag[i], 0xFFFFFFFFull);
       ts[8] = (uint32_t)(s_dbg[0] >> 4);
       ts[9] = (uint32_t)(s_dbg[1] >> 4);
       ts[10] = (uint32_t)(s_dbg[2] >> 4);
