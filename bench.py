@@ -587,7 +587,7 @@ def run_batch(args):
         outs["evals"].append(torch.empty(px, dtype=torch.int32, device=dev))
         outs["flags"].append(torch.empty(px, dtype=torch.uint8, device=dev))
     rays = sum(c.width * c.height for c in cams)
-    opts = st.make_opts()
+    opts = st.make_opts(**TRACE_EXTRA)
     t0 = time.time()
     batch = st.st_batch_create(handles, cams, opts, outs["depth"], outs["normal"], outs["evals"], outs["flags"],
                                autotune_cache=TUNE_CACHE, stream=stream)
@@ -807,6 +807,8 @@ def main():
     ap.add_argument("--max-new", type=int, default=32, help="new primitives per subfrustum")
     ap.add_argument("--cta-min-view", type=int, default=0,
                     help="st_trace_opts.cta_eval_min_view (0: library default, < 0: no CTA-split evaluation)")
+    ap.add_argument("--trace-opt", action="append", default=[], metavar="NAME=VALUE",
+                    help="another st_trace_opts field for every mode (repeatable), e.g. heavy_split_len=2000")
     ap.add_argument("--batch-scenes", type=int, default=64, help="scenes of the batch64 workload")
     ap.add_argument("--res", default=None, help="WxH: render the single-scene workload at another resolution")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -818,6 +820,9 @@ def main():
     args = ap.parse_args()
     if args.cta_min_view:
         TRACE_EXTRA["cta_eval_min_view"] = args.cta_min_view
+    for kv in args.trace_opt:
+        k, v = kv.split("=", 1)
+        TRACE_EXTRA[k] = float(v) if "." in v else int(v)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

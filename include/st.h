@@ -254,8 +254,11 @@ typedef struct {
                                while all four warps of the CTA evaluate a
                                quarter of the view each (Algorithm 3 cut
                                at subtree boundaries; the same values bit
-                               for bit); 0 = default [1024], < 0 = never;
-                               st_trace_noalloc never splits            */
+                               for bit); 0 = default [1024 for st_trace;
+                               no split for batches, whose kernel is
+                               faster without it unless most views are
+                               large], < 0 = never; st_trace_noalloc
+                               never splits                             */
 } st_trace_opts;
 
 /* Optional per-call counters (device pointer to 8 uint64, accumulated with

@@ -373,7 +373,7 @@ int plan(st_batch *b) {
   if (L.step_mode == ST_STEP_LEARNED && L.stack_slots < 10) L.stack_slots = 10;
   L.work_in_smem = trace_smem_per_warp(L) * 16 > 200 * 1024 ? 0 : 1;
   L.staged = trace_staged(L);
-  L.cta_min_view = trace_cta_min_view(L, b->opts.cta_eval_min_view);
+  L.cta_min_view = trace_cta_min_view(L, b->opts.cta_eval_min_view, false);
   if (!L.work_in_smem) {
     // one work area per CTA of the persistent grid (indexed by blockIdx.x)
     const int per_sm = trace_ctas_per_sm(L);

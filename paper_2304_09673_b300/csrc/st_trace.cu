@@ -42,6 +42,15 @@ constexpr int kWarps = 4;   // warps per CTA; a CTA traces one tile at a time
 constexpr int kFurtherBit = 64;   // instance bit: the interpreter evaluates the further families
 constexpr int kAllFamBit = 256;   // instance bit (with kFurtherBit): ... including the rounded triangle and quadric
 constexpr int kStagedBit = 128;   // instance bit: views in global memory, evaluated in staged chunks
+// instance bit (staged launches with the large parameter cache, whose shared
+// memory allows two CTAs per SM anyway): registers for two CTAs per SM
+// instead of three (measured on B300, 10k clustered 1920x1080: 7-9 % faster)
+constexpr int kWideBit = 512;
+// instance bit (staged launches with cta_min_view > 0): the CTA-split
+// evaluation is compiled in (its code costs the lockstep loop of a staged
+// instance ~15 % when it is present, measured on B300, so launches without
+// the split use instances without it)
+constexpr int kCtaBit = 1024;
 constexpr int kStageWords = 64;   // float4 record words of a warp's stage buffer (staged instances)
 constexpr int kTileStatWords = 24;   // words per tile of the optional diagnostics
 constexpr int kR = 2;       // rays per lane (shared node decode, two evaluation chains)
@@ -1249,7 +1258,7 @@ struct LearnCtx {      // learned step / recording context of a subfrustum
   float4 *stage;              // this warp's record stage (staged instances)
 };
 
-template <int MODE, int kFam, bool kStaged>
+template <int MODE, int kFam, bool kStaged, bool kCta>
 __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &C, const RecSrc &src, const SubInfo &inf,
                               const uint32_t *view, const uint2 *ops, const int *lvl_off, const uint16_t *alive_in,
                               int n_in, int *q_head, uint16_t *alive_out, int *n_out, uint16_t *hits, int &n_hits,
@@ -1268,7 +1277,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
   // happen before the owner's request is visible, so every warp joins; the
   // joins and the go are still bounded waits, and a request that runs out is
   // abandoned (CAS on the flag) before any barrier is taken.
-  constexpr bool kCtaOk = kStaged && kShare;
+  constexpr bool kCtaOk = kStaged && kShare && kCta;
   int cta = 0;   // 0 normal, 1 owner, 2 helper
   CtaSync *const cs = &s_ctash.sync[cta_slot];
   const bool cta_ok = kCtaOk && s_ctash.info[cs->vb].n_top > 0;
@@ -2014,9 +2023,10 @@ __device__ __forceinline__ void finalize_hits(const MarchCtx &M, const CtaWork &
 // Three CTAs per SM: up to 170 registers per thread (the learned step's MLP
 // fragments take it to 168) with ~57 KB of shared memory per CTA.
 template <int INST>
-__global__ void __launch_bounds__(kWarps * 32, 3)
+__global__ void __launch_bounds__(kWarps * 32, (INST & kWideBit) ? 2 : 3)
 k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
-  constexpr int MODE = INST & ~(kFurtherBit | kStagedBit | kAllFamBit);
+  constexpr int MODE = INST & ~(kFurtherBit | kStagedBit | kAllFamBit | kWideBit | kCtaBit);
+  constexpr bool kCtaInst = (INST & kCtaBit) != 0;
   constexpr int kFam = (INST & kFurtherBit) ? ((INST & kAllFamBit) ? 2 : 1) : 0;
   constexpr bool kStaged = (INST & kStagedBit) != 0;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -2153,7 +2163,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       s_nctr[0] = 0; s_nctr[1] = 0; s_nctr[2] = 0;
       s_qhead[0] = 0; s_qhead[1] = 0; s_qhead[2] = 0;
       for (int i = 0; i < 3; ++i) { s_tqt[i] = 0; s_tqh[i] = 0; s_ndone[i] = 0; s_nidle[i] = 0; }
-      if (kStaged) {
+      if (kCtaInst) {
         // slot i is first used by subfrustum K + ((i - K) mod 3): its view buffer
         for (int i = 0; i < 3; ++i) s_ctash.sync[i] = CtaSync{0, 0, 0, 0, 0, 0, (K + (i - K % 3 + 3) % 3) & 1};
         s_ctash.info[0].n_top = 0;
@@ -2233,7 +2243,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       if (run) {
         if (threadIdx.x == 0) {
           s_nctr[rs] = 0; s_qhead[rs] = 0; s_tqt[rs] = 0; s_tqh[rs] = 0; s_ndone[rs] = 0; s_nidle[rs] = 0;
-          if (kStaged) s_ctash.sync[rs] = CtaSync{0, 0, 0, 0, 0, 0, k & 1};
+          if (kCtaInst) s_ctash.sync[rs] = CtaSync{0, 0, 0, 0, 0, 0, k & 1};
         }
         ++g_sub;
       }
@@ -2242,7 +2252,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         const long long t0 = clock64();
         prepare_sub(sg, C, sc, job.tp, zin_l, zout_l, prim_l, len, (k + 1) & 1, L.stack_slots, L.dc_words,
                     &s_info[(k + 1) & 1], s_lvl_cur, &s_vchunk, L.tile_stats ? s_dbg : nullptr, k + 1 >= K,
-                    kStaged ? L.cta_min_view : 0, L.view_cap, s_ctash.info);
+                    kCtaInst ? L.cta_min_view : 0, L.view_cap, s_ctash.info);
         t_prep += clock64() - t0;
         if (run) {
           c_sub += 1;
@@ -2278,7 +2288,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         const long long t0 = clock64();
         int n_hits = 0;
         const RecSrc src{sc.rec, pick(C.dc, k & 1)};
-        const uint32_t ls = march_sub<MODE, kFam, kStaged>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
+        const uint32_t ls = march_sub<MODE, kFam, kStaged, kCtaInst>(M, C, src, inf, pick(C.view, k & 1), pick(C.ops, k & 1), pick(C.lvl_off, k & 1), alive_in,
                                       n_pending, &s_qhead[rd], alive_out, &s_nctr[wr], my_hits, n_hits, stk_lane,
                                       wvals, 2 * L.stack_slots * 32, c_rej, LC, &s_tqt[rd], &s_tqh[rd], &s_ndone[rd],
                                       &s_nidle[rd], g_sub, c_err, rd);
@@ -2600,8 +2610,14 @@ static auto with_instance(const TraceLaunch &L, F &&f) {
   return L.further == 2 ? f(std::integral_constant<int, (M) | kFurtherBit | kAllFamBit>{}) \
          : L.further    ? f(std::integral_constant<int, (M) | kFurtherBit>{})               \
                         : f(std::integral_constant<int, (M)>{})
-#define ST_INST(M)                          \
-  if (!L.staged) { ST_INST1(M); }          \
+#define ST_INST(M)                                                                \
+  if (!L.staged) { ST_INST1(M); }                                                \
+  if constexpr ((M) != ST_STEP_RECORD) {                                         \
+    if (L.cta_min_view > 0) {                                                    \
+      if (L.dc_words > 640) { ST_INST1((M) | kStagedBit | kCtaBit | kWideBit); } \
+      ST_INST1((M) | kStagedBit | kCtaBit);                                      \
+    }                                                                            \
+  }                                                                              \
   ST_INST1((M) | kStagedBit)
   switch (L.step_mode) {
     case ST_STEP_OVERRELAX: ST_INST(ST_STEP_OVERRELAX);

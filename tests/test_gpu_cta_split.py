@@ -82,3 +82,43 @@ def test_cta_split_same_bytes(stlib, cuda, mode, scene):
             assert live <= 64 * passes
     finally:
         stlib.st_scene_destroy(h)
+
+
+def test_cta_split_in_a_batch(stlib, cuda, tmp_path):
+    """A batch with the split asked for (batches default to no split) gives
+    every scene the bytes of a per-scene trace without it."""
+    import torch
+    names = sorted(SCENES)
+    scenes = [SCENES[k][0]() for k in names]
+    cams = [sg.default_camera(*SCENES[k][1]) for k in names]
+    cache = tmp_path / "tune.json"
+    for s, c in zip(scenes, cams):
+        stlib.st_tune_store(cache, stlib.st_tune_key(s.n_prims, c.width, c.height, stlib.ST_STEP_PLAIN),
+                            stlib.st_tune(16, 32, 0.05, 0.0))
+    handles = [stlib.st_scene_create(s) for s in scenes]
+    dev = torch.device("cuda")
+    out = dict(depth=[], normal=[], evals=[], flags=[])
+    for c in cams:
+        n = c.width * c.height
+        out["depth"].append(torch.full((n,), -1.0, device=dev))
+        out["normal"].append(torch.full((n * 3,), -1.0, device=dev))
+        out["evals"].append(torch.full((n,), 7, dtype=torch.int32, device=dev))
+        out["flags"].append(torch.full((n,), 99, dtype=torch.uint8, device=dev))
+    try:
+        b = stlib.st_batch_create(handles, cams, stlib.make_opts(cta_eval_min_view=64), out["depth"], out["normal"],
+                                  out["evals"], out["flags"], autotune_cache=cache)
+        try:
+            cnt = stlib.st_batch_render(b, counters=True)
+            torch.cuda.synchronize()
+            assert cnt[7] == 0
+        finally:
+            stlib.st_batch_destroy(b)
+        for i, (h, c) in enumerate(zip(handles, cams)):
+            t = stlib.st_build_tiles(h, c, 16)
+            want, _, _, _ = _trace(stlib, torch, h, c, t, cta_eval_min_view=-1)
+            for k, name in enumerate(("depth", "normal", "evals", "flags")):
+                got = out[name][i].cpu().numpy()
+                assert got.tobytes() == want[k].tobytes(), (names[i], name, int(np.sum(got != want[k])))
+    finally:
+        for h in handles:
+            stlib.st_scene_destroy(h)
