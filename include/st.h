@@ -259,10 +259,22 @@ typedef struct {
                                faster without it unless most views are
                                large], < 0 = never; st_trace_noalloc
                                never splits                             */
+    int32_t full_views;     /* 1: evaluate each subfrustum's pruned view
+                               as Algorithm 1 builds it (Sec. 8-9); 0
+                               [default]: without the subtrees whose
+                               values its usage rewrite discards (the
+                               operand an operator rewritten to "left",
+                               "right" or "+inf" drops: 50-70 % of the
+                               nodes on the synthetic scenes), by
+                               building the view again from the
+                               primitives whose values reach the root.
+                               Every value computed, hence every output
+                               byte, is the same; only counters [8], [9]
+                               differ                                   */
 } st_trace_opts;
 
-/* Optional per-call counters (device pointer to 8 uint64, accumulated with
- * atomics; the caller zeroes them):
+/* Optional per-call counters (device pointer to ST_NUM_COUNTERS uint64,
+ * accumulated with atomics; the caller zeroes them):
  *   [0] tracing steps (field evaluations on live rays)
  *   [1] useful primitive evaluations (pruned-view primitives x live steps)
  *   [2] useful operator evaluations
@@ -273,8 +285,11 @@ typedef struct {
  *   [6] finalisation field evaluations (Newton + normal)
  *   [7] device error flags (bit 0: view capacity, bit 1: stack overflow,
  *       bit 2: a tile list longer than the launch's capacity, bit 3: a
- *       bounded wait between the warps of a tile expired) */
-#define ST_NUM_COUNTERS 8
+ *       bounded wait between the warps of a tile expired)
+ *   [8] view nodes evaluated on live steps (the views actually evaluated:
+ *       without discarded subtrees unless full_views)
+ *   [9] FP32 flops of those evaluations (fixed per-node counts, + the step) */
+#define ST_NUM_COUNTERS 10
 
 /* ---- scenes --------------------------------------------------------------
  * st_scene_create: host preparation of a tree structure (the preparation

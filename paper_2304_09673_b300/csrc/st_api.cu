@@ -465,6 +465,7 @@ int trace_common(st_scene *s, const st_camera *cam, const st_tiles *tl, const st
   if (trace_smem_per_warp(L) * 16 > 200 * 1024) L.work_in_smem = 0;
   L.staged = trace_staged(L);
   L.cta_min_view = trace_cta_min_view(L, o.cta_eval_min_view, true);
+  L.prune_views = o.full_views ? 0 : 1;
   if (!L.work_in_smem) {
     // one work area per CTA of the persistent grid (indexed by blockIdx.x)
     const int per_sm = trace_ctas_per_sm(L);

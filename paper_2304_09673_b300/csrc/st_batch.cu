@@ -374,6 +374,7 @@ int plan(st_batch *b) {
   L.work_in_smem = trace_smem_per_warp(L) * 16 > 200 * 1024 ? 0 : 1;
   L.staged = trace_staged(L);
   L.cta_min_view = trace_cta_min_view(L, b->opts.cta_eval_min_view, false);
+  L.prune_views = b->opts.full_views ? 0 : 1;
   if (!L.work_in_smem) {
     // one work area per CTA of the persistent grid (indexed by blockIdx.x)
     const int per_sm = trace_ctas_per_sm(L);

@@ -123,6 +123,8 @@ struct TraceLaunch {
   const uint32_t *heavy_thr;  // optional device word: early-split threshold
                               // (written by launch_tile_order); overrides
                               // heavy_len
+  int32_t prune_views;     // 1: views without the subtrees their usage
+                           // rewrite discards (see live_prims)
   int32_t cta_min_view;    // staged launches: views of at least this many
                            // nodes are prepared for the CTA-split evaluation
                            // of a subfrustum's last rays (0: never; the work

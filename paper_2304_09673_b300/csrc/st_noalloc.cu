@@ -160,6 +160,7 @@ extern "C" int st_trace_noalloc(st_scene *s, const st_camera *cam, const st_tile
   L.work_in_smem = 1;
   if (trace_smem_per_warp(L) * 16 > 200 * 1024) L.work_in_smem = 0;
   L.staged = trace_staged(L);
+  L.prune_views = o.full_views ? 0 : 1;
   // (no CTA-split evaluation here: its per-CTA arrays would cut the lists
   // that fit the static scratch; it changes no output byte)
 

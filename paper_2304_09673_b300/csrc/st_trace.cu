@@ -648,7 +648,10 @@ struct SubInfo {    // one prepared subfrustum, published in shared memory
   float z_begin, z_end;
   int n_view, root_used, n_prim, n_op, err, done;
   int n_lvl;          // operator levels of the schedule (0: tail mode unavailable)
-  uint32_t flops;
+  uint32_t flops;      // n_prim, n_op, flops: the subfrustum's pruned view (Algorithm 1,
+                       // Sec. 9 usage); n_view and flops_eval: the view evaluated, without
+                       // the subtrees whose values that view discards
+  uint32_t flops_eval;
 };
 
 // Level schedule of a view for the warp-wide evaluation of a single point:
@@ -880,6 +883,63 @@ __device__ __forceinline__ void build_cta_split(const uint32_t *view, int n, con
   __syncwarp();
 }
 
+// ---- subtrees whose values the pruned view discards ------------------------------
+// The usage rewrite of Sec. 9 turns an operator with an unusable operand into
+// "right operand", "left operand" or "+inf": the discarded operand's whole
+// subtree is evaluated for nothing (with intersections and differences among
+// the operators, 50-70 % of a subfrustum's view on the synthetic scenes).
+// Liveness from the root down (reverse post-order, a stack of one bit per
+// pending child, 64 deep at most) marks the primitives whose values reach
+// the root; those, in view (= address) order, are written to act2.  The view
+// built from them holds exactly the live operators: every operator whose
+// operands are both live keeps them, and the rewritten operators vanish with
+// their discarded operands, so every value computed is the same bit for bit.
+// Warp-collective.  Returns the live primitive count, or -1 (no change: the
+// stack would exceed 64 entries).  masks: (n + 31) / 32 words of scratch.
+__device__ __forceinline__ int live_prims(const uint32_t *view, int n, const uint32_t *act, uint32_t *act2,
+                                          uint32_t *masks) {
+  const int lane = threadIdx.x & 31;
+  const int nch = (n + 31) / 32;
+  uint64_t bs = 1ull;   // bit stack, bottom = the root's liveness (the root is used)
+  int dep = 1;
+  bool over = false;
+  for (int c = nch - 1; c >= 0 && !over; --c) {
+    const int i = c * 32 + lane;
+    const uint32_t w = i < n ? view[i] : 0u;
+    uint32_t mine = 0u;
+    for (int j = min(31, n - 1 - c * 32); j >= 0; --j) {
+      const uint32_t code = __shfl_sync(0xFFFFFFFFu, w, j) >> kViewCodeShift;
+      --dep;
+      const uint64_t live = (bs >> dep) & 1ull;
+      if (!is_prim_code(code)) {
+        if (dep > 61) { over = true; break; }
+        const bool keep = code <= V_SDIFF;   // the operators themselves (codes 3..8)
+        const uint64_t lL = (keep || code == V_LEFT) ? live : 0ull;
+        const uint64_t lR = (keep || code == V_RIGHT) ? live : 0ull;
+        bs = (bs & ((1ull << dep) - 1ull)) | (lL << dep) | (lR << (dep + 1));
+        dep += 2;
+      }
+      if (lane == j) mine = (uint32_t)live;
+    }
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, mine && i < n && is_prim_code(w >> kViewCodeShift));
+    if (lane == 0) masks[c] = m;
+  }
+  if (over) return -1;
+  __syncwarp();
+  int rank = 0, out = 0;
+  for (int c = 0; c < nch; ++c) {
+    const int i = c * 32 + lane;
+    const uint32_t w = i < n ? view[i] : 0u;
+    const uint32_t pm = __ballot_sync(0xFFFFFFFFu, i < n && is_prim_code(w >> kViewCodeShift));
+    const uint32_t lm = masks[c];
+    if ((lm >> lane) & 1u) act2[out + __popc(lm & lanemask_lt())] = act[rank + __popc(pm & lanemask_lt())];
+    rank += __popc(pm);
+    out += __popc(lm);
+  }
+  __syncwarp();
+  return out;
+}
+
 // Tracking active primitives (Sec. 8): discard those with z_e <= z_end,
 // fetch new ones from the depth-sorted list while the four conditions hold,
 // keep the set sorted by node address; then Algorithm 1 (one lane) builds the
@@ -888,7 +948,8 @@ __device__ __forceinline__ void build_cta_split(const uint32_t *view, int n, con
 __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, const DevScene &sc, const TraceParams &tp,
                             const float *zin_l, const float *zout_l, const uint32_t *prim_l, uint32_t len,
                             int vb, int stack_slots, int dc_words, SubInfo *out, int *lvl_cur, ViewChunk *vch,
-                            unsigned long long *dbg, bool build, int cta_min, int view_cap, CtaInfo *cta_out) {
+                            unsigned long long *dbg, bool build, int cta_min, int view_cap, CtaInfo *cta_out,
+                            bool prune) {
   uint32_t *view = pick(C.view, vb);
   const int lane = threadIdx.x & 31;
   long long tc = dbg ? clock64() : 0;
@@ -928,7 +989,7 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
   info.done = (sg.n_act == 0 && sg.next >= len) ? 1 : 0;
   info.err = 0;
   info.n_view = info.root_used = info.n_prim = info.n_op = info.n_lvl = 0;
-  info.flops = 0u;
+  info.flops = info.flops_eval = 0u;
   info.z_begin = info.z_end = sg.z_end;
   if (!info.done) {
     // ---- fetch (no empty space, depth slab d, max new per turn; no overlap cap) ----
@@ -1018,13 +1079,33 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
   if (!info.done && build) {
     // ---- pruned view (the lowest-common-ancestor form of Algorithm 1) ----
     int n_lvl = 0;
-    const ViewInfo vi = build_view_lca<false>(sc, pick(C.act, sg.cur), sg.n_act, view, *vch, pick(C.ops, vb), C.sort_tmp,
-                                       pick(C.lvl_off, vb), lvl_cur, C.bstk, stack_slots, nullptr, &n_lvl);
-    info.n_view = vi.n_view;
+    ViewInfo vi = build_view_lca<false>(sc, pick(C.act, sg.cur), sg.n_act, view, *vch, pick(C.ops, vb), C.sort_tmp,
+                                        pick(C.lvl_off, vb), lvl_cur, C.bstk, stack_slots, nullptr, &n_lvl);
     info.root_used = vi.root_used;
     info.n_prim = vi.n_prim;
     info.n_op = vi.n_op;
     info.flops = vi.flops;
+    if (prune && !vi.err && vi.root_used) {
+      // the view again from its live primitives only (act[cur ^ 1] is free
+      // until the next discard)
+      uint32_t *act2 = pick(C.act, sg.cur ^ 1);
+      const int n2 = live_prims(view, vi.n_view, pick(C.act, sg.cur), act2, reinterpret_cast<uint32_t *>(C.sort_tmp));
+      if (n2 > 0 && n2 < sg.n_act) {
+        int n_lvl2 = 0;
+        const ViewInfo v2 = build_view_lca<false>(sc, act2, n2, view, *vch, pick(C.ops, vb), C.sort_tmp,
+                                                  pick(C.lvl_off, vb), lvl_cur, C.bstk, stack_slots, nullptr, &n_lvl2);
+        if (!v2.err && v2.root_used) {
+          vi = v2;
+          n_lvl = n_lvl2;
+        } else {
+          // (not expected) the whole view again
+          vi = build_view_lca<false>(sc, pick(C.act, sg.cur), sg.n_act, view, *vch, pick(C.ops, vb), C.sort_tmp,
+                                     pick(C.lvl_off, vb), lvl_cur, C.bstk, stack_slots, nullptr, &n_lvl);
+        }
+      }
+    }
+    info.n_view = vi.n_view;
+    info.flops_eval = vi.flops;
     info.err = vi.err;
     info.n_lvl = (!vi.err && vi.root_used) ? n_lvl : 0;
     lap(2);
@@ -1325,7 +1406,7 @@ __device__ __forceinline__ uint32_t march_sub(const MarchCtx &M, const CtaWork &
   // Tail mode pays one parallel pass per remaining ray instead of one
   // lockstep pass over the whole view for all rays.
   const bool tail_ok = inf.n_lvl > 0 && inf.n_view <= vals_cap;
-  const int tail_cost = (inf.n_prim + 31) / 32 + 2 * inf.n_lvl + 2;
+  const int tail_cost = ((inf.n_view + 1) / 2 + 31) / 32 + 2 * inf.n_lvl + 2;   // (n primitives: 2n - 1 nodes)
 
   // One step of slot s with field value fs: hit / leave the subfrustum /
   // step cap / advance.  Records hits and hand-overs in shared memory.
@@ -2053,7 +2134,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
   LC.stage = C.stage ? C.stage + (size_t)warp * kStageWords : nullptr;
   uint16_t *my_hits = C.hits + (size_t)warp * L.max_tile_rays;
 
-  uint64_t c_steps = 0, c_prim = 0, c_op = 0, c_flops = 0, c_sub = 0, c_fin = 0, c_rej = 0;
+  uint64_t c_steps = 0, c_prim = 0, c_op = 0, c_flops = 0, c_sub = 0, c_fin = 0, c_rej = 0, c_nev = 0, c_fev = 0;
   uint32_t c_err = 0;
   uint32_t g_sub = 0;   // subfrustums this CTA has started (tail-queue tag)
   // Shared memory is not cleared at launch: zero the tail queue so that no
@@ -2252,7 +2333,7 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         const long long t0 = clock64();
         prepare_sub(sg, C, sc, job.tp, zin_l, zout_l, prim_l, len, (k + 1) & 1, L.stack_slots, L.dc_words,
                     &s_info[(k + 1) & 1], s_lvl_cur, &s_vchunk, L.tile_stats ? s_dbg : nullptr, k + 1 >= K,
-                    kCtaInst ? L.cta_min_view : 0, L.view_cap, s_ctash.info);
+                    kCtaInst ? L.cta_min_view : 0, L.view_cap, s_ctash.info, L.prune_views != 0);
         t_prep += clock64() - t0;
         if (run) {
           c_sub += 1;
@@ -2297,6 +2378,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
         c_prim += (uint64_t)ls * inf.n_prim;
         c_op += (uint64_t)ls * inf.n_op;
         c_flops += (uint64_t)ls * (inf.flops + kFlopsStep);
+        c_nev += (uint64_t)ls * (uint32_t)inf.n_view;
+        c_fev += (uint64_t)ls * (s_info[k & 1].flops_eval + kFlopsStep);
         finalize_hits<kFam>(M, C, src, inf, pick(C.view, k & 1), my_hits, n_hits, alive_out, &s_nctr[wr],
                                 stk_lane, c_fin, LC.diag);
         if (L.tile_stats && lane == 0) {
@@ -2387,6 +2470,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       c_prim += __shfl_xor_sync(0xFFFFFFFFu, c_prim, o);
       c_op += __shfl_xor_sync(0xFFFFFFFFu, c_op, o);
       c_flops += __shfl_xor_sync(0xFFFFFFFFu, c_flops, o);
+      c_nev += __shfl_xor_sync(0xFFFFFFFFu, c_nev, o);
+      c_fev += __shfl_xor_sync(0xFFFFFFFFu, c_fev, o);
       c_fin += __shfl_xor_sync(0xFFFFFFFFu, c_fin, o);
       c_rej += __shfl_xor_sync(0xFFFFFFFFu, c_rej, o);
     }
@@ -2399,6 +2484,8 @@ k_trace(const Job *__restrict__ jobs, int n_jobs, TraceLaunch L) {
       if (warp == 0) atomicAdd((unsigned long long *)&L.counters[4], (unsigned long long)c_sub);
       atomicAdd((unsigned long long *)&L.counters[6], (unsigned long long)c_fin);
       if (c_err) atomicOr((unsigned long long *)&L.counters[7], (unsigned long long)c_err);
+      atomicAdd((unsigned long long *)&L.counters[8], (unsigned long long)c_nev);
+      atomicAdd((unsigned long long *)&L.counters[9], (unsigned long long)c_fev);
     }
   }
 }

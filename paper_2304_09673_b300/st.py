@@ -21,7 +21,7 @@ _lib = C.CDLL(str(LIB_PATH))
 ST_OK, ST_ERR_INVALID, ST_ERR_CAPACITY, ST_ERR_CUDA, ST_ERR_TIMEOUT, ST_ERR_NOMEM = 0, -1, -2, -3, -4, -5
 ST_STEP_PLAIN, ST_STEP_LEARNED, ST_STEP_OVERRELAX, ST_STEP_CROSSING = 0, 1, 2, 3
 ST_TRAVERSE_PARENT, ST_TRAVERSE_FAST = 0, 1
-ST_NUM_COUNTERS = 8
+ST_NUM_COUNTERS = 10
 ST_REC_FLOATS = 16
 
 
@@ -56,7 +56,7 @@ class st_trace_opts(C.Structure):
                 ("newton_clamp", C.c_float), ("mlp", C.c_void_p), ("tile_stats", C.c_void_p),
                 ("omega", C.c_float), ("min_step", C.c_float), ("split_kcycles", C.c_int32),
                 ("heavy_split_len", C.c_int32), ("heavy_split_rank", C.c_int32), ("wait_spin_limit", C.c_uint32),
-                ("check_status", C.c_int32), ("cta_eval_min_view", C.c_int32)]
+                ("check_status", C.c_int32), ("cta_eval_min_view", C.c_int32), ("full_views", C.c_int32)]
 
 
 class st_tune(C.Structure):
@@ -173,10 +173,11 @@ def make_camera(cam) -> st_camera:
 def make_opts(eps=1e-4, lipschitz=1.45, max_steps=256, step_mode=ST_STEP_PLAIN, depth_slab_frac=0.05,
               max_new_per_turn=32, newton_iters=2, newton_clamp=0.0, mlp=None, tile_stats=None,
               omega=1.7, min_step=0.0, split_kcycles=0, heavy_split_len=0, heavy_split_rank=0, wait_spin_limit=0,
-              check_status=0, cta_eval_min_view=0) -> st_trace_opts:
+              check_status=0, cta_eval_min_view=0, full_views=0) -> st_trace_opts:
     o = st_trace_opts(eps, lipschitz, max_steps, step_mode, depth_slab_frac, max_new_per_turn,
                       newton_iters, newton_clamp, mlp, None, omega, min_step, split_kcycles,
-                      heavy_split_len, heavy_split_rank, wait_spin_limit, check_status, cta_eval_min_view)
+                      heavy_split_len, heavy_split_rank, wait_spin_limit, check_status, cta_eval_min_view,
+                      full_views)
     if tile_stats is not None:
         o.tile_stats = tile_stats.data_ptr()
         o._keep = tile_stats
