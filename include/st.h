@@ -254,11 +254,12 @@ typedef struct {
                                while all four warps of the CTA evaluate a
                                quarter of the view each (Algorithm 3 cut
                                at subtree boundaries; the same values bit
-                               for bit); 0 = default [1024 for st_trace;
-                               no split for batches, whose kernel is
-                               faster without it unless most views are
-                               large], < 0 = never; st_trace_noalloc
-                               never splits                             */
+                               for bit); 0 = default [1024 for st_trace
+                               launches bound by their heaviest tiles
+                               (those with the large parameter cache);
+                               no split otherwise, nor for batches],
+                               < 0 = never; st_trace_noalloc never
+                               splits                                   */
     int32_t full_views;     /* 1: evaluate each subfrustum's pruned view
                                as Algorithm 1 builds it (Sec. 8-9); 0
                                [default]: without the subtrees whose

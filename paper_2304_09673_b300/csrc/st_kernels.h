@@ -164,13 +164,14 @@ inline long long trace_split_cycles(int32_t split_kcycles) {
 // 10k clustered primitives).
 inline int32_t trace_staged(const TraceLaunch &L) { return !L.work_in_smem && L.view_cap > 2048 ? 1 : 0; }
 // st_trace_opts::cta_eval_min_view -> TraceLaunch::cta_min_view (staged
-// launches only; 0 takes the default, on for st_trace, off for batches:
-// measured on B300, the 64-scene batch, few of whose views are large, is
-// 14 % slower with the split's kernel instance, while 10k clustered
-// primitives trace 1.2-1.7x faster with it).
+// launches only; 0 takes the default: on for st_trace launches with the
+// large parameter cache, i.e. bound by their heaviest tiles, off otherwise.
+// Measured on B300 with views without discarded subtrees: 10k clustered
+// primitives at 1920x1080 (large cache) 4-10 % faster with it, at 3840x2160
+// (small cache) 2-4 % slower, the 64-scene batch 24 % slower.
 constexpr int32_t kCtaMinViewDefault = 1024;
 inline int32_t trace_cta_min_view(const TraceLaunch &L, int32_t opt, bool on_by_default) {
-  if (!L.staged || opt < 0 || (opt == 0 && !on_by_default)) return 0;
+  if (!L.staged || opt < 0 || (opt == 0 && !(on_by_default && L.dc_words > 640))) return 0;
   return opt > 0 ? (opt < 64 ? 64 : opt) : kCtaMinViewDefault;
 }
 inline uint32_t trace_heavy_len(int32_t opt) { return opt > 0 ? (uint32_t)opt : 0u; }
