@@ -940,6 +940,41 @@ __device__ __forceinline__ int live_prims(const uint32_t *view, int n, const uin
   return out;
 }
 
+// The same liveness by levels when the view has a level schedule (operators
+// sorted by height, built with the view): from the top level down, each
+// operator passes its liveness to the operands it uses, all operators of a
+// level at once (a warp-wide pass per level instead of one dependent step per
+// node).  live: n bytes of scratch.  Returns the live primitive count.
+__device__ __forceinline__ int live_prims_levels(const uint32_t *view, int n, const uint2 *ops, const int *lvl_off,
+                                                 int n_lvl, const uint32_t *act, uint32_t *act2, uint8_t *live) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) live[n - 1] = 1;   // the root (post-order: last)
+  __syncwarp();
+  for (int h = n_lvl; h >= 1; --h) {
+    for (int k = lvl_off[h - 1] + lane; k < lvl_off[h]; k += 32) {
+      const uint2 o = ops[k];
+      const uint32_t t = o.x & 0xFFFFu, l = o.x >> 16, r = o.y & 0xFFFFu;
+      const uint32_t code = view[t] >> kViewCodeShift;
+      const bool keep = code <= V_SDIFF, on = live[t] != 0;
+      live[l] = (uint8_t)(on && (keep || code == V_LEFT));
+      live[r] = (uint8_t)(on && (keep || code == V_RIGHT));
+    }
+    __syncwarp();
+  }
+  int rank = 0, out = 0;
+  for (int c = 0; c < n; c += 32) {
+    const int i = c + lane;
+    const bool prim = i < n && is_prim_code(view[i] >> kViewCodeShift);
+    const uint32_t pm = __ballot_sync(0xFFFFFFFFu, prim);
+    const uint32_t lm = __ballot_sync(0xFFFFFFFFu, prim && live[i] != 0);
+    if ((lm >> lane) & 1u) act2[out + __popc(lm & lanemask_lt())] = act[rank + __popc(pm & lanemask_lt())];
+    rank += __popc(pm);
+    out += __popc(lm);
+  }
+  __syncwarp();
+  return out;
+}
+
 // Tracking active primitives (Sec. 8): discard those with z_e <= z_end,
 // fetch new ones from the depth-sorted list while the four conditions hold,
 // keep the set sorted by node address; then Algorithm 1 (one lane) builds the
@@ -1089,7 +1124,10 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
       // the view again from its live primitives only (act[cur ^ 1] is free
       // until the next discard)
       uint32_t *act2 = pick(C.act, sg.cur ^ 1);
-      const int n2 = live_prims(view, vi.n_view, pick(C.act, sg.cur), act2, reinterpret_cast<uint32_t *>(C.sort_tmp));
+      const int n2 = n_lvl > 0 ? live_prims_levels(view, vi.n_view, pick(C.ops, vb), pick(C.lvl_off, vb), n_lvl,
+                                                   pick(C.act, sg.cur), act2, reinterpret_cast<uint8_t *>(C.sort_tmp))
+                               : live_prims(view, vi.n_view, pick(C.act, sg.cur), act2,
+                                            reinterpret_cast<uint32_t *>(C.sort_tmp));
       if (n2 > 0 && n2 < sg.n_act) {
         int n_lvl2 = 0;
         const ViewInfo v2 = build_view_lca<false>(sc, act2, n2, view, *vch, pick(C.ops, vb), C.sort_tmp,
