@@ -888,63 +888,15 @@ __device__ __forceinline__ void build_cta_split(const uint32_t *view, int n, con
 // "right operand", "left operand" or "+inf": the discarded operand's whole
 // subtree is evaluated for nothing (with intersections and differences among
 // the operators, 50-70 % of a subfrustum's view on the synthetic scenes).
-// Liveness from the root down (reverse post-order, a stack of one bit per
-// pending child, 64 deep at most) marks the primitives whose values reach
-// the root; those, in view (= address) order, are written to act2.  The view
-// built from them holds exactly the live operators: every operator whose
-// operands are both live keeps them, and the rewritten operators vanish with
-// their discarded operands, so every value computed is the same bit for bit.
-// Warp-collective.  Returns the live primitive count, or -1 (no change: the
-// stack would exceed 64 entries).  masks: (n + 31) / 32 words of scratch.
-__device__ __forceinline__ int live_prims(const uint32_t *view, int n, const uint32_t *act, uint32_t *act2,
-                                          uint32_t *masks) {
-  const int lane = threadIdx.x & 31;
-  const int nch = (n + 31) / 32;
-  uint64_t bs = 1ull;   // bit stack, bottom = the root's liveness (the root is used)
-  int dep = 1;
-  bool over = false;
-  for (int c = nch - 1; c >= 0 && !over; --c) {
-    const int i = c * 32 + lane;
-    const uint32_t w = i < n ? view[i] : 0u;
-    uint32_t mine = 0u;
-    for (int j = min(31, n - 1 - c * 32); j >= 0; --j) {
-      const uint32_t code = __shfl_sync(0xFFFFFFFFu, w, j) >> kViewCodeShift;
-      --dep;
-      const uint64_t live = (bs >> dep) & 1ull;
-      if (!is_prim_code(code)) {
-        if (dep > 61) { over = true; break; }
-        const bool keep = code <= V_SDIFF;   // the operators themselves (codes 3..8)
-        const uint64_t lL = (keep || code == V_LEFT) ? live : 0ull;
-        const uint64_t lR = (keep || code == V_RIGHT) ? live : 0ull;
-        bs = (bs & ((1ull << dep) - 1ull)) | (lL << dep) | (lR << (dep + 1));
-        dep += 2;
-      }
-      if (lane == j) mine = (uint32_t)live;
-    }
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, mine && i < n && is_prim_code(w >> kViewCodeShift));
-    if (lane == 0) masks[c] = m;
-  }
-  if (over) return -1;
-  __syncwarp();
-  int rank = 0, out = 0;
-  for (int c = 0; c < nch; ++c) {
-    const int i = c * 32 + lane;
-    const uint32_t w = i < n ? view[i] : 0u;
-    const uint32_t pm = __ballot_sync(0xFFFFFFFFu, i < n && is_prim_code(w >> kViewCodeShift));
-    const uint32_t lm = masks[c];
-    if ((lm >> lane) & 1u) act2[out + __popc(lm & lanemask_lt())] = act[rank + __popc(pm & lanemask_lt())];
-    rank += __popc(pm);
-    out += __popc(lm);
-  }
-  __syncwarp();
-  return out;
-}
-
-// The same liveness by levels when the view has a level schedule (operators
+// Liveness from the root down, by levels of the view's schedule (operators
 // sorted by height, built with the view): from the top level down, each
 // operator passes its liveness to the operands it uses, all operators of a
-// level at once (a warp-wide pass per level instead of one dependent step per
-// node).  live: n bytes of scratch.  Returns the live primitive count.
+// level at once.  The primitives whose values reach the root, in view (=
+// address) order, go to act2; the view built from them holds exactly the live
+// operators (every operator whose operands are both live keeps them; the
+// rewritten operators vanish with their discarded operands), so every value
+// computed is the same bit for bit.  Warp-collective; live: n bytes of
+// scratch.  Returns the live primitive count.
 __device__ __forceinline__ int live_prims_levels(const uint32_t *view, int n, const uint2 *ops, const int *lvl_off,
                                                  int n_lvl, const uint32_t *act, uint32_t *act2, uint8_t *live) {
   const int lane = threadIdx.x & 31;
@@ -1113,34 +1065,31 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
   }
   if (!info.done && build) {
     // ---- pruned view (the lowest-common-ancestor form of Algorithm 1) ----
+    // One call site for both builds (instruction cache): the view of the
+    // active set, then, when it has discarded subtrees, the view of its live
+    // primitives (act[cur ^ 1] is free until the next discard).
     int n_lvl = 0;
-    ViewInfo vi = build_view_lca<false>(sc, pick(C.act, sg.cur), sg.n_act, view, *vch, pick(C.ops, vb), C.sort_tmp,
-                                        pick(C.lvl_off, vb), lvl_cur, C.bstk, stack_slots, nullptr, &n_lvl);
-    info.root_used = vi.root_used;
-    info.n_prim = vi.n_prim;
-    info.n_op = vi.n_op;
-    info.flops = vi.flops;
-    if (prune && !vi.err && vi.root_used) {
-      // the view again from its live primitives only (act[cur ^ 1] is free
-      // until the next discard)
-      uint32_t *act2 = pick(C.act, sg.cur ^ 1);
-      const int n2 = n_lvl > 0 ? live_prims_levels(view, vi.n_view, pick(C.ops, vb), pick(C.lvl_off, vb), n_lvl,
-                                                   pick(C.act, sg.cur), act2, reinterpret_cast<uint8_t *>(C.sort_tmp))
-                               : live_prims(view, vi.n_view, pick(C.act, sg.cur), act2,
-                                            reinterpret_cast<uint32_t *>(C.sort_tmp));
-      if (n2 > 0 && n2 < sg.n_act) {
-        int n_lvl2 = 0;
-        const ViewInfo v2 = build_view_lca<false>(sc, act2, n2, view, *vch, pick(C.ops, vb), C.sort_tmp,
-                                                  pick(C.lvl_off, vb), lvl_cur, C.bstk, stack_slots, nullptr, &n_lvl2);
-        if (!v2.err && v2.root_used) {
-          vi = v2;
-          n_lvl = n_lvl2;
-        } else {
-          // (not expected) the whole view again
-          vi = build_view_lca<false>(sc, pick(C.act, sg.cur), sg.n_act, view, *vch, pick(C.ops, vb), C.sort_tmp,
-                                     pick(C.lvl_off, vb), lvl_cur, C.bstk, stack_slots, nullptr, &n_lvl);
-        }
+    ViewInfo vi;
+    const uint32_t *bact = pick(C.act, sg.cur);
+    int bn = sg.n_act;
+    for (int pass = 0; pass < 2; ++pass) {
+      vi = build_view_lca<false>(sc, bact, bn, view, *vch, pick(C.ops, vb), C.sort_tmp, pick(C.lvl_off, vb), lvl_cur,
+                                 C.bstk, stack_slots, nullptr, &n_lvl);
+      if (pass == 0) {
+        info.root_used = vi.root_used;
+        info.n_prim = vi.n_prim;
+        info.n_op = vi.n_op;
+        info.flops = vi.flops;
+      } else if (!vi.err && !vi.root_used) {
+        vi.err = 1;   // (not expected: the live primitives' view has a used root)
       }
+      if (pass == 1 || !prune || vi.err || !vi.root_used || n_lvl == 0) break;
+      uint32_t *act2 = pick(C.act, sg.cur ^ 1);
+      const int n2 = live_prims_levels(view, vi.n_view, pick(C.ops, vb), pick(C.lvl_off, vb), n_lvl, bact, act2,
+                                       reinterpret_cast<uint8_t *>(C.sort_tmp));
+      if (n2 <= 0 || n2 >= bn) break;
+      bact = act2;
+      bn = n2;
     }
     info.n_view = vi.n_view;
     info.flops_eval = vi.flops;
