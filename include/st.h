@@ -567,6 +567,14 @@ int st_eval_sparse(const st_scene *scene, const uint32_t *act, int n, const floa
  * st_pruned_view_alg1: the same view by Algorithm 1 as stated (one thread,
  * fast ancestor pointers, clamping, popRequiredA / popRequiredB and the
  * usage rewrite); same arguments and outputs.
+ * st_pruned_view_live: the view st_trace evaluates by default (full_views =
+ * 0): st_pruned_view's view without the subtrees that its usage rewrite
+ * discards (the operators rewritten to "left operand", "right operand" or
+ * "+inf" and the operands they drop), i.e. the pruned view of the active
+ * primitives whose values reach the root; same arguments; info[0] is the
+ * length of that view, info[3] still the number of active primitives.  When
+ * the root is unused, or the view has more than 65,535 nodes or more than 64
+ * operator levels, the view is st_pruned_view's.
  *   act        device uint32[n], post-order addresses of active primitives,
  *              strictly ascending, 1 <= n <= number of primitives
  *   view       device uint32[2n-1] out: bits 27..31 node code (0 sphere,
@@ -588,6 +596,8 @@ int st_eval_sparse(const st_scene *scene, const uint32_t *act, int n, const floa
 int st_pruned_view(const st_scene *scene, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
                    int32_t *info, void *stream);
 int st_pruned_view_alg1(const st_scene *scene, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
+                        int32_t *info, void *stream);
+int st_pruned_view_live(const st_scene *scene, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
                         int32_t *info, void *stream);
 int st_eval_pruned(const st_scene *scene, const uint32_t *view, const int32_t *info, const float *pts,
                    int npts, float *f, float *grad, void *stream);

@@ -557,6 +557,11 @@ int st_pruned_view_alg1(const st_scene *s, const uint32_t *act, int n, uint32_t 
   return pruned_view_common(s, act, n, view, view_addr, info, stream, 1);
 }
 
+int st_pruned_view_live(const st_scene *s, const uint32_t *act, int n, uint32_t *view, uint32_t *view_addr,
+                        int32_t *info, void *stream) {
+  return pruned_view_common(s, act, n, view, view_addr, info, stream, 2);
+}
+
 int st_eval_pruned(const st_scene *s, const uint32_t *view, const int32_t *info, const float *pts, int npts,
                    float *f, float *grad, void *stream) {
   if (!s || !view || !info || (npts > 0 && (!pts || !f)) || npts < 0) { set_error("invalid arguments"); return ST_ERR_INVALID; }

@@ -891,15 +891,26 @@ __device__ __forceinline__ void build_cta_split(const uint32_t *view, int n, con
 // Liveness from the root down, by levels of the view's schedule (operators
 // sorted by height, built with the view): from the top level down, each
 // operator passes its liveness to the operands it uses, all operators of a
-// level at once.  The primitives whose values reach the root, in view (=
-// address) order, go to act2; the view built from them holds exactly the live
-// operators (every operator whose operands are both live keeps them; the
-// rewritten operators vanish with their discarded operands), so every value
-// computed is the same bit for bit.  Warp-collective; live: n bytes of
-// scratch.  Returns the live primitive count.
-__device__ __forceinline__ int live_prims_levels(const uint32_t *view, int n, const uint2 *ops, const int *lvl_off,
-                                                 int n_lvl, const uint32_t *act, uint32_t *act2, uint8_t *live) {
+// level at once.  The view of the live primitives holds exactly the live
+// nodes that are primitives or keep their operator (every operator whose
+// operands are both live keeps them; the rewritten operators vanish with
+// their discarded operands), in the same post-order, so every value computed
+// is the same bit for bit.  That view is made here by compacting the first
+// one instead of building it again: kept nodes move to their rank among the
+// kept nodes; a live "left" / "right" operator hands its parent the node of
+// the operand it passes on; heights and the level schedule are recomputed
+// bottom-up over the old levels (operands sit on lower levels).
+// Warp-collective.  scratch: 4 n + 2 bytes (live flags, the node that carries
+// each value, new heights), dead once the schedule is sorted into it.
+// Returns the new view size, 0 when nothing is discarded (the view is left
+// as it is).
+__device__ __forceinline__ int compact_live_view(uint32_t *view, int n, uint2 *ops, int *lvl_off, int *lvl_cur,
+                                                 int n_lvl, uint2 *scratch, int *nop_out, int *nlvl_out,
+                                                 uint32_t *flops_out, uint32_t *vaddr) {
   const int lane = threadIdx.x & 31;
+  uint8_t *live = reinterpret_cast<uint8_t *>(scratch);
+  uint16_t *rep = reinterpret_cast<uint16_t *>(live + ((n + 1) & ~1));
+  uint8_t *hn = reinterpret_cast<uint8_t *>(rep + n);
   if (lane == 0) live[n - 1] = 1;   // the root (post-order: last)
   __syncwarp();
   for (int h = n_lvl; h >= 1; --h) {
@@ -913,18 +924,111 @@ __device__ __forceinline__ int live_prims_levels(const uint32_t *view, int n, co
     }
     __syncwarp();
   }
-  int rank = 0, out = 0;
+  // new positions; primitives carry their own values at height 0
+  int nk = 0;
+  uint32_t fl = 0;
   for (int c = 0; c < n; c += 32) {
     const int i = c + lane;
-    const bool prim = i < n && is_prim_code(view[i] >> kViewCodeShift);
-    const uint32_t pm = __ballot_sync(0xFFFFFFFFu, prim);
-    const uint32_t lm = __ballot_sync(0xFFFFFFFFu, prim && live[i] != 0);
-    if ((lm >> lane) & 1u) act2[out + __popc(lm & lanemask_lt())] = act[rank + __popc(pm & lanemask_lt())];
-    rank += __popc(pm);
-    out += __popc(lm);
+    const uint32_t code = i < n ? view[i] >> kViewCodeShift : (uint32_t)V_INF;
+    const bool prim = i < n && is_prim_code(code);
+    const bool kept = i < n && live[i] != 0 && (prim || code <= V_SDIFF);
+    const uint32_t km = __ballot_sync(0xFFFFFFFFu, kept);
+    if (kept) {
+      rep[i] = (uint16_t)(nk + __popc(km & lanemask_lt()));
+      if (prim) hn[i] = 0;
+      fl += node_flops(code);
+    }
+    nk += __popc(km);
   }
   __syncwarp();
-  return out;
+  if (nk >= n) return 0;
+  // operands and heights of the kept operators, level by level; the new
+  // entries are written over the old ones (never ahead of the reads)
+  int nop = 0, maxh = 0;
+  for (int h = 1; h <= n_lvl; ++h) {
+    const int e = lvl_off[h];
+    for (int k0 = lvl_off[h - 1]; k0 < e; k0 += 32) {
+      const int k = k0 + lane;
+      uint2 o = make_uint2(0u, 0u);
+      bool kept = false;
+      if (k < e) {
+        o = ops[k];
+        const uint32_t t = o.x & 0xFFFFu, l = o.x >> 16, r = o.y & 0xFFFFu;
+        if (live[t]) {
+          const uint32_t code = view[t] >> kViewCodeShift;
+          if (code <= V_SDIFF) {
+            const uint32_t h2 = max(hn[l], hn[r]) + 1u;
+            hn[t] = (uint8_t)h2;
+            maxh = max(maxh, (int)h2);
+            o = make_uint2((uint32_t)rep[t] | ((uint32_t)rep[l] << 16), (uint32_t)rep[r] | (h2 << 16));
+            kept = true;
+          } else if (code == V_LEFT) {
+            rep[t] = rep[l];
+            hn[t] = hn[l];
+          } else if (code == V_RIGHT) {
+            rep[t] = rep[r];
+            hn[t] = hn[r];
+          }
+        }
+      }
+      const uint32_t km = __ballot_sync(0xFFFFFFFFu, kept);
+      __syncwarp();
+      if (kept) ops[nop + __popc(km & lanemask_lt())] = o;
+      nop += __popc(km);
+    }
+    __syncwarp();
+  }
+  // the view itself, in place
+  int out = 0;
+  for (int c = 0; c < n; c += 32) {
+    const int i = c + lane;
+    const uint32_t v = i < n ? view[i] : 0u;
+    const uint32_t va = (vaddr && i < n) ? vaddr[i] : 0u;
+    const uint32_t code = v >> kViewCodeShift;
+    const bool kept = i < n && live[i] != 0 && (is_prim_code(code) || code <= V_SDIFF);
+    const uint32_t km = __ballot_sync(0xFFFFFFFFu, kept);
+    __syncwarp();
+    if (kept) {
+      const int pos = out + __popc(km & lanemask_lt());
+      view[pos] = v;
+      if (vaddr) vaddr[pos] = va;
+    }
+    out += __popc(km);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fl += __shfl_xor_sync(0xFFFFFFFFu, fl, o);
+    maxh = max(maxh, __shfl_xor_sync(0xFFFFFFFFu, maxh, o));
+  }
+  __syncwarp();
+  // level schedule (counting sort by the new heights; scratch is free now)
+  for (int h = lane; h <= kMaxLevels; h += 32) lvl_off[h] = 0;
+  __syncwarp();
+  for (int k = lane; k < nop; k += 32) atomicAdd(&lvl_off[ops[k].y >> 16], 1);
+  __syncwarp();
+  if (lane == 0) {
+    int acc = 0;
+    lvl_off[0] = 0;
+    for (int h = 1; h <= maxh; ++h) {
+      const int c = lvl_off[h];
+      lvl_cur[h] = acc;
+      acc += c;
+      lvl_off[h] = acc;
+    }
+  }
+  __syncwarp();
+  for (int k = lane; k < nop; k += 32) {
+    const uint2 o = ops[k];
+    const int pos = atomicAdd(&lvl_cur[o.y >> 16], 1);
+    scratch[pos] = make_uint2(o.x, o.y & 0xFFFFu);
+  }
+  __syncwarp();
+  for (int k = lane; k < nop; k += 32) ops[k] = scratch[k];
+  __syncwarp();
+  *nop_out = nop;
+  *nlvl_out = maxh;
+  *flops_out = fl;
+  return nk;
 }
 
 // Tracking active primitives (Sec. 8): discard those with z_e <= z_end,
@@ -1065,31 +1169,25 @@ __device__ __forceinline__ void prepare_sub(SegState &sg, const CtaWork &C, cons
   }
   if (!info.done && build) {
     // ---- pruned view (the lowest-common-ancestor form of Algorithm 1) ----
-    // One call site for both builds (instruction cache): the view of the
-    // active set, then, when it has discarded subtrees, the view of its live
-    // primitives (act[cur ^ 1] is free until the next discard).
     int n_lvl = 0;
-    ViewInfo vi;
-    const uint32_t *bact = pick(C.act, sg.cur);
-    int bn = sg.n_act;
-    for (int pass = 0; pass < 2; ++pass) {
-      vi = build_view_lca<false>(sc, bact, bn, view, *vch, pick(C.ops, vb), C.sort_tmp, pick(C.lvl_off, vb), lvl_cur,
-                                 C.bstk, stack_slots, nullptr, &n_lvl);
-      if (pass == 0) {
-        info.root_used = vi.root_used;
-        info.n_prim = vi.n_prim;
-        info.n_op = vi.n_op;
-        info.flops = vi.flops;
-      } else if (!vi.err && !vi.root_used) {
-        vi.err = 1;   // (not expected: the live primitives' view has a used root)
+    ViewInfo vi = build_view_lca<false>(sc, pick(C.act, sg.cur), sg.n_act, view, *vch, pick(C.ops, vb), C.sort_tmp,
+                                        pick(C.lvl_off, vb), lvl_cur, C.bstk, stack_slots, nullptr, &n_lvl);
+    info.root_used = vi.root_used;
+    info.n_prim = vi.n_prim;
+    info.n_op = vi.n_op;
+    info.flops = vi.flops;
+    if (prune && !vi.err && vi.root_used && n_lvl > 0) {
+      // without the subtrees its usage rewrite discards (the view of the live primitives)
+      int nop2 = 0, nlvl2 = 0;
+      uint32_t fl2 = 0;
+      const int n2 = compact_live_view(view, vi.n_view, pick(C.ops, vb), pick(C.lvl_off, vb), lvl_cur, n_lvl,
+                                       C.sort_tmp, &nop2, &nlvl2, &fl2, nullptr);
+      if (n2 > 0) {
+        vi.n_view = n2;
+        vi.n_op = nop2;
+        vi.flops = fl2;
+        n_lvl = nlvl2;
       }
-      if (pass == 1 || !prune || vi.err || !vi.root_used || n_lvl == 0) break;
-      uint32_t *act2 = pick(C.act, sg.cur ^ 1);
-      const int n2 = live_prims_levels(view, vi.n_view, pick(C.ops, vb), pick(C.lvl_off, vb), n_lvl, bact, act2,
-                                       reinterpret_cast<uint8_t *>(C.sort_tmp));
-      if (n2 <= 0 || n2 >= bn) break;
-      bact = act2;
-      bn = n2;
     }
     info.n_view = vi.n_view;
     info.flops_eval = vi.flops;
@@ -2561,14 +2659,16 @@ void launch_tile_order(const Job *jobs, int n_jobs, uint32_t n_tiles, uint32_t *
 
 // ---- inspection kernels: the same view build and evaluator as k_trace ----------
 // method 0: the tracer's warp-parallel builder (build_view_lca); method 1:
-// Algorithm 1 as stated (one lane, fast ancestor pointers).  One warp;
+// Algorithm 1 as stated (one lane, fast ancestor pointers); method 2: method
+// 0 without the subtrees the usage rewrite discards (compact_live_view), the
+// view st_trace evaluates by default.  One warp;
 // `scratch` holds the builder's work arrays (pruned_view_scratch_words).
 __global__ void k_pruned_view(DevScene sc, const uint32_t *act, int n, uint32_t *view, uint32_t *vaddr,
                               int32_t *info, uint32_t *scratch, int stack_cap, int method) {
   if (blockIdx.x != 0) return;
   ViewInfo vi;
   int n_lvl = 0;
-  if (method == 0) {
+  if (method != 1) {
     __shared__ ViewChunk vch;
     uint32_t *stk = scratch;   // 16-byte aligned (device allocation base)
     uint2 *ops = reinterpret_cast<uint2 *>(scratch + align16((size_t)6 * (stack_cap + 2) * 4) / 4);
@@ -2577,6 +2677,13 @@ __global__ void k_pruned_view(DevScene sc, const uint32_t *act, int n, uint32_t 
     int *lvl_cur = lvl_off + kMaxLevels + 1;
     vi = vaddr ? build_view_lca<true>(sc, act, n, view, vch, ops, sort_tmp, lvl_off, lvl_cur, stk, stack_cap, vaddr, &n_lvl)
                : build_view_lca<false>(sc, act, n, view, vch, ops, sort_tmp, lvl_off, lvl_cur, stk, stack_cap, vaddr, &n_lvl);
+    if (method == 2 && !vi.err && vi.root_used && n_lvl > 0) {
+      int nop2 = 0, nlvl2 = 0;
+      uint32_t fl2 = 0;
+      const int n2 = compact_live_view(view, vi.n_view, ops, lvl_off, lvl_cur, n_lvl, sort_tmp, &nop2, &nlvl2, &fl2,
+                                       vaddr);
+      if (n2 > 0) vi.n_view = n2;
+    }
   } else {
     if (threadIdx.x != 0) return;
     vi = build_view(sc, act, n, view, scratch, stack_cap, vaddr);

@@ -79,6 +79,7 @@ _lib.st_trace.argtypes = [_P, C.POINTER(st_camera), C.POINTER(st_tiles), C.POINT
 _lib.st_tiles_copy.argtypes = [C.POINTER(st_tiles), _P, _P, _P, _P, _P]
 _lib.st_pruned_view.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
 _lib.st_pruned_view_alg1.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
+_lib.st_pruned_view_live.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
 _lib.st_eval_pruned.argtypes = [_P, _P, _P, _P, C.c_int, _P, _P, _P]
 _lib.st_eval_pruned_levels.argtypes = [_P, _P, C.c_int, _P, _P, _P, C.c_int, _P, _P]
 _lib.st_kernel_launches.restype = C.c_uint64
@@ -313,6 +314,11 @@ def st_pruned_view(h, act, view, view_addr, info, stream=None) -> None:
 def st_pruned_view_alg1(h, act, view, view_addr, info, stream=None) -> None:
     _check(_lib.st_pruned_view_alg1(h, _ptr(act), int(act.numel()), _ptr(view), _ptr(view_addr), _ptr(info),
                                     _stream(stream)), "st_pruned_view_alg1")
+
+
+def st_pruned_view_live(h, act, view, view_addr, info, stream=None) -> None:
+    _check(_lib.st_pruned_view_live(h, _ptr(act), int(act.numel()), _ptr(view), _ptr(view_addr), _ptr(info),
+                                    _stream(stream)), "st_pruned_view_live")
 
 
 def st_eval_pruned(h, view, info, pts, f, grad=None, stream=None) -> None:
